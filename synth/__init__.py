@@ -1,0 +1,73 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the oracle.
+
+This module holds input generation only (random right-hand sides, the CSR
+arrays of the stencil test matrices, problem lists); none of the method's
+arithmetic lives here.
+
+Recipes
+* b ~ N(0,1), FP64, numpy.random.default_rng(seed).standard_normal; seed 0
+  for single problems, 1000 + i for the i-th problem of a batch.  The paper
+  draws b at random (Sec. 6, Examples 1-3); relative errors do not depend on
+  the scale of b.
+* Stencil matrices in CSR with the grid ordering idx = (k*Ny + j)*Nx + i
+  (x fastest); neighbours listed in increasing column order.
+"""
+import numpy as np
+
+
+def rhs(n, seed=0, nrhs=1):
+    """FP64 right-hand side(s): shape (n,) or, for nrhs > 1, (nrhs, n) (one row per RHS)."""
+    rng = np.random.default_rng(seed)
+    if nrhs == 1:
+        return rng.standard_normal(n)
+    return rng.standard_normal((nrhs, n))
+
+
+def stencil_coeffs(kind, ch=0.0):
+    """(diag, [(axis, offset, value), ...]) of the constant-coefficient stencils.
+
+    laplace2d5 / laplace3d7: diagonal 4 / 6, every neighbour -1.
+    convdiff3d7: diagonal 6 + 3 ch, upwind neighbours (offset -1) -(1 + ch),
+    downwind neighbours (offset +1) -1.
+    """
+    if kind == "laplace2d5":
+        return 4.0, [(ax, o, -1.0) for ax in range(2) for o in (-1, 1)]
+    if kind == "laplace3d7":
+        return 6.0, [(ax, o, -1.0) for ax in range(3) for o in (-1, 1)]
+    if kind == "convdiff3d7":
+        return 6.0 + 3.0 * ch, [(ax, o, (-(1.0 + ch) if o < 0 else -1.0))
+                                for ax in range(3) for o in (-1, 1)]
+    raise ValueError(kind)
+
+
+def stencil_csr(kind, dims, ch=0.0):
+    """CSR arrays (rowptr int64, col int32, val float64) of a stencil on a Dirichlet grid."""
+    dims = tuple(int(N) for N in dims)
+    diag, nbrs = stencil_coeffs(kind, ch)
+    nd = len(dims)
+    n = int(np.prod(dims))
+    idx = np.arange(n, dtype=np.int64)
+    coords = []
+    rem = idx.copy()
+    for N in dims:
+        coords.append(rem % N)
+        rem //= N
+    strides = [1]
+    for N in dims[:-1]:
+        strides.append(strides[-1] * N)
+    rows, cols, vals = [idx], [idx], [np.full(n, diag)]
+    for ax, off, v in nbrs:
+        ok = (coords[ax] + off >= 0) & (coords[ax] + off < dims[ax])
+        r = idx[ok]
+        rows.append(r)
+        cols.append(r + off * strides[ax])
+        vals.append(np.full(r.shape[0], v))
+    rows = np.concatenate(rows)
+    cols = np.concatenate(cols)
+    vals = np.concatenate(vals)
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return rowptr, cols.astype(np.int32), vals.astype(np.float64)
