@@ -1,0 +1,225 @@
+/*
+ * pp.h -- C ABI of a GB300 (sm_103a) library for the action of the matrix
+ * inverse square root and square root, f(A) b with f(z) = z^{-1/2} or z^{1/2},
+ * by polynomially preconditioned Arnoldi / Lanczos (Frommer, Ramirez-Hidalgo,
+ * Schweitzer, Tsolakis, "Polynomial preconditioning for the action of the
+ * matrix square root and inverse square root").
+ *
+ * Problem statement (Sec. 1, Sec. 2 Prop. 2.1, Sec. 3 Eq. (3.1)): given a
+ * sparse A in C^{n x n} with no eigenvalue on (-inf, 0] and a vector b,
+ * compute the principal A^{-1/2} b or A^{1/2} b.  A polynomial q ~ z^{-1/2}
+ * (Sec. 5) turns the Krylov process onto A q(A)^2, whose spectrum clusters
+ * around 1, and
+ *     A^{-1/2} b = (A q(A)^2)^{-1/2} q(A) b          (left, Algorithm 1)
+ *                = q(A) (A q(A)^2)^{-1/2} b          (right, Algorithm 2)
+ *     A^{1/2} b  = A^{-1/2} (A b)                    (Sec. 4).
+ *
+ * Conventions for every entry point
+ *   - Every call returns an int status: PP_OK (0) or a negative pp_status.
+ *     pp_strerror() names it.  A failed call leaves the handle usable.
+ *   - Pointers with suffix _d are DEVICE pointers (e.g. torch CUDA tensors'
+ *     data_ptr()), owned by the caller; the library never frees them.
+ *     Pointers with suffix _h are HOST pointers.
+ *   - Device work is ordered on the handle's CUDA stream (the `stream`
+ *     argument of pp_create_*; NULL = the legacy default stream).  A call
+ *     returns after its work is queued, except where stated.  Handles are
+ *     not thread-safe; distinct handles may be used from distinct threads.
+ *   - Real vectors are FP64 (PP_F64) at the API; complex vectors are
+ *     interleaved complex128 (PP_C128).  The arithmetic inside is chosen by
+ *     pp_opts.precision.
+ *   - Grid vectors are ordered with x fastest: idx = (k*Ny + j)*Nx + i.
+ */
+#ifndef PP_H
+#define PP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pp_ctx *pp_handle;
+
+typedef enum {
+  PP_OK = 0,
+  PP_ERR_INVALID_ARG = -1,   /* bad pointer, size, enum value or option         */
+  PP_ERR_NOT_CONVERGED = -2, /* m_max reached; x holds the last iterate         */
+  PP_ERR_NONPRIMARY = -3,    /* q <= 0 somewhere on [a,b]: the result would be a
+                                non-primary root (Sec. 5, after Thm. 5.1)       */
+  PP_ERR_SINGULAR = -4,      /* A^{-1/2} requested for a numerically singular A */
+  PP_ERR_OOM = -5,           /* device allocation failed                        */
+  PP_ERR_CUDA = -6,          /* a CUDA runtime call failed                      */
+  PP_ERR_TIMEOUT = -7,       /* a bounded device wait ran out                   */
+  PP_ERR_STATE = -8,         /* call out of order (e.g. pp_apply before
+                                pp_build_poly)                                  */
+  PP_ERR_UNSUPPORTED = -9    /* valid request this build does not implement     */
+} pp_status;
+
+typedef enum { PP_F64 = 0, PP_F32 = 1, PP_C64 = 2, PP_C128 = 3 } pp_dtype;
+
+typedef enum { PP_INVSQRT = -1, PP_SQRT = 1 } pp_func;
+
+typedef enum {
+  PP_CHEBYSHEV = 0,      /* Sec. 5.1: interpolant at deg+1 first-kind nodes of [a,b] */
+  PP_RITZ_LEJA = 1,      /* Sec. 5.2 (not in this build)                              */
+  PP_HARMONIC_RITZ = 2,  /* Sec. 5.2 (not in this build)                              */
+  PP_LSQ_CONTOUR = 3     /* Sec. 5.3 (not in this build)                              */
+} pp_poly_kind;
+
+typedef enum {
+  PP_LAPLACE2D5 = 0,         /* 5-point Dirichlet Laplacian, dims = {Nx, Ny}      */
+  PP_LAPLACE3D7 = 1,         /* 7-point Dirichlet Laplacian, dims = {Nx, Ny, Nz}  */
+  PP_CONVDIFF3D7_UPWIND = 2, /* 7-point upwind -Lap u + c.grad u, c = (c,c,c)>0,
+                                params[0] = c*h; row: (6+3ch) u_c - (1+ch) (u at
+                                i-1, j-1, k-1) - (u at i+1, j+1, k+1)             */
+  PP_WILSON4D_DHD = 3        /* not in this build                                 */
+} pp_stencil_kind;
+
+typedef enum { PP_LEFT = 0, PP_RIGHT = 1 } pp_side;
+
+typedef enum {
+  PP_PREC_F64 = 0,   /* vectors, chain and basis in IEEE FP64                    */
+  PP_PREC_DW = 1,    /* vectors, chain and basis as double-word FP32 pairs
+                        (hi + lo, ~48-bit significand, 8 bytes per real): FP64-
+                        grade accuracy on the FP32 pipes                          */
+  PP_PREC_MIXED = 2  /* not in this build                                         */
+} pp_precision;
+
+typedef enum {
+  PP_ORTH_AUTO = 0,     /* Lanczos for Hermitian A, CGS2 Arnoldi otherwise        */
+  PP_ORTH_LANCZOS = 1,  /* three-term recurrence, no reorthogonalization          */
+  PP_ORTH_CGS2 = 2      /* classical Gram-Schmidt twice against the whole basis   */
+} pp_orth;
+
+typedef struct pp_opts {
+  int32_t side;         /* pp_side, default PP_LEFT                                  */
+  int32_t precision;    /* pp_precision, default PP_PREC_F64                         */
+  int32_t orth;         /* pp_orth, default PP_ORTH_AUTO                             */
+  int32_t check_every;  /* k of the stopping rule ||f_m - f_{m+k}|| / ||f_{m+k}||
+                           (Sec. 6, Example 1); 0 = max(1, floor(64/(deg+1)))      */
+  int32_t profile;      /* 1: time every operator launch of the polynomial chain
+                           with CUDA events (pp_stats.chain_*)                       */
+  int32_t reserved[7];
+} pp_opts;
+
+typedef struct pp_stats {
+  int32_t status;         /* same value pp_apply returned                           */
+  int32_t iters;          /* Krylov dimension m of the returned iterate             */
+  int32_t checks;         /* small f(H_m) solves performed                          */
+  int32_t breakdown;      /* 1 if h_{m+1,m} vanished (Krylov space invariant)       */
+  int64_t mvms;           /* products with A, counted as in Tables 1-3              */
+  int64_t inner_products; /* length-n inner products and norms in the loop          */
+  double est_err;         /* last ||f_m - f_{m-k}|| / ||f_m|| (inf if one check)    */
+  double beta0;           /* ||q(A) b|| (left) or ||b|| (right)                     */
+  double ms_total;        /* device time of the call, CUDA events                   */
+  int64_t launches;       /* kernels launched by the call                           */
+  int64_t chain_launches; /* operator launches (A and the Clenshaw steps of q(A))   */
+  double chain_bytes;     /* their algorithmic HBM bytes: vectors read + written,
+                             plus the CSR arrays for CSR handles                    */
+  double chain_ms;        /* their summed device time (opts.profile = 1, else 0)    */
+  double reserved[3];
+} pp_stats;
+
+/* Defaults for pp_opts (all fields). */
+void pp_default_opts(pp_opts *opts);
+
+/*
+ * Create a handle for a CSR matrix (Sec. 1: A sparse).  n rows/columns;
+ * rowptr_d[n+1] (int64, rowptr_d[0] = 0), col_d[nnz] (int32, 0-based),
+ * val_d[nnz] of dtype PP_F64 (PP_C128 not in this build).  The arrays are
+ * referenced, not copied (PP_PREC_DW keeps a converted copy of val), and must
+ * stay alive and unchanged for the handle's lifetime.  is_hermitian selects
+ * Lanczos under PP_ORTH_AUTO.  Errors: PP_ERR_INVALID_ARG for n <= 0 or NULL
+ * pointers, PP_ERR_UNSUPPORTED for other dtypes.
+ */
+int pp_create_csr(pp_handle *h, int64_t n, const int64_t *rowptr_d, const int32_t *col_d,
+                  const void *val_d, int32_t dtype, int32_t is_hermitian, void *cuda_stream);
+
+/*
+ * Create a handle for a matrix-free constant-coefficient stencil on a grid
+ * with Dirichlet boundary (Sec. 6, Example 1 uses the 3D Laplacian; Sec. 3.2
+ * the 2D one).  dims[4] = grid points per direction (unused entries ignored);
+ * params: PP_CONVDIFF3D7_UPWIND reads params[0] = c*h > 0, the others none
+ * (NULL allowed).  links_d is reserved (NULL).  dtype must be PP_F64.
+ */
+int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const double *params,
+                      const void *links_d, int32_t dtype, void *cuda_stream);
+
+/* Replace the handle's options; PP_ERR_INVALID_ARG for out-of-range values. */
+int pp_set_opts(pp_handle h, const pp_opts *opts);
+
+/*
+ * Build q with deg q = degree (paper: d = degree + 1 nodes) of the given kind
+ * on [a,b] = interval_ab_h[0..1] (host array), the interval enclosing
+ * spec(A) (Sec. 5.1).  interval_ab_h = NULL: the exact spectral interval of
+ * the stencil (Sec. 6, Example 1 formula and its convection-diffusion
+ * analogue); CSR handles need an interval.  degree = 0 gives constant q, i.e.
+ * plain Arnoldi/Lanczos.  The positivity of q on [a,b] is checked on a dense
+ * grid (Sec. 5.1, last paragraph); PP_ERR_NONPRIMARY if it fails.  Host
+ * work only, plus a small upload.  0 <= degree <= 128.
+ */
+int pp_build_poly(pp_handle h, int32_t degree, int32_t kind, const double *interval_ab_h);
+
+/*
+ * Read back the polynomial: coeffs_h[0..*ncoeffs-1] (Chebyshev coefficients
+ * c_i of q = sum c_i T_i((2z-a-b)/(b-a))), ab_h[2] = [a,b], image_h[2] =
+ * [min, max] of z q(z)^2 on [a,b] (the interval of Prop. 3.2).  Any output
+ * pointer may be NULL; cap = capacity of coeffs_h.
+ */
+int pp_get_poly(pp_handle h, double *coeffs_h, int32_t cap, int32_t *ncoeffs, double *ab_h,
+                double *image_h);
+
+/*
+ * x = f(A) b (Algorithm 1 or 2 by opts.side; Sec. 4 for PP_SQRT), iterating
+ * until the stopping estimate is below tol or m = m_max.  b_d, x_d: device
+ * vectors of n (nrhs = 1 in this build) entries of the handle's vector dtype;
+ * x_d must not alias b_d.  On PP_ERR_NOT_CONVERGED x_d still holds the last
+ * iterate.  stats (host, may be NULL) is filled on return.  Blocks the
+ * calling thread at each stopping check (a few bytes read back).
+ * Errors: PP_ERR_STATE before pp_build_poly, PP_ERR_INVALID_ARG for NULL or
+ * aliasing pointers, m_max < 1 or > 4096, tol < 0, non-finite ||b||.
+ */
+int pp_apply(pp_handle h, int32_t f, const void *b_d, int64_t nrhs, int32_t m_max, double tol,
+             void *x_d, pp_stats *stats);
+
+/*
+ * Same as pp_apply for HOST vectors b_h, x_h: copies b to the device, solves
+ * and copies x back, all inside the call (used for end-to-end timing).
+ * Returns after x_h is written.
+ */
+int pp_apply_host(pp_handle h, int32_t f, const double *b_h, int64_t nrhs, int32_t m_max,
+                  double tol, double *x_h, pp_stats *stats);
+
+/* y_d = A x_d (one operator application in the handle's precision). */
+int pp_op_apply(pp_handle h, const void *x_d, void *y_d);
+
+/* y_d = q(A) x_d by the matrix Clenshaw recurrence (Sec. 5.1), deg q
+   operator applications fused with the recurrence's vector updates.        */
+int pp_poly_apply(pp_handle h, const void *x_d, void *y_d);
+
+/*
+ * Read back the quadrature rule of the small projected solve: H^{-1/2} e_1 =
+ * sum_k wt_h[k] (H + sig_h[k] I)^{-1} e_1, the trapezoid rule in u = log t for
+ * z^{-1/2} = (2/pi) int_0^inf (t^2 + z)^{-1} dt (an integral representation
+ * of the inverse square root; the paper uses a Schur square root instead,
+ * Sec. 3.1).  *K = number of nodes; up to cap entries are written.
+ */
+int pp_get_quadrature(pp_handle h, double *sig_h, double *wt_h, int32_t cap, int32_t *K);
+
+/* Release the handle and its device workspace (NULL is a no-op). */
+void pp_destroy(pp_handle h);
+
+/* Static, NUL-terminated name of a status code. */
+const char *pp_strerror(int32_t status);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *pp_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int32_t pp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PP_H */

@@ -50,13 +50,14 @@ def fH_e1(H, beta, power=-0.5, hermitian=False):
 
 def pp_arnoldi(A_mv, b, power=-0.5, coeffs=(1.0,), ab=(0.0, 1.0), side="left",
                m_max=200, tol=1e-10, k_chk=1, hermitian=False, orth="mgs",
-               stop="estimate", exact=None, breakdown_tol=1e-14):
+               stop="estimate", exact=None, breakdown_tol=1e-14, on_iter=None):
     """Polynomially preconditioned Arnoldi for A^{power} b, power = -1/2 or +1/2.
 
     coeffs, ab: Chebyshev coefficients of q and its interval (see
     oracle.chebyshev); coeffs=(1.0,) is q = 1, i.e. plain Arnoldi.
     Returns a dict with the iterate x, the iteration count and the operation
-    counters (mvms, inner products) in the sense of Tables 1-3.
+    counters (mvms, inner products) in the sense of Tables 1-3.  on_iter(j), if
+    given, is called after every iteration (a timing hook; no effect on results).
     """
     c = np.asarray(coeffs, dtype=np.float64)
     a, bb = ab
@@ -93,6 +94,8 @@ def pp_arnoldi(A_mv, b, power=-0.5, coeffs=(1.0,), ab=(0.0, 1.0), side="left",
     x = None
     m = 0
     converged = False
+    if on_iter is not None:
+        on_iter(-1)
     for j in range(m_max):
         if side == "left":               # Algorithm 1, line 4
             u = A_mv(V[j])
@@ -133,6 +136,8 @@ def pp_arnoldi(A_mv, b, power=-0.5, coeffs=(1.0,), ab=(0.0, 1.0), side="left",
         lucky = hn <= breakdown_tol * max(scale, 1e-300)
         if not lucky:
             V[j + 1] = w / hn            # line 9
+        if on_iter is not None:
+            on_iter(j)
 
         if lucky or m % k_chk == 0 or m == m_max:
             z = fH_e1(H[:m, :m], beta, -0.5, tridiag)

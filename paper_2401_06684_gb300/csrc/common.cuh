@@ -1,0 +1,59 @@
+// Shared device helpers: the arithmetic traits that let every kernel be
+// written once for IEEE FP64 vectors and for double-word FP32-pair vectors,
+// and the warp/block reductions.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dw.cuh"
+
+template <typename T>
+struct num;
+
+template <>
+struct num<double> {
+  static __device__ __forceinline__ double zero() { return 0.0; }
+  static __device__ __forceinline__ double to_d(double x) { return x; }
+  static __device__ __forceinline__ double from_d(double x) { return x; }
+};
+
+template <>
+struct num<dw> {
+  static __device__ __forceinline__ dw zero() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ double to_d(dw x) { return dw_to_double(x); }
+  static __device__ __forceinline__ dw from_d(double x) { return dw_from_double(x); }
+};
+
+// Scalar coefficients passed by value to kernels, in the vector arithmetic.
+template <typename T>
+struct coef_of {
+  using type = T;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over the block; every thread gets the result.  `red` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  double s = 0.0;
+  // fixed order: deterministic
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+#define PP_CUDA_TRY(expr)                                      \
+  do {                                                         \
+    cudaError_t _e = (expr);                                   \
+    if (_e != cudaSuccess) return pp_cuda_fail(_e, #expr);     \
+  } while (0)
+
+int pp_cuda_fail(cudaError_t e, const char *what);

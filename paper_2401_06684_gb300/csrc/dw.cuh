@@ -1,0 +1,80 @@
+// Double-word ("double-float") arithmetic on the FP32 pipes.
+//
+// GB300 executes FP64 at 1/64 of its FP32 rate, so an FP64 stencil or
+// Gram-Schmidt sweep is bound by the FP64 ALU long before HBM.  A value is
+// kept as an unevaluated sum hi + lo of two floats with |lo| <= ulp(hi)/2
+// (about 48 significand bits, the same 8 bytes as an FP64).  The building
+// blocks are the error-free transformations of Knuth (TwoSum), Dekker
+// (FastTwoSum) and the FMA form of TwoProd; the compositions follow the
+// "sloppy" double-word sum and the FMA-based double-word products analysed by
+// Joldes, Muller and Popescu (ACM TOMS 44(2), 2017).  The sloppy sum's error
+// is bounded by a small multiple of u^2 (|x| + |y|), u = 2^-24: a normwise
+// bound of the same kind as an FP64 addition's, which is what the Krylov
+// process needs.
+//
+// All operations use the _rn intrinsics so that the compiler neither
+// contracts nor reassociates them.
+#pragma once
+#include <cuda_runtime.h>
+
+struct __align__(8) dw {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dw dw_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+
+// Requires |a| >= |b| (or a == 0) for exactness.
+__device__ __forceinline__ dw dw_fast_two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+
+__device__ __forceinline__ dw operator+(dw x, dw y) {
+  dw s = dw_two_sum(x.hi, y.hi);
+  float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return dw_fast_two_sum(s.hi, e);
+}
+
+__device__ __forceinline__ dw operator-(dw x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dw operator-(dw x, dw y) { return x + (-y); }
+
+// double-word x double-word (FMA form)
+__device__ __forceinline__ dw operator*(dw x, dw y) {
+  float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return dw_fast_two_sum(p, e);
+}
+
+// double-word x float
+__device__ __forceinline__ dw operator*(dw x, float y) {
+  float p = __fmul_rn(x.hi, y);
+  float e = __fmaf_rn(x.hi, y, -p);
+  e = __fmaf_rn(x.lo, y, e);
+  return dw_fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ dw dw_from_double(double v) {
+  float hi = __double2float_rn(v);
+  float lo = __double2float_rn(v - (double)hi);
+  return {hi, lo};
+}
+
+__device__ __forceinline__ double dw_to_double(dw x) { return (double)x.hi + (double)x.lo; }
+
+// Host-side split of an FP64 constant (same rounding as dw_from_double).
+static inline dw dw_split_host(double v) {
+  float hi = (float)v;
+  float lo = (float)(v - (double)hi);
+  dw r;
+  r.hi = hi;
+  r.lo = lo;
+  return r;
+}

@@ -1,0 +1,112 @@
+// Internal interfaces between the translation units of the library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pp.h"
+
+enum OpKind { OPK_CSR = 0, OPK_ST2D = 1, OPK_ST3D = 2 };
+
+// Everything a kernel needs to apply A.  Stencil rows are
+//   (A x)_c = d x_c + cm * (x at -1 offsets) + cp * (x at +1 offsets).
+struct OpDesc {
+  int kind;
+  int64_t n;
+  int64_t nx, ny, nz;
+  double d, cm, cp;
+  const int64_t *rowptr;
+  const int32_t *col;
+  const void *val;  // CSR values in the vector arithmetic (double or dw)
+};
+
+// out = alpha * (A x) + beta * x  [- y]  [+ delta * v]
+struct StepCoef {
+  double alpha, beta, delta;
+  bool sub_y, add_v;
+};
+
+template <typename T>
+int op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &c,
+            cudaStream_t s);
+
+// ---- vector kernels (vec.cu) ----
+template <typename T>
+int vec_from_f64(const double *in, T *out, int64_t n, cudaStream_t s);
+template <typename T>
+int vec_to_f64(const T *in, double *out, int64_t n, cudaStream_t s);
+template <typename T>
+int vec_scale(const T *in, T *out, int64_t n, double c, const double *c_dev, cudaStream_t s);
+template <typename T>
+int vec_copy(const T *in, T *out, int64_t n, cudaStream_t s);
+// partials[b] = sum over block b of x.y   (nb blocks)
+template <typename T>
+int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int nb, cudaStream_t s);
+// w -= alpha v_j + beta v_{j-1} (vjm1 may be NULL); norm^2 partials
+template <typename T>
+int vec_lanczos_update(T *w, const T *vj, const T *vjm1, int64_t n, const double *alpha,
+                       const double *beta_prev, double *partials, int nb, cudaStream_t s);
+// partials[b*J + c] = sum over block b of V_c . w
+template <typename T>
+int vec_multi_dot(const T *V, int64_t ldv, int J, const T *w, int64_t n, double *partials, int nb,
+                  cudaStream_t s);
+// w -= V h  (h on device, J entries); norm^2 partials if partials != NULL
+template <typename T>
+int vec_multi_update(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n,
+                     double *partials, int nb, cudaStream_t s);
+// x = V z, FP64 output
+template <typename T>
+int vec_reconstruct(const T *V, int64_t ldv, int m, const double *z, double *x, int64_t n,
+                    cudaStream_t s);
+
+// Reduction of block partials (vec.cu).
+//   mode 0: out_a[c] = s_c
+//   mode 1: out_a[c] = s_c, out_b[c] = s_c
+//   mode 2: out_a[c] = s_c, out_b[c] += s_c
+int reduce_cols(const double *partials, int nb, int ncols, int mode, double *out_a, double *out_b,
+                cudaStream_t s);
+
+// Norm finalization: beta = sqrt(sum partials); *beta_out = beta; *inv_out = 1/beta or 0 on
+// breakdown, i.e. beta <= rel * ||ref[0..nref)|| (nref = 0: only beta == 0 or non-finite).
+// On breakdown sets st->breakdown (first index recorded as m_bd).
+struct DevStatus {
+  int conv;
+  int breakdown;
+  int m_bd;
+  int bad;  // non-finite value seen
+  double est;
+  double beta0;
+  double znorm;
+  double pad;
+};
+int norm_finalize(const double *partials, int nb, double *beta_out, double *inv_out,
+                  const double *ref, int nref, double rel, int m_here, DevStatus *st,
+                  cudaStream_t s);
+
+// ---- small projected solve (small.cu) ----
+// X[k*m + i] = w_k ((H_m + s_k I)^{-1} e_1)_i for the K quadrature nodes.
+int small_tridiag_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
+                       double *X, double *scratch, cudaStream_t s);
+int small_hess_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
+                    double *X, double *scratch, cudaStream_t s);
+// z = beta0 * sum_k X[k] ; est = ||z - [zprev;0]|| / ||z||; conv = est < tol; zprev <- z
+int small_combine(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol,
+                  DevStatus *st, cudaStream_t s);
+
+// ---- host-side construction (poly.cpp) ----
+// Chebyshev interpolant of z^{-1/2} at d = degree+1 first-kind nodes of [a,b].
+std::vector<double> cheb_interp_coeffs(double a, double b, int degree);
+double cheb_eval(const std::vector<double> &c, double a, double b, double z);
+// min/max of q over a dense grid of [a,b] and of z q(z)^2
+void cheb_scan(const std::vector<double> &c, double a, double b, double *qmin, double *img_lo,
+               double *img_hi);
+// Trapezoid rule for z^{-1/2} = (2/pi) int_0^inf (t^2 + z)^{-1} dt, t = e^u.
+void invsqrt_quadrature(double lo, double hi, double tau, double theta_max, std::vector<double> *sig,
+                        std::vector<double> *wt);
+
+int pp_set_error(int status, const std::string &msg);
+
+// Kernels launched by this thread (every launcher increments it).
+int64_t &pp_launch_count();

@@ -1,0 +1,174 @@
+// Small projected solve z = beta0 H_m^{-1/2} e_1 (Algorithm 1, last line) on
+// the device, in FP64.
+//
+// The paper forms H_m^{1/2} by a blocked Schur method and solves a linear
+// system (Sec. 3.1).  Schur iterations are sequential and GB300's FP64 pipe is
+// narrow, so here the function is split into independent shifted solves that
+// run in parallel:
+//     z^{-1/2} = (2/pi) int_0^inf (t^2 + z)^{-1} dt,   t = e^u,
+// discretised by the trapezoid rule in u (nodes s_k = e^{2 u_k}, weights
+// w_k = (2h/pi) e^{u_k}; constructed on the host), so
+//     H^{-1/2} e_1 ~= sum_k w_k (H + s_k I)^{-1} e_1.
+// Every shifted matrix has its spectrum in the right half-plane shifted by
+// s_k > 0, so each solve is well posed.  One CTA (Hessenberg: Givens QR) or
+// one thread (symmetric tridiagonal: LDL^T recurrence) per node; a final
+// single-CTA pass sums the nodes in a fixed order and forms the stopping
+// estimate ||f_m - f_{m-k}|| / ||f_m|| from the coefficient vectors alone,
+// valid because V_m is orthonormal (Sec. 3.1, after Algorithm 2).
+#include "common.cuh"
+#include "internal.h"
+
+namespace {
+
+// Symmetric tridiagonal T = tridiag(beta, alpha, beta) read from the Lanczos
+// Hessenberg storage: alpha_i = H[i,i], beta_i = H[i+1,i].
+__global__ void k_tri_quad(const double *__restrict__ H, int ldh, int m, const double *__restrict__ sig,
+                           const double *__restrict__ wt, int K, double *__restrict__ X,
+                           double *__restrict__ scratch) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  const double s = sig[k];
+  double *cp = scratch + (int64_t)k * m;  // modified super-diagonal
+  double *x = X + (int64_t)k * m;         // modified rhs, then solution
+  // forward elimination of (T + sI) x = e_1
+  double den = H[0] + s;
+  double cprev = (m > 1) ? H[1] / den : 0.0;
+  double dprev = 1.0 / den;
+  cp[0] = cprev;
+  x[0] = dprev;
+  for (int i = 1; i < m; ++i) {
+    const double bsub = H[(int64_t)(i - 1) * ldh + i];  // beta_{i-1}
+    den = (H[(int64_t)i * ldh + i] + s) - bsub * cprev;
+    const double bsup = (i + 1 < m) ? H[(int64_t)i * ldh + i + 1] : 0.0;
+    cprev = bsup / den;
+    dprev = (-bsub * dprev) / den;
+    cp[i] = cprev;
+    x[i] = dprev;
+  }
+  // back substitution, scaled by the weight
+  double xn = x[m - 1];
+  const double w = wt[k];
+  x[m - 1] = w * xn;
+  for (int i = m - 2; i >= 0; --i) {
+    xn = x[i] - cp[i] * xn;
+    x[i] = w * xn;
+  }
+}
+
+// Upper Hessenberg: Givens QR of (H + sI) column by column, rotations applied
+// to the right-hand side e_1, then back substitution.  The working matrix is
+// column-major with leading dimension m+1 (odd strides avoid smem bank
+// conflicts), in dynamic shared memory or, for large m, in global scratch.
+__global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H, int ldh, int m,
+                                                   const double *__restrict__ sig,
+                                                   const double *__restrict__ wt,
+                                                   double *__restrict__ X, double *__restrict__ gscratch,
+                                                   int use_smem) {
+  extern __shared__ double sm[];
+  const int k = blockIdx.x;
+  const int ld = m + 1;
+  double *M = use_smem ? sm : gscratch + (int64_t)k * ((int64_t)ld * m + 2 * m);
+  double *g = M + (int64_t)ld * m;  // rhs / solution, m entries
+  const double s = sig[k];
+  for (int c = 0; c < m; ++c)
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+      double v = (r <= c + 1) ? H[(int64_t)c * ldh + r] : 0.0;
+      if (r == c) v += s;
+      M[(int64_t)c * ld + r] = v;
+    }
+  for (int r = threadIdx.x; r < m; r += blockDim.x) g[r] = (r == 0) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int c = 0; c + 1 < m; ++c) {
+    const double a = M[(int64_t)c * ld + c];
+    const double b = M[(int64_t)c * ld + c + 1];
+    const double r = hypot(a, b);
+    const double cs = (r > 0.0) ? a / r : 1.0;
+    const double sn = (r > 0.0) ? b / r : 0.0;
+    __syncthreads();  // everyone has read the pivot pair
+    for (int cc = c + threadIdx.x; cc < m; cc += blockDim.x) {
+      const double t1 = M[(int64_t)cc * ld + c];
+      const double t2 = M[(int64_t)cc * ld + c + 1];
+      M[(int64_t)cc * ld + c] = cs * t1 + sn * t2;
+      M[(int64_t)cc * ld + c + 1] = -sn * t1 + cs * t2;
+    }
+    if (threadIdx.x == 0) {
+      const double g1 = g[c], g2 = g[c + 1];
+      g[c] = cs * g1 + sn * g2;
+      g[c + 1] = -sn * g1 + cs * g2;
+    }
+    __syncthreads();
+  }
+  // back substitution R x = g, column oriented
+  for (int c = m - 1; c >= 0; --c) {
+    if (threadIdx.x == 0) g[c] = g[c] / M[(int64_t)c * ld + c];
+    __syncthreads();
+    const double xc = g[c];
+    for (int r = threadIdx.x; r < c; r += blockDim.x) g[r] -= M[(int64_t)c * ld + r] * xc;
+    __syncthreads();
+  }
+  const double w = wt[k];
+  for (int r = threadIdx.x; r < m; r += blockDim.x) X[(int64_t)k * m + r] = w * g[r];
+}
+
+__global__ void __launch_bounds__(256) k_combine(const double *__restrict__ X, int K, int m, int mprev,
+                                                 double *__restrict__ z, double *__restrict__ zprev,
+                                                 double tol, DevStatus *st) {
+  __shared__ double red[32];
+  const double beta0 = st->beta0;
+  double d2 = 0.0, z2 = 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < K; ++k) s += X[(int64_t)k * m + i];
+    s *= beta0;
+    z[i] = s;
+    const double p = (i < mprev) ? zprev[i] : 0.0;
+    d2 += (s - p) * (s - p);
+    z2 += s * s;
+  }
+  d2 = block_sum(d2, red);
+  z2 = block_sum(z2, red);
+  __syncthreads();
+  for (int i = threadIdx.x; i < m; i += blockDim.x) zprev[i] = z[i];
+  if (threadIdx.x == 0) {
+    const double est = (mprev > 0 && z2 > 0.0) ? sqrt(d2 / z2) : INFINITY;
+    st->est = est;
+    st->znorm = sqrt(z2);
+    if (!isfinite(z2)) st->bad = 1;
+    st->conv = (est < tol) ? 1 : 0;
+  }
+}
+
+}  // namespace
+
+int small_tridiag_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
+                       double *X, double *scratch, cudaStream_t s) {
+  k_tri_quad<<<(K + 127) / 128, 128, 0, s>>>(H, ldh, m, sig, wt, K, X, scratch);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
+int small_hess_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
+                    double *X, double *scratch, cudaStream_t s) {
+  const size_t bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * sizeof(double);
+  const size_t kSmemMax = 200 * 1024;
+  const int use_smem = bytes <= kSmemMax ? 1 : 0;
+  if (use_smem && bytes > 48 * 1024)
+    PP_CUDA_TRY(cudaFuncSetAttribute(k_hess_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  k_hess_quad<<<K, 128, use_smem ? bytes : 0, s>>>(H, ldh, m, sig, wt, X, scratch, use_smem);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
+size_t small_hess_scratch_doubles(int m, int K) {
+  return (size_t)K * ((size_t)(m + 1) * m + 2 * (size_t)m);
+}
+
+int small_combine(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol,
+                  DevStatus *st, cudaStream_t s) {
+  k_combine<<<1, 256, 0, s>>>(X, K, m, mprev, z, zprev, tol, st);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}

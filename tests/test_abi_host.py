@@ -1,0 +1,150 @@
+"""C-ABI checks that need no GPU: the library loads, exports every declared
+symbol, and its host-side construction (Chebyshev polynomial, quadrature
+rule of the small solve, argument validation) agrees with the oracle."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+from oracle import chebyshev as cheb, operators as ops
+from tests.libpp import load
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if hdr.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", hdr)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(pp_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_exports_every_declared_symbol():
+    pp = load()
+    names = declared_functions()
+    assert "pp_apply" in names and "pp_build_poly" in names and "pp_create_csr" in names
+    out = subprocess.run(["nm", "-D", "--defined-only", pp.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(l.split()[-1] for l in out.splitlines() if l.strip())
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        getattr(pp.lib(), n)
+    assert set(names) == set(pp.SYMBOLS)  # the binding covers the whole header
+
+
+def test_version_and_strerror():
+    pp = load()
+    assert pp.pp_version() >= 100
+    assert pp.pp_strerror(pp.PP_ERR_NONPRIMARY) == "PP_ERR_NONPRIMARY"
+    assert pp.pp_strerror(-99) == "PP_ERR_UNKNOWN"
+
+
+@pytest.mark.parametrize("dims", [(50, 50), (64, 64), (33, 17)])
+@pytest.mark.parametrize("degree", [0, 1, 8, 16, 31])
+def test_build_poly_matches_oracle_2d(dims, degree):
+    pp = load()
+    h = pp.pp_create_stencil(pp.PP_LAPLACE2D5, dims)
+    try:
+        pp.pp_build_poly(h, degree)
+        c, ab, img = pp.pp_get_poly(h)
+        a, b = ops.laplace_interval(dims)
+        assert np.allclose(ab, (a, b), rtol=1e-14)
+        ref = cheb.interp_coeffs(a, b, degree + 1)
+        assert np.max(np.abs(c - ref)) <= 1e-13 * np.max(np.abs(ref))
+        lo, hi = cheb.image_interval(ref, a, b, npts=20001)
+        assert abs(img[0] - lo) < 1e-9 and abs(img[1] - hi) < 1e-9
+    finally:
+        pp.pp_destroy(h)
+
+
+def test_build_poly_convdiff_interval():
+    pp = load()
+    dims = (40, 30, 20)
+    h = pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, dims, [0.5])
+    try:
+        pp.pp_build_poly(h, 4)
+        c, ab, img = pp.pp_get_poly(h)
+        assert np.allclose(ab, ops.convdiff_interval(dims, 0.5), rtol=1e-14)
+        assert np.allclose(c, cheb.interp_coeffs(ab[0], ab[1], 5), rtol=1e-13, atol=1e-15)
+    finally:
+        pp.pp_destroy(h)
+
+
+@pytest.mark.parametrize("kind,herm", [(0, True), (2, False)])
+def test_quadrature_rule_accuracy(kind, herm):
+    # sum_k w_k / (s_k + z) = z^{-1/2} on the (widened) image interval; complex z with
+    # |arg z| <= pi/3 for the non-Hermitian case
+    pp = load()
+    h = (pp.pp_create_stencil(pp.PP_LAPLACE2D5, (64, 64)) if herm else
+         pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (32, 32, 32), [0.5]))
+    try:
+        pp.pp_build_poly(h, 8)
+        _, _, img = pp.pp_get_poly(h)
+        s, w = pp.pp_get_quadrature(h)
+        assert np.all(s > 0) and np.all(w > 0) and len(s) < 600
+        z = np.geomspace(img[0] * 1e-3, img[1] * 1e3, 3001)
+        if not herm:
+            z = (z[:, None] * np.exp(1j * np.linspace(-np.pi / 3, np.pi / 3, 7))[None, :]).ravel()
+        approx = (w[None, :] / (s[None, :] + z[:, None])).sum(1)
+        assert np.max(np.abs(approx * np.sqrt(z) - 1)) < 1e-13
+    finally:
+        pp.pp_destroy(h)
+
+
+def test_argument_validation():
+    pp = load()
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_create_stencil(pp.PP_LAPLACE3D7, (0, 4, 4))
+    assert e.value.status == pp.PP_ERR_INVALID_ARG
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (4, 4, 4))  # needs c*h
+    assert e.value.status == pp.PP_ERR_INVALID_ARG
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_create_stencil(pp.PP_WILSON4D_DHD, (4, 4, 4, 4))
+    assert e.value.status == pp.PP_ERR_UNSUPPORTED
+    h = pp.pp_create_stencil(pp.PP_LAPLACE3D7, (4, 4, 4))
+    try:
+        with pytest.raises(pp.PPError) as e:  # apply before build_poly
+            pp.pp_apply(h, pp.PP_INVSQRT, 1, 2)
+        assert e.value.status == pp.PP_ERR_STATE
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_build_poly(h, -1)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_build_poly(h, 4, pp.PP_RITZ_LEJA)
+        assert e.value.status == pp.PP_ERR_UNSUPPORTED
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_build_poly(h, 4, interval_ab=(2.0, 1.0))
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+        pp.pp_build_poly(h, 4)
+        with pytest.raises(pp.PPError) as e:  # aliasing
+            pp.pp_apply(h, pp.PP_INVSQRT, 1024, 1024)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_apply(h, 3, 1024, 2048)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_apply(h, pp.PP_SQRT, 1024, 2048, m_max=0)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+        o = pp.pp_default_opts()
+        o.precision = 7
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_set_opts(h, o)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+    finally:
+        pp.pp_destroy(h)
+    # CSR handles need an interval
+    h = pp.pp_create_csr(16, 8, 8, 8, is_hermitian=True)
+    try:
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_build_poly(h, 4)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+    finally:
+        pp.pp_destroy(h)
+    pp.pp_destroy(None)
