@@ -32,7 +32,7 @@ WORKLOAD = "3D convection-diffusion 128^3 upwind 7-point (n=2097152, c*h=0.5), f
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--grid", type=int, default=128)
@@ -40,6 +40,7 @@ def parse():
     p.add_argument("--prec", default="dw", choices=["dw", "f64"])
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--cpu-iters", type=int, default=3)
+    p.add_argument("--m-max", type=int, default=400)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     return p.parse_args()
@@ -136,7 +137,7 @@ class ClockSampler:
         self.p = None
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(dev)], stdout=subprocess.PIPE,
+                                       "-lms", "50", "-i", str(dev)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
@@ -214,7 +215,7 @@ def run_ours(args):
     b = torch.from_numpy(synth.rhs(n, rank)).cuda()
     x = torch.empty(n, dtype=torch.float64, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    m_max = 400
+    m_max = args.m_max
 
     def solve():
         return pp.pp_apply(h, pp.PP_SQRT, b, x, m_max=m_max, tol=args.tol)
@@ -313,6 +314,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "kernel": "st3d_step (operator + Clenshaw update)", "peak_source": peak_src,
+                         "timing": "CUDA events around each run of consecutive operator launches "
+                                   "(one q(A) or one A product) during the timed steps",
                          "launches": chain_launches,
                          "bytes_per_launch": chain_bytes / max(chain_launches, 1)},
             "cpu_baseline": cpu,

@@ -16,6 +16,12 @@
 
 size_t small_hess_scratch_doubles(int m, int K);
 
+#define RC_(x)                  \
+  do {                          \
+    int _r = (x);               \
+    if (_r != PP_OK) return _r; \
+  } while (0)
+
 namespace {
 thread_local std::string g_last_error;
 thread_local int64_t g_launches = 0;
@@ -91,12 +97,6 @@ struct pp_ctx {
 
 namespace {
 
-int nblocks_for(int64_t n) {
-  int64_t nb = (n + 255) / 256;
-  if (nb > 152 * 4) nb = 152 * 4;
-  if (nb < 1) nb = 1;
-  return (int)nb;
-}
 
 void ws_free(Workspace &w) {
   if (w.V) cudaFree(w.V);
@@ -113,33 +113,50 @@ void ws_free(Workspace &w) {
   w = Workspace();
 }
 
-// One operator launch of the chain: counted, its algorithmic bytes added,
-// and bracketed by events when profiling.
+// Profiling brackets a run of consecutive operator launches (one q(A)
+// application or one product with A) with a pair of events on the handle's
+// stream; the per-launch average then includes the short gaps between the
+// launches of a run.
+int prof_begin(pp_ctx *c) {
+  if (!c->opts.profile) return PP_OK;
+  if (c->prof_used + 2 > c->prof_ev.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      PP_CUDA_TRY(cudaEventCreate(&e));
+      c->prof_ev.push_back(e);
+    }
+  }
+  PP_CUDA_TRY(cudaEventRecord(c->prof_ev[c->prof_used], c->stream));
+  return PP_OK;
+}
+
+int prof_end(pp_ctx *c) {
+  if (!c->opts.profile) return PP_OK;
+  PP_CUDA_TRY(cudaEventRecord(c->prof_ev[c->prof_used + 1], c->stream));
+  c->prof_used += 2;
+  return PP_OK;
+}
+
+// One operator launch of the chain: counted and its algorithmic bytes added.
 template <typename T>
 int run_op(pp_ctx *c, const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &k) {
-  const bool prof = c->opts.profile != 0;
-  if (prof) {
-    if (c->prof_used + 2 > c->prof_ev.size()) {
-      for (int i = 0; i < 256; ++i) {
-        cudaEvent_t e;
-        PP_CUDA_TRY(cudaEventCreate(&e));
-        c->prof_ev.push_back(e);
-      }
-    }
-    PP_CUDA_TRY(cudaEventRecord(c->prof_ev[c->prof_used], c->stream));
-  }
   int rc = op_step<T>(op, x, y, v, out, k, c->stream);
   if (rc) return rc;
-  if (prof) {
-    PP_CUDA_TRY(cudaEventRecord(c->prof_ev[c->prof_used + 1], c->stream));
-    c->prof_used += 2;
-  }
   c->chain_launches += 1;
   double vecs = 2.0 + (k.sub_y ? 1.0 : 0.0) + (k.add_v ? 1.0 : 0.0);
   double bytes = vecs * 8.0 * (double)c->n;
   if (c->op_kind == OPK_CSR) bytes += 12.0 * (double)c->nnz + 8.0 * (double)(c->n + 1);
   c->chain_bytes += bytes;
   return PP_OK;
+}
+
+// A run of operator launches bracketed for profiling.
+template <typename T>
+int run_op_timed(pp_ctx *c, const OpDesc &op, const T *x, const T *y, const T *v, T *out,
+                 const StepCoef &k) {
+  RC_(prof_begin(c));
+  RC_(run_op<T>(c, op, x, y, v, out, k));
+  return prof_end(c);
 }
 
 double prof_ms(pp_ctx *c) {
@@ -160,7 +177,7 @@ struct DLayout {
 DLayout dlayout(const pp_ctx *c, int m_cap) {
   DLayout L;
   L.ldh = m_cap + 1;
-  L.nb = nblocks_for(c->n);
+  L.nb = vec_nchunks(c->n);
   L.K = (int)c->qsig.size();
   size_t o = 0;
   L.H = o;
@@ -256,7 +273,7 @@ OpDesc make_op(const pp_ctx *c, int prec) {
 // y = q(A) x by the matrix Clenshaw recurrence with the first two steps
 // folded (b_{k+1} = 0, b_k = c_k x): deg q operator applications.
 template <typename T>
-int poly_apply_t(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3]) {
+int poly_apply_raw(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3]) {
   const std::vector<double> &cf = c->coef;
   const int k = (int)cf.size() - 1;
   const double s1 = 4.0 / (c->b - c->a), s2 = -2.0 * (c->a + c->b) / (c->b - c->a);
@@ -275,6 +292,14 @@ int poly_apply_t(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3]) {
     i0 = t;
   }
   return run_op<T>(c, op, bufs[i1], bufs[i2], in, out, {0.5 * s1, 0.5 * s2, cf[0], true, true});
+}
+
+template <typename T>
+int poly_apply_t(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3]) {
+  if (c->degree == 0) return poly_apply_raw<T>(c, op, in, out, bufs);
+  RC_(prof_begin(c));
+  RC_(poly_apply_raw<T>(c, op, in, out, bufs));
+  return prof_end(c);
 }
 
 template <typename T>
@@ -316,7 +341,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
     rhs = t[0];
   }
   if (f == PP_SQRT) {  // Sec. 4: A^{1/2} b = A^{-1/2} (A b)
-    RC(run_op<T>(c, op, rhs, nullptr, nullptr, t[1], {1.0, 0.0, 0.0, false, false}));
+    RC(run_op_timed<T>(c, op, rhs, nullptr, nullptr, t[1], {1.0, 0.0, 0.0, false, false}));
     rhs = t[1];
     mvms += 1;
   }
@@ -353,14 +378,14 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
     T *vj = V + (size_t)j * ldv;
     T *wv = V + (size_t)(j + 1) * ldv;
     if (!right) {  // Algorithm 1, line 4: u = A v_j, y = q(A) u, w = q(A) y
-      RC(run_op<T>(c, op, vj, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
+      RC(run_op_timed<T>(c, op, vj, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
       RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
       RC(poly_apply_t<T>(c, op, t[1], wv, pb));
     } else {       // Algorithm 2, line 4: y_j = q(A) v_j, u = q(A) y_j, w = A u
       T *yj = Y + (size_t)j * ldv;
       RC(poly_apply_t<T>(c, op, vj, yj, pb));
       RC(poly_apply_t<T>(c, op, yj, t[0], pb));
-      RC(run_op<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
+      RC(run_op_timed<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
     }
     mvms += 2 * deg + 1;
     double *hcol = H + (size_t)j * ldh;

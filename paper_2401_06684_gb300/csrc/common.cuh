@@ -24,11 +24,37 @@ struct num<dw> {
   static __device__ __forceinline__ dw from_d(double x) { return dw_from_double(x); }
 };
 
-// Scalar coefficients passed by value to kernels, in the vector arithmetic.
+// Accumulator of a linear combination in the vector arithmetic: plain FP64
+// for double; the lazy compensated pair (dw.cuh) for double-word.
 template <typename T>
-struct coef_of {
-  using type = T;
+struct acc_of;
+template <>
+struct acc_of<double> {
+  using type = double;
 };
+template <>
+struct acc_of<dw> {
+  using type = dwacc;
+};
+
+__device__ __forceinline__ void acc_set(double &a, double x) { a = x; }
+__device__ __forceinline__ void acc_add(double &a, double x) { a += x; }
+__device__ __forceinline__ void acc_sub(double &a, double x) { a -= x; }
+__device__ __forceinline__ void acc_set_prod(double &a, double c, double x) { a = c * x; }
+__device__ __forceinline__ void acc_add_prod(double &a, double c, double x) { a = fma(c, x, a); }
+__device__ __forceinline__ double acc_get(const double &a) { return a; }
+__device__ __forceinline__ double acc_raw(const double &a) { return a; }
+
+// Vectorised 8-byte loads through the read-only path.
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p) {
+  return __ldg(p);
+}
+template <>
+__device__ __forceinline__ dw ldg<dw>(const dw *p) {
+  float2 f = __ldg(reinterpret_cast<const float2 *>(p));
+  return {f.x, f.y};
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -78,3 +78,53 @@ static inline dw dw_split_host(double v) {
   r.lo = lo;
   return r;
 }
+
+// Lazy compensated accumulator (the compensated dot-product scheme of Ogita,
+// Rump and Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6),
+// 2005, with double-word operands): the running sum s collects the leading
+// parts through TwoSum, every rounding error and every trailing part goes
+// to e, and the pair is renormalised once at the end.  The result is as
+// accurate as a computation in twice the float precision: error about
+// n u^2 sum |terms|.
+struct dwacc {
+  float s, e;
+};
+
+__device__ __forceinline__ void acc_set(dwacc &a, dw x) {
+  a.s = x.hi;
+  a.e = x.lo;
+}
+
+__device__ __forceinline__ void acc_add(dwacc &a, dw x) {
+  dw t = dw_two_sum(a.s, x.hi);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, x.lo));
+}
+
+__device__ __forceinline__ void acc_sub(dwacc &a, dw x) { acc_add(a, {-x.hi, -x.lo}); }
+
+// product c*x as an unnormalised pair (p, pe): c.lo*x.lo is dropped (~u^2 |c x|)
+__device__ __forceinline__ dw dw_prod_raw(dw c, dw x) {
+  float p = __fmul_rn(c.hi, x.hi);
+  float e = __fmaf_rn(c.hi, x.hi, -p);
+  e = __fmaf_rn(c.hi, x.lo, e);
+  e = __fmaf_rn(c.lo, x.hi, e);
+  return {p, e};
+}
+
+__device__ __forceinline__ void acc_set_prod(dwacc &a, dw c, dw x) {
+  dw p = dw_prod_raw(c, x);
+  a.s = p.hi;
+  a.e = p.lo;
+}
+
+__device__ __forceinline__ void acc_add_prod(dwacc &a, dw c, dw x) {
+  dw p = dw_prod_raw(c, x);
+  dw t = dw_two_sum(a.s, p.hi);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, p.lo));
+}
+
+__device__ __forceinline__ dw acc_get(const dwacc &a) { return dw_fast_two_sum(a.s, a.e); }
+// the unnormalised pair, usable as a product operand
+__device__ __forceinline__ dw acc_raw(const dwacc &a) { return {a.s, a.e}; }

@@ -33,6 +33,8 @@ int op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const 
             cudaStream_t s);
 
 // ---- vector kernels (vec.cu) ----
+// Number of row chunks (= blocks, = partial sums) of the reduction kernels.
+int vec_nchunks(int64_t n);
 template <typename T>
 int vec_from_f64(const double *in, T *out, int64_t n, cudaStream_t s);
 template <typename T>

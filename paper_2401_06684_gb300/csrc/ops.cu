@@ -13,16 +13,6 @@
 namespace {
 
 template <typename T>
-__device__ __forceinline__ T ld(const T *p) {
-  return __ldg(p);
-}
-template <>
-__device__ __forceinline__ dw ld<dw>(const dw *p) {
-  float2 f = __ldg(reinterpret_cast<const float2 *>(p));
-  return {f.x, f.y};
-}
-
-template <typename T>
 __device__ __forceinline__ T shfl_xor_t(T v, int o, int width) {
   return __shfl_xor_sync(0xffffffffu, v, o, width);
 }
@@ -36,36 +26,71 @@ struct Konst {
   T K0, Km, Kp, D;
 };
 
-// 3D 7-point: thread per (i,j) column, marching over a chunk of k with the
-// k-1 / k / k+1 values kept in registers; in-plane neighbours through L1.
+// 3D 7-point: thread per (i,j) column, marching over a chunk of k.  The
+// k-1 / k / k+1 values stay in registers and every load of plane k+1 is
+// issued before plane k is computed (one plane of software prefetch); in-plane
+// neighbours come through L1.  The row is evaluated as one compensated linear
+// combination K0 x_c + Km (sum of -1 neighbours) + Kp (sum of +1 neighbours)
+// - y + D v.
 template <typename T, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(256) st3d_step(const T *__restrict__ x, const T *__restrict__ y,
                                                  const T *__restrict__ v, T *__restrict__ out,
                                                  int nx, int ny, int nz, int kchunk, Konst<T> K) {
+  using A = typename acc_of<T>::type;
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   const int k0 = blockIdx.z * kchunk;
   const int k1 = min(nz, k0 + kchunk);
   if (i >= nx || j >= ny || k0 >= nz) return;
   const int64_t plane = (int64_t)nx * ny;
-  const int64_t base = (int64_t)j * nx + i;
+  const bool hw = i > 0, he = i + 1 < nx, hs = j > 0, hn = j + 1 < ny;
   const T zero = num<T>::zero();
-  T xm = (k0 > 0) ? ld(x + (k0 - 1) * plane + base) : zero;
-  T xc = ld(x + k0 * plane + base);
+  int64_t off = (int64_t)k0 * plane + (int64_t)j * nx + i;
+  T xm = (k0 > 0) ? ldg(x + off - plane) : zero;
+  T xc = ldg(x + off);
+  T xu = (k0 + 1 < nz) ? ldg(x + off + plane) : zero;
+  T xw = hw ? ldg(x + off - 1) : zero;
+  T xe = he ? ldg(x + off + 1) : zero;
+  T xs = hs ? ldg(x + off - nx) : zero;
+  T xn = hn ? ldg(x + off + nx) : zero;
+  T yy = SUB_Y ? ldg(y + off) : zero;
+  T vv = ADD_V ? ldg(v + off) : zero;
   for (int k = k0; k < k1; ++k) {
-    const int64_t id = k * plane + base;
-    T xp = (k + 1 < nz) ? ld(x + id + plane) : zero;
-    T sm = xm, sp = xp;
-    if (i > 0) sm = sm + ld(x + id - 1);
-    if (i + 1 < nx) sp = sp + ld(x + id + 1);
-    if (j > 0) sm = sm + ld(x + id - nx);
-    if (j + 1 < ny) sp = sp + ld(x + id + nx);
-    T r = K.K0 * xc + K.Km * sm + K.Kp * sp;
-    if (SUB_Y) r = r - ld(y + id);
-    if (ADD_V) r = r + K.D * ld(v + id);
-    out[id] = r;
+    const int64_t offn = off + plane;
+    const bool more = k + 1 < k1;
+    T xu2 = zero, xw2 = zero, xe2 = zero, xs2 = zero, xn2 = zero, y2 = zero, v2 = zero;
+    if (more) {
+      if (k + 2 < nz) xu2 = ldg(x + offn + plane);
+      if (hw) xw2 = ldg(x + offn - 1);
+      if (he) xe2 = ldg(x + offn + 1);
+      if (hs) xs2 = ldg(x + offn - nx);
+      if (hn) xn2 = ldg(x + offn + nx);
+      if (SUB_Y) y2 = ldg(y + offn);
+      if (ADD_V) v2 = ldg(v + offn);
+    }
+    A nm, np, r;
+    acc_set(nm, xm);
+    acc_add(nm, xw);
+    acc_add(nm, xs);
+    acc_set(np, xu);
+    acc_add(np, xe);
+    acc_add(np, xn);
+    acc_set_prod(r, K.K0, xc);
+    acc_add_prod(r, K.Km, acc_raw(nm));
+    acc_add_prod(r, K.Kp, acc_raw(np));
+    if (SUB_Y) acc_sub(r, yy);
+    if (ADD_V) acc_add_prod(r, K.D, vv);
+    out[off] = acc_get(r);
     xm = xc;
-    xc = xp;
+    xc = xu;
+    xu = xu2;
+    xw = xw2;
+    xe = xe2;
+    xs = xs2;
+    xn = xn2;
+    yy = y2;
+    vv = v2;
+    off = offn;
   }
 }
 
@@ -74,20 +99,30 @@ template <typename T, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(256) st2d_step(const T *__restrict__ x, const T *__restrict__ y,
                                                  const T *__restrict__ v, T *__restrict__ out,
                                                  int nx, int ny, Konst<T> K) {
+  using A = typename acc_of<T>::type;
   const int i = blockIdx.x * 32 + threadIdx.x;
   const int j = blockIdx.y * 8 + threadIdx.y;
   if (i >= nx || j >= ny) return;
   const int64_t id = (int64_t)j * nx + i;
   const T zero = num<T>::zero();
-  T sm = zero, sp = zero;
-  if (i > 0) sm = ld(x + id - 1);
-  if (i + 1 < nx) sp = ld(x + id + 1);
-  if (j > 0) sm = sm + ld(x + id - nx);
-  if (j + 1 < ny) sp = sp + ld(x + id + nx);
-  T r = K.K0 * ld(x + id) + K.Km * sm + K.Kp * sp;
-  if (SUB_Y) r = r - ld(y + id);
-  if (ADD_V) r = r + K.D * ld(v + id);
-  out[id] = r;
+  const T xw = (i > 0) ? ldg(x + id - 1) : zero;
+  const T xe = (i + 1 < nx) ? ldg(x + id + 1) : zero;
+  const T xs = (j > 0) ? ldg(x + id - nx) : zero;
+  const T xn = (j + 1 < ny) ? ldg(x + id + nx) : zero;
+  const T xc = ldg(x + id);
+  const T yy = SUB_Y ? ldg(y + id) : zero;
+  const T vv = ADD_V ? ldg(v + id) : zero;
+  A nm, np, r;
+  acc_set(nm, xw);
+  acc_add(nm, xs);
+  acc_set(np, xe);
+  acc_add(np, xn);
+  acc_set_prod(r, K.K0, xc);
+  acc_add_prod(r, K.Km, acc_raw(nm));
+  acc_add_prod(r, K.Kp, acc_raw(np));
+  if (SUB_Y) acc_sub(r, yy);
+  if (ADD_V) acc_add_prod(r, K.D, vv);
+  out[id] = acc_get(r);
 }
 
 // CSR: L lanes per row, lane-strided over the row's entries, shuffle sum.
@@ -98,21 +133,26 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
                                                 const T *__restrict__ y, const T *__restrict__ v,
                                                 T *__restrict__ out, int64_t n, T alpha, T beta,
                                                 T delta) {
+  using A = typename acc_of<T>::type;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = t / L;
   const int lane = (int)(t % L);
-  T acc = num<T>::zero();
+  A acc;
+  acc_set(acc, num<T>::zero());
   if (row < n) {
     const int64_t p1 = __ldg(rowptr + row + 1);
-    for (int64_t p = __ldg(rowptr + row) + lane; p < p1; p += L) acc = acc + ld(val + p) * ld(x + __ldg(col + p));
+    for (int64_t p = __ldg(rowptr + row) + lane; p < p1; p += L) acc_add_prod(acc, ldg(val + p), ldg(x + __ldg(col + p)));
   }
+  T sum = acc_get(acc);
 #pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) acc = acc + shfl_xor_t(acc, o, L);
+  for (int o = L / 2; o > 0; o >>= 1) sum = sum + shfl_xor_t(sum, o, L);
   if (row < n && lane == 0) {
-    T r = alpha * acc + beta * ld(x + row);
-    if (SUB_Y) r = r - ld(y + row);
-    if (ADD_V) r = r + delta * ld(v + row);
-    out[row] = r;
+    A r;
+    acc_set_prod(r, alpha, sum);
+    acc_add_prod(r, beta, ldg(x + row));
+    if (SUB_Y) acc_sub(r, ldg(y + row));
+    if (ADD_V) acc_add_prod(r, delta, ldg(v + row));
+    out[row] = acc_get(r);
   }
 }
 

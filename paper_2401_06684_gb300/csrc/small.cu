@@ -110,30 +110,93 @@ __global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H,
   for (int r = threadIdx.x; r < m; r += blockDim.x) X[(int64_t)k * m + r] = w * g[r];
 }
 
-__global__ void __launch_bounds__(256) k_combine(const double *__restrict__ X, int K, int m, int mprev,
-                                                 double *__restrict__ z, double *__restrict__ zprev,
-                                                 double tol, DevStatus *st) {
-  __shared__ double red[32];
+// Warp-per-node variant for m <= 64: lanes own columns (rotations) and rows
+// (back substitution); warp-synchronous, several nodes per block.
+__global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict__ H, int ldh, int m,
+                                                        const double *__restrict__ sig,
+                                                        const double *__restrict__ wt, int K,
+                                                        double *__restrict__ X) {
+  extern __shared__ double sm[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int k = blockIdx.x * (blockDim.x >> 5) + wid;
+  if (k >= K) return;  // whole warp leaves together
+  const int ld = m + 1;
+  double *M = sm + (int64_t)wid * ((int64_t)ld * m + m);
+  double *g = M + (int64_t)ld * m;
+  const double s = sig[k];
+  for (int c = 0; c < m; ++c)
+    for (int r = lane; r < m; r += 32) {
+      double v = (r <= c + 1) ? H[(int64_t)c * ldh + r] : 0.0;
+      if (r == c) v += s;
+      M[(int64_t)c * ld + r] = v;
+    }
+  for (int r = lane; r < m; r += 32) g[r] = (r == 0) ? 1.0 : 0.0;
+  __syncwarp();
+  for (int c = 0; c + 1 < m; ++c) {
+    const double a = M[(int64_t)c * ld + c];
+    const double b = M[(int64_t)c * ld + c + 1];
+    const double r = hypot(a, b);
+    const double cs = (r > 0.0) ? a / r : 1.0;
+    const double sn = (r > 0.0) ? b / r : 0.0;
+    __syncwarp();
+    for (int cc = c + lane; cc < m; cc += 32) {
+      const double t1 = M[(int64_t)cc * ld + c];
+      const double t2 = M[(int64_t)cc * ld + c + 1];
+      M[(int64_t)cc * ld + c] = cs * t1 + sn * t2;
+      M[(int64_t)cc * ld + c + 1] = -sn * t1 + cs * t2;
+    }
+    if (lane == 0) {
+      const double g1 = g[c], g2 = g[c + 1];
+      g[c] = cs * g1 + sn * g2;
+      g[c + 1] = -sn * g1 + cs * g2;
+    }
+    __syncwarp();
+  }
+  for (int c = m - 1; c >= 0; --c) {
+    const double xc = g[c] / M[(int64_t)c * ld + c];
+    __syncwarp();
+    for (int r = lane; r < c; r += 32) g[r] -= M[(int64_t)c * ld + r] * xc;
+    if (lane == 0) g[c] = xc;
+    __syncwarp();
+  }
+  const double w = wt[k];
+  for (int r = lane; r < m; r += 32) X[(int64_t)k * m + r] = w * g[r];
+}
+
+// z_i = beta0 sum_k X[k][i]: one warp per component (lanes stride over the
+// nodes, fixed shuffle tree), then the stopping estimate over the components.
+__global__ void __launch_bounds__(1024) k_combine(const double *__restrict__ X, int K, int m, int mprev,
+                                                  double *__restrict__ z, double *__restrict__ zprev,
+                                                  double tol, DevStatus *st) {
+  __shared__ double rd[32], rz[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double beta0 = st->beta0;
   double d2 = 0.0, z2 = 0.0;
-  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+  for (int i = wid; i < m; i += 32) {
     double s = 0.0;
-    for (int k = 0; k < K; ++k) s += X[(int64_t)k * m + i];
-    s *= beta0;
-    z[i] = s;
+    for (int k = lane; k < K; k += 32) s += X[(int64_t)k * m + i];
+    s = warp_sum(s) * beta0;
     const double p = (i < mprev) ? zprev[i] : 0.0;
     d2 += (s - p) * (s - p);
     z2 += s * s;
+    if (lane == 0) z[i] = s;
   }
-  d2 = block_sum(d2, red);
-  z2 = block_sum(z2, red);
+  if (lane == 0) {
+    rd[wid] = d2;
+    rz[wid] = z2;
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < m; i += blockDim.x) zprev[i] = z[i];
   if (threadIdx.x == 0) {
-    const double est = (mprev > 0 && z2 > 0.0) ? sqrt(d2 / z2) : INFINITY;
+    double D = 0.0, Z = 0.0;
+    for (int q = 0; q < 32; ++q) {
+      D += rd[q];
+      Z += rz[q];
+    }
+    const double est = (mprev > 0 && Z > 0.0) ? sqrt(D / Z) : INFINITY;
     st->est = est;
-    st->znorm = sqrt(z2);
-    if (!isfinite(z2)) st->bad = 1;
+    st->znorm = sqrt(Z);
+    if (!isfinite(Z)) st->bad = 1;
     st->conv = (est < tol) ? 1 : 0;
   }
 }
@@ -150,6 +213,17 @@ int small_tridiag_quad(const double *H, int ldh, int m, const double *sig, const
 
 int small_hess_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
                     double *X, double *scratch, cudaStream_t s) {
+  if (m <= 64) {
+    const size_t per_warp = ((size_t)(m + 1) * m + m) * sizeof(double);
+    int wpb = (int)((48 * 1024) / per_warp);
+    if (wpb > 8) wpb = 8;
+    if (wpb < 1) wpb = 1;
+    const unsigned grid = (unsigned)((K + wpb - 1) / wpb);
+    k_hess_quad_warp<<<grid, 32 * wpb, per_warp * wpb, s>>>(H, ldh, m, sig, wt, K, X);
+    ++pp_launch_count();
+    PP_CUDA_TRY(cudaGetLastError());
+    return PP_OK;
+  }
   const size_t bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * sizeof(double);
   const size_t kSmemMax = 200 * 1024;
   const int use_smem = bytes <= kSmemMax ? 1 : 0;
@@ -167,7 +241,7 @@ size_t small_hess_scratch_doubles(int m, int K) {
 
 int small_combine(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol,
                   DevStatus *st, cudaStream_t s) {
-  k_combine<<<1, 256, 0, s>>>(X, K, m, mprev, z, zprev, tol, st);
+  k_combine<<<1, 1024, 0, s>>>(X, K, m, mprev, z, zprev, tol, st);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;

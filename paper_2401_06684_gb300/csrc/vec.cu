@@ -1,25 +1,48 @@
 // Vector kernels of the Krylov process: conversions at the API boundary,
-// inner products (per-block partials reduced in a fixed order, so results are
-// bitwise reproducible), the Lanczos three-term update, classical
-// Gram-Schmidt sweeps against the stored basis (Algorithm 1, lines 5-9, done
-// as two CGS passes), and the reconstruction f_m = V_m z (Algorithm 1, last
-// line).  Per-element products accumulate in the vector arithmetic (FP64 or
-// double-word); per-thread sums are widened to FP64 before any cross-thread
-// reduction.
+// inner products, the Lanczos three-term update, classical Gram-Schmidt
+// sweeps against the stored basis (Algorithm 1, lines 5-9, done as two CGS
+// passes), and the reconstruction f_m = V_m z (Algorithm 1, last line).
+//
+// Layout: every block owns a chunk of CHUNK = 2048 consecutive rows; thread t
+// owns rows chunk + t + 256 u, u < 8, so each column sweep issues 8
+// independent coalesced loads per thread.  Products accumulate in the vector
+// arithmetic (FP64, or the compensated double-word accumulator); warp
+// reductions stay in that arithmetic and only the 8 warp sums of a block are
+// widened to FP64, so every block writes one FP64 partial per column and a
+// fixed-order pass over the partials finishes the sum (results are bitwise
+// reproducible run to run).
 #include "common.cuh"
 #include "internal.h"
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ T ldv(const T *p) {
-  return *p;
+constexpr int TPB = 256;
+constexpr int U = 8;
+constexpr int CHUNK = TPB * U;
+constexpr int CG = 8;  // columns per block in the multi-dot
+
+__device__ __forceinline__ double warp_reduce_d(double v) { return warp_sum(v); }
+__device__ __forceinline__ dw warp_reduce_d(dw v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dw t = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = v + t;
+  }
+  return v;
 }
 
+// Block sum of per-thread values in arithmetic T; result (FP64) valid in thread 0.
 template <typename T>
-__device__ __forceinline__ double sq_d(T v) {
-  double d = num<T>::to_d(v);
-  return d * d;
+__device__ __forceinline__ double block_reduce_to_d(T v, double *red) {
+  v = warp_reduce_d(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[wid] = num<T>::to_d(v);
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < TPB / 32; ++i) s += red[i];
+  return s;
 }
 
 template <typename T>
@@ -49,105 +72,164 @@ __global__ void k_copy(const T *__restrict__ in, T *__restrict__ out, int64_t n)
     out[i] = in[i];
 }
 
+// partials[chunk] = sum over the chunk of x.y
 template <typename T>
-__global__ void __launch_bounds__(256) k_dot(const T *__restrict__ x, const T *__restrict__ y, int64_t n,
+__global__ void __launch_bounds__(TPB) k_dot(const T *__restrict__ x, const T *__restrict__ y, int64_t n,
                                              double *__restrict__ partials) {
-  __shared__ double red[32];
-  T acc = num<T>::zero();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    acc = acc + x[i] * y[i];
-  const double s = block_sum(num<T>::to_d(acc), red);
+  using A = typename acc_of<T>::type;
+  __shared__ double red[TPB / 32];
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  A acc;
+  acc_set(acc, num<T>::zero());
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB;
+    if (r < n) acc_add_prod(acc, ldg(x + r), ldg(y + r));
+  }
+  const double s = block_reduce_to_d(acc_get(acc), red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+// w -= alpha v_j + beta v_{j-1}; partials[chunk] = ||w||^2 over the chunk
 template <typename T>
-__global__ void __launch_bounds__(256) k_lanczos_update(T *__restrict__ w, const T *__restrict__ vj,
+__global__ void __launch_bounds__(TPB) k_lanczos_update(T *__restrict__ w, const T *__restrict__ vj,
                                                         const T *__restrict__ vjm1, int64_t n,
                                                         const double *__restrict__ alpha,
                                                         const double *__restrict__ beta_prev,
                                                         double *__restrict__ partials) {
-  __shared__ double red[32];
+  using A = typename acc_of<T>::type;
+  __shared__ double red[TPB / 32];
   const T a = num<T>::from_d(-(*alpha));
   const T b = num<T>::from_d(vjm1 ? -(*beta_prev) : 0.0);
-  T acc = num<T>::zero();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T r = w[i] + a * vj[i];
-    if (vjm1) r = r + b * vjm1[i];
-    w[i] = r;
-    acc = acc + r * r;
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  A nrm;
+  acc_set(nrm, num<T>::zero());
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB;
+    if (r < n) {
+      A acc;
+      acc_set(acc, w[r]);
+      acc_add_prod(acc, a, ldg(vj + r));
+      if (vjm1) acc_add_prod(acc, b, ldg(vjm1 + r));
+      const T wr = acc_get(acc);
+      w[r] = wr;
+      acc_add_prod(nrm, wr, wr);
+    }
   }
-  const double s = block_sum(num<T>::to_d(acc), red);
+  const double s = block_reduce_to_d(acc_get(nrm), red);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
-// Multi-dot: columns in groups of G; per-thread G accumulators over the
-// thread's rows, warp shuffles, then one smem pass over the warps.
-constexpr int G = 8;
+// partials[chunk*J + c] = sum over the chunk of V_c . w, for the CG columns
+// c = blockIdx.y*CG + g of this block.
 template <typename T>
-__global__ void __launch_bounds__(256) k_multi_dot(const T *__restrict__ V, int64_t ldv, int J,
+__global__ void __launch_bounds__(TPB) k_multi_dot(const T *__restrict__ V, int64_t ldv, int J,
                                                    const T *__restrict__ w, int64_t n,
                                                    double *__restrict__ partials) {
-  __shared__ double red[8][G];
+  using A = typename acc_of<T>::type;
+  __shared__ double red[CG][TPB / 32];
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  const int c0 = blockIdx.y * CG;
+  const int ncol = min(CG, J - c0);
+  T wv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB;
+    wv[u] = (r < n) ? ldg(w + r) : num<T>::zero();
+  }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int c0 = 0; c0 < J; c0 += G) {
-    T acc[G];
+  for (int g = 0; g < ncol; ++g) {
+    const T *col = V + (int64_t)(c0 + g) * ldv;
+    A acc;
+    acc_set(acc, num<T>::zero());
 #pragma unroll
-    for (int g = 0; g < G; ++g) acc[g] = num<T>::zero();
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-      const T wi = w[i];
-#pragma unroll
-      for (int g = 0; g < G; ++g)
-        if (c0 + g < J) acc[g] = acc[g] + V[(int64_t)(c0 + g) * ldv + i] * wi;
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = base + (int64_t)u * TPB;
+      if (r < n) acc_add_prod(acc, ldg(col + r), wv[u]);
     }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      double s = warp_sum(num<T>::to_d(acc[g]));
-      if (lane == 0) red[wid][g] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x < G && c0 + (int)threadIdx.x < J) {
-      double s = 0.0;
-      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) s += red[q][threadIdx.x];
-      partials[(int64_t)blockIdx.x * J + c0 + threadIdx.x] = s;
-    }
-    __syncthreads();
+    const T s = warp_reduce_d(acc_get(acc));
+    if (lane == 0) red[g][wid] = num<T>::to_d(s);
+  }
+  __syncthreads();
+  if (threadIdx.x < ncol) {
+    double s = 0.0;
+    for (int q = 0; q < TPB / 32; ++q) s += red[threadIdx.x][q];
+    partials[(int64_t)blockIdx.x * J + c0 + threadIdx.x] = s;
   }
 }
 
+// w -= V h (h: J FP64 values on the device); optional ||w||^2 partials
 template <typename T>
-__global__ void __launch_bounds__(256) k_multi_update(const T *__restrict__ V, int64_t ldv, int J,
+__global__ void __launch_bounds__(TPB) k_multi_update(const T *__restrict__ V, int64_t ldv, int J,
                                                       const double *__restrict__ h, T *__restrict__ w,
                                                       int64_t n, double *__restrict__ partials) {
+  using A = typename acc_of<T>::type;
   extern __shared__ unsigned char smem_raw[];
   T *hs = reinterpret_cast<T *>(smem_raw);
-  __shared__ double red[32];
-  for (int c = threadIdx.x; c < J; c += blockDim.x) hs[c] = num<T>::from_d(-h[c]);
+  __shared__ double red[TPB / 32];
+  for (int c = threadIdx.x; c < J; c += TPB) hs[c] = num<T>::from_d(-h[c]);
   __syncthreads();
-  T nrm = num<T>::zero();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T r = w[i];
-    for (int c = 0; c < J; ++c) r = r + V[(int64_t)c * ldv + i] * hs[c];
-    w[i] = r;
-    nrm = nrm + r * r;
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  A acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB;
+    acc_set(acc[u], (r < n) ? w[r] : num<T>::zero());
+  }
+  for (int c = 0; c < J; ++c) {
+    const T *col = V + (int64_t)c * ldv;
+    const T hc = hs[c];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = base + (int64_t)u * TPB;
+      if (r < n) acc_add_prod(acc[u], hc, ldg(col + r));
+    }
+  }
+  A nrm;
+  acc_set(nrm, num<T>::zero());
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB;
+    if (r < n) {
+      const T wr = acc_get(acc[u]);
+      w[r] = wr;
+      acc_add_prod(nrm, wr, wr);
+    }
   }
   if (partials) {
-    const double s = block_sum(num<T>::to_d(nrm), red);
+    const double s = block_reduce_to_d(acc_get(nrm), red);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
   }
 }
 
+// x = V z, FP64 output
 template <typename T>
-__global__ void __launch_bounds__(256) k_reconstruct(const T *__restrict__ V, int64_t ldv, int m,
+__global__ void __launch_bounds__(TPB) k_reconstruct(const T *__restrict__ V, int64_t ldv, int m,
                                                      const double *__restrict__ z, double *__restrict__ x,
                                                      int64_t n) {
+  using A = typename acc_of<T>::type;
   extern __shared__ unsigned char smem_raw[];
   T *zs = reinterpret_cast<T *>(smem_raw);
-  for (int c = threadIdx.x; c < m; c += blockDim.x) zs[c] = num<T>::from_d(z[c]);
+  for (int c = threadIdx.x; c < m; c += TPB) zs[c] = num<T>::from_d(z[c]);
   __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    T r = num<T>::zero();
-    for (int c = 0; c < m; ++c) r = r + V[(int64_t)c * ldv + i] * zs[c];
-    x[i] = num<T>::to_d(r);
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  A acc[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) acc_set(acc[u], num<T>::zero());
+  for (int c = 0; c < m; ++c) {
+    const T *col = V + (int64_t)c * ldv;
+    const T zc = zs[c];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int64_t r = base + (int64_t)u * TPB;
+      if (r < n) acc_add_prod(acc[u], zc, ldg(col + r));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB;
+    if (r < n) x[r] = num<T>::to_d(acc_get(acc[u]));
   }
 }
 
@@ -203,7 +285,11 @@ inline int grid_for(int64_t n, int bs, int max_blocks) {
 
 constexpr int kMaxGrid = 152 * 8;
 
+inline unsigned nchunks(int64_t n) { return (unsigned)((n + CHUNK - 1) / CHUNK); }
+
 }  // namespace
+
+int vec_nchunks(int64_t n) { return (int)nchunks(n); }
 
 template <typename T>
 int vec_from_f64(const double *in, T *out, int64_t n, cudaStream_t s) {
@@ -234,34 +320,35 @@ int vec_copy(const T *in, T *out, int64_t n, cudaStream_t s) {
   return PP_OK;
 }
 template <typename T>
-int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int nb, cudaStream_t s) {
-  k_dot<T><<<nb, 256, 0, s>>>(x, y, n, partials);
+int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int, cudaStream_t s) {
+  k_dot<T><<<nchunks(n), TPB, 0, s>>>(x, y, n, partials);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_lanczos_update(T *w, const T *vj, const T *vjm1, int64_t n, const double *alpha,
-                       const double *beta_prev, double *partials, int nb, cudaStream_t s) {
-  k_lanczos_update<T><<<nb, 256, 0, s>>>(w, vj, vjm1, n, alpha, beta_prev, partials);
+                       const double *beta_prev, double *partials, int, cudaStream_t s) {
+  k_lanczos_update<T><<<nchunks(n), TPB, 0, s>>>(w, vj, vjm1, n, alpha, beta_prev, partials);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
-int vec_multi_dot(const T *V, int64_t ldv, int J, const T *w, int64_t n, double *partials, int nb,
+int vec_multi_dot(const T *V, int64_t ldv, int J, const T *w, int64_t n, double *partials, int,
                   cudaStream_t s) {
-  k_multi_dot<T><<<nb, 256, 0, s>>>(V, ldv, J, w, n, partials);
+  dim3 grd(nchunks(n), (unsigned)((J + CG - 1) / CG));
+  k_multi_dot<T><<<grd, TPB, 0, s>>>(V, ldv, J, w, n, partials);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_multi_update(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n,
-                     double *partials, int nb, cudaStream_t s) {
+                     double *partials, int, cudaStream_t s) {
   const size_t sm = (size_t)J * sizeof(T);
   if (sm > 48 * 1024) PP_CUDA_TRY(cudaFuncSetAttribute(k_multi_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_multi_update<T><<<nb, 256, sm, s>>>(V, ldv, J, h, w, n, partials);
+  k_multi_update<T><<<nchunks(n), TPB, sm, s>>>(V, ldv, J, h, w, n, partials);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -271,7 +358,7 @@ int vec_reconstruct(const T *V, int64_t ldv, int m, const double *z, double *x, 
                     cudaStream_t s) {
   const size_t sm = (size_t)m * sizeof(T);
   if (sm > 48 * 1024) PP_CUDA_TRY(cudaFuncSetAttribute(k_reconstruct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_reconstruct<T><<<grid_for(n, 256, kMaxGrid), 256, sm, s>>>(V, ldv, m, z, x, n);
+  k_reconstruct<T><<<nchunks(n), TPB, sm, s>>>(V, ldv, m, z, x, n);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
