@@ -198,6 +198,40 @@ int pp_op_apply(pp_handle h, const void *x_d, void *y_d);
 int pp_poly_apply(pp_handle h, const void *x_d, void *y_d);
 
 /*
+ * y_d = q(A) x_d, the same computation as pp_poly_apply, for callers that
+ * must not allocate device memory.  (The paper has no counterpart: this is a
+ * deployment variant.)  Who needs it: a process whose device memory is all
+ * owned by an arena or caching allocator (a framework that has reserved the
+ * GPU, so a cudaMalloc from this library would fail or fragment it), and
+ * latency-critical loops that forbid cudaMalloc/cudaFree after start-up
+ * because those calls can block and synchronise the device.
+ *
+ * pp_poly_apply takes its three Clenshaw buffers (five in PP_PREC_DW, which
+ * also converts x and y) from the handle's workspace, allocated on first use.
+ * This variant takes them from one fixed array compiled into the library:
+ * 5 * PP_STATIC_MAX_N entries of 8 bytes (10 MiB), which every GPU that
+ * loads the library holds until the process exits.  It calls no cudaMalloc
+ * or cudaFree and no allocating library routine.
+ *
+ * Arguments as pp_poly_apply: x_d, y_d are caller-owned device vectors of n
+ * FP64 entries; y_d must not alias x_d.  Work is queued on the handle's
+ * stream; the call returns after queueing it.
+ * Limits and errors: PP_ERR_INVALID_ARG if n > PP_STATIC_MAX_N or for bad
+ * pointers; PP_ERR_STATE before pp_build_poly; PP_ERR_UNSUPPORTED for CSR
+ * handles in PP_PREC_DW (their converted values would need an allocation).
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current).  Make that first call
+ * before any stream capture.
+ * Sharing: all calls in the process use the same array.  Every scratch entry
+ * a call reads was written earlier in the same call, so nothing left by a
+ * previous call affects the result; but calls whose work overlaps on the GPU
+ * (other streams, other handles, other host threads) race on the array and
+ * must be serialised by the caller.
+ */
+#define PP_STATIC_MAX_N 262144
+int pp_poly_apply_static(pp_handle h, const void *x_d, void *y_d);
+
+/*
  * Read back the quadrature rule of the small projected solve: H^{-1/2} e_1 =
  * sum_k wt_h[k] (H + sig_h[k] I)^{-1} e_1, the trapezoid rule in u = log t for
  * z^{-1/2} = (2/pi) int_0^inf (t^2 + z)^{-1} dt (an integral representation

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -499,6 +500,56 @@ int poly_apply_api_t(pp_ctx *c, const double *x, double *y) {
   return vec_to_f64<T>(t[1], y, c->n, c->stream);
 }
 
+// ---- q(A) x without device allocation (pp_poly_apply_static) ----
+//
+// Scratch for pp_poly_apply_static: five vectors of PP_STATIC_MAX_N entries
+// of 8 bytes (10 MiB), resident on every device that loads the library until
+// the process exits.  Host code may not use the symbol as an address: the
+// device address is looked up once per device with cudaGetSymbolAddress.
+constexpr int kStaticVecs = 5;
+constexpr int kStaticMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) double pp_static_scratch[kStaticVecs * (size_t)PP_STATIC_MAX_N];
+
+namespace {
+
+std::mutex g_static_mu;
+void *g_static_addr[kStaticMaxDevices] = {};
+
+// Device address of pp_static_scratch on the current device (looked up on the
+// first call per device).
+int static_scratch_addr(void **out) {
+  int dev = 0;
+  PP_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return pp_set_error(PP_ERR_UNSUPPORTED, "device ordinal >= 64");
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *p = nullptr;
+    PP_CUDA_TRY(cudaGetSymbolAddress(&p, pp_static_scratch));
+    if (!p) return pp_set_error(PP_ERR_CUDA, "cudaGetSymbolAddress returned NULL");
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return PP_OK;
+}
+
+template <typename T>
+int poly_apply_static_t(pp_ctx *c, const double *x, double *y, void *base) {
+  const OpDesc op = make_op(c, c->opts.precision);
+  T *t[kStaticVecs];
+  for (int i = 0; i < kStaticVecs; ++i) t[i] = (T *)base + (size_t)i * PP_STATIC_MAX_N;
+  if (std::is_same<T, double>::value) {
+    T *pb[3] = {t[0], t[1], t[2]};
+    return poly_apply_raw<T>(c, op, (const T *)x, (T *)y, pb);
+  }
+  T *pb[3] = {t[2], t[3], t[4]};
+  RC(vec_from_f64<T>(x, t[0], c->n, c->stream));
+  RC(poly_apply_raw<T>(c, op, t[0], t[1], pb));
+  return vec_to_f64<T>(t[1], y, c->n, c->stream);
+}
+
 pp_ctx *new_ctx(void *stream) {
   pp_ctx *c = new pp_ctx();
   pp_default_opts(&c->opts);
@@ -742,6 +793,26 @@ int pp_poly_apply(pp_handle c, const void *x_d, void *y_d) {
   }
   if (c->opts.precision == PP_PREC_DW) return poly_apply_api_t<dw>(c, (const double *)x_d, (double *)y_d);
   return poly_apply_api_t<double>(c, (const double *)x_d, (double *)y_d);
+}
+
+int pp_poly_apply_static(pp_handle c, const void *x_d, void *y_d) {
+  RC(check_ready(c));
+  if (!x_d || !y_d || x_d == y_d) return pp_set_error(PP_ERR_INVALID_ARG, "bad arguments");
+  if (c->n > PP_STATIC_MAX_N)
+    return pp_set_error(PP_ERR_INVALID_ARG, "n = " + std::to_string(c->n) +
+                                                " exceeds PP_STATIC_MAX_N = " + std::to_string((long long)PP_STATIC_MAX_N));
+  if (c->op_kind == OPK_CSR && c->opts.precision == PP_PREC_DW)
+    return pp_set_error(PP_ERR_UNSUPPORTED,
+                        "CSR handles in PP_PREC_DW need a converted copy of the values; use PP_PREC_F64");
+  if (c->op_kind == OPK_CSR && c->nnz < 0) {
+    int64_t nnz = 0;
+    PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    c->nnz = nnz;
+  }
+  void *base = nullptr;
+  RC(static_scratch_addr(&base));
+  if (c->opts.precision == PP_PREC_DW) return poly_apply_static_t<dw>(c, (const double *)x_d, (double *)y_d, base);
+  return poly_apply_static_t<double>(c, (const double *)x_d, (double *)y_d, base);
 }
 
 void pp_destroy(pp_handle c) {

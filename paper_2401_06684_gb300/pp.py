@@ -79,6 +79,7 @@ SYMBOLS = {
                                      ctypes.c_double, _p, ctypes.POINTER(pp_stats)]),
     "pp_op_apply": (ctypes.c_int, [_h, _p, _p]),
     "pp_poly_apply": (ctypes.c_int, [_h, _p, _p]),
+    "pp_poly_apply_static": (ctypes.c_int, [_h, _p, _p]),
     "pp_destroy": (None, [_h]),
     "pp_strerror": (ctypes.c_char_p, [ctypes.c_int32]),
     "pp_last_error": (ctypes.c_char_p, []),
@@ -219,6 +220,13 @@ def pp_op_apply(h, x, y):
 
 def pp_poly_apply(h, x, y):
     _check(lib().pp_poly_apply(h, _ptr(x), _ptr(y)))
+
+
+def pp_poly_apply_static(h, x, y):
+    _check(lib().pp_poly_apply_static(h, _ptr(x), _ptr(y)))
+
+
+PP_STATIC_MAX_N = 262144
 
 
 def pp_destroy(h):
