@@ -71,3 +71,47 @@ def stencil_csr(kind, dims, ch=0.0):
     np.add.at(rowptr, rows + 1, 1)
     rowptr = np.cumsum(rowptr)
     return rowptr, cols.astype(np.int32), vals.astype(np.float64)
+
+
+# ---- lattice gauge fields (Wilson operator inputs) ------------------------
+
+def haar_su3(count, rng):
+    """`count` Haar-distributed SU(3) matrices, complex128, shape (count, 3, 3).
+
+    Mezzadri's method ("How to generate random matrices from the classical
+    compact groups", Notices AMS 54, 2007): QR of a complex Ginibre matrix
+    with the phases of R's diagonal moved into Q gives Haar U(3); dividing by
+    a cube root of the determinant keeps left invariance and lands in SU(3).
+    """
+    Z = (rng.standard_normal((count, 3, 3)) + 1j * rng.standard_normal((count, 3, 3))) / np.sqrt(2.0)
+    Q, R = np.linalg.qr(Z)
+    d = np.diagonal(R, axis1=1, axis2=2)
+    Q = Q * (d / np.abs(d))[:, None, :]
+    det = np.linalg.det(Q)
+    return Q * np.exp(-1j * np.angle(det) / 3.0)[:, None, None]
+
+
+def wilson_links(dims, seed=1):
+    """Gauge links U_mu(x) for a periodic 4D lattice, dims = (Lx, Ly, Lz, Lt).
+
+    complex64 array of shape (V, 4, 3, 3), V = Lx Ly Lz Lt, site index
+    s = ((t Lz + z) Ly + y) Lx + x, entry [s, mu, a, b] = U_mu(s)_{ab};
+    Haar SU(3) matrices rounded to complex64 (both sides use the rounded
+    values, so the operator is exactly the same on both).
+    """
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(seed)
+    return haar_su3(4 * V, rng).reshape(V, 4, 3, 3).astype(np.complex64)
+
+
+def unit_links(dims):
+    """The free field U_mu(x) = 1 (complex64, layout of wilson_links)."""
+    V = int(np.prod(dims))
+    return np.broadcast_to(np.eye(3, dtype=np.complex64), (V, 4, 3, 3)).copy()
+
+
+def spinor_field(dims, seed=0):
+    """Random complex right-hand side b ~ N(0,1) + i N(0,1), 12 complex per site, complex128 (12 V,)."""
+    V = int(np.prod(dims))
+    rng = np.random.default_rng(seed)
+    return rng.standard_normal(12 * V) + 1j * rng.standard_normal(12 * V)
