@@ -72,7 +72,9 @@ typedef enum {
   PP_CONVDIFF3D7_UPWIND = 2, /* 7-point upwind -Lap u + c.grad u, c = (c,c,c)>0,
                                 params[0] = c*h; row: (6+3ch) u_c - (1+ch) (u at
                                 i-1, j-1, k-1) - (u at i+1, j+1, k+1)             */
-  PP_WILSON4D_DHD = 3        /* not in this build                                 */
+  PP_WILSON4D_DHD = 3        /* A = D^H D of a Wilson-type operator on a periodic
+                                4D lattice, dims = {L0, L1, L2, L3} (see
+                                pp_create_stencil)                                */
 } pp_stencil_kind;
 
 typedef enum { PP_LEFT = 0, PP_RIGHT = 1 } pp_side;
@@ -82,7 +84,17 @@ typedef enum {
   PP_PREC_DW = 1,    /* vectors, chain and basis as double-word FP32 pairs
                         (hi + lo, ~48-bit significand, 8 bytes per real): FP64-
                         grade accuracy on the FP32 pipes                          */
-  PP_PREC_MIXED = 2  /* not in this build                                         */
+  PP_PREC_MIXED = 2  /* double-word for the start vector, the leading basis vectors
+                        and the result; FP32 chain, FP32 basis and FP32 vector
+                        updates from the first stopping check at which
+                        est * rho/(1-rho) * 4 u_32 * kappa_pre <= tol, where
+                        est = the stopping estimate, rho = its observed
+                        per-step decay, u_32 = 2^-24 and kappa_pre = the
+                        ratio of the ends of the image of z q(z)^2 (FP32
+                        rounding is amplified by about kappa_pre).  H_m, its
+                        coefficients and the small solve stay FP64.  Single
+                        applications (pp_op_apply, pp_poly_apply) run in FP32
+                        under this setting.                                  */
 } pp_precision;
 
 typedef enum {
@@ -117,7 +129,10 @@ typedef struct pp_stats {
   double chain_bytes;     /* their algorithmic HBM bytes: vectors read + written,
                              plus the CSR arrays for CSR handles                    */
   double chain_ms;        /* their summed device time (opts.profile = 1, else 0)    */
-  double reserved[3];
+  int32_t switch_iter;    /* PP_PREC_MIXED: Krylov dimension at which the loop
+                             moved to FP32 (-1: never); 0 for the other settings */
+  int32_t reserved_i;
+  double reserved[2];
 } pp_stats;
 
 /* Defaults for pp_opts (all fields). */
@@ -140,7 +155,22 @@ int pp_create_csr(pp_handle *h, int64_t n, const int64_t *rowptr_d, const int32_
  * with Dirichlet boundary (Sec. 6, Example 1 uses the 3D Laplacian; Sec. 3.2
  * the 2D one).  dims[4] = grid points per direction (unused entries ignored);
  * params: PP_CONVDIFF3D7_UPWIND reads params[0] = c*h > 0, the others none
- * (NULL allowed).  links_d is reserved (NULL).  dtype must be PP_F64.
+ * (NULL allowed).  links_d must be NULL and dtype PP_F64 for these kinds.
+ *
+ * PP_WILSON4D_DHD (a stand-in for the lattice QCD kernel of Sec. 6,
+ * Example 2, whose configuration is not available): A = D^H D with
+ *   (D psi)(x) = (4 + m0) psi(x) - 1/2 sum_mu [ (1 - gamma_mu) U_mu(x) psi(x + mu)
+ *                                  + (1 + gamma_mu) U_mu(x - mu)^H psi(x - mu) ]
+ * on a periodic L0 x L1 x L2 x L3 lattice, dims = {L0, L1, L2, L3}, site
+ * s = ((x3 L2 + x2) L1 + x1) L0 + x0, gamma matrices of the Euclidean chiral
+ * representation (gamma_k = [[0, -i sigma_k], [i sigma_k, 0]], gamma_4 =
+ * [[0, 1], [1, 0]]), params[0] = m0.  links_d: device array of 4 V 3 x 3
+ * complex64 matrices (interleaved float re/im), U_mu(s)_{ab} at index
+ * ((s * 4 + mu) * 3 + a) * 3 + b, referenced for the handle's lifetime.
+ * dtype must be PP_C128: b and x are 12 V complex128 entries, 12 per site in
+ * the order spin * 3 + colour.  A is Hermitian positive definite, so
+ * PP_ORTH_AUTO runs Lanczos; the vector work runs on the real view (24 V
+ * reals), which is exact for real recurrence coefficients.
  */
 int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const double *params,
                       const void *links_d, int32_t dtype, void *cuda_stream);
@@ -152,13 +182,35 @@ int pp_set_opts(pp_handle h, const pp_opts *opts);
  * Build q with deg q = degree (paper: d = degree + 1 nodes) of the given kind
  * on [a,b] = interval_ab_h[0..1] (host array), the interval enclosing
  * spec(A) (Sec. 5.1).  interval_ab_h = NULL: the exact spectral interval of
- * the stencil (Sec. 6, Example 1 formula and its convection-diffusion
- * analogue); CSR handles need an interval.  degree = 0 gives constant q, i.e.
- * plain Arnoldi/Lanczos.  The positivity of q on [a,b] is checked on a dense
- * grid (Sec. 5.1, last paragraph); PP_ERR_NONPRIMARY if it fails.  Host
- * work only, plus a small upload.  0 <= degree <= 128.
+ * the Laplacian and convection-diffusion stencils (Sec. 6, Example 1 formula
+ * and its convection-diffusion analogue); for the other Hermitian handles
+ * (Wilson, Hermitian CSR) the extreme Ritz values of 200 Lanczos steps from a
+ * fixed pseudo-random start, with a lowered by 5 % and b raised by 1 %
+ * (device work on the handle's stream; the call synchronises it).
+ * Non-Hermitian CSR handles need an interval.  degree = 0 gives constant q,
+ * i.e. plain Arnoldi/Lanczos.  The positivity of q on [a,b] is checked on a
+ * dense grid (Sec. 5.1, last paragraph); PP_ERR_NONPRIMARY if it fails.
+ * 0 <= degree <= 128.
  */
 int pp_build_poly(pp_handle h, int32_t degree, int32_t kind, const double *interval_ab_h);
+
+/*
+ * Autotuner (no counterpart in the paper, which fixes the degree per
+ * experiment): choose deg q for a target tolerance and build q as
+ * pp_build_poly would (interval from an earlier pp_build_poly, else the
+ * closed form or the Lanczos estimate).  For every candidate degree up to
+ * max_degree the image interval [lo, hi] of z q(z)^2 (Prop. 3.2) gives the
+ * Chebyshev bound 2 ((sqrt(k)-1)/(sqrt(k)+1))^m, k = hi/lo, for the number of
+ * steps m; the predicted time is m steps of (2 deg + 1) operator passes plus
+ * the orthogonalization (Lanczos: constant; CGS2: growing with m), in vector
+ * passes at 6 TB/s, plus 3 us per kernel launch and 40 us per stopping check,
+ * and the fastest degree is taken (*degree_out).
+ * For stencil handles in PP_PREC_DW / PP_PREC_MIXED it then times the
+ * operator kernel with block x-sizes 16, 32, 64, 128 on the handle's stream
+ * (CUDA events, synchronising) and keeps the fastest for later calls.
+ * Errors: as pp_build_poly; PP_ERR_INVALID_ARG for tol outside (0, 1).
+ */
+int pp_autotune(pp_handle h, double tol, int32_t max_degree, int32_t *degree_out);
 
 /*
  * Read back the polynomial: coeffs_h[0..*ncoeffs-1] (Chebyshev coefficients
@@ -172,8 +224,10 @@ int pp_get_poly(pp_handle h, double *coeffs_h, int32_t cap, int32_t *ncoeffs, do
 /*
  * x = f(A) b (Algorithm 1 or 2 by opts.side; Sec. 4 for PP_SQRT), iterating
  * until the stopping estimate is below tol or m = m_max.  b_d, x_d: device
- * vectors of n (nrhs = 1 in this build) entries of the handle's vector dtype;
- * x_d must not alias b_d.  On PP_ERR_NOT_CONVERGED x_d still holds the last
+ * vectors of n entries of the handle's vector dtype (nrhs > 1: n x nrhs,
+ * column-major, solved as independent processes in lockstep through
+ * pp_apply_batch; stencil handles only, m_max <= 1024); x_d must not alias
+ * b_d.  On PP_ERR_NOT_CONVERGED x_d still holds the last
  * iterate.  stats (host, may be NULL) is filled on return.  Blocks the
  * calling thread at each stopping check (a few bytes read back).
  * Errors: PP_ERR_STATE before pp_build_poly, PP_ERR_INVALID_ARG for NULL or
@@ -189,6 +243,31 @@ int pp_apply(pp_handle h, int32_t f, const void *b_d, int64_t nrhs, int32_t m_ma
  */
 int pp_apply_host(pp_handle h, int32_t f, const double *b_h, int64_t nrhs, int32_t m_max,
                   double tol, double *x_h, pp_stats *stats);
+
+/*
+ * Batched solves: x_i = f_i(A_i) b_i for `count` handles at once, every
+ * handle with nrhs[i] right-hand sides (b_d[i]: n_i x nrhs[i] FP64, column-
+ * major, device; x_d[i] likewise), each right-hand side an independent
+ * Krylov process (Algorithm 1 or 2 as in pp_apply).  All processes advance in
+ * lockstep: every kernel launch covers the whole batch, so a batch costs the
+ * launches of one solve; a process that meets its stopping estimate is masked
+ * out of later launches.  Handles are grouped by polynomial degree and
+ * orthogonalization; groups run concurrently on internal streams that are
+ * ordered after the work queued on cuda_stream, which waits for them before
+ * the call returns (the call blocks until done).  Every handle must be a 2D
+ * or 3D stencil (PP_ERR_UNSUPPORTED otherwise), have called pp_build_poly,
+ * and share the precision and side options of handles[0]
+ * (PP_ERR_INVALID_ARG otherwise).  With PP_PREC_MIXED a group moves to FP32
+ * when the switching rule holds for all of its unconverged processes.
+ * stats (host, count entries, may be NULL): per handle, iters = the largest
+ * Krylov dimension over its right-hand sides, mvms / inner_products summed
+ * over them, est_err the largest estimate, ms_total and launches of the
+ * whole batch.  Returns PP_ERR_NOT_CONVERGED if any process reached m_max
+ * (1 <= m_max <= 1024).
+ */
+int pp_apply_batch(const pp_handle *handles, int32_t count, const int32_t *f, const void *const *b_d,
+                   const int64_t *nrhs, void *const *x_d, int32_t m_max, double tol, void *cuda_stream,
+                   pp_stats *stats);
 
 /* y_d = A x_d (one operator application in the handle's precision). */
 int pp_op_apply(pp_handle h, const void *x_d, void *y_d);
@@ -218,7 +297,8 @@ int pp_poly_apply(pp_handle h, const void *x_d, void *y_d);
  * stream; the call returns after queueing it.
  * Limits and errors: PP_ERR_INVALID_ARG if n > PP_STATIC_MAX_N or for bad
  * pointers; PP_ERR_STATE before pp_build_poly; PP_ERR_UNSUPPORTED for CSR
- * handles in PP_PREC_DW (their converted values would need an allocation).
+ * handles in PP_PREC_DW or PP_PREC_MIXED (their converted values would need
+ * an allocation) and for Wilson handles (they need a sixth vector).
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current).  Make that first call
  * before any stream capture.

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "ctx.h"
 #include "internal.h"
 
 size_t small_hess_scratch_doubles(int m, int K);
@@ -46,58 +47,7 @@ namespace {
 constexpr int kMaxDegree = 128;
 constexpr int kMaxM = 4096;
 constexpr double kBreakdownRel = 1e-12;
-
-struct Workspace {
-  int prec = -1;
-  int m_cap = 0;
-  bool has_y = false;
-  int64_t ldv = 0;
-  size_t esz = 0;
-  void *V = nullptr;
-  void *Y = nullptr;
-  void *tmp = nullptr;  // 6 vectors
-  double *dmem = nullptr;
-  size_t dmem_n = 0;
-  double *hess = nullptr;
-  size_t hess_n = 0;
-  DevStatus *st = nullptr;
-  DevStatus *st_host = nullptr;
-  double *io = nullptr;  // 2 n doubles for pp_apply_host
-  void *val_dw = nullptr;
-  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
-
-}  // namespace
-
-struct pp_ctx {
-  int op_kind = OPK_CSR;
-  int stencil = -1;
-  int64_t n = 0;
-  int64_t dims[4] = {0, 0, 0, 0};
-  double st_d = 0, st_cm = 0, st_cp = 0, ch = 0;
-  const int64_t *rowptr = nullptr;
-  const int32_t *col = nullptr;
-  const double *val = nullptr;
-  int64_t nnz = 0;
-  int hermitian = 0;
-  cudaStream_t stream = nullptr;
-  pp_opts opts;
-  bool have_poly = false;
-  int degree = 0;
-  std::vector<double> coef;
-  double a = 0, b = 0, img_lo = 0, img_hi = 0;
-  std::vector<double> qsig, qwt;
-  bool quad_uploaded = false;
-  Workspace ws;
-  // operator-launch accounting of the current call (pp_stats.chain_*)
-  int64_t chain_launches = 0;
-  double chain_bytes = 0.0;
-  std::vector<cudaEvent_t> prof_ev;  // start/stop pairs, grown on demand
-  size_t prof_used = 0;
-};
-
-namespace {
-
+constexpr int kIntervalSteps = 200;
 
 void ws_free(Workspace &w) {
   if (w.V) cudaFree(w.V);
@@ -109,6 +59,9 @@ void ws_free(Workspace &w) {
   if (w.st_host) cudaFreeHost(w.st_host);
   if (w.io) cudaFree(w.io);
   if (w.val_dw) cudaFree(w.val_dw);
+  if (w.val_f) cudaFree(w.val_f);
+  if (w.Vf) cudaFree(w.Vf);
+  if (w.Yf) cudaFree(w.Yf);
   if (w.ev0) cudaEventDestroy(w.ev0);
   if (w.ev1) cudaEventDestroy(w.ev1);
   w = Workspace();
@@ -144,9 +97,16 @@ int run_op(pp_ctx *c, const OpDesc &op, const T *x, const T *y, const T *v, T *o
   int rc = op_step<T>(op, x, y, v, out, k, c->stream);
   if (rc) return rc;
   c->chain_launches += 1;
+  const double esz = (double)sizeof(T);
   double vecs = 2.0 + (k.sub_y ? 1.0 : 0.0) + (k.add_v ? 1.0 : 0.0);
-  double bytes = vecs * 8.0 * (double)c->n;
-  if (c->op_kind == OPK_CSR) bytes += 12.0 * (double)c->nnz + 8.0 * (double)(c->n + 1);
+  double bytes = vecs * esz * (double)c->n;
+  if (c->op_kind == OPK_CSR) bytes += (esz + 4.0) * (double)c->nnz + 8.0 * (double)(c->n + 1);
+  if (c->op_kind == OPK_WILSON) {
+    // t = D x (read x, write t) and out = alpha D^H t + beta x ...: the second
+    // launch reads t and x; both read the links (288 bytes per site)
+    const double sites = (double)c->n / 24.0;
+    bytes += (2.0 + (k.beta != 0.0 ? 1.0 : 0.0)) * esz * (double)c->n + 2.0 * 288.0 * sites;
+  }
   c->chain_bytes += bytes;
   return PP_OK;
 }
@@ -213,6 +173,8 @@ int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y) {
     if (w.Y) cudaFree(w.Y), w.Y = nullptr;
     if (w.tmp) cudaFree(w.tmp), w.tmp = nullptr;
     if (w.dmem) cudaFree(w.dmem), w.dmem = nullptr;
+    if (w.Vf) cudaFree(w.Vf), w.Vf = nullptr;
+    if (w.Yf) cudaFree(w.Yf), w.Yf = nullptr;
     const int mc = m_cap > w.m_cap ? m_cap : w.m_cap;
     w.ldv = (c->n + 31) / 32 * 32;
     w.esz = esz;
@@ -221,7 +183,11 @@ int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y) {
       PP_CUDA_TRY(cudaMalloc(&w.Y, (size_t)mc * w.ldv * esz));
       w.has_y = true;
     }
-    PP_CUDA_TRY(cudaMalloc(&w.tmp, (size_t)6 * w.ldv * esz));
+    PP_CUDA_TRY(cudaMalloc(&w.tmp, (size_t)kTmpVecs * w.ldv * esz));
+    if (prec == PP_PREC_MIXED) {
+      PP_CUDA_TRY(cudaMalloc(&w.Vf, (size_t)(mc + 1) * w.ldv * sizeof(float)));
+      if (w.has_y) PP_CUDA_TRY(cudaMalloc(&w.Yf, (size_t)mc * w.ldv * sizeof(float)));
+    }
     DLayout L = dlayout(c, mc);
     PP_CUDA_TRY(cudaMalloc(&w.dmem, L.total * sizeof(double)));
     w.dmem_n = L.total;
@@ -241,15 +207,28 @@ int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y) {
     PP_CUDA_TRY(cudaMemcpyAsync(w.dmem + L.wt, c->qwt.data(), L.K * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     c->quad_uploaded = true;
   }
-  if (prec == PP_PREC_DW && c->op_kind == OPK_CSR && !w.val_dw) {
+  if ((prec == PP_PREC_DW || prec == PP_PREC_MIXED) && c->op_kind == OPK_CSR && !w.val_dw) {
     PP_CUDA_TRY(cudaMalloc(&w.val_dw, (size_t)c->nnz * sizeof(dw)));
     int rc = vec_from_f64<dw>(c->val, (dw *)w.val_dw, c->nnz, c->stream);
+    if (rc) return rc;
+  }
+  if (prec == PP_PREC_MIXED && c->op_kind == OPK_CSR && !w.val_f) {
+    PP_CUDA_TRY(cudaMalloc(&w.val_f, (size_t)c->nnz * sizeof(float)));
+    int rc = vec_from_f64<float>(c->val, (float *)w.val_f, c->nnz, c->stream);
     if (rc) return rc;
   }
   return PP_OK;
 }
 
-OpDesc make_op(const pp_ctx *c, int prec) {
+// Arithmetic of the vectors: IEEE FP64, double-word pairs, or FP32.
+enum Arith { AR_F64 = 0, AR_DW = 1, AR_F32 = 2 };
+
+template <typename T>
+constexpr int arith_of() {
+  return std::is_same<T, double>::value ? AR_F64 : (std::is_same<T, dw>::value ? AR_DW : AR_F32);
+}
+
+OpDesc make_op(const pp_ctx *c, int arith) {
   OpDesc op;
   op.kind = c->op_kind;
   op.n = c->n;
@@ -261,7 +240,13 @@ OpDesc make_op(const pp_ctx *c, int prec) {
   op.cp = c->st_cp;
   op.rowptr = c->rowptr;
   op.col = c->col;
-  op.val = (prec == PP_PREC_DW) ? c->ws.val_dw : (const void *)c->val;
+  op.val = arith == AR_DW ? c->ws.val_dw : (arith == AR_F32 ? c->ws.val_f : (const void *)c->val);
+  for (int d = 0; d < 4; ++d) op.L[d] = c->dims[d];
+  op.mass = c->mass;
+  op.links = c->links;
+  const size_t esz = arith == AR_F32 ? sizeof(float) : sizeof(double);
+  op.tmp = c->ws.tmp ? (void *)((char *)c->ws.tmp + (size_t)(kTmpVecs - 1) * c->ws.ldv * esz) : nullptr;
+  op.tile_bdx = c->tile_bdx;
   return op;
 }
 
@@ -303,27 +288,131 @@ int poly_apply_t(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3]) {
   return prof_end(c);
 }
 
+// FP32 unit roundoff and the safety factor of the precision switch.
+constexpr double kU32 = 0x1p-24;
+constexpr double kMixedSafety = 4.0;
+// Breakdown threshold of FP32 steps: |h_{j+1,j}| at the level of FP32
+// rounding of the column means the direction is noise.
+constexpr double kBreakdownRelF32 = 4.0 * 0x1p-24;
+
+// State of one pp_apply call shared by the steps of the Krylov loop.
+struct Solve {
+  pp_ctx *c;
+  cudaStream_t s;
+  int64_t n, ldv;
+  double *H, *h1, *part, *X, *tri, *z, *zprev, *sig, *wt, *scal;
+  int ldh, nb, K;
+  bool right, lanczos;
+  int deg;
+  int64_t mvms, ip;
+};
+
+// Krylov step j in arithmetic T (Algorithm 1 or 2, one pass of the loop):
+// w = A q(A)^2 v_j applied in three stages, orthogonalization against the
+// stored basis (columns of V in arithmetic T), h_{j+1,j} = ||w|| and
+// v_{j+1} = w / h_{j+1,j} in column j+1 of V.
 template <typename T>
+int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double bd_rel) {
+  pp_ctx *c = S.c;
+  cudaStream_t s = S.s;
+  const int64_t n = S.n, ldv = S.ldv;
+  T *pb[3] = {t[2], t[3], t[4]};
+  T *vj = V + (size_t)j * ldv;
+  T *wv = V + (size_t)(j + 1) * ldv;
+  if (!S.right) {  // Algorithm 1: u = A v_j, y = q(A) u, w = q(A) y
+    RC(run_op_timed<T>(c, op, vj, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
+    RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
+    RC(poly_apply_t<T>(c, op, t[1], wv, pb));
+  } else {         // Algorithm 2: y_j = q(A) v_j, u = q(A) y_j, w = A u
+    T *yj = Y + (size_t)j * ldv;
+    RC(poly_apply_t<T>(c, op, vj, yj, pb));
+    RC(poly_apply_t<T>(c, op, yj, t[0], pb));
+    RC(run_op_timed<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
+  }
+  S.mvms += 2 * S.deg + 1;
+  double *hcol = S.H + (size_t)j * S.ldh;
+  const int nb = S.nb;
+  if (S.lanczos) {
+    RC(vec_dot_partials<T>(wv, vj, n, S.part, nb, s));
+    RC(reduce_cols(S.part, nb, 1, 0, hcol + j, nullptr, s));
+    RC(vec_lanczos_update<T>(wv, vj, j > 0 ? V + (size_t)(j - 1) * ldv : nullptr, n, hcol + j,
+                             j > 0 ? S.H + (size_t)(j - 1) * S.ldh + j : nullptr, S.part, nb, s));
+    RC(norm_finalize(S.part, nb, hcol + j + 1, S.scal, hcol + j, 1, bd_rel, j + 1, c->ws.st, s));
+    S.ip += 2;
+  } else {  // CGS2: h = V^* w, w -= V h, twice
+    const int J = j + 1;
+    RC(vec_multi_dot<T>(V, ldv, J, wv, n, S.part, nb, s));
+    RC(reduce_cols(S.part, nb, J, 1, S.h1, hcol, s));
+    RC(vec_multi_update<T>(V, ldv, J, S.h1, wv, n, nullptr, nb, s));
+    RC(vec_multi_dot<T>(V, ldv, J, wv, n, S.part, nb, s));
+    RC(reduce_cols(S.part, nb, J, 2, S.h1, hcol, s));
+    RC(vec_multi_update<T>(V, ldv, J, S.h1, wv, n, S.part, nb, s));
+    RC(norm_finalize(S.part, nb, hcol + j + 1, S.scal, hcol, J, bd_rel, J, c->ws.st, s));
+    S.ip += 2 * J + 1;
+  }
+  return vec_scale<T>(wv, wv, n, 1.0, S.scal, s);
+}
+
+// Solve in arithmetic T1; with PP_PREC_MIXED (T1 = dw, T2 = float) the loop
+// may move to FP32 at a stopping check.  A perturbation of relative size u
+// in a later step changes f_m by about u * kappa_pre times the part of the
+// solution still to come (inexact Krylov relaxation; kappa_pre = the ratio
+// of the ends of the image of z q(z)^2, which bounds how much a small
+// eigenvalue's error is amplified in z^{-1/2}).  That remaining part is
+// estimated from the stopping estimate est_m and the observed convergence
+// rate rho = (est_m / est_{m-k})^{1/k} as est_m rho / (1 - rho), so the
+// switch is taken once
+//     est_m rho / (1 - rho) * 4 u_32 * kappa_pre <= tol.
+// The start vector, the leading basis vectors and the result stay at
+// FP64-grade accuracy; H_m, its coefficients and the small solve are FP64
+// throughout.
+template <typename T1, typename T2>
 int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *x_dev, pp_stats *out) {
   const int prec = c->opts.precision;
+  const bool mixed = !std::is_same<T1, T2>::value;
   const bool right = c->opts.side == PP_RIGHT;
   RC(ensure_ws(c, prec, m_max, right));
   Workspace &w = c->ws;
   cudaStream_t s = c->stream;
-  const OpDesc op = make_op(c, prec);
+  const OpDesc op1 = make_op(c, arith_of<T1>());
+  const OpDesc op2 = make_op(c, arith_of<T2>());
   const int64_t n = c->n, ldv = w.ldv;
   const DLayout L = dlayout(c, w.m_cap);
   double *D = w.dmem;
-  double *H = D + L.H, *h1 = D + L.h1, *part = D + L.part, *X = D + L.X, *tri = D + L.tri;
-  double *z = D + L.z, *zprev = D + L.zprev, *sig = D + L.sig, *wt = D + L.wt, *scal = D + L.scal;
+  Solve S;
+  S.c = c;
+  S.s = s;
+  S.n = n;
+  S.ldv = ldv;
+  S.H = D + L.H;
+  S.h1 = D + L.h1;
+  S.part = D + L.part;
+  S.X = D + L.X;
+  S.tri = D + L.tri;
+  S.z = D + L.z;
+  S.zprev = D + L.zprev;
+  S.sig = D + L.sig;
+  S.wt = D + L.wt;
+  S.scal = D + L.scal;
+  S.ldh = L.ldh;
+  S.nb = L.nb;
+  S.K = L.K;
+  S.right = right;
+  S.lanczos = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
+  S.deg = c->degree;
+  S.mvms = 0;
+  S.ip = 0;
   const int ldh = L.ldh, nb = L.nb, K = L.K;
-  T *V = (T *)w.V, *Y = (T *)w.Y;
-  T *t[6];
-  for (int i = 0; i < 6; ++i) t[i] = (T *)w.tmp + (size_t)i * ldv;
+  T1 *V1 = (T1 *)w.V, *Y1 = (T1 *)w.Y;
+  T2 *V2 = (T2 *)(mixed ? w.Vf : w.V), *Y2 = (T2 *)(mixed ? w.Yf : w.Y);
+  T1 *t1[6];
+  T2 *t2[6];
+  for (int i = 0; i < 6; ++i) {
+    t1[i] = (T1 *)w.tmp + (size_t)i * ldv;
+    t2[i] = (T2 *)w.tmp + (size_t)i * ldv;
+  }
   const int deg = c->degree;
-  const bool lanczos = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
   const int kchk = c->opts.check_every > 0 ? c->opts.check_every : (64 / (deg + 1) > 1 ? 64 / (deg + 1) : 1);
-  int64_t mvms = 0, ip = 0;
   const int64_t launches0 = pp_launch_count();
   c->chain_launches = 0;
   c->chain_bytes = 0.0;
@@ -331,31 +420,31 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
 
   PP_CUDA_TRY(cudaEventRecord(w.ev0, s));
   PP_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(DevStatus), s));
-  PP_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)ldh * w.m_cap, s));
+  PP_CUDA_TRY(cudaMemsetAsync(S.H, 0, sizeof(double) * (size_t)ldh * w.m_cap, s));
 
-  // right-hand side in the vector arithmetic
-  const T *rhs;
-  if (std::is_same<T, double>::value) {
-    rhs = (const T *)b_dev;
+  // right-hand side in the phase-1 arithmetic
+  const T1 *rhs;
+  if (std::is_same<T1, double>::value) {
+    rhs = (const T1 *)b_dev;
   } else {
-    RC(vec_from_f64<T>(b_dev, t[0], n, s));
-    rhs = t[0];
+    RC(vec_from_f64<T1>(b_dev, t1[0], n, s));
+    rhs = t1[0];
   }
   if (f == PP_SQRT) {  // Sec. 4: A^{1/2} b = A^{-1/2} (A b)
-    RC(run_op_timed<T>(c, op, rhs, nullptr, nullptr, t[1], {1.0, 0.0, 0.0, false, false}));
-    rhs = t[1];
-    mvms += 1;
+    RC(run_op_timed<T1>(c, op1, rhs, nullptr, nullptr, t1[1], {1.0, 0.0, 0.0, false, false}));
+    rhs = t1[1];
+    S.mvms += 1;
   }
-  T *pb[3] = {t[2], t[3], t[4]};
+  T1 *pb[3] = {t1[2], t1[3], t1[4]};
   if (!right) {  // Algorithm 1: c = q(A) b, v_1 = c / ||c||
-    RC(poly_apply_t<T>(c, op, rhs, V, pb));
-    mvms += deg;
+    RC(poly_apply_t<T1>(c, op1, rhs, V1, pb));
+    S.mvms += deg;
   } else {       // Algorithm 2: v_1 = b / ||b||
-    RC(vec_copy<T>(rhs, V, n, s));
+    RC(vec_copy<T1>(rhs, V1, n, s));
   }
-  RC(vec_dot_partials<T>(V, V, n, part, nb, s));
-  RC(norm_finalize(part, nb, &w.st->beta0, scal, nullptr, 0, 0.0, 0, w.st, s));
-  RC(vec_scale<T>(V, V, n, 1.0, scal, s));
+  RC(vec_dot_partials<T1>(V1, V1, n, S.part, nb, s));
+  RC(norm_finalize(S.part, nb, &w.st->beta0, S.scal, nullptr, 0, 0.0, 0, w.st, s));
+  RC(vec_scale<T1>(V1, V1, n, 1.0, S.scal, s));
   PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   PP_CUDA_TRY(cudaStreamSynchronize(s));
   DevStatus hs = *w.st_host;
@@ -365,7 +454,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
     PP_CUDA_TRY(cudaStreamSynchronize(s));
     if (out) {
       memset(out, 0, sizeof(*out));
-      out->mvms = mvms;
+      out->mvms = S.mvms;
       out->launches = pp_launch_count() - launches0;
     }
     return PP_OK;
@@ -373,46 +462,40 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   // stop at the device: memset flags that record a breakdown of the start
   PP_CUDA_TRY(cudaMemsetAsync(&w.st->conv, 0, 3 * sizeof(int), s));
 
-  int m = 0, mprev = 0, checks = 0, status = PP_ERR_NOT_CONVERGED;
+  // Precision switch (PP_PREC_MIXED): columns [0, nv1) of V1 (and [0, ny1)
+  // of Y1) hold the phase-1 basis; V2 / Y2 hold FP32 copies of them and the
+  // FP32 columns after them.
+  const double kappa_pre = c->img_lo > 0.0 ? c->img_hi / c->img_lo : INFINITY;
+  const double amp = kMixedSafety * kU32 * kappa_pre;
+  double est_prev = INFINITY;
+  int phase = 1, nv1 = 0, ny1 = 0;
+  auto switch_phase = [&](int m_now) -> int {
+    if constexpr (!std::is_same<T1, T2>::value) {
+      for (int col = 0; col <= m_now; ++col)
+        RC((vec_convert<T1, T2>(V1 + (size_t)col * ldv, V2 + (size_t)col * ldv, n, s)));
+      if (right)
+        for (int col = 0; col < m_now; ++col)
+          RC((vec_convert<T1, T2>(Y1 + (size_t)col * ldv, Y2 + (size_t)col * ldv, n, s)));
+      nv1 = m_now + 1;
+      ny1 = m_now;
+      phase = 2;
+    }
+    (void)m_now;
+    return PP_OK;
+  };
+  if (mixed && amp <= tol) RC(switch_phase(0));  // FP32 suffices from the start
+
+  int m = 0, mprev = 0, checks = 0, status = PP_ERR_NOT_CONVERGED, switched_at = mixed ? (phase == 2 ? 0 : -1) : 0;
   bool bd = false;
   for (int j = 0; j < m_max; ++j) {
-    T *vj = V + (size_t)j * ldv;
-    T *wv = V + (size_t)(j + 1) * ldv;
-    if (!right) {  // Algorithm 1, line 4: u = A v_j, y = q(A) u, w = q(A) y
-      RC(run_op_timed<T>(c, op, vj, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
-      RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
-      RC(poly_apply_t<T>(c, op, t[1], wv, pb));
-    } else {       // Algorithm 2, line 4: y_j = q(A) v_j, u = q(A) y_j, w = A u
-      T *yj = Y + (size_t)j * ldv;
-      RC(poly_apply_t<T>(c, op, vj, yj, pb));
-      RC(poly_apply_t<T>(c, op, yj, t[0], pb));
-      RC(run_op_timed<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
-    }
-    mvms += 2 * deg + 1;
-    double *hcol = H + (size_t)j * ldh;
-    if (lanczos) {
-      RC(vec_dot_partials<T>(wv, vj, n, part, nb, s));
-      RC(reduce_cols(part, nb, 1, 0, hcol + j, nullptr, s));
-      RC(vec_lanczos_update<T>(wv, vj, j > 0 ? V + (size_t)(j - 1) * ldv : nullptr, n, hcol + j,
-                               j > 0 ? H + (size_t)(j - 1) * ldh + j : nullptr, part, nb, s));
-      RC(norm_finalize(part, nb, hcol + j + 1, scal, hcol + j, 1, kBreakdownRel, j + 1, w.st, s));
-      ip += 2;
-    } else {  // CGS2: h = V^* w, w -= V h, twice
-      const int J = j + 1;
-      RC(vec_multi_dot<T>(V, ldv, J, wv, n, part, nb, s));
-      RC(reduce_cols(part, nb, J, 1, h1, hcol, s));
-      RC(vec_multi_update<T>(V, ldv, J, h1, wv, n, nullptr, nb, s));
-      RC(vec_multi_dot<T>(V, ldv, J, wv, n, part, nb, s));
-      RC(reduce_cols(part, nb, J, 2, h1, hcol, s));
-      RC(vec_multi_update<T>(V, ldv, J, h1, wv, n, part, nb, s));
-      RC(norm_finalize(part, nb, hcol + j + 1, scal, hcol, J, kBreakdownRel, J, w.st, s));
-      ip += 2 * J + 1;
-    }
-    RC(vec_scale<T>(wv, wv, n, 1.0, scal, s));
+    if (phase == 1)
+      RC(krylov_step<T1>(S, op1, V1, Y1, t1, j, kBreakdownRel));
+    else
+      RC(krylov_step<T2>(S, op2, V2, Y2, t2, j, std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
     m = j + 1;
     if (m % kchk == 0 || m == m_max) {
-      if (lanczos)
-        RC(small_tridiag_quad(H, ldh, m, sig, wt, K, X, tri, s));
+      if (S.lanczos)
+        RC(small_tridiag_quad(S.H, ldh, m, S.sig, S.wt, K, S.X, S.tri, s));
       else {
         const size_t need = small_hess_scratch_doubles(m, K);
         const size_t smem_bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * sizeof(double);
@@ -423,9 +506,9 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
           PP_CUDA_TRY(cudaMalloc(&w.hess, need * sizeof(double)));
           w.hess_n = need;
         }
-        RC(small_hess_quad(H, ldh, m, sig, wt, K, X, w.hess, s));
+        RC(small_hess_quad(S.H, ldh, m, S.sig, S.wt, K, S.X, w.hess, s));
       }
-      RC(small_combine(X, K, m, mprev, z, zprev, tol, w.st, s));
+      RC(small_combine(S.X, K, m, mprev, S.z, S.zprev, tol, w.st, s));
       mprev = m;
       ++checks;
       PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -441,10 +524,28 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
         status = PP_OK;
         break;
       }
+      if (mixed && phase == 1 && std::isfinite(est_prev) && std::isfinite(hs.est) && est_prev > 0.0) {
+        double rho = std::pow(hs.est / est_prev, 1.0 / kchk);
+        if (!(rho < 0.999)) rho = 0.999;
+        if (hs.est * rho / (1.0 - rho) * amp <= tol) {
+          RC(switch_phase(m));
+          switched_at = m;
+        }
+      }
+      est_prev = hs.est;
     }
   }
-  // f_m = V_m z (left) or Y_m z (right)
-  RC(vec_reconstruct<T>(right ? Y : V, ldv, m, z, x_dev, n, s));
+  // f_m = V_m z (left) or Y_m z (right); with a precision switch the leading
+  // columns come from the phase-1 basis
+  if (phase == 1) {
+    RC(vec_reconstruct<T1>(right ? Y1 : V1, ldv, m, S.z, x_dev, n, 0, s));
+  } else {
+    const int k1 = std::min(m, right ? ny1 : nv1);
+    if (k1 > 0) RC(vec_reconstruct<T1>(right ? Y1 : V1, ldv, k1, S.z, x_dev, n, 0, s));
+    if (m > k1)
+      RC(vec_reconstruct<T2>((right ? Y2 : V2) + (size_t)k1 * ldv, ldv, m - k1, S.z + k1, x_dev, n,
+                             k1 > 0 ? 1 : 0, s));
+  }
   PP_CUDA_TRY(cudaEventRecord(w.ev1, s));
   PP_CUDA_TRY(cudaEventSynchronize(w.ev1));
   if (out) {
@@ -453,8 +554,8 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
     out->iters = bd ? hs.m_bd : m;
     out->checks = checks;
     out->breakdown = bd ? 1 : 0;
-    out->mvms = mvms;
-    out->inner_products = ip;
+    out->mvms = S.mvms;
+    out->inner_products = S.ip;
     out->est_err = hs.est;
     out->beta0 = hs.beta0;
     float ms = 0.f;
@@ -464,6 +565,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
     out->chain_launches = c->chain_launches;
     out->chain_bytes = c->chain_bytes;
     out->chain_ms = c->opts.profile ? prof_ms(c) : 0.0;
+    out->switch_iter = switched_at;
   }
   if (status != PP_OK) pp_set_error(status, "m_max reached before the stopping estimate fell below tol");
   return status;
@@ -478,7 +580,7 @@ int check_ready(pp_ctx *c) {
 template <typename T>
 int op_apply_t(pp_ctx *c, const double *x, double *y) {
   RC(ensure_ws(c, c->opts.precision, c->ws.m_cap > 0 ? c->ws.m_cap : 1, false));
-  const OpDesc op = make_op(c, c->opts.precision);
+  const OpDesc op = make_op(c, arith_of<T>());
   T *t0 = (T *)c->ws.tmp, *t1 = t0 + c->ws.ldv;
   if (std::is_same<T, double>::value)
     return op_step<T>(op, (const T *)x, nullptr, nullptr, (T *)y, {1.0, 0.0, 0.0, false, false}, c->stream);
@@ -490,7 +592,7 @@ int op_apply_t(pp_ctx *c, const double *x, double *y) {
 template <typename T>
 int poly_apply_api_t(pp_ctx *c, const double *x, double *y) {
   RC(ensure_ws(c, c->opts.precision, c->ws.m_cap > 0 ? c->ws.m_cap : 1, false));
-  const OpDesc op = make_op(c, c->opts.precision);
+  const OpDesc op = make_op(c, arith_of<T>());
   T *t[6];
   for (int i = 0; i < 6; ++i) t[i] = (T *)c->ws.tmp + (size_t)i * c->ws.ldv;
   T *pb[3] = {t[2], t[3], t[4]};
@@ -537,7 +639,7 @@ int static_scratch_addr(void **out) {
 
 template <typename T>
 int poly_apply_static_t(pp_ctx *c, const double *x, double *y, void *base) {
-  const OpDesc op = make_op(c, c->opts.precision);
+  const OpDesc op = make_op(c, arith_of<T>());
   T *t[kStaticVecs];
   for (int i = 0; i < kStaticVecs; ++i) t[i] = (T *)base + (size_t)i * PP_STATIC_MAX_N;
   if (std::is_same<T, double>::value) {
@@ -548,6 +650,102 @@ int poly_apply_static_t(pp_ctx *c, const double *x, double *y, void *base) {
   RC(vec_from_f64<T>(x, t[0], c->n, c->stream));
   RC(poly_apply_raw<T>(c, op, t[0], t[1], pb));
   return vec_to_f64<T>(t[1], y, c->n, c->stream);
+}
+
+// ---- spectral interval of a Hermitian operator (pp_build_poly without an interval) ----
+
+// Number of eigenvalues of the symmetric tridiagonal T = (al, be) below x:
+// the negative pivots of T - x I = L D L^T (Sturm sequence).
+int sturm_count(const std::vector<double> &al, const std::vector<double> &be, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (size_t i = 0; i < al.size(); ++i) {
+    d = (al[i] - x) - (i > 0 ? be[i - 1] * be[i - 1] / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+// k-th smallest eigenvalue (k = 0 .. m-1) by bisection inside the Gershgorin interval.
+double tridiag_eig(const std::vector<double> &al, const std::vector<double> &be, int k) {
+  double lo = INFINITY, hi = -INFINITY;
+  for (size_t i = 0; i < al.size(); ++i) {
+    const double r = (i > 0 ? std::fabs(be[i - 1]) : 0.0) + (i + 1 < al.size() ? std::fabs(be[i]) : 0.0);
+    lo = std::fmin(lo, al[i] - r);
+    hi = std::fmax(hi, al[i] + r);
+  }
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * std::fmax(std::fabs(lo), std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (sturm_count(al, be, mid) > k)
+      hi = mid;
+    else
+      lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Extreme Ritz values of A after `steps` Lanczos steps from a fixed
+// pseudo-random start, in arithmetic T on the device with three rotating
+// vectors (no basis is kept); the tridiagonal matrix is read back and its
+// extreme eigenvalues found on the host.
+template <typename T>
+int lanczos_extremes(pp_ctx *c, int steps, double *lo, double *hi) {
+  if (c->qsig.empty()) {  // the workspace layout needs a quadrature size
+    c->qsig.assign(1, 1.0);
+    c->qwt.assign(1, 1.0);
+  }
+  RC(ensure_ws(c, c->opts.precision, 1, false));
+  Workspace &w = c->ws;
+  cudaStream_t s = c->stream;
+  const OpDesc op = make_op(c, arith_of<T>());
+  const int64_t n = c->n, ldv = w.ldv;
+  const DLayout L = dlayout(c, w.m_cap);
+  double *part = w.dmem + L.part, *scal = w.dmem + L.scal;
+  const int nb = L.nb;
+  T *t[3];
+  for (int i = 0; i < 3; ++i) t[i] = (T *)w.tmp + (size_t)i * ldv;
+  double *coef = nullptr;  // alpha_j at [2 j], beta_j at [2 j + 1]
+  PP_CUDA_TRY(cudaMalloc(&coef, sizeof(double) * 2 * (size_t)steps));
+  auto body = [&]() -> int {
+    PP_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(DevStatus), s));
+    PP_CUDA_TRY(cudaMemsetAsync(coef, 0, sizeof(double) * 2 * (size_t)steps, s));
+    T *vprev = t[1], *vj = t[0], *wv = t[2];
+    RC(vec_fill_hash<T>(vj, n, 0x5eedull, s));
+    RC(vec_dot_partials<T>(vj, vj, n, part, nb, s));
+    RC(norm_finalize(part, nb, &w.st->beta0, scal, nullptr, 0, 0.0, 0, w.st, s));
+    RC(vec_scale<T>(vj, vj, n, 1.0, scal, s));
+    for (int j = 0; j < steps; ++j) {
+      RC(op_step<T>(op, vj, nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}, s));
+      RC(vec_dot_partials<T>(wv, vj, n, part, nb, s));
+      RC(reduce_cols(part, nb, 1, 0, coef + 2 * j, nullptr, s));
+      RC(vec_lanczos_update<T>(wv, vj, j > 0 ? vprev : nullptr, n, coef + 2 * j,
+                               j > 0 ? coef + 2 * j - 1 : nullptr, part, nb, s));
+      RC(norm_finalize(part, nb, coef + 2 * j + 1, scal, coef + 2 * j, 1, kBreakdownRel, j + 1, w.st, s));
+      RC(vec_scale<T>(wv, wv, n, 1.0, scal, s));
+      T *old = vprev;
+      vprev = vj;
+      vj = wv;
+      wv = old;
+    }
+    std::vector<double> ch(2 * (size_t)steps);
+    PP_CUDA_TRY(cudaMemcpyAsync(ch.data(), coef, sizeof(double) * ch.size(), cudaMemcpyDeviceToHost, s));
+    PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    PP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (w.st_host->bad) return pp_set_error(PP_ERR_CUDA, "non-finite values in the interval estimate");
+    const int m = w.st_host->breakdown ? std::max(1, w.st_host->m_bd) : steps;
+    std::vector<double> al(m), be(m > 1 ? m - 1 : 0);
+    for (int j = 0; j < m; ++j) {
+      al[j] = ch[2 * (size_t)j];
+      if (j + 1 < m) be[j] = ch[2 * (size_t)j + 1];
+    }
+    *lo = tridiag_eig(al, be, 0);
+    *hi = tridiag_eig(al, be, m - 1);
+    return PP_OK;
+  };
+  const int rc = body();
+  cudaFree(coef);
+  return rc;
 }
 
 pp_ctx *new_ctx(void *stream) {
@@ -576,7 +774,7 @@ int pp_create_csr(pp_handle *h, int64_t n, const int64_t *rowptr_d, const int32_
   *h = nullptr;
   if (n <= 0 || !rowptr_d || !col_d || !val_d) return pp_set_error(PP_ERR_INVALID_ARG, "n <= 0 or NULL CSR array");
   if (dtype != PP_F64) return pp_set_error(PP_ERR_UNSUPPORTED, "CSR values must be PP_F64 in this build");
-  if (n > (int64_t)1 << 40) return pp_set_error(PP_ERR_INVALID_ARG, "n too large");
+  if (n > INT32_MAX) return pp_set_error(PP_ERR_INVALID_ARG, "n > 2^31 - 1 (column indices are int32)");
   pp_ctx *c = new_ctx(cuda_stream);
   c->op_kind = OPK_CSR;
   c->n = n;
@@ -595,6 +793,27 @@ int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const d
   if (!h) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle pointer");
   *h = nullptr;
   if (!dims) return pp_set_error(PP_ERR_INVALID_ARG, "NULL dims");
+  if (kind == PP_WILSON4D_DHD) {
+    if (dtype != PP_C128) return pp_set_error(PP_ERR_UNSUPPORTED, "Wilson vectors must be PP_C128");
+    if (!links_d) return pp_set_error(PP_ERR_INVALID_ARG, "Wilson operator needs links_d");
+    if (!params || !std::isfinite(params[0])) return pp_set_error(PP_ERR_INVALID_ARG, "params[0] = m0 must be finite");
+    int64_t V = 1;
+    for (int i = 0; i < 4; ++i) {
+      if (dims[i] < 1 || dims[i] > (1 << 16)) return pp_set_error(PP_ERR_INVALID_ARG, "bad 4D dims");
+      V *= dims[i];
+    }
+    if (V > ((int64_t)1 << 28)) return pp_set_error(PP_ERR_INVALID_ARG, "lattice with more than 2^28 sites");
+    pp_ctx *c = new_ctx(cuda_stream);
+    c->op_kind = OPK_WILSON;
+    for (int i = 0; i < 4; ++i) c->dims[i] = dims[i];
+    c->links = links_d;
+    c->mass = params[0];
+    c->hermitian = 1;
+    c->stencil = kind;
+    c->n = 24 * V;  // real view of 12 complex components per site
+    *h = c;
+    return PP_OK;
+  }
   if (dtype != PP_F64) return pp_set_error(PP_ERR_UNSUPPORTED, "stencil vectors must be PP_F64 in this build");
   if (links_d) return pp_set_error(PP_ERR_INVALID_ARG, "links_d must be NULL for this stencil kind");
   pp_ctx *c = nullptr;
@@ -627,13 +846,15 @@ int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const d
     c->st_cm = -(1.0 + ch);
     c->st_cp = -1.0;
     c->hermitian = (kind == PP_LAPLACE3D7) ? 1 : 0;
-  } else if (kind == PP_WILSON4D_DHD) {
-    return pp_set_error(PP_ERR_UNSUPPORTED, "Wilson operator not in this build");
   } else {
     return pp_set_error(PP_ERR_INVALID_ARG, "unknown stencil kind");
   }
   c->stencil = kind;
   c->n = c->dims[0] * c->dims[1] * c->dims[2];
+  if (c->n > ((int64_t)1 << 34)) {
+    delete c;
+    return pp_set_error(PP_ERR_INVALID_ARG, "grid with more than 2^34 points");
+  }
   *h = c;
   return PP_OK;
 }
@@ -641,10 +862,8 @@ int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const d
 int pp_set_opts(pp_handle c, const pp_opts *o) {
   if (!c || !o) return pp_set_error(PP_ERR_INVALID_ARG, "NULL argument");
   if (o->side != PP_LEFT && o->side != PP_RIGHT) return pp_set_error(PP_ERR_INVALID_ARG, "bad side");
-  if (o->precision != PP_PREC_F64 && o->precision != PP_PREC_DW) {
-    if (o->precision == PP_PREC_MIXED) return pp_set_error(PP_ERR_UNSUPPORTED, "mixed precision not in this build");
+  if (o->precision != PP_PREC_F64 && o->precision != PP_PREC_DW && o->precision != PP_PREC_MIXED)
     return pp_set_error(PP_ERR_INVALID_ARG, "bad precision");
-  }
   if (o->orth < PP_ORTH_AUTO || o->orth > PP_ORTH_CGS2) return pp_set_error(PP_ERR_INVALID_ARG, "bad orth");
   if (o->check_every < 0) return pp_set_error(PP_ERR_INVALID_ARG, "check_every < 0");
   if (o->profile != 0 && o->profile != 1) return pp_set_error(PP_ERR_INVALID_ARG, "profile must be 0 or 1");
@@ -680,8 +899,23 @@ int pp_build_poly(pp_handle c, int32_t degree, int32_t kind, const double *ab) {
       a += (2.0 + c->ch) - 2.0 * r * std::cos(M_PI / (N + 1));
       b += (2.0 + c->ch) - 2.0 * r * std::cos(N * M_PI / (N + 1));
     }
+  } else if (c->hermitian) {
+    // no closed form: extreme Ritz values of kIntervalSteps Lanczos steps,
+    // a lowered by 5 % and b raised by 1 %
+    if (c->op_kind == OPK_CSR && c->nnz < 0) {
+      int64_t nnz = 0;
+      PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+      c->nnz = nnz;
+    }
+    const int steps = (int)std::min<int64_t>(kIntervalSteps, c->n);
+    double lo = 0.0, hi = 0.0;
+    const int rc = c->opts.precision == PP_PREC_F64 ? lanczos_extremes<double>(c, steps, &lo, &hi)
+                                                    : lanczos_extremes<dw>(c, steps, &lo, &hi);
+    if (rc != PP_OK) return rc;
+    a = 0.95 * lo;
+    b = 1.01 * hi;
   } else {
-    return pp_set_error(PP_ERR_INVALID_ARG, "CSR handles need interval_ab");
+    return pp_set_error(PP_ERR_INVALID_ARG, "non-Hermitian CSR handles need interval_ab");
   }
   if (!(a > 0.0) || !(b > a) || !std::isfinite(b)) return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
   std::vector<double> cf = cheb_interp_coeffs(a, b, degree);
@@ -741,7 +975,17 @@ int pp_apply(pp_handle c, int32_t f, const void *b_d, int64_t nrhs, int32_t m_ma
   if (f != PP_SQRT && f != PP_INVSQRT) return pp_set_error(PP_ERR_INVALID_ARG, "f must be PP_SQRT or PP_INVSQRT");
   if (!b_d || !x_d) return pp_set_error(PP_ERR_INVALID_ARG, "NULL vector");
   if (b_d == x_d) return pp_set_error(PP_ERR_INVALID_ARG, "x_d aliases b_d");
-  if (nrhs != 1) return pp_set_error(PP_ERR_UNSUPPORTED, "nrhs != 1 not in this build");
+  if (nrhs < 1) return pp_set_error(PP_ERR_INVALID_ARG, "nrhs < 1");
+  if (nrhs > 1) {
+    if (c->op_kind != OPK_ST2D && c->op_kind != OPK_ST3D)
+      return pp_set_error(PP_ERR_UNSUPPORTED, "nrhs > 1 is supported for the 2D/3D stencil operators");
+    pp_handle hs[1] = {c};
+    const int32_t fs[1] = {f};
+    const void *bs[1] = {b_d};
+    void *xs[1] = {x_d};
+    const int64_t rs[1] = {nrhs};
+    return pp_apply_batch(hs, 1, fs, bs, rs, xs, m_max, tol, c->stream, stats);
+  }
   if (m_max < 1 || m_max > kMaxM) return pp_set_error(PP_ERR_INVALID_ARG, "m_max out of [1, 4096]");
   if (!(tol >= 0.0)) return pp_set_error(PP_ERR_INVALID_ARG, "tol < 0");
   if (c->op_kind == OPK_CSR && c->nnz < 0) {
@@ -749,8 +993,10 @@ int pp_apply(pp_handle c, int32_t f, const void *b_d, int64_t nrhs, int32_t m_ma
     PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
     c->nnz = nnz;
   }
-  if (c->opts.precision == PP_PREC_DW) return solve<dw>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);
-  return solve<double>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);
+  if (c->opts.precision == PP_PREC_MIXED)
+    return solve<dw, float>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);
+  if (c->opts.precision == PP_PREC_DW) return solve<dw, dw>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);
+  return solve<double, double>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);
 }
 
 int pp_apply_host(pp_handle c, int32_t f, const double *b_h, int64_t nrhs, int32_t m_max, double tol,
@@ -779,6 +1025,7 @@ int pp_op_apply(pp_handle c, const void *x_d, void *y_d) {
     c->qsig.assign(1, 1.0);
     c->qwt.assign(1, 1.0);
   }
+  if (c->opts.precision == PP_PREC_MIXED) return op_apply_t<float>(c, (const double *)x_d, (double *)y_d);
   if (c->opts.precision == PP_PREC_DW) return op_apply_t<dw>(c, (const double *)x_d, (double *)y_d);
   return op_apply_t<double>(c, (const double *)x_d, (double *)y_d);
 }
@@ -791,8 +1038,95 @@ int pp_poly_apply(pp_handle c, const void *x_d, void *y_d) {
     PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
     c->nnz = nnz;
   }
+  if (c->opts.precision == PP_PREC_MIXED) return poly_apply_api_t<float>(c, (const double *)x_d, (double *)y_d);
   if (c->opts.precision == PP_PREC_DW) return poly_apply_api_t<dw>(c, (const double *)x_d, (double *)y_d);
   return poly_apply_api_t<double>(c, (const double *)x_d, (double *)y_d);
+}
+
+int pp_autotune(pp_handle c, double tol, int32_t max_degree, int32_t *degree_out) {
+  if (!c) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle");
+  if (!(tol > 0.0) || !(tol < 1.0)) return pp_set_error(PP_ERR_INVALID_ARG, "tol out of (0, 1)");
+  if (max_degree < 0 || max_degree > kMaxDegree) return pp_set_error(PP_ERR_INVALID_ARG, "max_degree out of [0, 128]");
+  // the interval: from an earlier pp_build_poly, else as pp_build_poly would take it
+  if (!c->have_poly) RC(pp_build_poly(c, 0, PP_CHEBYSHEV, nullptr));
+  const double a = c->a, b = c->b;
+  const bool lanczos = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
+  // operator pass cost in vector passes: Clenshaw step 4 (matrix-free) or 4 plus
+  // the matrix bytes in vector units (CSR), 2 for the Wilson pair of launches more
+  double op_cost = 4.0;
+  if (c->op_kind == OPK_CSR && c->nnz > 0) op_cost += (12.0 * (double)c->nnz) / (8.0 * (double)c->n);
+  if (c->op_kind == OPK_WILSON) op_cost = 10.0;
+  static const int cand[] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128};
+  // model constants: sustained HBM bandwidth, launch-plus-gap time, cost of a check
+  constexpr double kBW = 6.0e12, kLaunchS = 3.0e-6, kCheckS = 40.0e-6;
+  const double esz = c->opts.precision == PP_PREC_MIXED ? 6.0 : 8.0;  // FP32 / double-word mix
+  const double t_pass = esz * (double)c->n / kBW;
+  int best = 0;
+  double best_cost = INFINITY;
+  for (int d : cand) {
+    if (d > max_degree) break;
+    const std::vector<double> cf = cheb_interp_coeffs(a, b, d);
+    double qmin, lo, hi;
+    cheb_scan(cf, a, b, &qmin, &lo, &hi);
+    if (!(qmin > 0.0) || !(lo > 0.0)) continue;
+    // Chebyshev bound on the image interval: error ~ 2 ((sqrt(k) - 1) / (sqrt(k) + 1))^m
+    const double kap = hi / lo, sk = std::sqrt(kap);
+    const double rate = std::log((sk + 1.0) / std::fmax(sk - 1.0, 1e-300));
+    const double m = std::ceil(std::log(2.0 / tol) / std::fmax(rate, 1e-300));
+    const double orth = lanczos ? 6.0 : 4.0 * (0.5 * m) + 8.0;
+    // time: vector passes at HBM speed plus a fixed cost per launch and per
+    // stopping check (small solve and host synchronisation)
+    const double launches = (2.0 * d + 1.0) * (c->op_kind == OPK_WILSON ? 2.0 : 1.0) + (lanczos ? 5.0 : 9.0);
+    const int kchk = std::max(1, 64 / (d + 1));
+    const double cost = m * (t_pass * (op_cost * (2.0 * d + 1.0) + orth) + kLaunchS * launches) +
+                        (m / kchk) * kCheckS + d * (t_pass * op_cost + kLaunchS);
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = d;
+    }
+  }
+  const double ab[2] = {a, b};
+  RC(pp_build_poly(c, best, PP_CHEBYSHEV, ab));
+  if (degree_out) *degree_out = best;
+  // tile shape of the stencil step: time each block x-size on the handle's buffers
+  if ((c->op_kind == OPK_ST2D || c->op_kind == OPK_ST3D) && c->opts.precision != PP_PREC_F64) {
+    RC(ensure_ws(c, c->opts.precision, c->ws.m_cap > 0 ? c->ws.m_cap : 1, false));
+    const bool f32 = c->opts.precision == PP_PREC_MIXED;
+    cudaEvent_t e0 = c->ws.ev0, e1 = c->ws.ev1;
+    float best_ms = INFINITY;
+    int best_bdx = 0;
+    for (int bdx : {16, 32, 64, 128}) {
+      c->tile_bdx = bdx;
+      float ms = 0.f;
+      for (int rep = 0; rep < 2; ++rep) {  // first pass warms up
+        PP_CUDA_TRY(cudaEventRecord(e0, c->stream));
+        for (int it = 0; it < 5; ++it) {
+          int rc;
+          if (f32) {
+            const OpDesc op = make_op(c, AR_F32);
+            float *t = (float *)c->ws.tmp;
+            rc = op_step<float>(op, t, t + c->ws.ldv, t + 2 * c->ws.ldv, t + 3 * c->ws.ldv, {1.0, 0.5, 0.25, true, true},
+                                c->stream);
+          } else {
+            const OpDesc op = make_op(c, AR_DW);
+            dw *t = (dw *)c->ws.tmp;
+            rc = op_step<dw>(op, t, t + c->ws.ldv, t + 2 * c->ws.ldv, t + 3 * c->ws.ldv, {1.0, 0.5, 0.25, true, true},
+                             c->stream);
+          }
+          if (rc) return rc;
+        }
+        PP_CUDA_TRY(cudaEventRecord(e1, c->stream));
+        PP_CUDA_TRY(cudaEventSynchronize(e1));
+        PP_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_bdx = bdx;
+      }
+    }
+    c->tile_bdx = best_bdx;
+  }
+  return PP_OK;
 }
 
 int pp_poly_apply_static(pp_handle c, const void *x_d, void *y_d) {
@@ -801,9 +1135,11 @@ int pp_poly_apply_static(pp_handle c, const void *x_d, void *y_d) {
   if (c->n > PP_STATIC_MAX_N)
     return pp_set_error(PP_ERR_INVALID_ARG, "n = " + std::to_string(c->n) +
                                                 " exceeds PP_STATIC_MAX_N = " + std::to_string((long long)PP_STATIC_MAX_N));
-  if (c->op_kind == OPK_CSR && c->opts.precision == PP_PREC_DW)
+  if (c->op_kind == OPK_WILSON)
+    return pp_set_error(PP_ERR_UNSUPPORTED, "the Wilson operator needs a sixth scratch vector; use pp_poly_apply");
+  if (c->op_kind == OPK_CSR && c->opts.precision != PP_PREC_F64)
     return pp_set_error(PP_ERR_UNSUPPORTED,
-                        "CSR handles in PP_PREC_DW need a converted copy of the values; use PP_PREC_F64");
+                        "CSR handles in PP_PREC_DW / PP_PREC_MIXED need a converted copy of the values; use PP_PREC_F64");
   if (c->op_kind == OPK_CSR && c->nnz < 0) {
     int64_t nnz = 0;
     PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
@@ -811,6 +1147,7 @@ int pp_poly_apply_static(pp_handle c, const void *x_d, void *y_d) {
   }
   void *base = nullptr;
   RC(static_scratch_addr(&base));
+  if (c->opts.precision == PP_PREC_MIXED) return poly_apply_static_t<float>(c, (const double *)x_d, (double *)y_d, base);
   if (c->opts.precision == PP_PREC_DW) return poly_apply_static_t<dw>(c, (const double *)x_d, (double *)y_d, base);
   return poly_apply_static_t<double>(c, (const double *)x_d, (double *)y_d, base);
 }

@@ -1,0 +1,793 @@
+// Batched solves (pp_apply_batch): many independent problems and right-hand
+// sides of the matrix-free stencil operators advance in lockstep, so every
+// kernel launch covers all of them and the launch count of a batch is that
+// of one solve.
+//
+// Every (handle, right-hand side) pair is a segment.  Segments are grouped by
+// polynomial degree and orthogonalization (Lanczos or CGS2); a group's
+// vectors are the concatenation of its segments, each padded to whole
+// reduction chunks (padding stays zero), so the vector kernels find a
+// block's segment from a chunk table and read per-segment scalars from
+// per-segment FP64 scratch blocks (Seg in internal.h).  The stencil steps use
+// a per-segment geometry table and per-segment Clenshaw constants, uploaded
+// once per call.  A segment that meets its stopping estimate (or breaks down)
+// is masked out of all later launches and keeps its iterate.  Groups run on
+// their own streams from their own host threads, concurrently.
+//
+// The method per segment is that of pp_apply (Algorithm 1 or 2, Sec. 4 for
+// the square root, the stopping rule of Sec. 6, Example 1); with
+// PP_PREC_MIXED a group moves to FP32 when every active segment satisfies the
+// switching rule of pp_apply.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <thread>
+#include <type_traits>
+#include <vector>
+
+#include "common.cuh"
+#include "ctx.h"
+#include "internal.h"
+
+size_t small_hess_scratch_doubles(int m, int K);
+
+#define BRC(x)                  \
+  do {                          \
+    int _r = (x);               \
+    if (_r != PP_OK) return _r; \
+  } while (0)
+
+namespace {
+
+constexpr double kBdRel = 1e-12;
+constexpr double kBdRelF32 = 4.0 * 0x1p-24;
+constexpr double kU32 = 0x1p-24;
+constexpr double kMixedSafety = 4.0;
+constexpr int kMaxBatchM = 1024;
+
+struct SegIn {
+  pp_ctx *c;
+  int member;
+  int f;
+  const double *b;  // device, this right-hand side
+  double *x;        // device, this solution
+};
+
+struct SegOut {
+  int status = PP_ERR_NOT_CONVERGED, iters = 0, breakdown = 0, switch_iter = 0;
+  int64_t mvms = 0, ip = 0;
+  double est = INFINITY, beta0 = 0.0;
+};
+
+// Per-segment FP64 scratch (offsets in doubles).
+struct BLayout {
+  size_t H, h1, X, tri, z, zprev, sig, wt, scal, qc0, total;
+  int ldh;
+};
+
+BLayout blayout(int m_cap, int K) {
+  BLayout L;
+  L.ldh = m_cap + 1;
+  size_t o = 0;
+  L.H = o;
+  o += (size_t)(m_cap + 1) * m_cap;
+  L.h1 = o;
+  o += (size_t)m_cap + 1;
+  L.X = o;
+  o += (size_t)K * m_cap;
+  L.tri = o;
+  o += (size_t)K * m_cap;
+  L.z = o;
+  o += (size_t)m_cap;
+  L.zprev = o;
+  o += (size_t)m_cap;
+  L.sig = o;
+  o += (size_t)K;
+  L.wt = o;
+  o += (size_t)K;
+  L.scal = o;
+  o += 8;
+  L.qc0 = o;
+  o += 8;
+  L.total = (o + 31) / 32 * 32;
+  return L;
+}
+
+// dst[r] = src[seg][r - off[seg]] inside the segment, 0 in its padding
+__global__ void k_gather(const double *const *__restrict__ src, const int64_t *__restrict__ off,
+                         const int64_t *__restrict__ len, const int *__restrict__ chunk_seg, int chunk,
+                         double *__restrict__ dst, int64_t N) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+    const int s = chunk_seg[r / chunk];
+    const int64_t i = r - off[s];
+    dst[r] = i < len[s] ? src[s][i] : 0.0;
+  }
+}
+
+// dst[seg][r - off[seg]] = src[r] inside the segment
+__global__ void k_scatter(double *const *__restrict__ dst, const int64_t *__restrict__ off,
+                          const int64_t *__restrict__ len, const int *__restrict__ chunk_seg, int chunk,
+                          const double *__restrict__ src, int64_t N) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
+    const int s = chunk_seg[r / chunk];
+    const int64_t i = r - off[s];
+    if (i < len[s]) dst[s][i] = src[r];
+  }
+}
+
+// dst[s * dstride + i] = src[i], i < K, for every segment s
+__global__ void k_broadcast(const double *__restrict__ src, int K, double *__restrict__ dst, int64_t dstride) {
+  const int s = blockIdx.x;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) dst[s * dstride + i] = src[i];
+}
+
+// clear the stopping flags (keep beta0)
+__global__ void k_clear_flags(DevStatus *st, int nseg) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < nseg) {
+    st[s].conv = 0;
+    st[s].breakdown = 0;
+    st[s].m_bd = 0;
+  }
+}
+
+// A basis of columns of N entries that grows on demand (doubling, up to a
+// cap); the first `used` columns are copied when it moves.
+template <typename T>
+struct GrowCols {
+  T *p = nullptr;
+  int cap = 0, cap_max = 0;
+  int64_t N = 0;
+  ~GrowCols() {
+    if (p) cudaFree(p);
+  }
+  int init(int64_t n, int first, int maxc, cudaStream_t s) {
+    N = n;
+    cap_max = maxc;
+    cap = std::min(first, maxc);
+    PP_CUDA_TRY(cudaMalloc(&p, sizeof(T) * (size_t)cap * N));
+    PP_CUDA_TRY(cudaMemsetAsync(p, 0, sizeof(T) * (size_t)cap * N, s));
+    return PP_OK;
+  }
+  int ensure(int need, cudaStream_t s) {
+    if (need <= cap) return PP_OK;
+    const int nc = std::min(cap_max, std::max(need, 2 * cap));
+    T *q = nullptr;
+    PP_CUDA_TRY(cudaMalloc(&q, sizeof(T) * (size_t)nc * N));
+    PP_CUDA_TRY(cudaMemcpyAsync(q, p, sizeof(T) * (size_t)cap * N, cudaMemcpyDeviceToDevice, s));
+    PP_CUDA_TRY(cudaMemsetAsync(q + (size_t)cap * N, 0, sizeof(T) * (size_t)(nc - cap) * N, s));
+    PP_CUDA_TRY(cudaStreamSynchronize(s));
+    cudaFree(p);
+    p = q;
+    cap = nc;
+    return PP_OK;
+  }
+};
+constexpr int kFirstCols = 32;
+
+// Device allocations of one group, freed together.
+struct Allocs {
+  std::vector<void *> p;
+  ~Allocs() {
+    for (void *q : p) cudaFree(q);
+  }
+  template <typename X>
+  int get(X **out, size_t bytes) {
+    void *q = nullptr;
+    PP_CUDA_TRY(cudaMalloc(&q, bytes > 0 ? bytes : 16));
+    p.push_back(q);
+    *out = (X *)q;
+    return PP_OK;
+  }
+};
+
+// Clenshaw coefficients of step t (0 .. k-1) of q(A) for one segment, the
+// same schedule as the single-vector driver: b_k = c_k v folded into the
+// first step, the last step with the factors 1/2.
+StepCoef clenshaw_step(const std::vector<double> &cf, double s1, double s2, int t) {
+  const int k = (int)cf.size() - 1;
+  if (k == 1) return {0.5 * s1 * cf[1], 0.5 * s2 * cf[1] + cf[0], 0.0, false, false};
+  if (t == 0) return {s1 * cf[k], s2 * cf[k] + cf[k - 1], 0.0, false, false};
+  if (t == 1 && k == 2) return {0.5 * s1, 0.5 * s2, cf[0] - cf[2], false, true};
+  if (t == 1) return {s1, s2, cf[k - 2] - cf[k], false, true};
+  if (t == k - 1) return {0.5 * s1, 0.5 * s2, cf[0], true, true};
+  return {s1, s2, cf[k - 1 - t], true, true};
+}
+
+// Everything a group's kernels need for one arithmetic.
+template <typename T>
+struct ArithTabs {
+  const BatchSeg *bseg = nullptr;  // geometry table
+  unsigned nblk = 0;
+  int P = 1;
+  const Konst<T> *K = nullptr;     // (deg + 1) x nseg: [0] = A, [1 + t] = Clenshaw step t
+};
+
+struct GroupCtx {
+  int nseg = 0, deg = 0, nb = 0, K = 0;
+  int64_t N = 0;
+  BLayout L;
+  bool lanczos = true, right = false;
+  cudaStream_t s = nullptr;
+  double *dmem = nullptr, *part = nullptr, *hess = nullptr;
+  size_t hess_n = 0;
+  DevStatus *st = nullptr;
+  int *active = nullptr, *sqrt_mask = nullptr, *chunk_seg = nullptr, *chunk0 = nullptr;
+  Allocs *alloc = nullptr;
+  Seg seg(bool with_active) const {
+    Seg S;
+    S.nseg = nseg;
+    S.chunk_seg = chunk_seg;
+    S.chunk0 = chunk0;
+    S.active = with_active ? active : nullptr;
+    S.dstride = (int64_t)L.total;
+    return S;
+  }
+};
+
+// y = q(A) x for every active segment (deg operator launches, or a scaled copy for deg 0)
+template <typename T>
+int poly_batch(GroupCtx &G, const ArithTabs<T> &A, const T *in, T *out, T *bufs[3]) {
+  const int k = G.deg;
+  const int ns = G.nseg;
+  cudaStream_t s = G.s;
+  auto step = [&](int t, const T *x, const T *y, const T *v, T *o, bool sy, bool av) {
+    return op_step_batch<T>(A.bseg, ns, A.nblk, A.P, A.K + (size_t)(1 + t) * ns, G.active, x, y, v, o, sy, av, s);
+  };
+  if (k == 0) return vec_scale<T>(in, out, G.N, 1.0, G.dmem + G.L.qc0, s, G.seg(true));
+  if (k == 1) return step(0, in, nullptr, nullptr, out, false, false);
+  int i2 = 0, i1 = 1, i0 = 2;
+  BRC(step(0, in, nullptr, nullptr, bufs[i2], false, false));
+  if (k == 2) return step(1, bufs[i2], nullptr, in, out, false, true);
+  BRC(step(1, bufs[i2], nullptr, in, bufs[i1], false, true));
+  for (int t = 2; t <= k - 2; ++t) {
+    BRC(step(t, bufs[i1], bufs[i2], in, bufs[i0], true, true));
+    const int tmp = i2;
+    i2 = i1;
+    i1 = i0;
+    i0 = tmp;
+  }
+  return step(k - 1, bufs[i1], bufs[i2], in, out, true, true);
+}
+
+template <typename T>
+int aop_batch(GroupCtx &G, const ArithTabs<T> &A, const int *mask, const T *x, T *out) {
+  return op_step_batch<T>(A.bseg, G.nseg, A.nblk, A.P, A.K, mask, x, nullptr, nullptr, out, false, false, G.s);
+}
+
+// One lockstep Krylov step j in arithmetic T (the step of pp_apply for every segment).
+template <typename T>
+int krylov_step_batch(GroupCtx &G, const ArithTabs<T> &A, T *V, T *Y, T *t[6], int j, double bd_rel,
+                      int64_t *ip) {
+  cudaStream_t s = G.s;
+  const int64_t N = G.N;
+  T *pb[3] = {t[2], t[3], t[4]};
+  T *vj = V + (size_t)j * N;
+  T *wv = V + (size_t)(j + 1) * N;
+  if (!G.right) {
+    BRC(aop_batch<T>(G, A, G.active, vj, t[0]));
+    BRC(poly_batch<T>(G, A, t[0], t[1], pb));
+    BRC(poly_batch<T>(G, A, t[1], wv, pb));
+  } else {
+    T *yj = Y + (size_t)j * N;
+    BRC(poly_batch<T>(G, A, vj, yj, pb));
+    BRC(poly_batch<T>(G, A, yj, t[0], pb));
+    BRC(aop_batch<T>(G, A, G.active, t[0], wv));
+  }
+  const Seg S = G.seg(true);
+  const BLayout &L = G.L;
+  double *H = G.dmem + L.H;
+  double *hcol = H + (size_t)j * L.ldh;
+  double *scal = G.dmem + L.scal;
+  if (G.lanczos) {
+    BRC(vec_dot_partials<T>(wv, vj, N, G.part, G.nb, s, S));
+    BRC(reduce_cols(G.part, G.nb, 1, 0, hcol + j, nullptr, s, S));
+    BRC(vec_lanczos_update<T>(wv, vj, j > 0 ? vj - N : nullptr, N, hcol + j,
+                              j > 0 ? H + (size_t)(j - 1) * L.ldh + j : nullptr, G.part, G.nb, s, S));
+    BRC(norm_finalize(G.part, G.nb, hcol + j + 1, scal, hcol + j, 1, bd_rel, j + 1, G.st, s, S));
+    *ip += 2;
+  } else {
+    const int J = j + 1;
+    double *h1 = G.dmem + L.h1;
+    BRC(vec_multi_dot<T>(V, N, J, wv, N, G.part, G.nb, s, S));
+    BRC(reduce_cols(G.part, G.nb, J, 1, h1, hcol, s, S));
+    BRC(vec_multi_update<T>(V, N, J, h1, wv, N, nullptr, G.nb, s, S));
+    BRC(vec_multi_dot<T>(V, N, J, wv, N, G.part, G.nb, s, S));
+    BRC(reduce_cols(G.part, G.nb, J, 2, h1, hcol, s, S));
+    BRC(vec_multi_update<T>(V, N, J, h1, wv, N, G.part, G.nb, s, S));
+    BRC(norm_finalize(G.part, G.nb, hcol + j + 1, scal, hcol, J, bd_rel, J, G.st, s, S));
+    *ip += 2 * J + 1;
+  }
+  return vec_scale<T>(wv, wv, N, 1.0, scal, s, S);
+}
+
+// Geometry and constants of one arithmetic, uploaded to the group's allocations.
+template <typename T>
+int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<int64_t> &off, ArithTabs<T> *out) {
+  const int ns = G.nseg;
+  constexpr int PW = 16 / (int)sizeof(T);
+  bool vec = true;
+  for (const SegIn &q : segs) vec = vec && (q.c->dims[0] % PW == 0);
+  const int P = vec ? PW : 1;
+  const int bdy = 128 / kBatchBlockX;
+  std::vector<BatchSeg> g(ns);
+  uint64_t nblk = 0;
+  for (int i = 0; i < ns; ++i) {
+    const pp_ctx *c = segs[i].c;
+    g[i].off = off[i];
+    g[i].nx = (int)c->dims[0];
+    g[i].ny = (int)c->dims[1];
+    g[i].nz = c->op_kind == OPK_ST2D ? 1 : (int)c->dims[2];
+    g[i].gx = (unsigned)((g[i].nx / P + kBatchBlockX - 1) / kBatchBlockX);
+    g[i].gy = (unsigned)((g[i].ny + bdy - 1) / bdy);
+    g[i].blk0 = (unsigned)nblk;
+    nblk += (uint64_t)g[i].gx * g[i].gy * g[i].nz;
+  }
+  if (nblk > 0x7fffffffull) return pp_set_error(PP_ERR_INVALID_ARG, "batch too large for one launch");
+  // constants: [0] = A, [1 + t] = Clenshaw step t
+  const int nt = G.deg + 1;
+  std::vector<Konst<T>> Kh((size_t)nt * ns);
+  std::vector<double> d(ns), cm(ns), cp(ns);
+  std::vector<StepCoef> coefs(ns);
+  for (int i = 0; i < ns; ++i) {
+    d[i] = segs[i].c->st_d;
+    cm[i] = segs[i].c->st_cm;
+    cp[i] = segs[i].c->st_cp;
+  }
+  for (int t = 0; t < nt; ++t) {
+    for (int i = 0; i < ns; ++i) {
+      const pp_ctx *c = segs[i].c;
+      if (t == 0) {
+        coefs[i] = {1.0, 0.0, 0.0, false, false};
+      } else {
+        const double s1 = 4.0 / (c->b - c->a), s2 = -2.0 * (c->a + c->b) / (c->b - c->a);
+        coefs[i] = clenshaw_step(c->coef, s1, s2, t - 1);
+      }
+    }
+    batch_konst<T>(d.data(), cm.data(), cp.data(), coefs.data(), ns, Kh.data() + (size_t)t * ns);
+  }
+  BatchSeg *gd = nullptr;
+  Konst<T> *Kd = nullptr;
+  BRC(G.alloc->get(&gd, sizeof(BatchSeg) * ns));
+  BRC(G.alloc->get(&Kd, sizeof(Konst<T>) * Kh.size()));
+  PP_CUDA_TRY(cudaMemcpyAsync(gd, g.data(), sizeof(BatchSeg) * ns, cudaMemcpyHostToDevice, G.s));
+  PP_CUDA_TRY(cudaMemcpyAsync(Kd, Kh.data(), sizeof(Konst<T>) * Kh.size(), cudaMemcpyHostToDevice, G.s));
+  out->bseg = gd;
+  out->nblk = (unsigned)nblk;
+  out->P = P;
+  out->K = Kd;
+  return PP_OK;
+}
+
+// Lockstep solve of one group; T1 = phase-1 arithmetic, T2 = FP32 for
+// PP_PREC_MIXED (else T2 = T1).
+template <typename T1, typename T2>
+int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int kchk, int m_max, double tol,
+              cudaStream_t s, std::vector<SegOut> &res, int64_t *launches_out) {
+  const bool mixed = !std::is_same<T1, T2>::value;
+  const int ns = (int)segs.size();
+  const int CH = vec_chunk_rows();
+  const int64_t launches0 = pp_launch_count();
+  Allocs al;
+  GroupCtx G;
+  G.alloc = &al;
+  G.nseg = ns;
+  G.deg = deg;
+  G.lanczos = lanczos;
+  G.right = right;
+  G.s = s;
+  // concatenated layout
+  std::vector<int64_t> off(ns), len(ns);
+  std::vector<int> cseg, c0(ns + 1);
+  int64_t N = 0;
+  for (int i = 0; i < ns; ++i) {
+    len[i] = segs[i].c->n;
+    off[i] = N;
+    c0[i] = (int)(N / CH);
+    const int64_t padded = (len[i] + CH - 1) / CH * CH;
+    for (int64_t q = 0; q < padded / CH; ++q) cseg.push_back(i);
+    N += padded;
+  }
+  c0[ns] = (int)(N / CH);
+  G.N = N;
+  G.nb = (int)(N / CH);
+  // one quadrature for the group, valid on the union of the segments' images
+  double lo = INFINITY, hi = 0.0;
+  bool herm = true;
+  for (const SegIn &q : segs) {
+    lo = std::fmin(lo, q.c->img_lo);
+    hi = std::fmax(hi, q.c->img_hi);
+    herm = herm && q.c->hermitian;
+  }
+  std::vector<double> qs, qw;
+  invsqrt_quadrature(lo * 1e-3, hi * 1e3, 1e-15, herm ? 0.0 : M_PI / 3.0, &qs, &qw);
+  G.K = (int)qs.size();
+  G.L = blayout(m_max, G.K);
+  const BLayout &L = G.L;
+  // allocations
+  GrowCols<T1> V1g, Y1g;
+  GrowCols<float> V2g, Y2g;
+  void *tmp = nullptr;
+  double *bcat = nullptr, *xcat = nullptr, *qsd = nullptr;
+  int *mseg = nullptr, *mseg2 = nullptr;
+  int64_t *offd = nullptr, *lend = nullptr;
+  const double **srcd = nullptr;
+  double **dstd = nullptr;
+  BRC(V1g.init(N, kFirstCols, m_max + 1, s));
+  if (right) BRC(Y1g.init(N, kFirstCols, m_max, s));
+  BRC(al.get(&tmp, 8 * (size_t)6 * N));
+  BRC(al.get(&G.dmem, sizeof(double) * L.total * ns));
+  BRC(al.get(&G.part, sizeof(double) * (size_t)G.nb * (m_max + 1)));
+  BRC(al.get(&G.st, sizeof(DevStatus) * ns));
+  BRC(al.get(&G.active, sizeof(int) * ns));
+  BRC(al.get(&G.sqrt_mask, sizeof(int) * ns));
+  BRC(al.get(&mseg, sizeof(int) * ns));
+  BRC(al.get(&mseg2, sizeof(int) * ns));
+  BRC(al.get(&G.chunk_seg, sizeof(int) * cseg.size()));
+  BRC(al.get(&G.chunk0, sizeof(int) * (ns + 1)));
+  BRC(al.get(&bcat, sizeof(double) * N));
+  BRC(al.get(&xcat, sizeof(double) * N));
+  BRC(al.get(&qsd, sizeof(double) * 2 * G.K));
+  BRC(al.get(&offd, sizeof(int64_t) * ns));
+  BRC(al.get(&lend, sizeof(int64_t) * ns));
+  BRC(al.get(&srcd, sizeof(double *) * ns));
+  BRC(al.get(&dstd, sizeof(double *) * ns));
+  PP_CUDA_TRY(cudaMemsetAsync(tmp, 0, 8 * (size_t)6 * N, s));
+  PP_CUDA_TRY(cudaMemsetAsync(G.dmem, 0, sizeof(double) * L.total * ns, s));
+  PP_CUDA_TRY(cudaMemsetAsync(G.st, 0, sizeof(DevStatus) * ns, s));
+  std::vector<int> ones(ns, 1), sq(ns), zeros(ns, 0);
+  std::vector<const double *> src(ns);
+  std::vector<double *> dst(ns);
+  std::vector<double> cf0(ns);
+  for (int i = 0; i < ns; ++i) {
+    sq[i] = segs[i].f == PP_SQRT ? 1 : 0;
+    src[i] = segs[i].b;
+    dst[i] = segs[i].x;
+    cf0[i] = segs[i].c->coef[0];
+  }
+  PP_CUDA_TRY(cudaMemcpyAsync(G.active, ones.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(G.sqrt_mask, sq.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(mseg, zeros.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(G.chunk_seg, cseg.data(), sizeof(int) * cseg.size(), cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(G.chunk0, c0.data(), sizeof(int) * (ns + 1), cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(offd, off.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(lend, len.data(), sizeof(int64_t) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(srcd, src.data(), sizeof(double *) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(dstd, dst.data(), sizeof(double *) * ns, cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(qsd, qs.data(), sizeof(double) * G.K, cudaMemcpyHostToDevice, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(qsd + G.K, qw.data(), sizeof(double) * G.K, cudaMemcpyHostToDevice, s));
+  // per-segment constants: quadrature nodes / weights and q's constant term
+  k_broadcast<<<ns, 128, 0, s>>>(qsd, G.K, G.dmem + L.sig, (int64_t)L.total);
+  k_broadcast<<<ns, 128, 0, s>>>(qsd + G.K, G.K, G.dmem + L.wt, (int64_t)L.total);
+  launches_out[0] += 2;
+  PP_CUDA_TRY(cudaGetLastError());
+  PP_CUDA_TRY(cudaMemcpy2DAsync(G.dmem + L.qc0, sizeof(double) * L.total, cf0.data(), sizeof(double),
+                                sizeof(double), ns, cudaMemcpyHostToDevice, s));
+  ArithTabs<T1> A1;
+  ArithTabs<T2> A2;
+  BRC(build_tabs<T1>(G, segs, off, &A1));
+  if (mixed) BRC(build_tabs<T2>(G, segs, off, &A2));
+  T1 *t1[6];
+  T2 *t2[6];
+  for (int i = 0; i < 6; ++i) {
+    t1[i] = (T1 *)tmp + (size_t)i * N;
+    t2[i] = (T2 *)tmp + (size_t)i * N;
+  }
+  const Seg Sall = G.seg(false);
+  // right-hand sides, A b for the square roots (Sec. 4), start vectors
+  k_gather<<<1024, 256, 0, s>>>(srcd, offd, lend, G.chunk_seg, CH, bcat, N);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  BRC(vec_from_f64<T1>(bcat, t1[0], N, s));
+  BRC(vec_copy<T1>(t1[0], t1[1], N, s));
+  BRC(aop_batch<T1>(G, A1, G.sqrt_mask, t1[0], t1[1]));
+  T1 *pb[3] = {t1[2], t1[3], t1[4]};
+  if (!right)
+    BRC(poly_batch<T1>(G, A1, t1[1], V1g.p, pb));
+  else
+    BRC(vec_copy<T1>(t1[1], V1g.p, N, s));
+  BRC(vec_dot_partials<T1>(V1g.p, V1g.p, N, G.part, G.nb, s, Sall));
+  // beta0 of every segment into its status record (stride of DevStatus in doubles)
+  {
+    Seg Sb = Sall;
+    BRC(norm_finalize(G.part, G.nb, G.dmem + L.scal + 1, G.dmem + L.scal, nullptr, 0, 0.0, 0, G.st, s, Sb));
+  }
+  BRC(vec_scale<T1>(V1g.p, V1g.p, N, 1.0, G.dmem + L.scal, s, Sall));
+  std::vector<DevStatus> hs(ns);
+  std::vector<double> beta0(ns);
+  PP_CUDA_TRY(cudaMemcpyAsync(hs.data(), G.st, sizeof(DevStatus) * ns, cudaMemcpyDeviceToHost, s));
+  PP_CUDA_TRY(cudaMemcpy2DAsync(beta0.data(), sizeof(double), G.dmem + L.scal + 1, sizeof(double) * L.total,
+                                sizeof(double), ns, cudaMemcpyDeviceToHost, s));
+  PP_CUDA_TRY(cudaStreamSynchronize(s));
+  std::vector<int> act(ns, 1), m_of(ns, 0);
+  int nact = ns;
+  for (int i = 0; i < ns; ++i) {
+    res[i].beta0 = beta0[i];
+    res[i].mvms = (segs[i].f == PP_SQRT ? 1 : 0) + (right ? 0 : deg);
+    if (hs[i].bad) return pp_set_error(PP_ERR_INVALID_ARG, "non-finite norm of a start vector");
+    if (hs[i].breakdown) {  // zero right-hand side: x = 0
+      act[i] = 0;
+      --nact;
+      res[i].status = PP_OK;
+      res[i].iters = 0;
+    }
+  }
+  // beta0 is read by the small solves from the status record
+  for (int i = 0; i < ns; ++i) hs[i].beta0 = beta0[i];
+  PP_CUDA_TRY(cudaMemcpyAsync(G.st, hs.data(), sizeof(DevStatus) * ns, cudaMemcpyHostToDevice, s));
+  k_clear_flags<<<(ns + 127) / 128, 128, 0, s>>>(G.st, ns);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaMemcpyAsync(G.active, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+
+  const Seg S = G.seg(true);
+  double kappa = 0.0;
+  for (const SegIn &q : segs) kappa = std::fmax(kappa, q.c->img_lo > 0 ? q.c->img_hi / q.c->img_lo : INFINITY);
+  const double amp = kMixedSafety * kU32 * kappa;
+  std::vector<double> est_prev(ns, INFINITY);
+  int phase = 1, nv1 = 0, ny1 = 0, switched_at = mixed ? -1 : 0;
+  auto switch_phase = [&](int m_now) -> int {
+    if constexpr (!std::is_same<T1, T2>::value) {
+      BRC(V2g.init(N, std::max(kFirstCols, 2 * (m_now + 1)), m_max + 1, s));
+      if (right) BRC(Y2g.init(N, std::max(kFirstCols, 2 * (m_now + 1)), m_max, s));
+      for (int col = 0; col <= m_now; ++col)
+        BRC((vec_convert<T1, T2>(V1g.p + (size_t)col * N, V2g.p + (size_t)col * N, N, s)));
+      if (right)
+        for (int col = 0; col < m_now; ++col)
+          BRC((vec_convert<T1, T2>(Y1g.p + (size_t)col * N, Y2g.p + (size_t)col * N, N, s)));
+      nv1 = m_now + 1;
+      ny1 = m_now;
+      phase = 2;
+    }
+    (void)m_now;
+    return PP_OK;
+  };
+  if (mixed && amp <= tol) {
+    BRC(switch_phase(0));
+    switched_at = 0;
+  }
+  int64_t ip = 0;
+  int m = 0, mprev = 0;
+  for (int j = 0; j < m_max && nact > 0; ++j) {
+    if (phase == 1) {
+      BRC(V1g.ensure(j + 2, s));
+      if (right) BRC(Y1g.ensure(j + 1, s));
+      BRC(krylov_step_batch<T1>(G, A1, V1g.p, Y1g.p, t1, j, kBdRel, &ip));
+    } else {
+      BRC(V2g.ensure(j + 2, s));
+      if (right) BRC(Y2g.ensure(j + 1, s));
+      BRC(krylov_step_batch<T2>(G, A2, (T2 *)V2g.p, (T2 *)Y2g.p, t2, j,
+                                std::is_same<T2, float>::value ? kBdRelF32 : kBdRel, &ip));
+    }
+    m = j + 1;
+    for (int i = 0; i < ns; ++i)
+      if (act[i]) res[i].mvms += 2 * deg + 1;
+    if (m % kchk == 0 || m == m_max) {
+      double *H = G.dmem + L.H;
+      if (lanczos)
+        BRC(small_tridiag_quad(H, L.ldh, m, G.dmem + L.sig, G.dmem + L.wt, G.K, G.dmem + L.X, G.dmem + L.tri, s, S));
+      else {
+        const size_t per = small_hess_scratch_doubles(m, G.K);
+        const size_t smem_bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * sizeof(double);
+        if (smem_bytes > 200 * 1024 && G.hess_n < per * ns) {
+          BRC(al.get(&G.hess, sizeof(double) * per * ns));
+          G.hess_n = per * ns;
+        }
+        BRC(small_hess_quad(H, L.ldh, m, G.dmem + L.sig, G.dmem + L.wt, G.K, G.dmem + L.X, G.hess, s, S));
+      }
+      BRC(small_combine(G.dmem + L.X, G.K, m, mprev, G.dmem + L.z, G.dmem + L.zprev, tol, G.st, s, S));
+      mprev = m;
+      PP_CUDA_TRY(cudaMemcpyAsync(hs.data(), G.st, sizeof(DevStatus) * ns, cudaMemcpyDeviceToHost, s));
+      PP_CUDA_TRY(cudaStreamSynchronize(s));
+      bool all_relaxed = true;
+      for (int i = 0; i < ns; ++i) {
+        if (!act[i]) continue;
+        if (hs[i].bad) return pp_set_error(PP_ERR_CUDA, "non-finite values in a batched Krylov process");
+        res[i].est = hs[i].est;
+        if (hs[i].breakdown || hs[i].conv) {
+          act[i] = 0;
+          --nact;
+          res[i].status = PP_OK;
+          res[i].breakdown = hs[i].breakdown;
+          res[i].iters = hs[i].breakdown ? hs[i].m_bd : m;
+          m_of[i] = m;
+          continue;
+        }
+        bool relaxed = false;
+        if (std::isfinite(est_prev[i]) && std::isfinite(hs[i].est) && est_prev[i] > 0.0) {
+          double rho = std::pow(hs[i].est / est_prev[i], 1.0 / kchk);
+          if (!(rho < 0.999)) rho = 0.999;
+          relaxed = hs[i].est * rho / (1.0 - rho) * amp <= tol;
+        }
+        all_relaxed = all_relaxed && relaxed;
+        est_prev[i] = hs[i].est;
+      }
+      PP_CUDA_TRY(cudaMemcpyAsync(G.active, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+      if (mixed && phase == 1 && nact > 0 && all_relaxed) {
+        BRC(switch_phase(m));
+        switched_at = m;
+      }
+    }
+  }
+  for (int i = 0; i < ns; ++i) {
+    if (act[i]) {
+      res[i].iters = m;
+      m_of[i] = m;
+    }
+    res[i].ip = ip;
+    res[i].switch_iter = switched_at;
+  }
+  // f_m = V_m z (left) or Y_m z (right) per segment, then scattered to the callers' x
+  PP_CUDA_TRY(cudaMemcpyAsync(mseg, m_of.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+  const Seg Sr = G.seg(false);
+  T1 *B1 = right ? Y1g.p : V1g.p;
+  if (phase == 1) {
+    BRC(vec_reconstruct<T1>(B1, N, std::max(m, 1), G.dmem + L.z, xcat, N, 0, s, Sr, mseg));
+  } else {
+    const int k1 = right ? ny1 : nv1;
+    std::vector<int> m2(ns);
+    for (int i = 0; i < ns; ++i) m2[i] = std::max(0, m_of[i] - k1);
+    PP_CUDA_TRY(cudaMemcpyAsync(mseg2, m2.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+    BRC(vec_reconstruct<T1>(B1, N, std::max(k1, 1), G.dmem + L.z, xcat, N, 0, s, Sr, mseg));
+    if (m > k1)
+      BRC(vec_reconstruct<T2>((right ? (T2 *)Y2g.p : (T2 *)V2g.p) + (size_t)k1 * N, N, m - k1, G.dmem + L.z + k1,
+                              xcat, N, 1, s, Sr, mseg2));
+  }
+  k_scatter<<<1024, 256, 0, s>>>(dstd, offd, lend, G.chunk_seg, CH, xcat, N);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  PP_CUDA_TRY(cudaStreamSynchronize(s));
+  *launches_out += pp_launch_count() - launches0;
+  return PP_OK;
+}
+
+}  // namespace
+
+extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int32_t *f, const void *const *b_d,
+                              const int64_t *nrhs, void *const *x_d, int32_t m_max, double tol,
+                              void *cuda_stream, pp_stats *stats) {
+  if (!handles || count < 1 || !f || !b_d || !nrhs || !x_d)
+    return pp_set_error(PP_ERR_INVALID_ARG, "NULL argument or count < 1");
+  if (m_max < 1 || m_max > kMaxBatchM) return pp_set_error(PP_ERR_INVALID_ARG, "m_max out of [1, 1024]");
+  if (!(tol >= 0.0)) return pp_set_error(PP_ERR_INVALID_ARG, "tol < 0");
+  int prec = -1, side = -1;
+  for (int i = 0; i < count; ++i) {
+    pp_ctx *c = handles[i];
+    if (!c) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle");
+    if (!c->have_poly) return pp_set_error(PP_ERR_STATE, "pp_build_poly has not been called on every handle");
+    if (c->op_kind != OPK_ST2D && c->op_kind != OPK_ST3D)
+      return pp_set_error(PP_ERR_UNSUPPORTED, "batched solves take the 2D/3D stencil operators only");
+    if (f[i] != PP_SQRT && f[i] != PP_INVSQRT) return pp_set_error(PP_ERR_INVALID_ARG, "f must be PP_SQRT or PP_INVSQRT");
+    if (nrhs[i] < 1) return pp_set_error(PP_ERR_INVALID_ARG, "nrhs < 1");
+    if (!b_d[i] || !x_d[i] || b_d[i] == (const void *)x_d[i]) return pp_set_error(PP_ERR_INVALID_ARG, "bad vector pointers");
+    if (prec < 0) prec = c->opts.precision, side = c->opts.side;
+    if (c->opts.precision != prec || c->opts.side != side)
+      return pp_set_error(PP_ERR_INVALID_ARG, "all handles of a batch need the same precision and side");
+  }
+  // groups: same degree and orthogonalization
+  struct Key {
+    int deg;
+    bool lanczos;
+  };
+  std::vector<Key> keys;
+  std::vector<std::vector<SegIn>> groups;
+  std::vector<std::vector<std::pair<int, int>>> where;  // (member, rhs) per segment
+  for (int i = 0; i < count; ++i) {
+    pp_ctx *c = handles[i];
+    const bool lz = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
+    int g = -1;
+    for (size_t q = 0; q < keys.size(); ++q)
+      if (keys[q].deg == c->degree && keys[q].lanczos == lz) g = (int)q;
+    if (g < 0) {
+      keys.push_back({c->degree, lz});
+      groups.emplace_back();
+      where.emplace_back();
+      g = (int)keys.size() - 1;
+    }
+    for (int64_t r = 0; r < nrhs[i]; ++r) {
+      SegIn q;
+      q.c = c;
+      q.member = i;
+      q.f = f[i];
+      q.b = (const double *)b_d[i] + r * c->n;
+      q.x = (double *)x_d[i] + r * c->n;
+      groups[g].push_back(q);
+      where[g].push_back({i, (int)r});
+    }
+  }
+  int dev = 0;
+  PP_CUDA_TRY(cudaGetDevice(&dev));
+  cudaStream_t caller = (cudaStream_t)cuda_stream;
+  cudaEvent_t e0, e1, start;
+  PP_CUDA_TRY(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+  PP_CUDA_TRY(cudaEventCreate(&start));
+  PP_CUDA_TRY(cudaEventCreate(&e1));
+  PP_CUDA_TRY(cudaEventRecord(start, caller));
+  PP_CUDA_TRY(cudaEventRecord(e0, caller));
+  const size_t ng = groups.size();
+  std::vector<cudaStream_t> streams(ng, nullptr);
+  for (size_t g = 0; g < ng; ++g) {
+    PP_CUDA_TRY(cudaStreamCreateWithFlags(&streams[g], cudaStreamNonBlocking));
+    PP_CUDA_TRY(cudaStreamWaitEvent(streams[g], e0, 0));
+  }
+  std::vector<std::vector<SegOut>> outs(ng);
+  std::vector<int> rcs(ng, PP_OK);
+  std::vector<std::string> errs(ng);
+  std::vector<int64_t> launches(ng, 0);
+  auto work = [&](size_t g) {
+    cudaSetDevice(dev);
+    outs[g].resize(groups[g].size());
+    const int deg = keys[g].deg;
+    const pp_ctx *c0 = groups[g][0].c;
+    const int kchk = c0->opts.check_every > 0 ? c0->opts.check_every : std::max(1, 64 / (deg + 1));
+    int rc;
+    if (prec == PP_PREC_MIXED)
+      rc = run_group<dw, float>(groups[g], deg, keys[g].lanczos, side == PP_RIGHT, kchk, m_max, tol, streams[g],
+                                outs[g], &launches[g]);
+    else if (prec == PP_PREC_DW)
+      rc = run_group<dw, dw>(groups[g], deg, keys[g].lanczos, side == PP_RIGHT, kchk, m_max, tol, streams[g],
+                             outs[g], &launches[g]);
+    else
+      rc = run_group<double, double>(groups[g], deg, keys[g].lanczos, side == PP_RIGHT, kchk, m_max, tol,
+                                     streams[g], outs[g], &launches[g]);
+    rcs[g] = rc;
+    if (rc != PP_OK) errs[g] = pp_last_error();
+  };
+  std::vector<std::thread> th;
+  for (size_t g = 1; g < ng; ++g) th.emplace_back(work, g);
+  work(0);
+  for (std::thread &t : th) t.join();
+  int rc = PP_OK;
+  for (size_t g = 0; g < ng; ++g) {
+    cudaEvent_t eg;
+    if (cudaEventCreateWithFlags(&eg, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(eg, streams[g]);
+      cudaStreamWaitEvent(caller, eg, 0);
+      cudaEventDestroy(eg);
+    }
+    cudaStreamDestroy(streams[g]);
+    if (rcs[g] != PP_OK && rc == PP_OK) {
+      rc = rcs[g];
+      pp_set_error(rc, errs[g]);
+    }
+  }
+  cudaEventRecord(e1, caller);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, start, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(start);
+  if (rc != PP_OK) return rc;
+  int64_t total_launches = 0;
+  for (int64_t l : launches) total_launches += l;
+  int worst = PP_OK;
+  if (stats) {
+    for (int i = 0; i < count; ++i) {
+      memset(&stats[i], 0, sizeof(pp_stats));
+      stats[i].status = PP_OK;
+      stats[i].est_err = 0.0;
+      stats[i].ms_total = ms;
+      stats[i].launches = total_launches;
+    }
+  }
+  for (size_t g = 0; g < ng; ++g) {
+    for (size_t q = 0; q < groups[g].size(); ++q) {
+      const SegOut &o = outs[g][q];
+      const int i = where[g][q].first;
+      if (o.status != PP_OK) worst = o.status;
+      if (!stats) continue;
+      pp_stats &st = stats[i];
+      if (o.status != PP_OK) st.status = o.status;
+      st.iters = std::max(st.iters, o.iters);
+      st.breakdown |= o.breakdown;
+      st.mvms += o.mvms;
+      st.inner_products += o.ip;
+      st.est_err = std::fmax(st.est_err, o.est);
+      if (where[g][q].second == 0) st.beta0 = o.beta0;
+      st.switch_iter = o.switch_iter;
+    }
+  }
+  if (worst != PP_OK) pp_set_error(worst, "m_max reached before every stopping estimate fell below tol");
+  return worst;
+}

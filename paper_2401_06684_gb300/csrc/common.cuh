@@ -18,6 +18,13 @@ struct num<double> {
 };
 
 template <>
+struct num<float> {
+  static __device__ __forceinline__ float zero() { return 0.f; }
+  static __device__ __forceinline__ double to_d(float x) { return (double)x; }
+  static __device__ __forceinline__ float from_d(double x) { return __double2float_rn(x); }
+};
+
+template <>
 struct num<dw> {
   static __device__ __forceinline__ dw zero() { return {0.f, 0.f}; }
   static __device__ __forceinline__ double to_d(dw x) { return dw_to_double(x); }
@@ -33,6 +40,10 @@ struct acc_of<double> {
   using type = double;
 };
 template <>
+struct acc_of<float> {
+  using type = float;
+};
+template <>
 struct acc_of<dw> {
   using type = dwacc;
 };
@@ -44,6 +55,14 @@ __device__ __forceinline__ void acc_set_prod(double &a, double c, double x) { a 
 __device__ __forceinline__ void acc_add_prod(double &a, double c, double x) { a = fma(c, x, a); }
 __device__ __forceinline__ double acc_get(const double &a) { return a; }
 __device__ __forceinline__ double acc_raw(const double &a) { return a; }
+// FP32: plain FP32 arithmetic with FMA (the mixed-precision chain accumulates in FP32)
+__device__ __forceinline__ void acc_set(float &a, float x) { a = x; }
+__device__ __forceinline__ void acc_add(float &a, float x) { a = __fadd_rn(a, x); }
+__device__ __forceinline__ void acc_sub(float &a, float x) { a = __fsub_rn(a, x); }
+__device__ __forceinline__ void acc_set_prod(float &a, float c, float x) { a = __fmul_rn(c, x); }
+__device__ __forceinline__ void acc_add_prod(float &a, float c, float x) { a = __fmaf_rn(c, x, a); }
+__device__ __forceinline__ float acc_get(const float &a) { return a; }
+__device__ __forceinline__ float acc_raw(const float &a) { return a; }
 
 // Vectorised 8-byte loads through the read-only path.
 template <typename T>

@@ -1,0 +1,66 @@
+// Handle state shared by the translation units of the C ABI (api.cu, batch.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "internal.h"
+
+// Scratch vectors of the workspace: 6 for the driver and q(A), a 7th for
+// the intermediate D x of the Wilson operator.
+constexpr int kTmpVecs = 7;
+
+struct Workspace {
+  int prec = -1;
+  int m_cap = 0;
+  bool has_y = false;
+  int64_t ldv = 0;
+  size_t esz = 0;
+  void *V = nullptr;
+  void *Y = nullptr;
+  void *tmp = nullptr;  // kTmpVecs vectors
+  double *dmem = nullptr;
+  size_t dmem_n = 0;
+  double *hess = nullptr;
+  size_t hess_n = 0;
+  DevStatus *st = nullptr;
+  DevStatus *st_host = nullptr;
+  double *io = nullptr;  // 2 n doubles for pp_apply_host
+  void *val_dw = nullptr;
+  void *val_f = nullptr;  // FP32 CSR values (PP_PREC_MIXED)
+  void *Vf = nullptr;     // FP32 basis of the second phase (PP_PREC_MIXED)
+  void *Yf = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+struct pp_ctx {
+  int op_kind = OPK_CSR;
+  int stencil = -1;
+  int64_t n = 0;
+  int64_t dims[4] = {0, 0, 0, 0};
+  double st_d = 0, st_cm = 0, st_cp = 0, ch = 0;
+  const int64_t *rowptr = nullptr;
+  const int32_t *col = nullptr;
+  const double *val = nullptr;
+  int64_t nnz = 0;
+  const void *links = nullptr;  // Wilson: complex64 links (caller-owned)
+  double mass = 0.0;
+  int hermitian = 0;
+  cudaStream_t stream = nullptr;
+  pp_opts opts;
+  bool have_poly = false;
+  int degree = 0;
+  std::vector<double> coef;
+  double a = 0, b = 0, img_lo = 0, img_hi = 0;
+  std::vector<double> qsig, qwt;
+  int tile_bdx = 0;  // stencil block x-size chosen by pp_autotune (0 = default)
+  bool quad_uploaded = false;
+  Workspace ws;
+  // operator-launch accounting of the current call (pp_stats.chain_*)
+  int64_t chain_launches = 0;
+  double chain_bytes = 0.0;
+  std::vector<cudaEvent_t> prof_ev;  // start/stop pairs, grown on demand
+  size_t prof_used = 0;
+};
+

@@ -8,7 +8,7 @@
 
 #include "../../include/pp.h"
 
-enum OpKind { OPK_CSR = 0, OPK_ST2D = 1, OPK_ST3D = 2 };
+enum OpKind { OPK_CSR = 0, OPK_ST2D = 1, OPK_ST3D = 2, OPK_WILSON = 3 };
 
 // Everything a kernel needs to apply A.  Stencil rows are
 //   (A x)_c = d x_c + cm * (x at -1 offsets) + cp * (x at +1 offsets).
@@ -19,7 +19,14 @@ struct OpDesc {
   double d, cm, cp;
   const int64_t *rowptr;
   const int32_t *col;
-  const void *val;  // CSR values in the vector arithmetic (double or dw)
+  const void *val;  // CSR values in the vector arithmetic (double, dw or float)
+  // Wilson D^H D: lattice extents, mass shift, complex64 links and one
+  // scratch vector (in the vector arithmetic) for the intermediate D x
+  int64_t L[4];
+  double mass;
+  const void *links;
+  void *tmp;
+  int tile_bdx;  // stencil kernels: threads per block in x (0 = sized to the row)
 };
 
 // out = alpha * (A x) + beta * x  [- y]  [+ delta * v]
@@ -32,43 +39,100 @@ template <typename T>
 int op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &c,
             cudaStream_t s);
 
+// Constants of one stencil row: K0 x_c + Km (sum of -1 neighbours) + Kp (sum
+// of +1 neighbours) [- y] [+ D v], in the vector arithmetic.
+template <typename T>
+struct Konst {
+  T K0, Km, Kp, D;
+};
+
+// One grid of a batched stencil launch: rows [off, off + nx ny nz) of the
+// concatenated vectors, gx x gy blocks per plane, first flat block blk0.
+struct BatchSeg {
+  int64_t off;
+  int nx, ny, nz;
+  unsigned gx, gy, blk0;
+};
+// Threads in x of a batched stencil block (128 threads per block).
+constexpr int kBatchBlockX = 32;
+
+// Host: Konst of out = alpha A x + beta x [- y] + delta v for every segment
+// (stencil diagonal d, neighbour weights cm / cp, coefficients c[i]).
+template <typename T>
+void batch_konst(const double *d, const double *cm, const double *cp, const StepCoef *c, int nseg,
+                 Konst<T> *out);
+// Batched stencil step over all segments (P entries per thread: 1, or the
+// 16-byte width when every segment's nx allows it); inactive segments skipped.
+template <typename T>
+int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Konst<T> *K, const int *active,
+                  const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v, cudaStream_t s);
+
+// Wilson D^H D step (wilson.cu): t = D x into op.tmp, then
+// out = alpha D^H t + beta x [- y] [+ delta v]
+template <typename T>
+int wilson_op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &c,
+                   cudaStream_t s);
+
 // ---- vector kernels (vec.cu) ----
+// A vector may be the concatenation of independent problems ("segments"),
+// each padded to whole chunks of vec_chunk_rows() rows (padding zero).
+// nseg = 1 (the default) is a single vector.
+struct Seg {
+  int nseg = 1;
+  const int *chunk_seg = nullptr;  // segment of each chunk (device)
+  const int *chunk0 = nullptr;     // first chunk of each segment, nseg + 1 entries (device)
+  const int *active = nullptr;     // nonzero while the segment iterates (device; NULL = all)
+  int64_t dstride = 0;             // doubles between consecutive segments' FP64 scratch
+};
+
 // Number of row chunks (= blocks, = partial sums) of the reduction kernels.
 int vec_nchunks(int64_t n);
+int vec_chunk_rows();
 template <typename T>
 int vec_from_f64(const double *in, T *out, int64_t n, cudaStream_t s);
 template <typename T>
 int vec_to_f64(const T *in, double *out, int64_t n, cudaStream_t s);
+// out = in * c * c_dev[segment] (c_dev may be NULL)
 template <typename T>
-int vec_scale(const T *in, T *out, int64_t n, double c, const double *c_dev, cudaStream_t s);
+int vec_scale(const T *in, T *out, int64_t n, double c, const double *c_dev, cudaStream_t s,
+              const Seg &S = Seg());
 template <typename T>
 int vec_copy(const T *in, T *out, int64_t n, cudaStream_t s);
-// partials[b] = sum over block b of x.y   (nb blocks)
+// partials[chunk] = sum over the chunk of x.y
 template <typename T>
-int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int nb, cudaStream_t s);
+int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int nb, cudaStream_t s,
+                     const Seg &S = Seg());
 // w -= alpha v_j + beta v_{j-1} (vjm1 may be NULL); norm^2 partials
 template <typename T>
 int vec_lanczos_update(T *w, const T *vj, const T *vjm1, int64_t n, const double *alpha,
-                       const double *beta_prev, double *partials, int nb, cudaStream_t s);
-// partials[b*J + c] = sum over block b of V_c . w
+                       const double *beta_prev, double *partials, int nb, cudaStream_t s,
+                       const Seg &S = Seg());
+// partials[chunk*J + c] = sum over the chunk of V_c . w
 template <typename T>
 int vec_multi_dot(const T *V, int64_t ldv, int J, const T *w, int64_t n, double *partials, int nb,
-                  cudaStream_t s);
-// w -= V h  (h on device, J entries); norm^2 partials if partials != NULL
+                  cudaStream_t s, const Seg &S = Seg());
+// w -= V h  (h on device, J entries per segment); norm^2 partials if partials != NULL
 template <typename T>
 int vec_multi_update(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n,
-                     double *partials, int nb, cudaStream_t s);
-// x = V z, FP64 output
+                     double *partials, int nb, cudaStream_t s, const Seg &S = Seg());
+// x = V z (accumulate = 0) or x += V z (accumulate = 1), FP64 output; with
+// m_seg, segment s uses min(m, m_seg[s]) columns
 template <typename T>
 int vec_reconstruct(const T *V, int64_t ldv, int m, const double *z, double *x, int64_t n,
-                    cudaStream_t s);
+                    int accumulate, cudaStream_t s, const Seg &S = Seg(), const int *m_seg = nullptr);
+// out[i] = fixed pseudo-random value in [-1, 1) (instantiated for double, dw)
+template <typename T>
+int vec_fill_hash(T *out, int64_t n, uint64_t seed, cudaStream_t s);
+// out = in rounded to the output arithmetic (instantiated for dw -> float)
+template <typename TI, typename TO>
+int vec_convert(const TI *in, TO *out, int64_t n, cudaStream_t s);
 
-// Reduction of block partials (vec.cu).
+// Reduction of chunk partials per (column, segment):
 //   mode 0: out_a[c] = s_c
 //   mode 1: out_a[c] = s_c, out_b[c] = s_c
 //   mode 2: out_a[c] = s_c, out_b[c] += s_c
 int reduce_cols(const double *partials, int nb, int ncols, int mode, double *out_a, double *out_b,
-                cudaStream_t s);
+                cudaStream_t s, const Seg &S = Seg());
 
 // Norm finalization: beta = sqrt(sum partials); *beta_out = beta; *inv_out = 1/beta or 0 on
 // breakdown, i.e. beta <= rel * ||ref[0..nref)|| (nref = 0: only beta == 0 or non-finite).
@@ -85,17 +149,20 @@ struct DevStatus {
 };
 int norm_finalize(const double *partials, int nb, double *beta_out, double *inv_out,
                   const double *ref, int nref, double rel, int m_here, DevStatus *st,
-                  cudaStream_t s);
+                  cudaStream_t s, const Seg &S = Seg());
 
 // ---- small projected solve (small.cu) ----
 // X[k*m + i] = w_k ((H_m + s_k I)^{-1} e_1)_i for the K quadrature nodes.
+// With segments, every per-segment array (H, sig, wt, X, scratch, z, zprev)
+// sits at base + segment * S.dstride and st at st + segment; the global
+// Hessenberg scratch of large m holds nseg * K blocks.
 int small_tridiag_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
-                       double *X, double *scratch, cudaStream_t s);
+                       double *X, double *scratch, cudaStream_t s, const Seg &S = Seg());
 int small_hess_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
-                    double *X, double *scratch, cudaStream_t s);
+                    double *X, double *scratch, cudaStream_t s, const Seg &S = Seg());
 // z = beta0 * sum_k X[k] ; est = ||z - [zprev;0]|| / ||z||; conv = est < tol; zprev <- z
 int small_combine(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol,
-                  DevStatus *st, cudaStream_t s);
+                  DevStatus *st, cudaStream_t s, const Seg &S = Seg());
 
 // ---- host-side construction (poly.cpp) ----
 // Chebyshev interpolant of z^{-1/2} at d = degree+1 first-kind nodes of [a,b].

@@ -6,7 +6,8 @@
 // (a+b) I)/(b-a).  The stencil is folded into three constants
 //     K0 = alpha d + beta, Km = alpha cm, Kp = alpha cp,
 // so one pass reads x (with its neighbours), y, v and writes out: 4 vectors
-// of HBM traffic per step for the matrix-free operators.
+// of HBM traffic per step for the matrix-free operators.  The arithmetic is
+// that of the vectors: FP64, double-word pairs or FP32.
 #include "common.cuh"
 #include "internal.h"
 
@@ -21,108 +22,147 @@ __device__ __forceinline__ dw shfl_xor_t<dw>(dw v, int o, int width) {
   return {__shfl_xor_sync(0xffffffffu, v.hi, o, width), __shfl_xor_sync(0xffffffffu, v.lo, o, width)};
 }
 
-template <typename T>
-struct Konst {
-  T K0, Km, Kp, D;
-};
 
-// 3D 7-point: thread per (i,j) column, marching over a chunk of k.  The
-// k-1 / k / k+1 values stay in registers and every load of plane k+1 is
-// issued before plane k is computed (one plane of software prefetch); in-plane
-// neighbours come through L1.  The row is evaluated as one compensated linear
-// combination K0 x_c + Km (sum of -1 neighbours) + Kp (sum of +1 neighbours)
-// - y + D v.
+// One stencil row evaluated as a compensated linear combination
+//   K0 x_c + Km (x_w + x_s + x_d) + Kp (x_e + x_n + x_u) [- y] [+ D v].
 template <typename T, bool SUB_Y, bool ADD_V>
-__global__ void __launch_bounds__(256) st3d_step(const T *__restrict__ x, const T *__restrict__ y,
-                                                 const T *__restrict__ v, T *__restrict__ out,
-                                                 int nx, int ny, int nz, int kchunk, Konst<T> K) {
+__device__ __forceinline__ T stencil_row(T xc, T xw, T xe, T xs, T xn, T xd, T xu, T yy, T vv,
+                                         const Konst<T> &K) {
   using A = typename acc_of<T>::type;
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y;
-  const int k0 = blockIdx.z * kchunk;
-  const int k1 = min(nz, k0 + kchunk);
-  if (i >= nx || j >= ny || k0 >= nz) return;
-  const int64_t plane = (int64_t)nx * ny;
-  const bool hw = i > 0, he = i + 1 < nx, hs = j > 0, hn = j + 1 < ny;
-  const T zero = num<T>::zero();
-  int64_t off = (int64_t)k0 * plane + (int64_t)j * nx + i;
-  T xm = (k0 > 0) ? ldg(x + off - plane) : zero;
-  T xc = ldg(x + off);
-  T xu = (k0 + 1 < nz) ? ldg(x + off + plane) : zero;
-  T xw = hw ? ldg(x + off - 1) : zero;
-  T xe = he ? ldg(x + off + 1) : zero;
-  T xs = hs ? ldg(x + off - nx) : zero;
-  T xn = hn ? ldg(x + off + nx) : zero;
-  T yy = SUB_Y ? ldg(y + off) : zero;
-  T vv = ADD_V ? ldg(v + off) : zero;
-  for (int k = k0; k < k1; ++k) {
-    const int64_t offn = off + plane;
-    const bool more = k + 1 < k1;
-    T xu2 = zero, xw2 = zero, xe2 = zero, xs2 = zero, xn2 = zero, y2 = zero, v2 = zero;
-    if (more) {
-      if (k + 2 < nz) xu2 = ldg(x + offn + plane);
-      if (hw) xw2 = ldg(x + offn - 1);
-      if (he) xe2 = ldg(x + offn + 1);
-      if (hs) xs2 = ldg(x + offn - nx);
-      if (hn) xn2 = ldg(x + offn + nx);
-      if (SUB_Y) y2 = ldg(y + offn);
-      if (ADD_V) v2 = ldg(v + offn);
-    }
-    A nm, np, r;
-    acc_set(nm, xm);
-    acc_add(nm, xw);
-    acc_add(nm, xs);
-    acc_set(np, xu);
-    acc_add(np, xe);
-    acc_add(np, xn);
-    acc_set_prod(r, K.K0, xc);
-    acc_add_prod(r, K.Km, acc_raw(nm));
-    acc_add_prod(r, K.Kp, acc_raw(np));
-    if (SUB_Y) acc_sub(r, yy);
-    if (ADD_V) acc_add_prod(r, K.D, vv);
-    out[off] = acc_get(r);
-    xm = xc;
-    xc = xu;
-    xu = xu2;
-    xw = xw2;
-    xe = xe2;
-    xs = xs2;
-    xn = xn2;
-    yy = y2;
-    vv = v2;
-    off = offn;
-  }
-}
-
-// 2D 5-point: thread per grid point.
-template <typename T, bool SUB_Y, bool ADD_V>
-__global__ void __launch_bounds__(256) st2d_step(const T *__restrict__ x, const T *__restrict__ y,
-                                                 const T *__restrict__ v, T *__restrict__ out,
-                                                 int nx, int ny, Konst<T> K) {
-  using A = typename acc_of<T>::type;
-  const int i = blockIdx.x * 32 + threadIdx.x;
-  const int j = blockIdx.y * 8 + threadIdx.y;
-  if (i >= nx || j >= ny) return;
-  const int64_t id = (int64_t)j * nx + i;
-  const T zero = num<T>::zero();
-  const T xw = (i > 0) ? ldg(x + id - 1) : zero;
-  const T xe = (i + 1 < nx) ? ldg(x + id + 1) : zero;
-  const T xs = (j > 0) ? ldg(x + id - nx) : zero;
-  const T xn = (j + 1 < ny) ? ldg(x + id + nx) : zero;
-  const T xc = ldg(x + id);
-  const T yy = SUB_Y ? ldg(y + id) : zero;
-  const T vv = ADD_V ? ldg(v + id) : zero;
   A nm, np, r;
-  acc_set(nm, xw);
+  acc_set(nm, xd);
+  acc_add(nm, xw);
   acc_add(nm, xs);
-  acc_set(np, xe);
+  acc_set(np, xu);
+  acc_add(np, xe);
   acc_add(np, xn);
   acc_set_prod(r, K.K0, xc);
   acc_add_prod(r, K.Km, acc_raw(nm));
   acc_add_prod(r, K.Kp, acc_raw(np));
   if (SUB_Y) acc_sub(r, yy);
   if (ADD_V) acc_add_prod(r, K.D, vv);
-  out[id] = acc_get(r);
+  return acc_get(r);
+}
+
+// P consecutive entries through one vector load / store of P * sizeof(T)
+// bytes (4, 8 or 16; the address must be aligned to it).
+template <int BYTES>
+struct raw_vec;
+template <>
+struct raw_vec<16> {
+  using type = int4;
+};
+template <>
+struct raw_vec<8> {
+  using type = int2;
+};
+template <>
+struct raw_vec<4> {
+  using type = int;
+};
+
+template <typename T, int P>
+__device__ __forceinline__ void ld_p(const T *p, T (&r)[P]) {
+  using R = typename raw_vec<sizeof(T) * P>::type;
+  const R v = __ldg(reinterpret_cast<const R *>(p));
+  memcpy(r, &v, sizeof(R));
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void st_p(T *p, const T (&r)[P]) {
+  using R = typename raw_vec<sizeof(T) * P>::type;
+  R v;
+  memcpy(&v, r, sizeof(R));
+  *reinterpret_cast<R *>(p) = v;
+}
+
+template <typename T, int P>
+__device__ __forceinline__ void zero_p(T (&r)[P]) {
+#pragma unroll
+  for (int q = 0; q < P; ++q) r[q] = num<T>::zero();
+}
+
+constexpr int ST_THREADS = 128;  // threads per block of the stencil kernels
+
+// 2D 5-point and 3D 7-point stencils (nz = 1 for 2D): one thread per P
+// consecutive x entries of one grid row, one block per blockDim.x * P x
+// blockDim.y tile of one plane (blockDim.x sized to the row so no thread is
+// idle on rows shorter than 64 P); the flat block index runs over (x tile,
+// y tile, plane).  Every load is a coalesced vector load: the row itself, its four
+// y/z neighbour rows, y and v; the two x neighbours outside the thread's P
+// entries are scalar loads.  Neighbour reuse between threads and planes is
+// left to L1/L2.  Requires nx % P == 0 and P * sizeof(T)-aligned pointers.
+template <typename T, int P, bool SUB_Y, bool ADD_V>
+__device__ __forceinline__ void stencil_rows(const T *__restrict__ x, const T *__restrict__ y,
+                                             const T *__restrict__ v, T *__restrict__ out, int nx, int ny,
+                                             int nz, int i0, int j, int k, const Konst<T> &K) {
+  const int64_t plane = (int64_t)nx * ny;
+  const int64_t off = (int64_t)k * plane + (int64_t)j * nx + i0;
+  const T zero = num<T>::zero();
+  T xc[P], xs[P], xn[P], xd[P], xu[P], yy[P], vv[P];
+  ld_p<T, P>(x + off, xc);
+  if (j > 0) ld_p<T, P>(x + off - nx, xs); else zero_p<T, P>(xs);
+  if (j + 1 < ny) ld_p<T, P>(x + off + nx, xn); else zero_p<T, P>(xn);
+  if (k > 0) ld_p<T, P>(x + off - plane, xd); else zero_p<T, P>(xd);
+  if (k + 1 < nz) ld_p<T, P>(x + off + plane, xu); else zero_p<T, P>(xu);
+  if (SUB_Y) ld_p<T, P>(y + off, yy); else zero_p<T, P>(yy);
+  if (ADD_V) ld_p<T, P>(v + off, vv); else zero_p<T, P>(vv);
+  const T xw0 = i0 > 0 ? ldg(x + off - 1) : zero;
+  const T xeP = i0 + P < nx ? ldg(x + off + P) : zero;
+  T o[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) {
+    const T xw = q == 0 ? xw0 : xc[q - 1];
+    const T xe = q == P - 1 ? xeP : xc[q + 1];
+    o[q] = stencil_row<T, SUB_Y, ADD_V>(xc[q], xw, xe, xs[q], xn[q], xd[q], xu[q], yy[q], vv[q], K);
+  }
+  st_p<T, P>(out + off, o);
+}
+
+template <typename T, int P, bool SUB_Y, bool ADD_V>
+__global__ void __launch_bounds__(ST_THREADS) st_step(const T *__restrict__ x, const T *__restrict__ y,
+                                                        const T *__restrict__ v, T *__restrict__ out,
+                                                        int nx, int ny, int nz, unsigned gx, unsigned gy,
+                                                        Konst<T> K) {
+  const unsigned blk = blockIdx.x;
+  const unsigned bx = blk % gx, rest = blk / gx;
+  const unsigned by = rest % gy;
+  const int k = (int)(rest / gy);
+  const int i0 = (int)(bx * blockDim.x + threadIdx.x) * P;
+  const int j = (int)(by * blockDim.y + threadIdx.y);
+  if (i0 >= nx || j >= ny) return;
+  stencil_rows<T, P, SUB_Y, ADD_V>(x, y, v, out, nx, ny, nz, i0, j, k, K);
+}
+
+// Batched form: many grids (segments of concatenated vectors) in one launch.
+// The flat block index is located in the segments' first-block table by
+// binary search; each segment has its own geometry and constants.
+template <typename T, int P, bool SUB_Y, bool ADD_V>
+__global__ void __launch_bounds__(ST_THREADS) bst_step(const T *__restrict__ x, const T *__restrict__ y,
+                                                         const T *__restrict__ v, T *__restrict__ out,
+                                                         const BatchSeg *__restrict__ segs, int nseg,
+                                                         const Konst<T> *__restrict__ K,
+                                                         const int *__restrict__ active) {
+  const unsigned blk = blockIdx.x;
+  int lo = 0, hi = nseg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (segs[mid].blk0 <= blk)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  if (active && !active[lo]) return;
+  const BatchSeg g = segs[lo];
+  const unsigned b = blk - g.blk0;
+  const unsigned bx = b % g.gx, rest = b / g.gx;
+  const unsigned by = rest % g.gy;
+  const int k = (int)(rest / g.gy);
+  const int i0 = (int)(bx * blockDim.x + threadIdx.x) * P;
+  const int j = (int)(by * blockDim.y + threadIdx.y);
+  if (i0 >= g.nx || j >= g.ny) return;
+  stencil_rows<T, P, SUB_Y, ADD_V>(x + g.off, SUB_Y ? y + g.off : y, ADD_V ? v + g.off : v, out + g.off,
+                                   g.nx, g.ny, g.nz, i0, j, k, K[lo]);
 }
 
 // CSR: L lanes per row, lane-strided over the row's entries, shuffle sum.
@@ -163,19 +203,12 @@ double host_const<double>(double v) {
   return v;
 }
 template <>
+float host_const<float>(double v) {
+  return (float)v;
+}
+template <>
 dw host_const<dw>(double v) {
   return dw_split_host(v);
-}
-
-int g_sm_count = 0;
-int sm_count() {
-  if (g_sm_count == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_sm_count, cudaDevAttrMultiProcessorCount, dev);
-    if (g_sm_count <= 0) g_sm_count = 152;
-  }
-  return g_sm_count;
 }
 
 template <typename T, bool SY, bool AV>
@@ -195,21 +228,28 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     K.Km = host_const<T>(c.alpha * op.cm);
     K.Kp = host_const<T>(c.alpha * op.cp);
     K.D = host_const<T>(c.delta);
-    dim3 blk(32, 8);
-    if (op.kind == OPK_ST2D) {
-      dim3 grd((unsigned)((op.nx + 31) / 32), (unsigned)((op.ny + 7) / 8));
-      st2d_step<T, SY, AV><<<grd, blk, 0, s>>>(x, y, v, out, (int)op.nx, (int)op.ny, K);
-    } else {
-      const int64_t bxy = ((op.nx + 31) / 32) * ((op.ny + 7) / 8);
-      const int64_t want = 8LL * sm_count();
-      int64_t nzc = (want + bxy - 1) / bxy;
-      if (nzc > op.nz) nzc = op.nz;
-      if (nzc < 1) nzc = 1;
-      const int kchunk = (int)((op.nz + nzc - 1) / nzc);
-      nzc = (op.nz + kchunk - 1) / kchunk;
-      dim3 grd((unsigned)((op.nx + 31) / 32), (unsigned)((op.ny + 7) / 8), (unsigned)nzc);
-      st3d_step<T, SY, AV><<<grd, blk, 0, s>>>(x, y, v, out, (int)op.nx, (int)op.ny, (int)op.nz, kchunk, K);
-    }
+    const int nz = op.kind == OPK_ST2D ? 1 : (int)op.nz;
+    // widest vector access the row length and every pointer allow
+    constexpr int PW = 16 / (int)sizeof(T);
+    const size_t align = (size_t)PW * sizeof(T);
+    auto ok = [&](const void *p) { return p == nullptr || ((uintptr_t)p % align) == 0; };
+    const bool vec = op.nx % PW == 0 && ok(x) && ok(out) && (!SY || ok(y)) && (!AV || ok(v));
+    const int P = vec ? PW : 1;
+    // threads in x: the row's thread count rounded up to a power of two, 8 .. 64
+    const int64_t tx = op.nx / P;
+    int bdx = 8;
+    while (bdx < 64 && bdx < tx) bdx *= 2;
+    if (op.tile_bdx >= 8 && op.tile_bdx <= 128 && (op.tile_bdx & (op.tile_bdx - 1)) == 0) bdx = op.tile_bdx;
+    const int bdy = ST_THREADS / bdx;
+    const unsigned gx = (unsigned)((tx + bdx - 1) / bdx);
+    const unsigned gy = (unsigned)((op.ny + bdy - 1) / bdy);
+    const uint64_t nblk = (uint64_t)gx * gy * (uint64_t)nz;
+    if (nblk > 0x7fffffffull) return pp_set_error(PP_ERR_INVALID_ARG, "grid too large for one launch");
+    const dim3 blk(bdx, bdy);
+    if (vec)
+      st_step<T, PW, SY, AV><<<(unsigned)nblk, blk, 0, s>>>(x, y, v, out, (int)op.nx, (int)op.ny, nz, gx, gy, K);
+    else
+      st_step<T, 1, SY, AV><<<(unsigned)nblk, blk, 0, s>>>(x, y, v, out, (int)op.nx, (int)op.ny, nz, gx, gy, K);
   }
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
@@ -221,13 +261,59 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
 template <typename T>
 int op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &c,
             cudaStream_t s) {
+  if (op.kind == OPK_WILSON) return wilson_op_step<T>(op, x, y, v, out, c, s);
   if (c.sub_y && c.add_v) return launch_step<T, true, true>(op, x, y, v, out, c, s);
   if (c.sub_y) return launch_step<T, true, false>(op, x, y, v, out, c, s);
   if (c.add_v) return launch_step<T, false, true>(op, x, y, v, out, c, s);
   return launch_step<T, false, false>(op, x, y, v, out, c, s);
 }
 
+template <typename T>
+void batch_konst(const double *d, const double *cm, const double *cp, const StepCoef *c, int nseg,
+                 Konst<T> *out) {
+  for (int i = 0; i < nseg; ++i) {
+    out[i].K0 = host_const<T>(c[i].alpha * d[i] + c[i].beta);
+    out[i].Km = host_const<T>(c[i].alpha * cm[i]);
+    out[i].Kp = host_const<T>(c[i].alpha * cp[i]);
+    out[i].D = host_const<T>(c[i].delta);
+  }
+}
+
+template <typename T>
+int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Konst<T> *K, const int *active,
+                  const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v, cudaStream_t s) {
+  constexpr int PW = 16 / (int)sizeof(T);
+  const dim3 blk(kBatchBlockX, ST_THREADS / kBatchBlockX);
+#define PP_BST(PP, SY, AV) bst_step<T, PP, SY, AV><<<nblk, blk, 0, s>>>(x, y, v, out, segs, nseg, K, active)
+  if (P == PW) {
+    if (sub_y && add_v) PP_BST(PW, true, true);
+    else if (sub_y) PP_BST(PW, true, false);
+    else if (add_v) PP_BST(PW, false, true);
+    else PP_BST(PW, false, false);
+  } else {
+    if (sub_y && add_v) PP_BST(1, true, true);
+    else if (sub_y) PP_BST(1, true, false);
+    else if (add_v) PP_BST(1, false, true);
+    else PP_BST(1, false, false);
+  }
+#undef PP_BST
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
+#define PP_BINST(T)                                                                                   \
+  template void batch_konst<T>(const double *, const double *, const double *, const StepCoef *, int, \
+                               Konst<T> *);                                                          \
+  template int op_step_batch<T>(const BatchSeg *, int, unsigned, int, const Konst<T> *, const int *,  \
+                                const T *, const T *, const T *, T *, bool, bool, cudaStream_t);
+PP_BINST(double)
+PP_BINST(float)
+PP_BINST(dw)
+
 template int op_step<double>(const OpDesc &, const double *, const double *, const double *, double *,
                              const StepCoef &, cudaStream_t);
+template int op_step<float>(const OpDesc &, const float *, const float *, const float *, float *,
+                            const StepCoef &, cudaStream_t);
 template int op_step<dw>(const OpDesc &, const dw *, const dw *, const dw *, dw *, const StepCoef &,
                          cudaStream_t);

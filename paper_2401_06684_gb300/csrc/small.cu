@@ -24,9 +24,16 @@ namespace {
 // Hessenberg storage: alpha_i = H[i,i], beta_i = H[i+1,i].
 __global__ void k_tri_quad(const double *__restrict__ H, int ldh, int m, const double *__restrict__ sig,
                            const double *__restrict__ wt, int K, double *__restrict__ X,
-                           double *__restrict__ scratch) {
+                           double *__restrict__ scratch, Seg S) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= K) return;
+  const int seg = blockIdx.y;
+  if (k >= K || (S.active && !S.active[seg])) return;
+  const int64_t so = seg * S.dstride;
+  H += so;
+  sig += so;
+  wt += so;
+  X += so;
+  scratch += so;
   const double s = sig[k];
   double *cp = scratch + (int64_t)k * m;  // modified super-diagonal
   double *x = X + (int64_t)k * m;         // modified rhs, then solution
@@ -63,11 +70,19 @@ __global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H,
                                                    const double *__restrict__ sig,
                                                    const double *__restrict__ wt,
                                                    double *__restrict__ X, double *__restrict__ gscratch,
-                                                   int use_smem) {
+                                                   int use_smem, Seg S) {
   extern __shared__ double sm[];
   const int k = blockIdx.x;
+  const int seg = blockIdx.y;
+  if (S.active && !S.active[seg]) return;
+  const int64_t so = seg * S.dstride;
+  H += so;
+  sig += so;
+  wt += so;
+  X += so;
   const int ld = m + 1;
-  double *M = use_smem ? sm : gscratch + (int64_t)k * ((int64_t)ld * m + 2 * m);
+  double *M = use_smem ? sm
+                       : gscratch + ((int64_t)seg * gridDim.x + k) * ((int64_t)ld * m + 2 * m);
   double *g = M + (int64_t)ld * m;  // rhs / solution, m entries
   const double s = sig[k];
   for (int c = 0; c < m; ++c)
@@ -115,11 +130,17 @@ __global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H,
 __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict__ H, int ldh, int m,
                                                         const double *__restrict__ sig,
                                                         const double *__restrict__ wt, int K,
-                                                        double *__restrict__ X) {
+                                                        double *__restrict__ X, Seg S) {
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int k = blockIdx.x * (blockDim.x >> 5) + wid;
-  if (k >= K) return;  // whole warp leaves together
+  const int seg = blockIdx.y;
+  if (k >= K || (S.active && !S.active[seg])) return;  // whole warp leaves together
+  const int64_t so = seg * S.dstride;
+  H += so;
+  sig += so;
+  wt += so;
+  X += so;
   const int ld = m + 1;
   double *M = sm + (int64_t)wid * ((int64_t)ld * m + m);
   double *g = M + (int64_t)ld * m;
@@ -167,8 +188,15 @@ __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict
 // nodes, fixed shuffle tree), then the stopping estimate over the components.
 __global__ void __launch_bounds__(1024) k_combine(const double *__restrict__ X, int K, int m, int mprev,
                                                   double *__restrict__ z, double *__restrict__ zprev,
-                                                  double tol, DevStatus *st) {
+                                                  double tol, DevStatus *st, Seg S) {
   __shared__ double rd[32], rz[32];
+  const int seg = blockIdx.x;
+  if (S.active && !S.active[seg]) return;
+  const int64_t so = seg * S.dstride;
+  X += so;
+  z += so;
+  zprev += so;
+  st += seg;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double beta0 = st->beta0;
   double d2 = 0.0, z2 = 0.0;
@@ -204,22 +232,22 @@ __global__ void __launch_bounds__(1024) k_combine(const double *__restrict__ X, 
 }  // namespace
 
 int small_tridiag_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
-                       double *X, double *scratch, cudaStream_t s) {
-  k_tri_quad<<<(K + 127) / 128, 128, 0, s>>>(H, ldh, m, sig, wt, K, X, scratch);
+                       double *X, double *scratch, cudaStream_t s, const Seg &S) {
+  k_tri_quad<<<dim3((K + 127) / 128, S.nseg), 128, 0, s>>>(H, ldh, m, sig, wt, K, X, scratch, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 
 int small_hess_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
-                    double *X, double *scratch, cudaStream_t s) {
+                    double *X, double *scratch, cudaStream_t s, const Seg &S) {
   if (m <= 64) {
     const size_t per_warp = ((size_t)(m + 1) * m + m) * sizeof(double);
     int wpb = (int)((48 * 1024) / per_warp);
     if (wpb > 8) wpb = 8;
     if (wpb < 1) wpb = 1;
     const unsigned grid = (unsigned)((K + wpb - 1) / wpb);
-    k_hess_quad_warp<<<grid, 32 * wpb, per_warp * wpb, s>>>(H, ldh, m, sig, wt, K, X);
+    k_hess_quad_warp<<<dim3(grid, S.nseg), 32 * wpb, per_warp * wpb, s>>>(H, ldh, m, sig, wt, K, X, S);
     ++pp_launch_count();
     PP_CUDA_TRY(cudaGetLastError());
     return PP_OK;
@@ -229,7 +257,7 @@ int small_hess_quad(const double *H, int ldh, int m, const double *sig, const do
   const int use_smem = bytes <= kSmemMax ? 1 : 0;
   if (use_smem && bytes > 48 * 1024)
     PP_CUDA_TRY(cudaFuncSetAttribute(k_hess_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  k_hess_quad<<<K, 128, use_smem ? bytes : 0, s>>>(H, ldh, m, sig, wt, X, scratch, use_smem);
+  k_hess_quad<<<dim3(K, S.nseg), 128, use_smem ? bytes : 0, s>>>(H, ldh, m, sig, wt, X, scratch, use_smem, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -240,8 +268,8 @@ size_t small_hess_scratch_doubles(int m, int K) {
 }
 
 int small_combine(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol,
-                  DevStatus *st, cudaStream_t s) {
-  k_combine<<<1, 1024, 0, s>>>(X, K, m, mprev, z, zprev, tol, st);
+                  DevStatus *st, cudaStream_t s, const Seg &S) {
+  k_combine<<<S.nseg, 1024, 0, s>>>(X, K, m, mprev, z, zprev, tol, st, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;

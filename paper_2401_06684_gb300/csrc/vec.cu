@@ -1,16 +1,23 @@
 // Vector kernels of the Krylov process: conversions at the API boundary,
 // inner products, the Lanczos three-term update, classical Gram-Schmidt
-// sweeps against the stored basis (Algorithm 1, lines 5-9, done as two CGS
-// passes), and the reconstruction f_m = V_m z (Algorithm 1, last line).
+// sweeps against the stored basis (the orthogonalization loop of
+// Algorithm 1, done as two CGS passes), and the reconstruction f_m = V_m z
+// (the final step of Algorithm 1).
 //
 // Layout: every block owns a chunk of CHUNK = 2048 consecutive rows; thread t
 // owns rows chunk + t + 256 u, u < 8, so each column sweep issues 8
 // independent coalesced loads per thread.  Products accumulate in the vector
-// arithmetic (FP64, or the compensated double-word accumulator); warp
+// arithmetic (FP64, FP32, or the compensated double-word accumulator); warp
 // reductions stay in that arithmetic and only the 8 warp sums of a block are
 // widened to FP64, so every block writes one FP64 partial per column and a
 // fixed-order pass over the partials finishes the sum (results are bitwise
 // reproducible run to run).
+//
+// Segments (Seg): a vector may be the concatenation of several independent
+// problems ("segments", each padded to whole chunks, padding kept at zero).
+// A block finds its segment from the chunk table, skips inactive segments,
+// and reads its per-segment FP64 scalars at base + segment * dstride.  A
+// single vector is the case nseg = 1.
 #include "common.cuh"
 #include "internal.h"
 
@@ -22,6 +29,11 @@ constexpr int CHUNK = TPB * U;
 constexpr int CG = 8;  // columns per block in the multi-dot
 
 __device__ __forceinline__ double warp_reduce_d(double v) { return warp_sum(v); }
+__device__ __forceinline__ float warp_reduce_d(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 __device__ __forceinline__ dw warp_reduce_d(dw v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -45,6 +57,14 @@ __device__ __forceinline__ double block_reduce_to_d(T v, double *red) {
   return s;
 }
 
+// Segment of the chunk a block owns, and whether it still iterates.
+__device__ __forceinline__ int chunk_seg(const Seg &S, int64_t chunk) {
+  return S.chunk_seg ? __ldg(S.chunk_seg + chunk) : 0;
+}
+__device__ __forceinline__ bool seg_active(const Seg &S, int seg) {
+  return !S.active || __ldg(S.active + seg) != 0;
+}
+
 template <typename T>
 __global__ void k_from_f64(const double *__restrict__ in, T *__restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -57,13 +77,38 @@ __global__ void k_to_f64(const T *__restrict__ in, double *__restrict__ out, int
     out[i] = num<T>::to_d(in[i]);
 }
 
+// Fixed pseudo-random vector in [-1, 1): splitmix64 of (seed + index).
 template <typename T>
-__global__ void k_scale(const T *__restrict__ in, T *__restrict__ out, int64_t n, double c,
-                        const double *__restrict__ c_dev) {
-  const double cc = c_dev ? c * (*c_dev) : c;
-  const T ct = num<T>::from_d(cc);
+__global__ void k_fill_hash(T *__restrict__ out, int64_t n, uint64_t seed) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    out[i] = num<T>::from_d((double)(z >> 11) * 0x1p-52 - 1.0);
+  }
+}
+
+template <typename TI, typename TO>
+__global__ void k_convert(const TI *__restrict__ in, TO *__restrict__ out, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = in[i] * ct;
+    out[i] = num<TO>::from_d(num<TI>::to_d(in[i]));
+}
+
+// out = in * (c * c_dev[segment]) (c_dev may be NULL); inactive segments untouched
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_scale(const T *__restrict__ in, T *__restrict__ out, int64_t n, double c,
+                                               const double *__restrict__ c_dev, Seg S) {
+  const int seg = chunk_seg(S, blockIdx.x);
+  if (!seg_active(S, seg)) return;
+  const double cc = c_dev ? c * c_dev[seg * S.dstride] : c;
+  const T ct = num<T>::from_d(cc);
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB;
+    if (r < n) out[r] = in[r] * ct;
+  }
 }
 
 template <typename T>
@@ -75,9 +120,13 @@ __global__ void k_copy(const T *__restrict__ in, T *__restrict__ out, int64_t n)
 // partials[chunk] = sum over the chunk of x.y
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_dot(const T *__restrict__ x, const T *__restrict__ y, int64_t n,
-                                             double *__restrict__ partials) {
+                                             double *__restrict__ partials, Seg S) {
   using A = typename acc_of<T>::type;
   __shared__ double red[TPB / 32];
+  if (!seg_active(S, chunk_seg(S, blockIdx.x))) {
+    if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+    return;
+  }
   const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
   A acc;
   acc_set(acc, num<T>::zero());
@@ -96,11 +145,16 @@ __global__ void __launch_bounds__(TPB) k_lanczos_update(T *__restrict__ w, const
                                                         const T *__restrict__ vjm1, int64_t n,
                                                         const double *__restrict__ alpha,
                                                         const double *__restrict__ beta_prev,
-                                                        double *__restrict__ partials) {
+                                                        double *__restrict__ partials, Seg S) {
   using A = typename acc_of<T>::type;
   __shared__ double red[TPB / 32];
-  const T a = num<T>::from_d(-(*alpha));
-  const T b = num<T>::from_d(vjm1 ? -(*beta_prev) : 0.0);
+  const int seg = chunk_seg(S, blockIdx.x);
+  if (!seg_active(S, seg)) {
+    if (threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+    return;
+  }
+  const T a = num<T>::from_d(-alpha[seg * S.dstride]);
+  const T b = num<T>::from_d(vjm1 ? -beta_prev[seg * S.dstride] : 0.0);
   const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
   A nrm;
   acc_set(nrm, num<T>::zero());
@@ -126,12 +180,16 @@ __global__ void __launch_bounds__(TPB) k_lanczos_update(T *__restrict__ w, const
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_multi_dot(const T *__restrict__ V, int64_t ldv, int J,
                                                    const T *__restrict__ w, int64_t n,
-                                                   double *__restrict__ partials) {
+                                                   double *__restrict__ partials, Seg S) {
   using A = typename acc_of<T>::type;
   __shared__ double red[CG][TPB / 32];
-  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
   const int c0 = blockIdx.y * CG;
   const int ncol = min(CG, J - c0);
+  if (!seg_active(S, chunk_seg(S, blockIdx.x))) {
+    if (threadIdx.x < ncol) partials[(int64_t)blockIdx.x * J + c0 + threadIdx.x] = 0.0;
+    return;
+  }
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
   T wv[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
@@ -159,16 +217,22 @@ __global__ void __launch_bounds__(TPB) k_multi_dot(const T *__restrict__ V, int6
   }
 }
 
-// w -= V h (h: J FP64 values on the device); optional ||w||^2 partials
+// w -= V h (h: J FP64 values per segment on the device); optional ||w||^2 partials
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_multi_update(const T *__restrict__ V, int64_t ldv, int J,
                                                       const double *__restrict__ h, T *__restrict__ w,
-                                                      int64_t n, double *__restrict__ partials) {
+                                                      int64_t n, double *__restrict__ partials, Seg S) {
   using A = typename acc_of<T>::type;
   extern __shared__ unsigned char smem_raw[];
   T *hs = reinterpret_cast<T *>(smem_raw);
   __shared__ double red[TPB / 32];
-  for (int c = threadIdx.x; c < J; c += TPB) hs[c] = num<T>::from_d(-h[c]);
+  const int seg = chunk_seg(S, blockIdx.x);
+  if (!seg_active(S, seg)) {
+    if (partials && threadIdx.x == 0) partials[blockIdx.x] = 0.0;
+    return;
+  }
+  const double *hseg = h + seg * S.dstride;
+  for (int c = threadIdx.x; c < J; c += TPB) hs[c] = num<T>::from_d(-hseg[c]);
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
   A acc[U];
@@ -203,21 +267,31 @@ __global__ void __launch_bounds__(TPB) k_multi_update(const T *__restrict__ V, i
   }
 }
 
-// x = V z, FP64 output
+// x = V z (x += V z with accumulate), FP64 output; m columns, or m_seg[segment]
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_reconstruct(const T *__restrict__ V, int64_t ldv, int m,
+                                                     const int *__restrict__ m_seg,
                                                      const double *__restrict__ z, double *__restrict__ x,
-                                                     int64_t n) {
+                                                     int64_t n, int accumulate, Seg S) {
   using A = typename acc_of<T>::type;
   extern __shared__ unsigned char smem_raw[];
   T *zs = reinterpret_cast<T *>(smem_raw);
-  for (int c = threadIdx.x; c < m; c += TPB) zs[c] = num<T>::from_d(z[c]);
+  const int seg = chunk_seg(S, blockIdx.x);
+  const int mm = m_seg ? min(m, m_seg[seg]) : m;
+  const double *zseg = z + seg * S.dstride;
+  for (int c = threadIdx.x; c < mm; c += TPB) zs[c] = num<T>::from_d(zseg[c]);
   __syncthreads();
   const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
   A acc[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) acc_set(acc[u], num<T>::zero());
-  for (int c = 0; c < m; ++c) {
+  double prev[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB;
+    prev[u] = (accumulate && r < n) ? x[r] : 0.0;
+  }
+  for (int c = 0; c < mm; ++c) {
     const T *col = V + (int64_t)c * ldv;
     const T zc = zs[c];
 #pragma unroll
@@ -229,50 +303,62 @@ __global__ void __launch_bounds__(TPB) k_reconstruct(const T *__restrict__ V, in
 #pragma unroll
   for (int u = 0; u < U; ++u) {
     const int64_t r = base + (int64_t)u * TPB;
-    if (r < n) x[r] = num<T>::to_d(acc_get(acc[u]));
+    if (r < n) x[r] = prev[u] + num<T>::to_d(acc_get(acc[u]));
   }
 }
 
+// Per (column, segment) sum of the chunk partials of the segment's chunks.
 __global__ void __launch_bounds__(256) k_reduce_cols(const double *__restrict__ partials, int nb, int ncols,
                                                      int mode, double *__restrict__ out_a,
-                                                     double *__restrict__ out_b) {
+                                                     double *__restrict__ out_b, Seg S) {
   __shared__ double red[32];
-  const int c = blockIdx.x;
+  const int c = blockIdx.x, seg = blockIdx.y;
+  if (!seg_active(S, seg)) return;
+  const int b0 = S.chunk0 ? S.chunk0[seg] : 0, b1 = S.chunk0 ? S.chunk0[seg + 1] : nb;
   double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[(int64_t)b * ncols + c];
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += partials[(int64_t)b * ncols + c];
   s = block_sum(s, red);
   if (threadIdx.x == 0) {
-    out_a[c] = s;
-    if (mode == 1) out_b[c] = s;
-    if (mode == 2) out_b[c] += s;
+    const int64_t o = seg * S.dstride + c;
+    out_a[o] = s;
+    if (mode == 1) out_b[o] = s;
+    if (mode == 2) out_b[o] += s;
   }
 }
 
+// Per segment: beta = sqrt(sum of the segment's partials), breakdown test
+// against ||ref||, 1/beta for the normalisation.
 __global__ void __launch_bounds__(256) k_norm_finalize(const double *__restrict__ partials, int nb,
                                                        double *beta_out, double *inv_out,
                                                        const double *__restrict__ ref, int nref,
-                                                       double rel, int m_here, DevStatus *st) {
+                                                       double rel, int m_here, DevStatus *st, Seg S) {
   __shared__ double red[32];
+  const int seg = blockIdx.x;
+  if (!seg_active(S, seg)) return;
+  const int b0 = S.chunk0 ? S.chunk0[seg] : 0, b1 = S.chunk0 ? S.chunk0[seg + 1] : nb;
+  const int64_t so = seg * S.dstride;
+  DevStatus *sts = st + seg;
   double s = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partials[b];
+  for (int b = b0 + threadIdx.x; b < b1; b += blockDim.x) s += partials[b];
   s = block_sum(s, red);
   double r2 = 0.0;
-  for (int i = threadIdx.x; i < nref; i += blockDim.x) r2 += ref[i] * ref[i];
+  if (ref)
+    for (int i = threadIdx.x; i < nref; i += blockDim.x) r2 += ref[so + i] * ref[so + i];
   r2 = block_sum(r2, red);
   if (threadIdx.x == 0) {
     const double beta = sqrt(s);
     const bool finite = isfinite(beta);
     bool bd = !(beta > 0.0) || (nref > 0 && beta <= rel * sqrt(r2));
     if (!finite) {
-      st->bad = 1;
+      sts->bad = 1;
       bd = true;
     }
-    if (bd && !st->breakdown) {
-      st->breakdown = 1;
-      st->m_bd = m_here;
+    if (bd && !sts->breakdown) {
+      sts->breakdown = 1;
+      sts->m_bd = m_here;
     }
-    *beta_out = finite ? (bd ? 0.0 : beta) : 0.0;
-    *inv_out = bd ? 0.0 : 1.0 / beta;
+    beta_out[so] = finite ? (bd ? 0.0 : beta) : 0.0;
+    inv_out[so] = bd ? 0.0 : 1.0 / beta;
   }
 }
 
@@ -290,6 +376,7 @@ inline unsigned nchunks(int64_t n) { return (unsigned)((n + CHUNK - 1) / CHUNK);
 }  // namespace
 
 int vec_nchunks(int64_t n) { return (int)nchunks(n); }
+int vec_chunk_rows() { return CHUNK; }
 
 template <typename T>
 int vec_from_f64(const double *in, T *out, int64_t n, cudaStream_t s) {
@@ -306,8 +393,27 @@ int vec_to_f64(const T *in, double *out, int64_t n, cudaStream_t s) {
   return PP_OK;
 }
 template <typename T>
-int vec_scale(const T *in, T *out, int64_t n, double c, const double *c_dev, cudaStream_t s) {
-  k_scale<T><<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(in, out, n, c, c_dev);
+int vec_fill_hash(T *out, int64_t n, uint64_t seed, cudaStream_t s) {
+  k_fill_hash<T><<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(out, n, seed);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+template int vec_fill_hash<double>(double *, int64_t, uint64_t, cudaStream_t);
+template int vec_fill_hash<dw>(dw *, int64_t, uint64_t, cudaStream_t);
+
+template <typename TI, typename TO>
+int vec_convert(const TI *in, TO *out, int64_t n, cudaStream_t s) {
+  k_convert<TI, TO><<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(in, out, n);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+template int vec_convert<dw, float>(const dw *, float *, int64_t, cudaStream_t);
+
+template <typename T>
+int vec_scale(const T *in, T *out, int64_t n, double c, const double *c_dev, cudaStream_t s, const Seg &S) {
+  k_scale<T><<<nchunks(n), TPB, 0, s>>>(in, out, n, c, c_dev, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -320,53 +426,53 @@ int vec_copy(const T *in, T *out, int64_t n, cudaStream_t s) {
   return PP_OK;
 }
 template <typename T>
-int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int, cudaStream_t s) {
-  k_dot<T><<<nchunks(n), TPB, 0, s>>>(x, y, n, partials);
+int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int, cudaStream_t s, const Seg &S) {
+  k_dot<T><<<nchunks(n), TPB, 0, s>>>(x, y, n, partials, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_lanczos_update(T *w, const T *vj, const T *vjm1, int64_t n, const double *alpha,
-                       const double *beta_prev, double *partials, int, cudaStream_t s) {
-  k_lanczos_update<T><<<nchunks(n), TPB, 0, s>>>(w, vj, vjm1, n, alpha, beta_prev, partials);
+                       const double *beta_prev, double *partials, int, cudaStream_t s, const Seg &S) {
+  k_lanczos_update<T><<<nchunks(n), TPB, 0, s>>>(w, vj, vjm1, n, alpha, beta_prev, partials, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_multi_dot(const T *V, int64_t ldv, int J, const T *w, int64_t n, double *partials, int,
-                  cudaStream_t s) {
+                  cudaStream_t s, const Seg &S) {
   dim3 grd(nchunks(n), (unsigned)((J + CG - 1) / CG));
-  k_multi_dot<T><<<grd, TPB, 0, s>>>(V, ldv, J, w, n, partials);
+  k_multi_dot<T><<<grd, TPB, 0, s>>>(V, ldv, J, w, n, partials, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_multi_update(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n,
-                     double *partials, int, cudaStream_t s) {
+                     double *partials, int, cudaStream_t s, const Seg &S) {
   const size_t sm = (size_t)J * sizeof(T);
   if (sm > 48 * 1024) PP_CUDA_TRY(cudaFuncSetAttribute(k_multi_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_multi_update<T><<<nchunks(n), TPB, sm, s>>>(V, ldv, J, h, w, n, partials);
+  k_multi_update<T><<<nchunks(n), TPB, sm, s>>>(V, ldv, J, h, w, n, partials, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_reconstruct(const T *V, int64_t ldv, int m, const double *z, double *x, int64_t n,
-                    cudaStream_t s) {
+                    int accumulate, cudaStream_t s, const Seg &S, const int *m_seg) {
   const size_t sm = (size_t)m * sizeof(T);
   if (sm > 48 * 1024) PP_CUDA_TRY(cudaFuncSetAttribute(k_reconstruct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_reconstruct<T><<<nchunks(n), TPB, sm, s>>>(V, ldv, m, z, x, n);
+  k_reconstruct<T><<<nchunks(n), TPB, sm, s>>>(V, ldv, m, m_seg, z, x, n, accumulate, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 
 int reduce_cols(const double *partials, int nb, int ncols, int mode, double *out_a, double *out_b,
-                cudaStream_t s) {
-  k_reduce_cols<<<ncols, 256, 0, s>>>(partials, nb, ncols, mode, out_a, out_b);
+                cudaStream_t s, const Seg &S) {
+  k_reduce_cols<<<dim3(ncols, S.nseg), 256, 0, s>>>(partials, nb, ncols, mode, out_a, out_b, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -374,8 +480,8 @@ int reduce_cols(const double *partials, int nb, int ncols, int mode, double *out
 
 int norm_finalize(const double *partials, int nb, double *beta_out, double *inv_out,
                   const double *ref, int nref, double rel, int m_here, DevStatus *st,
-                  cudaStream_t s) {
-  k_norm_finalize<<<1, 256, 0, s>>>(partials, nb, beta_out, inv_out, ref, nref, rel, m_here, st);
+                  cudaStream_t s, const Seg &S) {
+  k_norm_finalize<<<S.nseg, 256, 0, s>>>(partials, nb, beta_out, inv_out, ref, nref, rel, m_here, st, S);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -384,16 +490,19 @@ int norm_finalize(const double *partials, int nb, double *beta_out, double *inv_
 #define PP_INST(T)                                                                                  \
   template int vec_from_f64<T>(const double *, T *, int64_t, cudaStream_t);                       \
   template int vec_to_f64<T>(const T *, double *, int64_t, cudaStream_t);                         \
-  template int vec_scale<T>(const T *, T *, int64_t, double, const double *, cudaStream_t);       \
+  template int vec_scale<T>(const T *, T *, int64_t, double, const double *, cudaStream_t,        \
+                            const Seg &);                                                         \
   template int vec_copy<T>(const T *, T *, int64_t, cudaStream_t);                                \
-  template int vec_dot_partials<T>(const T *, const T *, int64_t, double *, int, cudaStream_t);   \
+  template int vec_dot_partials<T>(const T *, const T *, int64_t, double *, int, cudaStream_t,    \
+                                   const Seg &);                                                  \
   template int vec_lanczos_update<T>(T *, const T *, const T *, int64_t, const double *,          \
-                                     const double *, double *, int, cudaStream_t);                \
+                                     const double *, double *, int, cudaStream_t, const Seg &);   \
   template int vec_multi_dot<T>(const T *, int64_t, int, const T *, int64_t, double *, int,       \
-                                cudaStream_t);                                                    \
+                                cudaStream_t, const Seg &);                                       \
   template int vec_multi_update<T>(const T *, int64_t, int, const double *, T *, int64_t, double *, \
-                                   int, cudaStream_t);                                            \
-  template int vec_reconstruct<T>(const T *, int64_t, int, const double *, double *, int64_t,     \
-                                  cudaStream_t);
+                                   int, cudaStream_t, const Seg &);                               \
+  template int vec_reconstruct<T>(const T *, int64_t, int, const double *, double *, int64_t, int, \
+                                  cudaStream_t, const Seg &, const int *);
 PP_INST(double)
+PP_INST(float)
 PP_INST(dw)

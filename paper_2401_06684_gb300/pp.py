@@ -46,10 +46,11 @@ class pp_stats(ctypes.Structure):
                 ("beta0", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("launches", ctypes.c_int64), ("chain_launches", ctypes.c_int64),
                 ("chain_bytes", ctypes.c_double), ("chain_ms", ctypes.c_double),
-                ("reserved", ctypes.c_double * 3)]
+                ("switch_iter", ctypes.c_int32), ("reserved_i", ctypes.c_int32),
+                ("reserved", ctypes.c_double * 2)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
 
 
 class PPError(RuntimeError):
@@ -77,6 +78,10 @@ SYMBOLS = {
                                 _p, ctypes.POINTER(pp_stats)]),
     "pp_apply_host": (ctypes.c_int, [_h, ctypes.c_int32, _p, ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_double, _p, ctypes.POINTER(pp_stats)]),
+    "pp_apply_batch": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(_p), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_p),
+                                      ctypes.c_int32, ctypes.c_double, _p, ctypes.POINTER(pp_stats)]),
+    "pp_autotune": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "pp_op_apply": (ctypes.c_int, [_h, _p, _p]),
     "pp_poly_apply": (ctypes.c_int, [_h, _p, _p]),
     "pp_poly_apply_static": (ctypes.c_int, [_h, _p, _p]),
@@ -212,6 +217,28 @@ def pp_apply_host(h, f, b, x, m_max=200, tol=1e-10, nrhs=1):
         _check(rc)
     st.status = rc
     return st
+
+
+def pp_apply_batch(handles, fs, bs, xs, nrhs=None, m_max=200, tol=1e-10, stream=None):
+    """Batched solves; returns one pp_stats per handle (see pp.h)."""
+    n = len(handles)
+    nrhs = nrhs or [1] * n
+    hs = (_h * n)(*[h.value if hasattr(h, "value") else h for h in handles])
+    fa = (ctypes.c_int32 * n)(*fs)
+    ba = (_p * n)(*[_ptr(b) for b in bs])
+    xa = (_p * n)(*[_ptr(x) for x in xs])
+    ra = (ctypes.c_int64 * n)(*nrhs)
+    st = (pp_stats * n)()
+    rc = lib().pp_apply_batch(hs, n, fa, ba, ra, xa, m_max, tol, _stream(stream), st)
+    if rc not in (PP_OK, PP_ERR_NOT_CONVERGED):
+        _check(rc)
+    return list(st)
+
+
+def pp_autotune(h, tol, max_degree=64):
+    d = ctypes.c_int32()
+    _check(lib().pp_autotune(h, tol, max_degree, ctypes.byref(d)))
+    return d.value
 
 
 def pp_op_apply(h, x, y):

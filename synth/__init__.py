@@ -115,3 +115,27 @@ def spinor_field(dims, seed=0):
     V = int(np.prod(dims))
     rng = np.random.default_rng(seed)
     return rng.standard_normal(12 * V) + 1j * rng.standard_normal(12 * V)
+
+
+# ---- batched workload (many independent problems) --------------------------
+
+def batch_problems(count=64, seed=2, n_lo=1e3, n_hi=1e6, max_rhs=16):
+    """Problem list of a batched run: dicts with kind ('laplace2d5',
+    'laplace3d7' or 'convdiff3d7', uniform), dims (n log-uniform in
+    [n_lo, n_hi], rounded to a square / cubic grid), nrhs ~ U{1..max_rhs}
+    and f (+1 square root / -1 inverse square root, uniform)."""
+    rng = np.random.default_rng(seed)
+    kinds = ["laplace2d5", "laplace3d7", "convdiff3d7"]
+    out = []
+    for _ in range(count):
+        kind = kinds[rng.integers(3)]
+        n = float(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        if kind == "laplace2d5":
+            N = max(2, int(round(n ** 0.5)))
+            dims = (N, N)
+        else:
+            N = max(2, int(round(n ** (1.0 / 3.0))))
+            dims = (N, N, N)
+        out.append({"kind": kind, "dims": dims, "nrhs": int(rng.integers(1, max_rhs + 1)),
+                    "f": int(1 if rng.integers(2) else -1)})
+    return out

@@ -105,9 +105,21 @@ def test_argument_validation():
     with pytest.raises(pp.PPError) as e:
         pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (4, 4, 4))  # needs c*h
     assert e.value.status == pp.PP_ERR_INVALID_ARG
+    # Wilson: complex128 vectors, links and a finite mass required (host checks only)
     with pytest.raises(pp.PPError) as e:
-        pp.pp_create_stencil(pp.PP_WILSON4D_DHD, (4, 4, 4, 4))
+        pp.pp_create_stencil(pp.PP_WILSON4D_DHD, (4, 4, 4, 4), [0.1], links=64)
     assert e.value.status == pp.PP_ERR_UNSUPPORTED
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_create_stencil(pp.PP_WILSON4D_DHD, (4, 4, 4, 4), [0.1], dtype=pp.PP_C128)
+    assert e.value.status == pp.PP_ERR_INVALID_ARG
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_create_stencil(pp.PP_WILSON4D_DHD, (4, 0, 4, 4), [0.1], links=64, dtype=pp.PP_C128)
+    assert e.value.status == pp.PP_ERR_INVALID_ARG
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_create_stencil(pp.PP_WILSON4D_DHD, (4, 4, 4, 4), [float("nan")], links=64, dtype=pp.PP_C128)
+    assert e.value.status == pp.PP_ERR_INVALID_ARG
+    hw = pp.pp_create_stencil(pp.PP_WILSON4D_DHD, (4, 4, 4, 4), [0.1], links=64, dtype=pp.PP_C128)
+    pp.pp_destroy(hw)
     h = pp.pp_create_stencil(pp.PP_LAPLACE3D7, (4, 4, 4))
     try:
         with pytest.raises(pp.PPError) as e:  # apply before build_poly
@@ -139,8 +151,8 @@ def test_argument_validation():
         assert e.value.status == pp.PP_ERR_INVALID_ARG
     finally:
         pp.pp_destroy(h)
-    # CSR handles need an interval
-    h = pp.pp_create_csr(16, 8, 8, 8, is_hermitian=True)
+    # non-Hermitian CSR handles need an interval (Hermitian ones estimate it on the device)
+    h = pp.pp_create_csr(16, 8, 8, 8, is_hermitian=False)
     try:
         with pytest.raises(pp.PPError) as e:
             pp.pp_build_poly(h, 4)

@@ -89,10 +89,14 @@ class Problem:
 CASES = [("laplace", (61, 37), 0.0, False), ("laplace", (33, 17, 29), 0.0, False),
          ("convdiff", (33, 17, 29), 0.5, False), ("laplace", (61, 37), 0.0, True),
          ("convdiff", (19, 23, 9), 0.5, True)]
+# even row lengths: the stencil kernels take the vector-load path (nx a
+# multiple of the entries per 16-byte access); the cases above take the
+# scalar path
+CASES_EVEN = [("laplace", (64, 38), 0.0, False), ("convdiff", (32, 18, 21), 0.5, False)]
 
 
 @pytest.mark.parametrize("prec", ["f64", "dw"])
-@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}{c[1]}{'csr' if c[3] else ''}")
+@pytest.mark.parametrize("case", CASES + CASES_EVEN, ids=lambda c: f"{c[0]}{c[1]}{'csr' if c[3] else ''}")
 def test_op_apply(case, prec):
     pp = load()
     P = Problem(pp, case[0], case[1], case[2], case[3])
@@ -108,7 +112,8 @@ def test_op_apply(case, prec):
 
 @pytest.mark.parametrize("prec", ["f64", "dw"])
 @pytest.mark.parametrize("degree", [0, 1, 2, 3, 8, 17])
-@pytest.mark.parametrize("case", CASES[:3] + CASES[4:], ids=lambda c: f"{c[0]}{c[1]}{'csr' if c[3] else ''}")
+@pytest.mark.parametrize("case", CASES[:3] + CASES[4:] + CASES_EVEN,
+                         ids=lambda c: f"{c[0]}{c[1]}{'csr' if c[3] else ''}")
 def test_poly_apply(case, degree, prec):
     pp = load()
     P = Problem(pp, case[0], case[1], case[2], case[3], degree=degree)
@@ -127,7 +132,7 @@ def test_poly_apply(case, degree, prec):
 @pytest.mark.parametrize("f", [-1, 1], ids=["invsqrt", "sqrt"])
 @pytest.mark.parametrize("side", [0, 1], ids=["left", "right"])
 @pytest.mark.parametrize("degree", [0, 4, 9])
-@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[3]],
+@pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[3], CASES_EVEN[1]],
                          ids=lambda c: f"{c[0]}{c[1]}{'csr' if c[3] else ''}")
 def test_solve_parity(case, degree, side, f, prec):
     pp = load()
@@ -143,6 +148,26 @@ def test_solve_parity(case, degree, side, f, prec):
         # counters as in Table 1: 2d - 1 mvms per iteration plus start-up products
         extra = (degree if side == 0 else 0) + (1 if f == 1 else 0)
         assert st.mvms == st.iters * (2 * degree + 1) + extra
+    finally:
+        P.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "dw"])
+def test_misaligned_vectors_take_scalar_path(prec):
+    # device vectors offset by one entry (8-byte aligned only): same result
+    pp = load()
+    P = Problem(pp, *CASES_EVEN[1], degree=5)
+    try:
+        set_prec(pp, P.h, prec)
+        x = synth.rhs(P.n, 13)
+        base = torch.zeros(P.n + 1, dtype=torch.float64, device="cuda")
+        base[1:] = dev(x)
+        out = torch.zeros(P.n + 1, dtype=torch.float64, device="cuda")
+        pp.pp_op_apply(P.h, base[1:], out[1:])
+        assert rel(host(out)[1:], P.A @ x) < OP_TOL[prec]
+        pp.pp_poly_apply(P.h, base[1:], out[1:])
+        ref = cheb.q_apply(P.A.dot, P.coef, P.ab[0], P.ab[1], x)
+        assert rel(host(out)[1:], ref) < POLY_TOL[prec]
     finally:
         P.close()
 
