@@ -67,6 +67,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--plain-m-max", type=int, default=1000)
+    p.add_argument("--autotune", action="store_true", help="degree and tile from pp_autotune")
     a = p.parse_args()
     w = WORKLOADS[a.workload]
     a.desc, a.kind, a.dims, a.func = w[0], w[1], w[2], w[3]
@@ -90,7 +91,8 @@ def dist_env():
 
 
 def config(args, ws):
-    return {"workload": args.desc, "grid": list(args.dims), "n": args.n,
+    return {"workload": args.desc + (" (degree and tile autotuned)" if args.autotune else ""),
+            "grid": list(args.dims), "n": args.n,
             "ch": 0.5 if args.kind == "convdiff3d7" else 0.0,
             "func": "sqrt" if args.func > 0 else "invsqrt", "poly": "chebyshev", "degree": args.degree,
             "side": "left", "orth": args.orth, "tol": args.tol, "rhs_per_rank": 1,
@@ -284,6 +286,8 @@ def run_ours(args):
     o = pp.pp_default_opts()
     o.precision = {"dw": pp.PP_PREC_DW, "f64": pp.PP_PREC_F64, "mixed": pp.PP_PREC_MIXED}[args.prec]
     pp.pp_set_opts(h, o)
+    if args.autotune:
+        args.degree = pp.pp_autotune(h, args.tol, 64)
     vdt = torch.complex128 if args.complex else torch.float64
     esz = 16 if args.complex else 8
 

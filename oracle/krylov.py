@@ -78,10 +78,10 @@ def pp_arnoldi(A_mv, b, power=-0.5, coeffs=(1.0,), ab=(0.0, 1.0), side="left",
     Y = np.zeros((m_max, n), dtype=dt) if side == "right" else None
     H = np.zeros((m_max + 1, m_max), dtype=dt)
 
-    if side == "left":                   # Algorithm 1, line 2
+    if side == "left":                   # Algorithm 1: start from c = q(A) b
         start = q_mv(rhs)
         mvms += deg
-    else:                                # Algorithm 2, line 2
+    else:                                # Algorithm 2: start from b
         start = rhs
     beta = np.linalg.norm(start)         # not counted: Tables 1-3 count the loop only
     V[0] = start / beta
@@ -97,17 +97,17 @@ def pp_arnoldi(A_mv, b, power=-0.5, coeffs=(1.0,), ab=(0.0, 1.0), side="left",
     if on_iter is not None:
         on_iter(-1)
     for j in range(m_max):
-        if side == "left":               # Algorithm 1, line 4
+        if side == "left":               # Algorithm 1: u = A v_j, y = q(A) u, w = q(A) y
             u = A_mv(V[j])
             y = q_mv(u)
             w = q_mv(y)
-        else:                            # Algorithm 2, line 4
+        else:                            # Algorithm 2: y_j = q(A) v_j, u = q(A) y_j, w = A u
             Y[j] = q_mv(V[j])
             u = q_mv(Y[j])
             w = A_mv(u)
         mvms += 2 * deg + 1
 
-        if orth == "mgs":                # lines 5-7 as printed
+        if orth == "mgs":                # the modified Gram-Schmidt loop as printed
             for i in range(j + 1):
                 H[i, j] = np.vdot(V[i], w)
                 w = w - V[i] * H[i, j]
@@ -128,14 +128,14 @@ def pp_arnoldi(A_mv, b, power=-0.5, coeffs=(1.0,), ab=(0.0, 1.0), side="left",
         else:
             raise ValueError(orth)
 
-        hn = np.linalg.norm(w)           # line 8
+        hn = np.linalg.norm(w)           # h_{j+1,j} = ||w||
         ip += 1
         H[j + 1, j] = hn
         m = j + 1
         scale = np.linalg.norm(H[: j + 2, j])
         lucky = hn <= breakdown_tol * max(scale, 1e-300)
         if not lucky:
-            V[j + 1] = w / hn            # line 9
+            V[j + 1] = w / hn            # v_{j+1} = w / h_{j+1,j}
         if on_iter is not None:
             on_iter(j)
 

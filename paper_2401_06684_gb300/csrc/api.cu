@@ -265,19 +265,19 @@ int poly_apply_raw(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3])
   const double s1 = 4.0 / (c->b - c->a), s2 = -2.0 * (c->a + c->b) / (c->b - c->a);
   cudaStream_t s = c->stream;
   if (k == 0) return vec_scale<T>(in, out, c->n, cf[0], nullptr, s);
-  if (k == 1) return run_op<T>(c, op, in, nullptr, nullptr, out, {0.5 * s1 * cf[1], 0.5 * s2 * cf[1] + cf[0], 0.0, false, false});
+  if (k == 1) return run_op<T>(c, op, in, nullptr, nullptr, out, clenshaw_coef(cf, s1, s2, 0));
   int i2 = 0, i1 = 1, i0 = 2;  // buffer indices of b_{i+2}, b_{i+1}, free
-  RC(run_op<T>(c, op, in, nullptr, nullptr, bufs[i2], {s1 * cf[k], s2 * cf[k] + cf[k - 1], 0.0, false, false}));
-  if (k == 2) return run_op<T>(c, op, bufs[i2], nullptr, in, out, {0.5 * s1, 0.5 * s2, cf[0] - cf[2], false, true});
-  RC(run_op<T>(c, op, bufs[i2], nullptr, in, bufs[i1], {s1, s2, cf[k - 2] - cf[k], false, true}));
-  for (int i = k - 3; i >= 1; --i) {
-    RC(run_op<T>(c, op, bufs[i1], bufs[i2], in, bufs[i0], {s1, s2, cf[i], true, true}));
-    const int t = i2;
+  RC(run_op<T>(c, op, in, nullptr, nullptr, bufs[i2], clenshaw_coef(cf, s1, s2, 0)));
+  if (k == 2) return run_op<T>(c, op, bufs[i2], nullptr, in, out, clenshaw_coef(cf, s1, s2, 1));
+  RC(run_op<T>(c, op, bufs[i2], nullptr, in, bufs[i1], clenshaw_coef(cf, s1, s2, 1)));
+  for (int t = 2; t <= k - 2; ++t) {
+    RC(run_op<T>(c, op, bufs[i1], bufs[i2], in, bufs[i0], clenshaw_coef(cf, s1, s2, t)));
+    const int tmp = i2;
     i2 = i1;
     i1 = i0;
-    i0 = t;
+    i0 = tmp;
   }
-  return run_op<T>(c, op, bufs[i1], bufs[i2], in, out, {0.5 * s1, 0.5 * s2, cf[0], true, true});
+  return run_op<T>(c, op, bufs[i1], bufs[i2], in, out, clenshaw_coef(cf, s1, s2, k - 1));
 }
 
 template <typename T>

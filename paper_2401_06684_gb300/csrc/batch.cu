@@ -98,6 +98,8 @@ BLayout blayout(int m_cap, int K) {
 __global__ void k_gather(const double *const *__restrict__ src, const int64_t *__restrict__ off,
                          const int64_t *__restrict__ len, const int *__restrict__ chunk_seg, int chunk,
                          double *__restrict__ dst, int64_t N) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
     const int s = chunk_seg[r / chunk];
     const int64_t i = r - off[s];
@@ -109,6 +111,8 @@ __global__ void k_gather(const double *const *__restrict__ src, const int64_t *_
 __global__ void k_scatter(double *const *__restrict__ dst, const int64_t *__restrict__ off,
                           const int64_t *__restrict__ len, const int *__restrict__ chunk_seg, int chunk,
                           const double *__restrict__ src, int64_t N) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N; r += (int64_t)gridDim.x * blockDim.x) {
     const int s = chunk_seg[r / chunk];
     const int64_t i = r - off[s];
@@ -118,12 +122,16 @@ __global__ void k_scatter(double *const *__restrict__ dst, const int64_t *__rest
 
 // dst[s * dstride + i] = src[i], i < K, for every segment s
 __global__ void k_broadcast(const double *__restrict__ src, int K, double *__restrict__ dst, int64_t dstride) {
+  pdl_wait();
+  pdl_trigger();
   const int s = blockIdx.x;
   for (int i = threadIdx.x; i < K; i += blockDim.x) dst[s * dstride + i] = src[i];
 }
 
 // clear the stopping flags (keep beta0)
 __global__ void k_clear_flags(DevStatus *st, int nseg) {
+  pdl_wait();
+  pdl_trigger();
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s < nseg) {
     st[s].conv = 0;
@@ -181,19 +189,6 @@ struct Allocs {
     return PP_OK;
   }
 };
-
-// Clenshaw coefficients of step t (0 .. k-1) of q(A) for one segment, the
-// same schedule as the single-vector driver: b_k = c_k v folded into the
-// first step, the last step with the factors 1/2.
-StepCoef clenshaw_step(const std::vector<double> &cf, double s1, double s2, int t) {
-  const int k = (int)cf.size() - 1;
-  if (k == 1) return {0.5 * s1 * cf[1], 0.5 * s2 * cf[1] + cf[0], 0.0, false, false};
-  if (t == 0) return {s1 * cf[k], s2 * cf[k] + cf[k - 1], 0.0, false, false};
-  if (t == 1 && k == 2) return {0.5 * s1, 0.5 * s2, cf[0] - cf[2], false, true};
-  if (t == 1) return {s1, s2, cf[k - 2] - cf[k], false, true};
-  if (t == k - 1) return {0.5 * s1, 0.5 * s2, cf[0], true, true};
-  return {s1, s2, cf[k - 1 - t], true, true};
-}
 
 // Everything a group's kernels need for one arithmetic.
 template <typename T>
@@ -342,7 +337,7 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
         coefs[i] = {1.0, 0.0, 0.0, false, false};
       } else {
         const double s1 = 4.0 / (c->b - c->a), s2 = -2.0 * (c->a + c->b) / (c->b - c->a);
-        coefs[i] = clenshaw_step(c->coef, s1, s2, t - 1);
+        coefs[i] = clenshaw_coef(c->coef, s1, s2, t - 1);
       }
     }
     batch_konst<T>(d.data(), cm.data(), cp.data(), coefs.data(), ns, Kh.data() + (size_t)t * ns);
@@ -458,8 +453,8 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
   PP_CUDA_TRY(cudaMemcpyAsync(qsd, qs.data(), sizeof(double) * G.K, cudaMemcpyHostToDevice, s));
   PP_CUDA_TRY(cudaMemcpyAsync(qsd + G.K, qw.data(), sizeof(double) * G.K, cudaMemcpyHostToDevice, s));
   // per-segment constants: quadrature nodes / weights and q's constant term
-  k_broadcast<<<ns, 128, 0, s>>>(qsd, G.K, G.dmem + L.sig, (int64_t)L.total);
-  k_broadcast<<<ns, 128, 0, s>>>(qsd + G.K, G.K, G.dmem + L.wt, (int64_t)L.total);
+  PP_CUDA_TRY(pdl_launch(k_broadcast, dim3(ns), dim3(128), 0, s, qsd, G.K, G.dmem + L.sig, (int64_t)L.total));
+  PP_CUDA_TRY(pdl_launch(k_broadcast, dim3(ns), dim3(128), 0, s, qsd + G.K, G.K, G.dmem + L.wt, (int64_t)L.total));
   launches_out[0] += 2;
   PP_CUDA_TRY(cudaGetLastError());
   PP_CUDA_TRY(cudaMemcpy2DAsync(G.dmem + L.qc0, sizeof(double) * L.total, cf0.data(), sizeof(double),
@@ -476,7 +471,7 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
   }
   const Seg Sall = G.seg(false);
   // right-hand sides, A b for the square roots (Sec. 4), start vectors
-  k_gather<<<1024, 256, 0, s>>>(srcd, offd, lend, G.chunk_seg, CH, bcat, N);
+  PP_CUDA_TRY(pdl_launch(k_gather, dim3(1024), dim3(256), 0, s, srcd, offd, lend, G.chunk_seg, CH, bcat, N));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   BRC(vec_from_f64<T1>(bcat, t1[0], N, s));
@@ -516,7 +511,7 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
   // beta0 is read by the small solves from the status record
   for (int i = 0; i < ns; ++i) hs[i].beta0 = beta0[i];
   PP_CUDA_TRY(cudaMemcpyAsync(G.st, hs.data(), sizeof(DevStatus) * ns, cudaMemcpyHostToDevice, s));
-  k_clear_flags<<<(ns + 127) / 128, 128, 0, s>>>(G.st, ns);
+  PP_CUDA_TRY(pdl_launch(k_clear_flags, dim3((ns + 127) / 128), dim3(128), 0, s, G.st, ns));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaMemcpyAsync(G.active, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
 
@@ -633,7 +628,7 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
       BRC(vec_reconstruct<T2>((right ? (T2 *)Y2g.p : (T2 *)V2g.p) + (size_t)k1 * N, N, m - k1, G.dmem + L.z + k1,
                               xcat, N, 1, s, Sr, mseg2));
   }
-  k_scatter<<<1024, 256, 0, s>>>(dstd, offd, lend, G.chunk_seg, CH, xcat, N);
+  PP_CUDA_TRY(pdl_launch(k_scatter, dim3(1024), dim3(256), 0, s, dstd, offd, lend, G.chunk_seg, CH, xcat, N));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   PP_CUDA_TRY(cudaStreamSynchronize(s));

@@ -95,6 +95,32 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
   return s;
 }
 
+// Programmatic dependent launch.  Kernels of the solve are launched with
+// pdl_launch, which lets the next grid in the stream be scheduled while the
+// previous one drains (its CTAs then wait in pdl_wait).  Every such kernel
+// calls pdl_wait() before touching device memory (it returns once the
+// preceding grid has completed and its writes are visible) and
+// pdl_trigger() to let its own dependents launch; on a grid launched without
+// the attribute both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 #define PP_CUDA_TRY(expr)                                      \
   do {                                                         \
     cudaError_t _e = (expr);                                   \

@@ -39,6 +39,21 @@ template <typename T>
 int op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &c,
             cudaStream_t s);
 
+// Step t (0 .. k-1) of the matrix Clenshaw recurrence for q(A) v with
+// q = sum_{i<=k} cf_i T_i(sigma), sigma(A) = (2A - (a+b) I)/(b-a), s1 = 4/(b-a),
+// s2 = -2(a+b)/(b-a): b_k = cf_k v is folded into the first step and the
+// last step carries the factors 1/2 (q(A) v = (b_0 - b_2)/2 + cf_0 v / 2 ...
+// in the operator form out = alpha A x + beta x [- y] [+ delta v]).
+inline StepCoef clenshaw_coef(const std::vector<double> &cf, double s1, double s2, int t) {
+  const int k = (int)cf.size() - 1;
+  if (k == 1) return {0.5 * s1 * cf[1], 0.5 * s2 * cf[1] + cf[0], 0.0, false, false};
+  if (t == 0) return {s1 * cf[k], s2 * cf[k] + cf[k - 1], 0.0, false, false};
+  if (t == 1 && k == 2) return {0.5 * s1, 0.5 * s2, cf[0] - cf[2], false, true};
+  if (t == 1) return {s1, s2, cf[k - 2] - cf[k], false, true};
+  if (t == k - 1) return {0.5 * s1, 0.5 * s2, cf[0], true, true};
+  return {s1, s2, cf[k - 1 - t], true, true};
+}
+
 // Constants of one stencil row: K0 x_c + Km (sum of -1 neighbours) + Kp (sum
 // of +1 neighbours) [- y] [+ D v], in the vector arithmetic.
 template <typename T>

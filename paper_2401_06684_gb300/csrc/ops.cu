@@ -124,6 +124,8 @@ __global__ void __launch_bounds__(ST_THREADS) st_step(const T *__restrict__ x, c
                                                         const T *__restrict__ v, T *__restrict__ out,
                                                         int nx, int ny, int nz, unsigned gx, unsigned gy,
                                                         Konst<T> K) {
+  pdl_wait();
+  pdl_trigger();
   const unsigned blk = blockIdx.x;
   const unsigned bx = blk % gx, rest = blk / gx;
   const unsigned by = rest % gy;
@@ -143,6 +145,8 @@ __global__ void __launch_bounds__(ST_THREADS) bst_step(const T *__restrict__ x, 
                                                          const BatchSeg *__restrict__ segs, int nseg,
                                                          const Konst<T> *__restrict__ K,
                                                          const int *__restrict__ active) {
+  pdl_wait();
+  pdl_trigger();
   const unsigned blk = blockIdx.x;
   int lo = 0, hi = nseg - 1;
   while (lo < hi) {
@@ -173,6 +177,8 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
                                                 const T *__restrict__ y, const T *__restrict__ v,
                                                 T *__restrict__ out, int64_t n, T alpha, T beta,
                                                 T delta) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename acc_of<T>::type;
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t row = t / L;
@@ -219,9 +225,9 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     const int64_t threads = op.n * L;
     const int bs = 256;
     const int64_t nb = (threads + bs - 1) / bs;
-    csr_step<T, L, SY, AV><<<(unsigned)nb, bs, 0, s>>>(op.rowptr, op.col, (const T *)op.val, x, y, v,
+    PP_CUDA_TRY(pdl_launch(csr_step<T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col, (const T *)op.val, x, y, v,
                                                        out, op.n, host_const<T>(c.alpha),
-                                                       host_const<T>(c.beta), host_const<T>(c.delta));
+                                                       host_const<T>(c.beta), host_const<T>(c.delta)));
   } else {
     Konst<T> K;
     K.K0 = host_const<T>(c.alpha * op.d + c.beta);
@@ -247,9 +253,9 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     if (nblk > 0x7fffffffull) return pp_set_error(PP_ERR_INVALID_ARG, "grid too large for one launch");
     const dim3 blk(bdx, bdy);
     if (vec)
-      st_step<T, PW, SY, AV><<<(unsigned)nblk, blk, 0, s>>>(x, y, v, out, (int)op.nx, (int)op.ny, nz, gx, gy, K);
+      PP_CUDA_TRY(pdl_launch(st_step<T, PW, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out, (int)op.nx, (int)op.ny, nz, gx, gy, K));
     else
-      st_step<T, 1, SY, AV><<<(unsigned)nblk, blk, 0, s>>>(x, y, v, out, (int)op.nx, (int)op.ny, nz, gx, gy, K);
+      PP_CUDA_TRY(pdl_launch(st_step<T, 1, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out, (int)op.nx, (int)op.ny, nz, gx, gy, K));
   }
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
@@ -284,7 +290,9 @@ int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Ko
                   const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v, cudaStream_t s) {
   constexpr int PW = 16 / (int)sizeof(T);
   const dim3 blk(kBatchBlockX, ST_THREADS / kBatchBlockX);
-#define PP_BST(PP, SY, AV) bst_step<T, PP, SY, AV><<<nblk, blk, 0, s>>>(x, y, v, out, segs, nseg, K, active)
+#define PP_BST(PP, SY, AV) \
+  e = pdl_launch(bst_step<T, PP, SY, AV>, dim3(nblk), blk, 0, s, x, y, v, out, segs, nseg, K, active)
+  cudaError_t e;
   if (P == PW) {
     if (sub_y && add_v) PP_BST(PW, true, true);
     else if (sub_y) PP_BST(PW, true, false);
@@ -297,6 +305,7 @@ int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Ko
     else PP_BST(1, false, false);
   }
 #undef PP_BST
+  PP_CUDA_TRY(e);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;

@@ -1,4 +1,4 @@
-// Small projected solve z = beta0 H_m^{-1/2} e_1 (Algorithm 1, last line) on
+// Small projected solve z = beta0 H_m^{-1/2} e_1 (the final step of Algorithm 1) on
 // the device, in FP64.
 //
 // The paper forms H_m^{1/2} by a blocked Schur method and solves a linear
@@ -25,6 +25,8 @@ namespace {
 __global__ void k_tri_quad(const double *__restrict__ H, int ldh, int m, const double *__restrict__ sig,
                            const double *__restrict__ wt, int K, double *__restrict__ X,
                            double *__restrict__ scratch, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int seg = blockIdx.y;
   if (k >= K || (S.active && !S.active[seg])) return;
@@ -71,6 +73,8 @@ __global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H,
                                                    const double *__restrict__ wt,
                                                    double *__restrict__ X, double *__restrict__ gscratch,
                                                    int use_smem, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double sm[];
   const int k = blockIdx.x;
   const int seg = blockIdx.y;
@@ -131,6 +135,8 @@ __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict
                                                         const double *__restrict__ sig,
                                                         const double *__restrict__ wt, int K,
                                                         double *__restrict__ X, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   extern __shared__ double sm[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int k = blockIdx.x * (blockDim.x >> 5) + wid;
@@ -189,6 +195,8 @@ __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict
 __global__ void __launch_bounds__(1024) k_combine(const double *__restrict__ X, int K, int m, int mprev,
                                                   double *__restrict__ z, double *__restrict__ zprev,
                                                   double tol, DevStatus *st, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double rd[32], rz[32];
   const int seg = blockIdx.x;
   if (S.active && !S.active[seg]) return;
@@ -233,7 +241,7 @@ __global__ void __launch_bounds__(1024) k_combine(const double *__restrict__ X, 
 
 int small_tridiag_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
                        double *X, double *scratch, cudaStream_t s, const Seg &S) {
-  k_tri_quad<<<dim3((K + 127) / 128, S.nseg), 128, 0, s>>>(H, ldh, m, sig, wt, K, X, scratch, S);
+  PP_CUDA_TRY(pdl_launch(k_tri_quad, dim3((K + 127) / 128, S.nseg), dim3(128), 0, s, H, ldh, m, sig, wt, K, X, scratch, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -247,7 +255,7 @@ int small_hess_quad(const double *H, int ldh, int m, const double *sig, const do
     if (wpb > 8) wpb = 8;
     if (wpb < 1) wpb = 1;
     const unsigned grid = (unsigned)((K + wpb - 1) / wpb);
-    k_hess_quad_warp<<<dim3(grid, S.nseg), 32 * wpb, per_warp * wpb, s>>>(H, ldh, m, sig, wt, K, X, S);
+    PP_CUDA_TRY(pdl_launch(k_hess_quad_warp, dim3(grid, S.nseg), dim3(32 * wpb), per_warp * wpb, s, H, ldh, m, sig, wt, K, X, S));
     ++pp_launch_count();
     PP_CUDA_TRY(cudaGetLastError());
     return PP_OK;
@@ -257,7 +265,7 @@ int small_hess_quad(const double *H, int ldh, int m, const double *sig, const do
   const int use_smem = bytes <= kSmemMax ? 1 : 0;
   if (use_smem && bytes > 48 * 1024)
     PP_CUDA_TRY(cudaFuncSetAttribute(k_hess_quad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  k_hess_quad<<<dim3(K, S.nseg), 128, use_smem ? bytes : 0, s>>>(H, ldh, m, sig, wt, X, scratch, use_smem, S);
+  PP_CUDA_TRY(pdl_launch(k_hess_quad, dim3(K, S.nseg), dim3(128), use_smem ? bytes : 0, s, H, ldh, m, sig, wt, X, scratch, use_smem, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -269,7 +277,7 @@ size_t small_hess_scratch_doubles(int m, int K) {
 
 int small_combine(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol,
                   DevStatus *st, cudaStream_t s, const Seg &S) {
-  k_combine<<<S.nseg, 1024, 0, s>>>(X, K, m, mprev, z, zprev, tol, st, S);
+  PP_CUDA_TRY(pdl_launch(k_combine, dim3(S.nseg), dim3(1024), 0, s, X, K, m, mprev, z, zprev, tol, st, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;

@@ -67,12 +67,16 @@ __device__ __forceinline__ bool seg_active(const Seg &S, int seg) {
 
 template <typename T>
 __global__ void k_from_f64(const double *__restrict__ in, T *__restrict__ out, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = num<T>::from_d(in[i]);
 }
 
 template <typename T>
 __global__ void k_to_f64(const T *__restrict__ in, double *__restrict__ out, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = num<T>::to_d(in[i]);
 }
@@ -80,6 +84,8 @@ __global__ void k_to_f64(const T *__restrict__ in, double *__restrict__ out, int
 // Fixed pseudo-random vector in [-1, 1): splitmix64 of (seed + index).
 template <typename T>
 __global__ void k_fill_hash(T *__restrict__ out, int64_t n, uint64_t seed) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(i + 1);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -91,6 +97,8 @@ __global__ void k_fill_hash(T *__restrict__ out, int64_t n, uint64_t seed) {
 
 template <typename TI, typename TO>
 __global__ void k_convert(const TI *__restrict__ in, TO *__restrict__ out, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = num<TO>::from_d(num<TI>::to_d(in[i]));
 }
@@ -99,6 +107,8 @@ __global__ void k_convert(const TI *__restrict__ in, TO *__restrict__ out, int64
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_scale(const T *__restrict__ in, T *__restrict__ out, int64_t n, double c,
                                                const double *__restrict__ c_dev, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   const int seg = chunk_seg(S, blockIdx.x);
   if (!seg_active(S, seg)) return;
   const double cc = c_dev ? c * c_dev[seg * S.dstride] : c;
@@ -113,6 +123,8 @@ __global__ void __launch_bounds__(TPB) k_scale(const T *__restrict__ in, T *__re
 
 template <typename T>
 __global__ void k_copy(const T *__restrict__ in, T *__restrict__ out, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     out[i] = in[i];
 }
@@ -121,6 +133,8 @@ __global__ void k_copy(const T *__restrict__ in, T *__restrict__ out, int64_t n)
 template <typename T>
 __global__ void __launch_bounds__(TPB) k_dot(const T *__restrict__ x, const T *__restrict__ y, int64_t n,
                                              double *__restrict__ partials, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename acc_of<T>::type;
   __shared__ double red[TPB / 32];
   if (!seg_active(S, chunk_seg(S, blockIdx.x))) {
@@ -146,6 +160,8 @@ __global__ void __launch_bounds__(TPB) k_lanczos_update(T *__restrict__ w, const
                                                         const double *__restrict__ alpha,
                                                         const double *__restrict__ beta_prev,
                                                         double *__restrict__ partials, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename acc_of<T>::type;
   __shared__ double red[TPB / 32];
   const int seg = chunk_seg(S, blockIdx.x);
@@ -181,6 +197,8 @@ template <typename T>
 __global__ void __launch_bounds__(TPB) k_multi_dot(const T *__restrict__ V, int64_t ldv, int J,
                                                    const T *__restrict__ w, int64_t n,
                                                    double *__restrict__ partials, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename acc_of<T>::type;
   __shared__ double red[CG][TPB / 32];
   const int c0 = blockIdx.y * CG;
@@ -197,17 +215,30 @@ __global__ void __launch_bounds__(TPB) k_multi_dot(const T *__restrict__ V, int6
     wv[u] = (r < n) ? ldg(w + r) : num<T>::zero();
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int g = 0; g < ncol; ++g) {
-    const T *col = V + (int64_t)(c0 + g) * ldv;
-    A acc;
-    acc_set(acc, num<T>::zero());
+  // CU columns per pass, their loads issued together (same per-column order)
+  constexpr int CU = sizeof(T) == 4 ? 4 : 2;
+  for (int g0 = 0; g0 < ncol; g0 += CU) {
+    T vals[CU][U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int64_t r = base + (int64_t)u * TPB;
-      if (r < n) acc_add_prod(acc, ldg(col + r), wv[u]);
+    for (int q = 0; q < CU; ++q) {
+      const T *col = V + (int64_t)(c0 + min(g0 + q, ncol - 1)) * ldv;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t r = base + (int64_t)u * TPB;
+        vals[q][u] = (r < n && g0 + q < ncol) ? ldg(col + r) : num<T>::zero();
+      }
     }
-    const T s = warp_reduce_d(acc_get(acc));
-    if (lane == 0) red[g][wid] = num<T>::to_d(s);
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      if (g0 + q >= ncol) break;
+      A acc;
+      acc_set(acc, num<T>::zero());
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + (int64_t)u * TPB < n) acc_add_prod(acc, vals[q][u], wv[u]);
+      const T s = warp_reduce_d(acc_get(acc));
+      if (lane == 0) red[g0 + q][wid] = num<T>::to_d(s);
+    }
   }
   __syncthreads();
   if (threadIdx.x < ncol) {
@@ -222,6 +253,8 @@ template <typename T>
 __global__ void __launch_bounds__(TPB) k_multi_update(const T *__restrict__ V, int64_t ldv, int J,
                                                       const double *__restrict__ h, T *__restrict__ w,
                                                       int64_t n, double *__restrict__ partials, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename acc_of<T>::type;
   extern __shared__ unsigned char smem_raw[];
   T *hs = reinterpret_cast<T *>(smem_raw);
@@ -241,7 +274,30 @@ __global__ void __launch_bounds__(TPB) k_multi_update(const T *__restrict__ V, i
     const int64_t r = base + (int64_t)u * TPB;
     acc_set(acc[u], (r < n) ? w[r] : num<T>::zero());
   }
-  for (int c = 0; c < J; ++c) {
+  // CU columns per pass: all their loads are issued before the (in-order)
+  // accumulation, for more memory-level parallelism
+  constexpr int CU = sizeof(T) == 4 ? 4 : 2;
+  int c = 0;
+  for (; c + CU <= J; c += CU) {
+    T vals[CU][U];
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      const T *col = V + (int64_t)(c + q) * ldv;
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int64_t r = base + (int64_t)u * TPB;
+        vals[q][u] = (r < n) ? ldg(col + r) : num<T>::zero();
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      const T hc = hs[c + q];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + (int64_t)u * TPB < n) acc_add_prod(acc[u], hc, vals[q][u]);
+    }
+  }
+  for (; c < J; ++c) {
     const T *col = V + (int64_t)c * ldv;
     const T hc = hs[c];
 #pragma unroll
@@ -273,6 +329,8 @@ __global__ void __launch_bounds__(TPB) k_reconstruct(const T *__restrict__ V, in
                                                      const int *__restrict__ m_seg,
                                                      const double *__restrict__ z, double *__restrict__ x,
                                                      int64_t n, int accumulate, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename acc_of<T>::type;
   extern __shared__ unsigned char smem_raw[];
   T *zs = reinterpret_cast<T *>(smem_raw);
@@ -311,6 +369,8 @@ __global__ void __launch_bounds__(TPB) k_reconstruct(const T *__restrict__ V, in
 __global__ void __launch_bounds__(256) k_reduce_cols(const double *__restrict__ partials, int nb, int ncols,
                                                      int mode, double *__restrict__ out_a,
                                                      double *__restrict__ out_b, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[32];
   const int c = blockIdx.x, seg = blockIdx.y;
   if (!seg_active(S, seg)) return;
@@ -332,6 +392,8 @@ __global__ void __launch_bounds__(256) k_norm_finalize(const double *__restrict_
                                                        double *beta_out, double *inv_out,
                                                        const double *__restrict__ ref, int nref,
                                                        double rel, int m_here, DevStatus *st, Seg S) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ double red[32];
   const int seg = blockIdx.x;
   if (!seg_active(S, seg)) return;
@@ -380,21 +442,21 @@ int vec_chunk_rows() { return CHUNK; }
 
 template <typename T>
 int vec_from_f64(const double *in, T *out, int64_t n, cudaStream_t s) {
-  k_from_f64<T><<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(in, out, n);
+  PP_CUDA_TRY(pdl_launch(k_from_f64<T>, dim3(grid_for(n, 256, kMaxGrid)), dim3(256), 0, s, in, out, n));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_to_f64(const T *in, double *out, int64_t n, cudaStream_t s) {
-  k_to_f64<T><<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(in, out, n);
+  PP_CUDA_TRY(pdl_launch(k_to_f64<T>, dim3(grid_for(n, 256, kMaxGrid)), dim3(256), 0, s, in, out, n));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_fill_hash(T *out, int64_t n, uint64_t seed, cudaStream_t s) {
-  k_fill_hash<T><<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(out, n, seed);
+  PP_CUDA_TRY(pdl_launch(k_fill_hash<T>, dim3(grid_for(n, 256, kMaxGrid)), dim3(256), 0, s, out, n, seed));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -404,7 +466,7 @@ template int vec_fill_hash<dw>(dw *, int64_t, uint64_t, cudaStream_t);
 
 template <typename TI, typename TO>
 int vec_convert(const TI *in, TO *out, int64_t n, cudaStream_t s) {
-  k_convert<TI, TO><<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(in, out, n);
+  PP_CUDA_TRY(pdl_launch(k_convert<TI, TO>, dim3(grid_for(n, 256, kMaxGrid)), dim3(256), 0, s, in, out, n));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -413,21 +475,21 @@ template int vec_convert<dw, float>(const dw *, float *, int64_t, cudaStream_t);
 
 template <typename T>
 int vec_scale(const T *in, T *out, int64_t n, double c, const double *c_dev, cudaStream_t s, const Seg &S) {
-  k_scale<T><<<nchunks(n), TPB, 0, s>>>(in, out, n, c, c_dev, S);
+  PP_CUDA_TRY(pdl_launch(k_scale<T>, dim3(nchunks(n)), dim3(TPB), 0, s, in, out, n, c, c_dev, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_copy(const T *in, T *out, int64_t n, cudaStream_t s) {
-  k_copy<T><<<grid_for(n, 256, kMaxGrid), 256, 0, s>>>(in, out, n);
+  PP_CUDA_TRY(pdl_launch(k_copy<T>, dim3(grid_for(n, 256, kMaxGrid)), dim3(256), 0, s, in, out, n));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
 int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int, cudaStream_t s, const Seg &S) {
-  k_dot<T><<<nchunks(n), TPB, 0, s>>>(x, y, n, partials, S);
+  PP_CUDA_TRY(pdl_launch(k_dot<T>, dim3(nchunks(n)), dim3(TPB), 0, s, x, y, n, partials, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -435,7 +497,7 @@ int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int, c
 template <typename T>
 int vec_lanczos_update(T *w, const T *vj, const T *vjm1, int64_t n, const double *alpha,
                        const double *beta_prev, double *partials, int, cudaStream_t s, const Seg &S) {
-  k_lanczos_update<T><<<nchunks(n), TPB, 0, s>>>(w, vj, vjm1, n, alpha, beta_prev, partials, S);
+  PP_CUDA_TRY(pdl_launch(k_lanczos_update<T>, dim3(nchunks(n)), dim3(TPB), 0, s, w, vj, vjm1, n, alpha, beta_prev, partials, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -444,7 +506,7 @@ template <typename T>
 int vec_multi_dot(const T *V, int64_t ldv, int J, const T *w, int64_t n, double *partials, int,
                   cudaStream_t s, const Seg &S) {
   dim3 grd(nchunks(n), (unsigned)((J + CG - 1) / CG));
-  k_multi_dot<T><<<grd, TPB, 0, s>>>(V, ldv, J, w, n, partials, S);
+  PP_CUDA_TRY(pdl_launch(k_multi_dot<T>, grd, dim3(TPB), 0, s, V, ldv, J, w, n, partials, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -454,7 +516,7 @@ int vec_multi_update(const T *V, int64_t ldv, int J, const double *h, T *w, int6
                      double *partials, int, cudaStream_t s, const Seg &S) {
   const size_t sm = (size_t)J * sizeof(T);
   if (sm > 48 * 1024) PP_CUDA_TRY(cudaFuncSetAttribute(k_multi_update<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_multi_update<T><<<nchunks(n), TPB, sm, s>>>(V, ldv, J, h, w, n, partials, S);
+  PP_CUDA_TRY(pdl_launch(k_multi_update<T>, dim3(nchunks(n)), dim3(TPB), sm, s, V, ldv, J, h, w, n, partials, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -464,7 +526,7 @@ int vec_reconstruct(const T *V, int64_t ldv, int m, const double *z, double *x, 
                     int accumulate, cudaStream_t s, const Seg &S, const int *m_seg) {
   const size_t sm = (size_t)m * sizeof(T);
   if (sm > 48 * 1024) PP_CUDA_TRY(cudaFuncSetAttribute(k_reconstruct<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_reconstruct<T><<<nchunks(n), TPB, sm, s>>>(V, ldv, m, m_seg, z, x, n, accumulate, S);
+  PP_CUDA_TRY(pdl_launch(k_reconstruct<T>, dim3(nchunks(n)), dim3(TPB), sm, s, V, ldv, m, m_seg, z, x, n, accumulate, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -472,7 +534,7 @@ int vec_reconstruct(const T *V, int64_t ldv, int m, const double *z, double *x, 
 
 int reduce_cols(const double *partials, int nb, int ncols, int mode, double *out_a, double *out_b,
                 cudaStream_t s, const Seg &S) {
-  k_reduce_cols<<<dim3(ncols, S.nseg), 256, 0, s>>>(partials, nb, ncols, mode, out_a, out_b, S);
+  PP_CUDA_TRY(pdl_launch(k_reduce_cols, dim3(ncols, S.nseg), dim3(256), 0, s, partials, nb, ncols, mode, out_a, out_b, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -481,7 +543,7 @@ int reduce_cols(const double *partials, int nb, int ncols, int mode, double *out
 int norm_finalize(const double *partials, int nb, double *beta_out, double *inv_out,
                   const double *ref, int nref, double rel, int m_here, DevStatus *st,
                   cudaStream_t s, const Seg &S) {
-  k_norm_finalize<<<S.nseg, 256, 0, s>>>(partials, nb, beta_out, inv_out, ref, nref, rel, m_here, st, S);
+  PP_CUDA_TRY(pdl_launch(k_norm_finalize, dim3(S.nseg), dim3(256), 0, s, partials, nb, beta_out, inv_out, ref, nref, rel, m_here, st, S));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;

@@ -185,6 +185,8 @@ __global__ void __launch_bounds__(128) wilson_step(const T *__restrict__ in, con
                                                    const T *__restrict__ y, const T *__restrict__ v,
                                                    T *__restrict__ out, const float2 *__restrict__ U,
                                                    Lat lat, T Kd, T Kh, T Kb, T Kv) {
+  pdl_wait();
+  pdl_trigger();
   using A = typename acc_of<T>::type;
   const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (s >= lat.V) return;
@@ -235,8 +237,8 @@ int launch(const T *in, const T *x, const T *y, const T *v, T *out, const float2
            double kd, double kh, double kb, double kv, cudaStream_t s) {
   const int bs = 128;
   const int64_t nb = (lat.V + bs - 1) / bs;
-  wilson_step<T, DAG, AX, SY, AV><<<(unsigned)nb, bs, 0, s>>>(in, x, y, v, out, U, lat, host_c<T>(kd),
-                                                             host_c<T>(kh), host_c<T>(kb), host_c<T>(kv));
+  PP_CUDA_TRY(pdl_launch(wilson_step<T, DAG, AX, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, in, x, y, v, out, U, lat, host_c<T>(kd),
+                                                             host_c<T>(kh), host_c<T>(kb), host_c<T>(kv)));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;

@@ -160,3 +160,31 @@ def test_argument_validation():
     finally:
         pp.pp_destroy(h)
     pp.pp_destroy(None)
+
+
+def test_autotune_degree_model():
+    # F64 stencil handles: the degree choice needs no device work (closed-form
+    # interval); the chosen degree is a candidate and q is built with it
+    pp = load()
+    cands = {0, 1, 2, 3, 4, 6, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128}
+    for kind, dims in ((pp.PP_LAPLACE2D5, (1000, 1000)), (pp.PP_LAPLACE3D7, (100, 100, 100)),
+                       (pp.PP_LAPLACE2D5, (12, 10))):
+        h = pp.pp_create_stencil(kind, dims)
+        try:
+            d = pp.pp_autotune(h, 1e-9, 64)
+            assert d in cands and d <= 64
+            c, ab, img = pp.pp_get_poly(h)
+            assert len(c) == d + 1
+        finally:
+            pp.pp_destroy(h)
+    # harder problem (larger kappa) never gets a lower degree than an easy one of the same kind
+    hs = [pp.pp_create_stencil(pp.PP_LAPLACE2D5, dims) for dims in ((1000, 1000), (20, 20))]
+    try:
+        d_hard, d_easy = (pp.pp_autotune(h, 1e-9, 64) for h in hs)
+        assert d_hard >= d_easy
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_autotune(hs[0], 0.0, 64)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+    finally:
+        for h in hs:
+            pp.pp_destroy(h)
