@@ -67,6 +67,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--plain-m-max", type=int, default=1000)
+    p.add_argument("--two-pass", action="store_true",
+                   help="two-pass Lanczos (O(n) basis memory, twice the operator passes)")
     p.add_argument("--autotune", action="store_true", help="degree and tile from pp_autotune")
     a = p.parse_args()
     w = WORKLOADS[a.workload]
@@ -91,7 +93,8 @@ def dist_env():
 
 
 def config(args, ws):
-    return {"workload": args.desc + (" (degree and tile autotuned)" if args.autotune else ""),
+    return {"workload": args.desc + (" (degree and tile autotuned)" if args.autotune else "")
+            + (", two-pass Lanczos" if args.two_pass else ""),
             "grid": list(args.dims), "n": args.n,
             "ch": 0.5 if args.kind == "convdiff3d7" else 0.0,
             "func": "sqrt" if args.func > 0 else "invsqrt", "poly": "chebyshev", "degree": args.degree,
@@ -146,6 +149,35 @@ def cpu_sample(args, m_full):
                       f"Gram-Schmidt products) run for {k} iterations on the full workload: set-up "
                       f"{setup:.2f}s + {t_iter:.2f}s/iteration, extrapolated to the {m_full} iterations "
                       f"of a solve = {t_solve:.1f}s"}
+
+
+def cpu_sample_batch(args, probs, budget_s=15.0):
+    """The oracle (Algorithm 1, FP64) on one right-hand side of each problem of
+    the batch's list, in list order, until about budget_s seconds of work."""
+    from oracle import chebyshev as cheb, krylov, operators as ops
+    import synth
+    solved, t_used, used = 0, 0.0, []
+    for i, p in enumerate(probs):
+        dims = p["dims"]
+        if p["kind"] == "convdiff3d7":
+            A, ab = ops.convdiff(dims, 0.5), ops.convdiff_interval(dims, 0.5)
+        else:
+            A, ab = ops.laplace(dims), ops.laplace_interval(dims)
+        deg = 16
+        c = cheb.interp_coeffs(ab[0], ab[1], deg + 1)
+        b = synth.rhs(A.shape[0], 1000 + i, nrhs=p["nrhs"]) if p["nrhs"] > 1 else synth.rhs(A.shape[0], 1000 + i)[None, :]
+        t0 = time.perf_counter()
+        krylov.pp_arnoldi(A.dot, b[0], 0.5 * p["f"], c, ab, side="left", m_max=1000, tol=args.tol,
+                          k_chk=max(1, 64 // (deg + 1)), hermitian=p["kind"] != "convdiff3d7",
+                          orth="lanczos" if p["kind"] != "convdiff3d7" else "cgs2")
+        t_used += time.perf_counter() - t0
+        solved += 1
+        used.append(i)
+        if t_used > budget_s:
+            break
+    return {"value": solved / t_used, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"oracle Algorithm 1 (numpy/scipy FP64, degree 16) on one right-hand side of each of "
+                      f"problems {used[0]}..{used[-1]} of the batch's list ({solved} solves, {t_used:.1f}s)"}
 
 
 def run_reference(args):
@@ -286,6 +318,9 @@ def run_ours(args):
     o = pp.pp_default_opts()
     o.precision = {"dw": pp.PP_PREC_DW, "f64": pp.PP_PREC_F64, "mixed": pp.PP_PREC_MIXED}[args.prec]
     pp.pp_set_opts(h, o)
+    if args.two_pass:  # O(n) basis memory: two-pass Lanczos
+        o.two_pass = 1
+        pp.pp_set_opts(h, o)
     if args.autotune:
         args.degree = pp.pp_autotune(h, args.tol, 64)
     vdt = torch.complex128 if args.complex else torch.float64
@@ -323,6 +358,7 @@ def run_ours(args):
     ident = float(torch.linalg.norm(s2 - ref_id) / torch.linalg.norm(ref_id))
     o_t = pp.pp_default_opts()
     o_t.precision = pp.PP_PREC_DW
+    o_t.two_pass = o.two_pass
     pp.pp_set_opts(h, o_t)
     pp.pp_apply(h, args.func, b, s2, m_max=max(m_max, 1000), tol=1e-13)
     pp.pp_set_opts(h, o)
@@ -478,6 +514,11 @@ def run_batch(args):
     for _ in range(args.warmup):
         st = step()
         assert all(q.status == pp.PP_OK for q in st)
+    # operator-chain profiling (CUDA events around every run of batched stencil launches)
+    o = pp.pp_default_opts()
+    o.precision = prec
+    o.profile = 1
+    pp.pp_set_opts(hs[0], o)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clk = ClockSampler(local)
@@ -492,6 +533,25 @@ def run_batch(args):
     clocks = clk.stop()
     t_total = sum(a.elapsed_time(e) for a, e in ev) / 1e3
     value = args.steps * nsolves / t_total
+    o.profile = 0
+    pp.pp_set_opts(hs[0], o)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    cb, cms, cl = stats[0].chain_bytes, stats[0].chain_ms, stats[0].chain_launches
+    achieved = cb / (cms / 1e3) / 1e9 if cms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "bst_step (batched operator + Clenshaw update, one step of every process)",
+                "peak_source": peak_src,
+                "timing": "CUDA events around each run of batched operator launches of the last timed step, "
+                          "summed over the groups' streams",
+                "launches": cl, "bytes_per_launch": cb / max(cl, 1)}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = cpu_sample_batch(args, probs)
     # end to end: pinned host b in, batch, host x out
     e2e_t = []
     for i in range(args.steps):
@@ -518,7 +578,7 @@ def run_batch(args):
         "gpu_launches": int(stats[0].launches), "e2e": {"value": args.steps * nsolves / sum(e2e_t),
                                                          "unit": "solves/s", "h2d_bytes_per_step": 8 * rows,
                                                          "d2h_bytes_per_step": 8 * rows},
-        "clocks": clocks, "roofline": None, "cpu_baseline": None,
+        "clocks": clocks, "roofline": roofline, "cpu_baseline": cpu,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

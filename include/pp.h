@@ -111,7 +111,12 @@ typedef struct pp_opts {
                            (Sec. 6, Example 1); 0 = max(1, floor(64/(deg+1)))      */
   int32_t profile;      /* 1: time every operator launch of the polynomial chain
                            with CUDA events (pp_stats.chain_*)                       */
-  int32_t reserved[7];
+  int32_t two_pass;     /* 1: two-pass Lanczos (Hermitian A, Lanczos only): the first
+                           pass keeps three basis vectors and H_m, the second
+                           regenerates v_1..v_m from the stored coefficients and
+                           accumulates x; twice the operator work, O(n) memory
+                           instead of O(m n).  mvms counts both passes.            */
+  int32_t reserved[6];
 } pp_opts;
 
 typedef struct pp_stats {
@@ -261,9 +266,10 @@ int pp_apply_host(pp_handle h, int32_t f, const double *b_h, int64_t nrhs, int32
  * when the switching rule holds for all of its unconverged processes.
  * stats (host, count entries, may be NULL): per handle, iters = the largest
  * Krylov dimension over its right-hand sides, mvms / inner_products summed
- * over them, est_err the largest estimate, ms_total and launches of the
- * whole batch.  Returns PP_ERR_NOT_CONVERGED if any process reached m_max
- * (1 <= m_max <= 1024).
+ * over them, est_err the largest estimate; ms_total, launches and the
+ * chain_* operator accounting of the whole batch (chain_ms with
+ * handles[0]'s opts.profile = 1, summed over the groups' streams).  Returns
+ * PP_ERR_NOT_CONVERGED if any process reached m_max (1 <= m_max <= 1024).
  */
 int pp_apply_batch(const pp_handle *handles, int32_t count, const int32_t *f, const void *const *b_d,
                    const int64_t *nrhs, void *const *x_d, int32_t m_max, double tol, void *cuda_stream,

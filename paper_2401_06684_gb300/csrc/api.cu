@@ -165,10 +165,15 @@ DLayout dlayout(const pp_ctx *c, int m_cap) {
   return L;
 }
 
-int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y) {
+// Basis layout requested from ensure_ws.
+enum Layout { LAYOUT_KEEP = -1, LAYOUT_FULL = 0, LAYOUT_TWO_PASS = 1 };
+
+int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y, int layout = LAYOUT_KEEP) {
   Workspace &w = c->ws;
   const size_t esz = 8;  // double and double-word are both 8 bytes
-  if (w.prec != prec || m_cap > w.m_cap || (need_y && !w.has_y) || !w.dmem) {
+  const bool two_pass = layout == LAYOUT_KEEP ? w.two_pass : layout == LAYOUT_TWO_PASS;
+  if (two_pass) need_y = false;
+  if (w.prec != prec || m_cap > w.m_cap || (need_y && !w.has_y) || !w.dmem || w.two_pass != two_pass) {
     if (w.V) cudaFree(w.V), w.V = nullptr;
     if (w.Y) cudaFree(w.Y), w.Y = nullptr;
     if (w.tmp) cudaFree(w.tmp), w.tmp = nullptr;
@@ -176,16 +181,19 @@ int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y) {
     if (w.Vf) cudaFree(w.Vf), w.Vf = nullptr;
     if (w.Yf) cudaFree(w.Yf), w.Yf = nullptr;
     const int mc = m_cap > w.m_cap ? m_cap : w.m_cap;
+    const int vcols = two_pass ? 4 : mc + 1;
+    if (two_pass) w.has_y = false;
     w.ldv = (c->n + 31) / 32 * 32;
     w.esz = esz;
-    PP_CUDA_TRY(cudaMalloc(&w.V, (size_t)(mc + 1) * w.ldv * esz));
+    w.two_pass = two_pass;
+    PP_CUDA_TRY(cudaMalloc(&w.V, (size_t)vcols * w.ldv * esz));
     if (need_y || w.has_y) {
       PP_CUDA_TRY(cudaMalloc(&w.Y, (size_t)mc * w.ldv * esz));
       w.has_y = true;
     }
     PP_CUDA_TRY(cudaMalloc(&w.tmp, (size_t)kTmpVecs * w.ldv * esz));
     if (prec == PP_PREC_MIXED) {
-      PP_CUDA_TRY(cudaMalloc(&w.Vf, (size_t)(mc + 1) * w.ldv * sizeof(float)));
+      PP_CUDA_TRY(cudaMalloc(&w.Vf, (size_t)vcols * w.ldv * sizeof(float)));
       if (w.has_y) PP_CUDA_TRY(cudaMalloc(&w.Yf, (size_t)mc * w.ldv * sizeof(float)));
     }
     DLayout L = dlayout(c, mc);
@@ -343,8 +351,14 @@ int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double b
     const int J = j + 1;
     RC(vec_multi_dot<T>(V, ldv, J, wv, n, S.part, nb, s));
     RC(reduce_cols(S.part, nb, J, 1, S.h1, hcol, s));
-    RC(vec_multi_update<T>(V, ldv, J, S.h1, wv, n, nullptr, nb, s));
-    RC(vec_multi_dot<T>(V, ldv, J, wv, n, S.part, nb, s));
+    // first update and second inner products in one pass over V where J allows
+    const int rc = vec_update_dot<T>(V, ldv, J, S.h1, wv, n, S.part, s);
+    if (rc == PP_ERR_UNSUPPORTED) {
+      RC(vec_multi_update<T>(V, ldv, J, S.h1, wv, n, nullptr, nb, s));
+      RC(vec_multi_dot<T>(V, ldv, J, wv, n, S.part, nb, s));
+    } else if (rc != PP_OK) {
+      return rc;
+    }
     RC(reduce_cols(S.part, nb, J, 2, S.h1, hcol, s));
     RC(vec_multi_update<T>(V, ldv, J, S.h1, wv, n, S.part, nb, s));
     RC(norm_finalize(S.part, nb, hcol + j + 1, S.scal, hcol, J, bd_rel, J, c->ws.st, s));
@@ -371,7 +385,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   const int prec = c->opts.precision;
   const bool mixed = !std::is_same<T1, T2>::value;
   const bool right = c->opts.side == PP_RIGHT;
-  RC(ensure_ws(c, prec, m_max, right));
+  RC(ensure_ws(c, prec, m_max, right, LAYOUT_FULL));
   Workspace &w = c->ws;
   cudaStream_t s = c->stream;
   const OpDesc op1 = make_op(c, arith_of<T1>());
@@ -566,6 +580,233 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
     out->chain_bytes = c->chain_bytes;
     out->chain_ms = c->opts.profile ? prof_ms(c) : 0.0;
     out->switch_iter = switched_at;
+  }
+  if (status != PP_OK) pp_set_error(status, "m_max reached before the stopping estimate fell below tol");
+  return status;
+}
+
+// Two-pass Lanczos (Hermitian A): pass 1 is the Lanczos loop of solve() with
+// three rotating basis vectors, keeping H_m and the stopping checks; pass 2
+// regenerates v_1 .. v_m from the stored alpha_j, beta_j (the same kernels on
+// the same data, so the same vectors bit for bit) and accumulates f_m = V_m z
+// (left) or Y_m z (right, y_j = q(A) v_j recomputed in the step) as it goes.
+// The precision switch of PP_PREC_MIXED happens at the same step in both
+// passes.  Basis storage: columns j mod 3, plus v_1 kept in column 3.
+template <typename T1, typename T2>
+int solve_two_pass(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *x_dev, pp_stats *out) {
+  const int prec = c->opts.precision;
+  const bool mixed = !std::is_same<T1, T2>::value;
+  const bool right = c->opts.side == PP_RIGHT;
+  RC(ensure_ws(c, prec, m_max, false, LAYOUT_TWO_PASS));
+  Workspace &w = c->ws;
+  cudaStream_t s = c->stream;
+  const OpDesc op1 = make_op(c, arith_of<T1>());
+  const OpDesc op2 = make_op(c, arith_of<T2>());
+  const int64_t n = c->n, ldv = w.ldv;
+  const DLayout L = dlayout(c, w.m_cap);
+  double *D = w.dmem;
+  double *H = D + L.H, *part = D + L.part, *X = D + L.X, *tri = D + L.tri, *z = D + L.z, *zprev = D + L.zprev;
+  double *sig = D + L.sig, *wt = D + L.wt, *scal = D + L.scal;
+  const int ldh = L.ldh, nb = L.nb, K = L.K, deg = c->degree;
+  T1 *V1 = (T1 *)w.V;
+  T2 *V2 = (T2 *)(mixed ? w.Vf : w.V);
+  T1 *t1[6];
+  T2 *t2[6];
+  for (int i = 0; i < 6; ++i) {
+    t1[i] = (T1 *)w.tmp + (size_t)i * ldv;
+    t2[i] = (T2 *)w.tmp + (size_t)i * ldv;
+  }
+  auto col1 = [&](int j) { return V1 + (size_t)(j % 3) * ldv; };
+  auto col2 = [&](int j) { return V2 + (size_t)(j % 3) * ldv; };
+  const int kchk = c->opts.check_every > 0 ? c->opts.check_every : (64 / (deg + 1) > 1 ? 64 / (deg + 1) : 1);
+  const int64_t launches0 = pp_launch_count();
+  int64_t mvms = 0, ip = 0;
+  c->chain_launches = 0;
+  c->chain_bytes = 0.0;
+  c->prof_used = 0;
+  PP_CUDA_TRY(cudaEventRecord(w.ev0, s));
+  PP_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(DevStatus), s));
+  PP_CUDA_TRY(cudaMemsetAsync(H, 0, sizeof(double) * (size_t)ldh * w.m_cap, s));
+  // w = A q(A)^2 v (three stages; right preconditioning leaves y = q(A) v in ty)
+  auto apply_pre = [&](auto tag, const OpDesc &op, auto *v, auto *wv, auto **t, auto *ty) -> int {
+    using T = decltype(tag);
+    T *pb[3] = {t[2], t[3], t[4]};
+    if (!right) {
+      RC_(run_op_timed<T>(c, op, v, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
+      RC_(poly_apply_t<T>(c, op, t[0], t[1], pb));
+      RC_(poly_apply_t<T>(c, op, t[1], wv, pb));
+    } else {
+      RC_(poly_apply_t<T>(c, op, v, ty, pb));
+      RC_(poly_apply_t<T>(c, op, ty, t[0], pb));
+      RC_(run_op_timed<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
+    }
+    mvms += 2 * deg + 1;
+    return PP_OK;
+  };
+  // start vector (as solve())
+  const T1 *rhs;
+  if (std::is_same<T1, double>::value) {
+    rhs = (const T1 *)b_dev;
+  } else {
+    RC(vec_from_f64<T1>(b_dev, t1[0], n, s));
+    rhs = t1[0];
+  }
+  if (f == PP_SQRT) {
+    RC(run_op_timed<T1>(c, op1, rhs, nullptr, nullptr, t1[1], {1.0, 0.0, 0.0, false, false}));
+    rhs = t1[1];
+    mvms += 1;
+  }
+  T1 *v0 = V1 + (size_t)3 * ldv;
+  {
+    T1 *pb[3] = {t1[2], t1[3], t1[4]};
+    if (!right) {
+      RC(poly_apply_t<T1>(c, op1, rhs, v0, pb));
+      mvms += deg;
+    } else {
+      RC(vec_copy<T1>(rhs, v0, n, s));
+    }
+  }
+  RC(vec_dot_partials<T1>(v0, v0, n, part, nb, s));
+  RC(norm_finalize(part, nb, &w.st->beta0, scal, nullptr, 0, 0.0, 0, w.st, s));
+  RC(vec_scale<T1>(v0, v0, n, 1.0, scal, s));
+  RC(vec_copy<T1>(v0, col1(0), n, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  PP_CUDA_TRY(cudaStreamSynchronize(s));
+  DevStatus hs = *w.st_host;
+  if (hs.bad) return pp_set_error(PP_ERR_INVALID_ARG, "non-finite norm of the start vector");
+  if (hs.breakdown) {
+    PP_CUDA_TRY(cudaMemsetAsync(x_dev, 0, sizeof(double) * n, s));
+    PP_CUDA_TRY(cudaStreamSynchronize(s));
+    if (out) {
+      memset(out, 0, sizeof(*out));
+      out->mvms = mvms;
+      out->launches = pp_launch_count() - launches0;
+    }
+    return PP_OK;
+  }
+  PP_CUDA_TRY(cudaMemsetAsync(&w.st->conv, 0, 3 * sizeof(int), s));
+  // Lanczos step j in arithmetic T on the rotating columns; pass 1 forms
+  // alpha_j and beta_j, pass 2 (regen) reuses the stored ones
+  auto lanczos_step = [&](auto tag, const OpDesc &op, auto *vj, auto *vjm1, auto *wv, auto **t, int j, bool regen,
+                          double bd_rel) -> int {
+    using T = decltype(tag);
+    RC_(apply_pre(tag, op, vj, wv, t, t[5]));
+    double *hcol = H + (size_t)j * ldh;
+    if (!regen) {
+      RC_(vec_dot_partials<T>(wv, vj, n, part, nb, s));
+      RC_(reduce_cols(part, nb, 1, 0, hcol + j, nullptr, s));
+    }
+    RC_(vec_lanczos_update<T>(wv, vj, j > 0 ? vjm1 : nullptr, n, hcol + j, j > 0 ? H + (size_t)(j - 1) * ldh + j : nullptr,
+                              part, nb, s));
+    if (!regen) {
+      RC_(norm_finalize(part, nb, hcol + j + 1, scal, hcol + j, 1, bd_rel, j + 1, w.st, s));
+      ip += 2;
+    } else {
+      RC_(vec_recip(hcol + j + 1, scal, s));
+    }
+    return vec_scale<T>(wv, wv, n, 1.0, scal, s);
+  };
+  const double kappa_pre = c->img_lo > 0.0 ? c->img_hi / c->img_lo : INFINITY;
+  const double amp = kMixedSafety * kU32 * kappa_pre;
+  double est_prev = INFINITY;
+  int phase = 1, sw = mixed ? -1 : 0;
+  auto convert_live = [&](int m_now) -> int {  // v_{m_now} and v_{m_now - 1} to FP32
+    if constexpr (!std::is_same<T1, T2>::value) {
+      for (int q = std::max(0, m_now - 1); q <= m_now; ++q) RC_((vec_convert<T1, T2>(col1(q), col2(q), n, s)));
+    }
+    (void)m_now;
+    return PP_OK;
+  };
+  if (mixed && amp <= tol) {
+    RC(convert_live(0));
+    phase = 2;
+    sw = 0;
+  }
+  int m = 0, mprev = 0, checks = 0, status = PP_ERR_NOT_CONVERGED;
+  bool bd = false;
+  for (int j = 0; j < m_max; ++j) {  // pass 1
+    if (phase == 1)
+      RC(lanczos_step(T1(), op1, col1(j), col1(j + 2), col1(j + 1), t1, j, false, kBreakdownRel));
+    else
+      RC(lanczos_step(T2(), op2, col2(j), col2(j + 2), col2(j + 1), t2, j, false,
+                      std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
+    m = j + 1;
+    if (m % kchk == 0 || m == m_max) {
+      RC(small_tridiag_quad(H, ldh, m, sig, wt, K, X, tri, s));
+      RC(small_combine(X, K, m, mprev, z, zprev, tol, w.st, s));
+      mprev = m;
+      ++checks;
+      PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+      PP_CUDA_TRY(cudaStreamSynchronize(s));
+      hs = *w.st_host;
+      if (hs.bad) return pp_set_error(PP_ERR_CUDA, "non-finite values in the Krylov process");
+      if (hs.breakdown) {
+        bd = true;
+        status = PP_OK;
+        break;
+      }
+      if (hs.conv) {
+        status = PP_OK;
+        break;
+      }
+      if (mixed && phase == 1 && std::isfinite(est_prev) && std::isfinite(hs.est) && est_prev > 0.0) {
+        double rho = std::pow(hs.est / est_prev, 1.0 / kchk);
+        if (!(rho < 0.999)) rho = 0.999;
+        if (hs.est * rho / (1.0 - rho) * amp <= tol) {
+          RC(convert_live(m));
+          phase = 2;
+          sw = m;
+        }
+      }
+      est_prev = hs.est;
+    }
+  }
+  // pass 2: regenerate the basis and accumulate x (mz columns, the last
+  // check's z).  As in solve(), the leading columns 0 .. sw of the
+  // reconstruction come from the phase-1 vectors and step j runs in FP32 from
+  // j = sw on (sw = the pass-1 switch).
+  const int mz = mprev > 0 ? mprev : m;
+  RC(vec_copy<T1>(v0, col1(0), n, s));
+  for (int j = 0; j < mz; ++j) {
+    const bool phase2 = mixed && sw >= 0 && j >= sw;
+    if (!right) {
+      if (!mixed || sw < 0 || j <= sw)
+        RC(vec_reconstruct<T1>(col1(j), ldv, 1, z + j, x_dev, n, j > 0 ? 1 : 0, s));
+      else
+        RC(vec_reconstruct<T2>(col2(j), ldv, 1, z + j, x_dev, n, 1, s));
+    }
+    if (mixed && j == sw) RC(convert_live(j));
+    if (j + 1 < mz || right) {
+      if (!phase2) {
+        RC(lanczos_step(T1(), op1, col1(j), col1(j + 2), col1(j + 1), t1, j, true, kBreakdownRel));
+        if (right) RC(vec_reconstruct<T1>(t1[5], ldv, 1, z + j, x_dev, n, j > 0 ? 1 : 0, s));
+      } else {
+        RC(lanczos_step(T2(), op2, col2(j), col2(j + 2), col2(j + 1), t2, j, true,
+                        std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
+        if (right) RC(vec_reconstruct<T2>(t2[5], ldv, 1, z + j, x_dev, n, j > 0 ? 1 : 0, s));
+      }
+    }
+  }
+  PP_CUDA_TRY(cudaEventRecord(w.ev1, s));
+  PP_CUDA_TRY(cudaEventSynchronize(w.ev1));
+  if (out) {
+    memset(out, 0, sizeof(*out));
+    out->status = status;
+    out->iters = bd ? hs.m_bd : m;
+    out->checks = checks;
+    out->breakdown = bd ? 1 : 0;
+    out->mvms = mvms;
+    out->inner_products = ip;
+    out->est_err = hs.est;
+    out->beta0 = hs.beta0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, w.ev0, w.ev1);
+    out->ms_total = ms;
+    out->launches = pp_launch_count() - launches0;
+    out->chain_launches = c->chain_launches;
+    out->chain_bytes = c->chain_bytes;
+    out->chain_ms = c->opts.profile ? prof_ms(c) : 0.0;
+    out->switch_iter = sw;
   }
   if (status != PP_OK) pp_set_error(status, "m_max reached before the stopping estimate fell below tol");
   return status;
@@ -867,6 +1108,7 @@ int pp_set_opts(pp_handle c, const pp_opts *o) {
   if (o->orth < PP_ORTH_AUTO || o->orth > PP_ORTH_CGS2) return pp_set_error(PP_ERR_INVALID_ARG, "bad orth");
   if (o->check_every < 0) return pp_set_error(PP_ERR_INVALID_ARG, "check_every < 0");
   if (o->profile != 0 && o->profile != 1) return pp_set_error(PP_ERR_INVALID_ARG, "profile must be 0 or 1");
+  if (o->two_pass != 0 && o->two_pass != 1) return pp_set_error(PP_ERR_INVALID_ARG, "two_pass must be 0 or 1");
   c->opts = *o;
   return PP_OK;
 }
@@ -992,6 +1234,15 @@ int pp_apply(pp_handle c, int32_t f, const void *b_d, int64_t nrhs, int32_t m_ma
     int64_t nnz = 0;
     PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
     c->nnz = nnz;
+  }
+  if (c->opts.two_pass) {
+    const bool lanczos = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
+    if (!lanczos) return pp_set_error(PP_ERR_INVALID_ARG, "two-pass needs the Lanczos recurrence (Hermitian A)");
+    if (c->opts.precision == PP_PREC_MIXED)
+      return solve_two_pass<dw, float>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);
+    if (c->opts.precision == PP_PREC_DW)
+      return solve_two_pass<dw, dw>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);
+    return solve_two_pass<double, double>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);
   }
   if (c->opts.precision == PP_PREC_MIXED)
     return solve<dw, float>(c, f, (const double *)b_d, m_max, tol, (double *)x_d, stats);

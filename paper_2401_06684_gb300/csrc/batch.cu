@@ -210,6 +210,48 @@ struct GroupCtx {
   DevStatus *st = nullptr;
   int *active = nullptr, *sqrt_mask = nullptr, *chunk_seg = nullptr, *chunk0 = nullptr;
   Allocs *alloc = nullptr;
+  // operator-launch accounting (pp_stats.chain_*): launches, algorithmic bytes
+  // over the unconverged processes, and with profiling CUDA events around
+  // every run of operator launches
+  bool profile = false;
+  double active_rows = 0.0;
+  int64_t chain_launches = 0;
+  double chain_bytes = 0.0;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  ~GroupCtx() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
+  int prof_begin() {
+    if (!profile) return PP_OK;
+    if (ev_used + 2 > ev.size())
+      for (int i = 0; i < 64; ++i) {
+        cudaEvent_t e;
+        PP_CUDA_TRY(cudaEventCreate(&e));
+        ev.push_back(e);
+      }
+    PP_CUDA_TRY(cudaEventRecord(ev[ev_used], s));
+    return PP_OK;
+  }
+  int prof_end() {
+    if (!profile) return PP_OK;
+    PP_CUDA_TRY(cudaEventRecord(ev[ev_used + 1], s));
+    ev_used += 2;
+    return PP_OK;
+  }
+  double prof_ms() const {
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < ev_used; i += 2) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) == cudaSuccess) t += ms;
+    }
+    return t;
+  }
+  template <typename T>
+  void count(bool sy, bool av) {
+    chain_launches += 1;
+    chain_bytes += (2.0 + (sy ? 1.0 : 0.0) + (av ? 1.0 : 0.0)) * (double)sizeof(T) * active_rows;
+  }
   Seg seg(bool with_active) const {
     Seg S;
     S.nseg = nseg;
@@ -228,6 +270,7 @@ int poly_batch(GroupCtx &G, const ArithTabs<T> &A, const T *in, T *out, T *bufs[
   const int ns = G.nseg;
   cudaStream_t s = G.s;
   auto step = [&](int t, const T *x, const T *y, const T *v, T *o, bool sy, bool av) {
+    G.count<T>(sy, av);
     return op_step_batch<T>(A.bseg, ns, A.nblk, A.P, A.K + (size_t)(1 + t) * ns, G.active, x, y, v, o, sy, av, s);
   };
   if (k == 0) return vec_scale<T>(in, out, G.N, 1.0, G.dmem + G.L.qc0, s, G.seg(true));
@@ -248,7 +291,17 @@ int poly_batch(GroupCtx &G, const ArithTabs<T> &A, const T *in, T *out, T *bufs[
 
 template <typename T>
 int aop_batch(GroupCtx &G, const ArithTabs<T> &A, const int *mask, const T *x, T *out) {
-  return op_step_batch<T>(A.bseg, G.nseg, A.nblk, A.P, A.K, mask, x, nullptr, nullptr, out, false, false, G.s);
+  G.count<T>(false, false);
+  BRC(G.prof_begin());
+  BRC(op_step_batch<T>(A.bseg, G.nseg, A.nblk, A.P, A.K, mask, x, nullptr, nullptr, out, false, false, G.s));
+  return G.prof_end();
+}
+
+template <typename T>
+int poly_batch_timed(GroupCtx &G, const ArithTabs<T> &A, const T *in, T *out, T *bufs[3]) {
+  BRC(G.prof_begin());
+  BRC(poly_batch<T>(G, A, in, out, bufs));
+  return G.prof_end();
 }
 
 // One lockstep Krylov step j in arithmetic T (the step of pp_apply for every segment).
@@ -262,12 +315,12 @@ int krylov_step_batch(GroupCtx &G, const ArithTabs<T> &A, T *V, T *Y, T *t[6], i
   T *wv = V + (size_t)(j + 1) * N;
   if (!G.right) {
     BRC(aop_batch<T>(G, A, G.active, vj, t[0]));
-    BRC(poly_batch<T>(G, A, t[0], t[1], pb));
-    BRC(poly_batch<T>(G, A, t[1], wv, pb));
+    BRC(poly_batch_timed<T>(G, A, t[0], t[1], pb));
+    BRC(poly_batch_timed<T>(G, A, t[1], wv, pb));
   } else {
     T *yj = Y + (size_t)j * N;
-    BRC(poly_batch<T>(G, A, vj, yj, pb));
-    BRC(poly_batch<T>(G, A, yj, t[0], pb));
+    BRC(poly_batch_timed<T>(G, A, vj, yj, pb));
+    BRC(poly_batch_timed<T>(G, A, yj, t[0], pb));
     BRC(aop_batch<T>(G, A, G.active, t[0], wv));
   }
   const Seg S = G.seg(true);
@@ -287,8 +340,13 @@ int krylov_step_batch(GroupCtx &G, const ArithTabs<T> &A, T *V, T *Y, T *t[6], i
     double *h1 = G.dmem + L.h1;
     BRC(vec_multi_dot<T>(V, N, J, wv, N, G.part, G.nb, s, S));
     BRC(reduce_cols(G.part, G.nb, J, 1, h1, hcol, s, S));
-    BRC(vec_multi_update<T>(V, N, J, h1, wv, N, nullptr, G.nb, s, S));
-    BRC(vec_multi_dot<T>(V, N, J, wv, N, G.part, G.nb, s, S));
+    const int rc = vec_update_dot<T>(V, N, J, h1, wv, N, G.part, s, S);
+    if (rc == PP_ERR_UNSUPPORTED) {
+      BRC(vec_multi_update<T>(V, N, J, h1, wv, N, nullptr, G.nb, s, S));
+      BRC(vec_multi_dot<T>(V, N, J, wv, N, G.part, G.nb, s, S));
+    } else if (rc != PP_OK) {
+      return rc;
+    }
     BRC(reduce_cols(G.part, G.nb, J, 2, h1, hcol, s, S));
     BRC(vec_multi_update<T>(V, N, J, h1, wv, N, G.part, G.nb, s, S));
     BRC(norm_finalize(G.part, G.nb, hcol + j + 1, scal, hcol, J, bd_rel, J, G.st, s, S));
@@ -357,9 +415,14 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
 
 // Lockstep solve of one group; T1 = phase-1 arithmetic, T2 = FP32 for
 // PP_PREC_MIXED (else T2 = T1).
+struct ChainOut {
+  int64_t launches = 0;
+  double bytes = 0.0, ms = 0.0;
+};
+
 template <typename T1, typename T2>
 int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int kchk, int m_max, double tol,
-              cudaStream_t s, std::vector<SegOut> &res, int64_t *launches_out) {
+              cudaStream_t s, std::vector<SegOut> &res, int64_t *launches_out, ChainOut *chain, bool profile) {
   const bool mixed = !std::is_same<T1, T2>::value;
   const int ns = (int)segs.size();
   const int CH = vec_chunk_rows();
@@ -372,6 +435,7 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
   G.lanczos = lanczos;
   G.right = right;
   G.s = s;
+  G.profile = profile;
   // concatenated layout
   std::vector<int64_t> off(ns), len(ns);
   std::vector<int> cseg, c0(ns + 1);
@@ -508,6 +572,11 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
       res[i].iters = 0;
     }
   }
+  auto update_rows = [&]() {
+    G.active_rows = 0.0;
+    for (int i = 0; i < ns; ++i)
+      if (act[i]) G.active_rows += (double)len[i];
+  };
   // beta0 is read by the small solves from the status record
   for (int i = 0; i < ns; ++i) hs[i].beta0 = beta0[i];
   PP_CUDA_TRY(cudaMemcpyAsync(G.st, hs.data(), sizeof(DevStatus) * ns, cudaMemcpyHostToDevice, s));
@@ -515,6 +584,7 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
   ++pp_launch_count();
   PP_CUDA_TRY(cudaMemcpyAsync(G.active, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
 
+  update_rows();
   const Seg S = G.seg(true);
   double kappa = 0.0;
   for (const SegIn &q : segs) kappa = std::fmax(kappa, q.c->img_lo > 0 ? q.c->img_hi / q.c->img_lo : INFINITY);
@@ -598,6 +668,7 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
         est_prev[i] = hs[i].est;
       }
       PP_CUDA_TRY(cudaMemcpyAsync(G.active, act.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
+      update_rows();
       if (mixed && phase == 1 && nact > 0 && all_relaxed) {
         BRC(switch_phase(m));
         switched_at = m;
@@ -633,6 +704,9 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
   PP_CUDA_TRY(cudaGetLastError());
   PP_CUDA_TRY(cudaStreamSynchronize(s));
   *launches_out += pp_launch_count() - launches0;
+  chain->launches = G.chain_launches;
+  chain->bytes = G.chain_bytes;
+  chain->ms = G.prof_ms();
   return PP_OK;
 }
 
@@ -690,6 +764,7 @@ extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int
       where[g].push_back({i, (int)r});
     }
   }
+  const bool profile = handles[0]->opts.profile != 0;
   int dev = 0;
   PP_CUDA_TRY(cudaGetDevice(&dev));
   cudaStream_t caller = (cudaStream_t)cuda_stream;
@@ -709,6 +784,7 @@ extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int
   std::vector<int> rcs(ng, PP_OK);
   std::vector<std::string> errs(ng);
   std::vector<int64_t> launches(ng, 0);
+  std::vector<ChainOut> chains(ng);
   auto work = [&](size_t g) {
     cudaSetDevice(dev);
     outs[g].resize(groups[g].size());
@@ -718,13 +794,13 @@ extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int
     int rc;
     if (prec == PP_PREC_MIXED)
       rc = run_group<dw, float>(groups[g], deg, keys[g].lanczos, side == PP_RIGHT, kchk, m_max, tol, streams[g],
-                                outs[g], &launches[g]);
+                                outs[g], &launches[g], &chains[g], profile);
     else if (prec == PP_PREC_DW)
       rc = run_group<dw, dw>(groups[g], deg, keys[g].lanczos, side == PP_RIGHT, kchk, m_max, tol, streams[g],
-                             outs[g], &launches[g]);
+                             outs[g], &launches[g], &chains[g], profile);
     else
       rc = run_group<double, double>(groups[g], deg, keys[g].lanczos, side == PP_RIGHT, kchk, m_max, tol,
-                                     streams[g], outs[g], &launches[g]);
+                                     streams[g], outs[g], &launches[g], &chains[g], profile);
     rcs[g] = rc;
     if (rc != PP_OK) errs[g] = pp_last_error();
   };
@@ -755,7 +831,13 @@ extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int
   cudaEventDestroy(start);
   if (rc != PP_OK) return rc;
   int64_t total_launches = 0;
+  ChainOut chain_total;
   for (int64_t l : launches) total_launches += l;
+  for (const ChainOut &q : chains) {
+    chain_total.launches += q.launches;
+    chain_total.bytes += q.bytes;
+    chain_total.ms += q.ms;
+  }
   int worst = PP_OK;
   if (stats) {
     for (int i = 0; i < count; ++i) {
@@ -764,6 +846,9 @@ extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int
       stats[i].est_err = 0.0;
       stats[i].ms_total = ms;
       stats[i].launches = total_launches;
+      stats[i].chain_launches = chain_total.launches;
+      stats[i].chain_bytes = chain_total.bytes;
+      stats[i].chain_ms = chain_total.ms;
     }
   }
   for (size_t g = 0; g < ng; ++g) {

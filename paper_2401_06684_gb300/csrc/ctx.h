@@ -14,6 +14,7 @@ constexpr int kTmpVecs = 7;
 struct Workspace {
   int prec = -1;
   int m_cap = 0;
+  bool two_pass = false;  // basis of 4 columns (two-pass Lanczos) instead of m_cap + 1
   bool has_y = false;
   int64_t ldv = 0;
   size_t esz = 0;

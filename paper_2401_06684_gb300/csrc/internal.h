@@ -113,6 +113,8 @@ int vec_scale(const T *in, T *out, int64_t n, double c, const double *c_dev, cud
               const Seg &S = Seg());
 template <typename T>
 int vec_copy(const T *in, T *out, int64_t n, cudaStream_t s);
+// out[0] = 1 / in[0] (0 for 0), on the device
+int vec_recip(const double *in, double *out, cudaStream_t s);
 // partials[chunk] = sum over the chunk of x.y
 template <typename T>
 int vec_dot_partials(const T *x, const T *y, int64_t n, double *partials, int nb, cudaStream_t s,
@@ -130,6 +132,11 @@ int vec_multi_dot(const T *V, int64_t ldv, int J, const T *w, int64_t n, double 
 template <typename T>
 int vec_multi_update(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n,
                      double *partials, int nb, cudaStream_t s, const Seg &S = Seg());
+// w -= V h, then partials[chunk*J + c] = sum over the chunk of V_c . (new w),
+// V read once (J <= 8; PP_ERR_UNSUPPORTED otherwise, nothing launched)
+template <typename T>
+int vec_update_dot(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n, double *partials,
+                   cudaStream_t s, const Seg &S = Seg());
 // x = V z (accumulate = 0) or x += V z (accumulate = 1), FP64 output; with
 // m_seg, segment s uses min(m, m_seg[s]) columns
 template <typename T>
