@@ -50,18 +50,20 @@ def fH_e1(H, beta, power=-0.5, hermitian=False):
 
 def pp_arnoldi(A_mv, b, power=-0.5, coeffs=(1.0,), ab=(0.0, 1.0), side="left",
                m_max=200, tol=1e-10, k_chk=1, hermitian=False, orth="mgs",
-               stop="estimate", exact=None, breakdown_tol=1e-14, on_iter=None):
+               stop="estimate", exact=None, breakdown_tol=1e-14, on_iter=None, q=None):
     """Polynomially preconditioned Arnoldi for A^{power} b, power = -1/2 or +1/2.
 
     coeffs, ab: Chebyshev coefficients of q and its interval (see
     oracle.chebyshev); coeffs=(1.0,) is q = 1, i.e. plain Arnoldi.
+    q = (degree, q_mv), if given, replaces the Chebyshev q by another
+    polynomial of that degree applied by q_mv(v) = q(A) v (Sec. 5.2).
     Returns a dict with the iterate x, the iteration count and the operation
     counters (mvms, inner products) in the sense of Tables 1-3.  on_iter(j), if
     given, is called after every iteration (a timing hook; no effect on results).
     """
     c = np.asarray(coeffs, dtype=np.float64)
     a, bb = ab
-    deg = len(c) - 1
+    deg = len(c) - 1 if q is None else q[0]
     mvms = 0
     ip = 0
     rhs = np.asarray(b)
@@ -70,6 +72,8 @@ def pp_arnoldi(A_mv, b, power=-0.5, coeffs=(1.0,), ab=(0.0, 1.0), side="left",
         mvms += 1
 
     def q_mv(v):
+        if q is not None:
+            return q[1](v)
         return cheb.q_apply(A_mv, c, a, bb, v)
 
     n = rhs.shape[0]
