@@ -13,9 +13,10 @@ Test infrastructure only.
 * harmonic_ritz_values: the eigenvalues of H_d + h_{d+1,d}^2 H_d^{-*} e_d e_d^*
   (the matrix of Sec. 5.2); Hermitian: of T_d + beta_d^2 T_d^{-1} e_d e_d^T,
   which is real-diagonalizable for positive definite T_d.
-* leja_order: Leja ordering of real nodes: first a node of largest modulus,
-  then each time the remaining node with the largest product of distances
-  to the nodes already taken (ties: the earliest in the input order).
+* leja_order: Leja ordering: first a node of largest modulus, then each time
+  the remaining node with the largest product of distances to the nodes
+  already taken (ties: the earliest in the input order); complex nodes of a
+  real problem come in conjugate pairs, each pair kept adjacent.
 * newton_coeffs / newton_eval / newton_apply: q of degree d-1 interpolating
   f at the ordered nodes, in Newton form
       q(z) = sum_{i<d} a_i prod_{k<i} (z - x_k),  a_i = f[x_0, ..., x_i],
@@ -119,9 +120,28 @@ def harmonic_ritz_values(H, hermitian=True):
 
 
 def leja_order(nodes):
-    rest = [float(x) for x in np.asarray(nodes, dtype=np.float64)]
+    """Leja order; real input gives a real array.
+
+    Complex nodes (conjugate pairs of a real problem): the candidates are the
+    nodes with Im >= 0; a chosen complex node is followed at once by its
+    conjugate, so every pair is adjacent (a conjugation-closed node set after
+    each pair).
+    """
+    arr = np.asarray(nodes)
+    real = not np.iscomplexobj(arr) or np.all(arr.imag == 0)
+    if real:
+        rest = [complex(x) for x in np.real(arr).astype(np.float64)]
+    else:
+        rest = [complex(x) for x in arr if x.imag >= 0]
     first = max(range(len(rest)), key=lambda i: (abs(rest[i]), -i))
-    out = [rest.pop(first)]
+    out = []
+
+    def take(z):
+        out.append(z)
+        if z.imag > 0:
+            out.append(z.conjugate())
+
+    take(rest.pop(first))
 
     def logprod(z):
         return sum(np.log(abs(z - x)) if z != x else -np.inf for x in out)
@@ -129,15 +149,22 @@ def leja_order(nodes):
     while rest:
         scores = [logprod(z) for z in rest]
         best = int(np.argmax(scores))  # first maximum
-        out.append(rest.pop(best))
-    return np.array(out)
+        take(rest.pop(best))
+    out = np.array(out)
+    return out.real.copy() if real else out
+
+
+def _dtype(x):
+    return np.complex128 if np.iscomplexobj(x) else np.float64
 
 
 def newton_coeffs(nodes, f=lambda z: z ** -0.5):
-    """a_i = f[x_0, ..., x_i] from the recursive divided-difference table."""
-    x = np.asarray(nodes, dtype=np.float64)
+    """a_i = f[x_0, ..., x_i] from the recursive divided-difference table
+    (complex for complex nodes; f(z) = z^{-1/2} on the principal branch)."""
+    x = np.asarray(nodes)
+    x = x.astype(_dtype(x))
     d = len(x)
-    col = np.asarray(f(x), dtype=np.float64)
+    col = np.asarray(f(x), dtype=x.dtype)
     a = [col[0]]
     for k in range(1, d):
         col = (col[1:] - col[:-1]) / (x[k:] - x[:-k])
@@ -146,7 +173,10 @@ def newton_coeffs(nodes, f=lambda z: z ** -0.5):
 
 
 def newton_eval(a, nodes, z):
-    z = np.asarray(z, dtype=np.float64)
+    a = np.asarray(a)
+    z = np.asarray(z)
+    dt = np.result_type(a.dtype, np.asarray(nodes).dtype, z.dtype, np.float64)
+    z = z.astype(dt)
     out = np.zeros_like(z)
     prod = np.ones_like(z)
     for i in range(len(a)):
@@ -156,24 +186,39 @@ def newton_eval(a, nodes, z):
 
 
 def newton_apply(A_mv, a, nodes, v):
-    """q(A) v = sum_i a_i prod_{k<i} (A - x_k I) v, term by term."""
+    """q(A) v = sum_i a_i prod_{k<i} (A - x_k I) v, term by term (complex
+    arithmetic when the nodes are complex; a real q of a real A gives a real
+    result up to rounding, returned as its real part for real v)."""
     v = np.asarray(v)
-    out = np.zeros(v.shape, dtype=np.result_type(v.dtype, np.float64))
-    p = v.astype(out.dtype)
+    dt = np.result_type(v.dtype, np.asarray(a).dtype, np.asarray(nodes).dtype, np.float64)
+    out = np.zeros(v.shape, dtype=dt)
+    p = v.astype(dt)
     for i in range(len(a)):
         out = out + a[i] * p
         if i + 1 < len(a):
             p = A_mv(p) - nodes[i] * p
+    if not np.iscomplexobj(v) and np.iscomplexobj(out):
+        return out.real.copy()
     return out
 
 
 def ritz_poly(A_mv, n, degree, harmonic=False, complex_=False, hermitian=True):
     """Leja-ordered nodes and Newton coefficients of q, deg q = degree, from
-    degree + 1 Arnoldi steps on the library's start vector (Hermitian A).
+    degree + 1 Arnoldi steps on the library's start vector.
 
+    Hermitian A: real nodes.  Real non-Hermitian A: the eigenvalues of H_d
+    (or of the harmonic matrix), complex ones in conjugate pairs.
     Returns (nodes, coeffs); fewer nodes if the Krylov space became invariant.
     """
     H, _ = arnoldi(A_mv, start_vector(n, complex_), degree + 1)
     th = harmonic_ritz_values(H, hermitian) if harmonic else ritz_values(H, hermitian)
-    x = leja_order(np.sort(np.real(th)))
+    if hermitian or np.all(np.abs(np.imag(th)) == 0):
+        x = leja_order(np.sort(np.real(th)))
+    else:
+        # snap the conjugate pairs of the real H_d exactly (eigvals returns them
+        # conjugate to rounding) and order the set
+        th = np.asarray(th)
+        up = th[th.imag > 0]
+        re = np.real(th[th.imag == 0])
+        x = leja_order(np.concatenate([re, up, up.conj()]))
     return x, newton_coeffs(x)

@@ -182,3 +182,103 @@ def test_invariant_subspace_stops_early():
     H, V = ritz.arnoldi(lambda u: A @ u, v, 3)
     assert H.shape == (3, 2)
     assert np.allclose(ritz.ritz_values(H), [1.0, 2.0])
+
+
+# ---- non-Hermitian A: complex Ritz values in conjugate pairs ----
+
+def same_set(a, b, tol):
+    """Every entry of a within tol of an entry of b and vice versa (equal multisets up to rounding)."""
+    a, b = np.asarray(a), np.asarray(b)
+    return len(a) == len(b) and max(np.abs(b - z).min() for z in a) < tol and \
+        max(np.abs(a - z).min() for z in b) < tol
+
+
+def _nonnormal(n=40, seed=7):
+    # real non-symmetric matrix with eigenvalues in the right half-plane, some
+    # complex: a shifted upper triangle plus a random rotation block structure
+    rng = np.random.default_rng(seed)
+    A = np.diag(np.linspace(1.0, 6.0, n)) + 0.6 * np.triu(rng.standard_normal((n, n)), 1)
+    for k in range(0, n - 1, 5):  # 2x2 rotation blocks give complex pairs
+        A[k + 1, k] = -1.5
+        A[k, k + 1] = 1.5
+    return A
+
+
+def test_leja_complex_pairs_adjacent():
+    z = np.array([1.0, 2 + 1j, 2 - 1j, 4.0, 3 + 0.5j, 3 - 0.5j, 0.5])
+    x = ritz.leja_order(z)
+    assert len(x) == len(z) and np.allclose(np.sort_complex(x), np.sort_complex(z))
+    assert x[0] == 4.0
+    k = 0
+    while k < len(x):
+        if x[k].imag != 0:
+            assert x[k].imag > 0 and x[k + 1] == x[k].conjugate()
+            k += 2
+        else:
+            k += 1
+    # worked by hand: after 4, the product |z - 4| is largest at 0.5 (3.5 vs
+    # |2 +- i - 4| = 2.24, |3 +- 0.5i - 4| = 1.12, |1 - 4| = 3)
+    assert x[1] == 0.5
+
+
+def test_newton_complex_nodes_real_polynomial():
+    x = ritz.leja_order(np.array([0.8, 1.5 + 0.7j, 1.5 - 0.7j, 3.0 + 1.2j, 3.0 - 1.2j, 5.0, 2.2]))
+    a = ritz.newton_coeffs(x)
+    # interpolation at every (complex) node, principal branch
+    assert np.allclose(ritz.newton_eval(a, x, x), x ** -0.5, rtol=1e-12)
+    # real on the real axis (conjugation-closed node set, f(conj z) = conj f(z))
+    zr = np.linspace(0.5, 6.0, 101)
+    qr = ritz.newton_eval(a, x, zr)
+    assert np.abs(qr.imag).max() < 1e-13 * np.abs(qr).max()
+    # the unique interpolant: a complex Vandermonde solve gives the same values
+    V = np.vander(x, increasing=True)
+    c = np.linalg.solve(V, x ** -0.5)
+    assert np.allclose(np.polynomial.polynomial.polyval(zr, c), qr, rtol=1e-8)
+
+
+def test_newton_apply_nonnormal_matches_eigen_form():
+    A = _nonnormal(30, 3)
+    lam, W = np.linalg.eig(A)
+    x = ritz.leja_order(np.array([1.2, 2.0 + 1.0j, 2.0 - 1.0j, 4.5, 3.3]))
+    a = ritz.newton_coeffs(x)
+    v = synth.rhs(30, 2)
+    got = ritz.newton_apply(lambda u: A @ u, a, x, v)
+    assert not np.iscomplexobj(got)
+    want = W @ (ritz.newton_eval(a, x, lam) * np.linalg.solve(W, v))
+    assert np.abs(want.imag).max() < 1e-10 * np.abs(want).max()
+    assert rel(got, want.real) < 1e-10
+
+
+def test_nonhermitian_ritz_values_are_projection_eigenvalues():
+    A = _nonnormal(40, 7)
+    d = 9
+    H, V = ritz.arnoldi(lambda u: A @ u, ritz.start_vector(40), d)
+    Vd = V[:d].T
+    proj = np.linalg.eigvals(Vd.T @ A @ Vd)
+    th = ritz.ritz_values(H, hermitian=False)
+    assert same_set(th, proj, 1e-10 * np.abs(proj).max())
+    assert np.any(np.abs(th.imag) > 1e-3)  # the case exercises complex pairs
+    # harmonic: A u - theta u orthogonal to A K_d, i.e. the pencil
+    # ((A V)^T A V, (A V)^T V), solved by a generalized eigensolver
+    AV = A @ Vd
+    pen = sla.eigvals(AV.T @ AV, AV.T @ Vd)
+    hh = ritz.harmonic_ritz_values(H, hermitian=False)
+    assert same_set(hh, pen, 1e-8 * np.abs(pen).max())
+
+
+@pytest.mark.parametrize("harmonic", [False, True])
+def test_nonhermitian_ritz_solve(harmonic):
+    # convection-diffusion (real, non-symmetric): q from the Arnoldi Ritz
+    # values, Algorithm 1 with CGS2, against the dense definition
+    dims = (7, 6, 5)
+    A = ops.convdiff(dims, 0.5)
+    n = A.shape[0]
+    b = synth.rhs(n, 4)
+    deg = 6
+    x, an = ritz.ritz_poly(A.dot, n, deg, harmonic=harmonic, hermitian=False)
+    assert len(x) == deg + 1
+    q = (deg, lambda v: ritz.newton_apply(A.dot, an, x, v))
+    for power in (-0.5, 0.5):
+        r = krylov.pp_arnoldi(A.dot, b, power, q=q, m_max=200, tol=1e-12, k_chk=2, orth="cgs2")
+        assert r["converged"]
+        assert rel(r["x"], exact.dense_fun(A.toarray(), b, power, hermitian=False)) < 1e-10
