@@ -67,6 +67,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--plain-m-max", type=int, default=1000)
+    p.add_argument("--probe", action="store_true",
+                   help="per-launch timing of the operator kernels on the workload (no bench line)")
+    p.add_argument("--clenshaw", action="store_true",
+                   help="evaluate q by the Chebyshev Clenshaw recurrence instead of the Newton/Horner form")
     p.add_argument("--two-pass", action="store_true",
                    help="two-pass Lanczos (O(n) basis memory, twice the operator passes)")
     p.add_argument("--autotune", action="store_true", help="degree and tile from pp_autotune")
@@ -98,6 +102,7 @@ def config(args, ws):
             "grid": list(args.dims), "n": args.n,
             "ch": 0.5 if args.kind == "convdiff3d7" else 0.0,
             "func": "sqrt" if args.func > 0 else "invsqrt", "poly": "chebyshev", "degree": args.degree,
+            "q_eval": "clenshaw" if args.clenshaw else "newton-horner at Leja-ordered Chebyshev nodes",
             "side": "left", "orth": args.orth, "tol": args.tol, "rhs_per_rank": 1,
             "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MB write)"}
 
@@ -320,7 +325,8 @@ def run_ours(args):
     pp.pp_set_opts(h, o)
     if args.two_pass:  # O(n) basis memory: two-pass Lanczos
         o.two_pass = 1
-        pp.pp_set_opts(h, o)
+    o.clenshaw = 1 if args.clenshaw else 0
+    pp.pp_set_opts(h, o)
     if args.autotune:
         args.degree = pp.pp_autotune(h, args.tol, 64)
     vdt = torch.complex128 if args.complex else torch.float64
@@ -359,6 +365,7 @@ def run_ours(args):
     o_t = pp.pp_default_opts()
     o_t.precision = pp.PP_PREC_DW
     o_t.two_pass = o.two_pass
+    o_t.clenshaw = o.clenshaw
     pp.pp_set_opts(h, o_t)
     pp.pp_apply(h, args.func, b, s2, m_max=max(m_max, 1000), tol=1e-13)
     pp.pp_set_opts(h, o)
@@ -448,7 +455,8 @@ def run_ours(args):
             "data": "synthetic (b ~ N(0,1), seed = rank)", "config": config(args, ws),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                         "kernel": "st3d_step (operator + Clenshaw update)", "peak_source": peak_src,
+                         "kernel": "st_step (operator + %s update)" % ("Clenshaw" if args.clenshaw else "Horner"),
+                         "peak_source": peak_src,
                          "timing": "CUDA events around each run of consecutive operator launches "
                                    "(one q(A) or one A product) during the timed steps",
                          "launches": chain_launches,
@@ -514,11 +522,6 @@ def run_batch(args):
     for _ in range(args.warmup):
         st = step()
         assert all(q.status == pp.PP_OK for q in st)
-    # operator-chain profiling (CUDA events around every run of batched stencil launches)
-    o = pp.pp_default_opts()
-    o.precision = prec
-    o.profile = 1
-    pp.pp_set_opts(hs[0], o)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clk = ClockSampler(local)
@@ -533,6 +536,15 @@ def run_batch(args):
     clocks = clk.stop()
     t_total = sum(a.elapsed_time(e) for a, e in ev) / 1e3
     value = args.steps * nsolves / t_total
+    # operator-chain profiling in one more (untimed) step: CUDA events around
+    # every run of batched stencil launches, the groups run one after another
+    o = pp.pp_default_opts()
+    o.precision = prec
+    o.profile = 1
+    pp.pp_set_opts(hs[0], o)
+    flush.zero_()
+    stats = step()
+    torch.cuda.synchronize()
     o.profile = 0
     pp.pp_set_opts(hs[0], o)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -544,10 +556,10 @@ def run_batch(args):
     achieved = cb / (cms / 1e3) / 1e9 if cms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": None,
-                "kernel": "bst_step (batched operator + Clenshaw update, one step of every process)",
+                "kernel": "bst_step (batched operator + Horner update, one step of every process)",
                 "peak_source": peak_src,
-                "timing": "CUDA events around each run of batched operator launches of the last timed step, "
-                          "summed over the groups' streams",
+                "timing": "CUDA events around each run of batched operator launches in one untimed step after "
+                          "the timed ones, groups run one after another",
                 "launches": cl, "bytes_per_launch": cb / max(cl, 1)}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -586,9 +598,69 @@ def run_batch(args):
         pp.pp_destroy(h)
 
 
+def run_probe(args):
+    """Per-launch timing of the operator kernels on the workload's stencil
+    (not a bench line): q(A) v by pp_poly_apply (one launch per step) in FP32
+    and double-word, Horner and Clenshaw, one operator application in each
+    arithmetic, and device copies of 8 MB / 32 MB / 1 GB for scale.  The
+    command an ncu capture of the stencil step kernel runs."""
+    import torch
+    from paper_2401_06684_gb300 import pp
+    import synth
+    if args.kind not in ("convdiff3d7", "laplace2d5"):
+        raise SystemExit("--probe: stencil workloads only")
+    dims = tuple(args.dims)
+    n = int(np.prod(dims))
+    if args.kind == "convdiff3d7":
+        h = pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, dims, [0.5])
+    else:
+        h = pp.pp_create_stencil(pp.PP_LAPLACE2D5, dims)
+    pp.pp_build_poly(h, args.degree)
+    x = torch.from_numpy(synth.rhs(n, 1)).cuda()
+    y = torch.empty_like(x)
+    reps = args.steps
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return 1e3 * e0.elapsed_time(e1) / reps
+
+    res = {}
+    for name, prec in (("f32", pp.PP_PREC_MIXED), ("dw", pp.PP_PREC_DW)):
+        for scheme in ("horner", "clenshaw"):
+            o = pp.pp_default_opts()
+            o.precision = prec
+            o.clenshaw = int(scheme == "clenshaw")
+            pp.pp_set_opts(h, o)
+            us = timed(lambda: pp.pp_poly_apply(h, x, y))
+            res[f"{name}_{scheme}_us_per_step"] = us / max(args.degree, 1)
+    for name, prec in (("f32", pp.PP_PREC_MIXED), ("dw", pp.PP_PREC_DW), ("f64", pp.PP_PREC_F64)):
+        o = pp.pp_default_opts()
+        o.precision = prec
+        pp.pp_set_opts(h, o)
+        res[f"{name}_op_apply_us"] = timed(lambda: pp.pp_op_apply(h, x, y))
+    for mb in (8, 32, 1024):
+        a = torch.empty(mb << 18, dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        us = timed(lambda: b.copy_(a))
+        res[f"copy_{mb}MB_us"] = us
+        res[f"copy_{mb}MB_GBs"] = 2 * (mb << 20) / (us * 1e-6) / 1e9
+    pp.pp_destroy(h)
+    print(json.dumps({"probe": res, "workload": args.desc, "degree": args.degree, "reps": reps}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.probe:
+        run_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.kind == "batch":
         run_batch(args)

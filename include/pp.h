@@ -61,9 +61,11 @@ typedef enum { PP_INVSQRT = -1, PP_SQRT = 1 } pp_func;
 
 typedef enum {
   PP_CHEBYSHEV = 0,      /* Sec. 5.1: interpolant at deg+1 first-kind nodes of [a,b] */
-  PP_RITZ_LEJA = 1,      /* Sec. 5.2 (not in this build)                              */
-  PP_HARMONIC_RITZ = 2,  /* Sec. 5.2 (not in this build)                              */
-  PP_LSQ_CONTOUR = 3     /* Sec. 5.3 (not in this build)                              */
+  PP_RITZ_LEJA = 1,      /* Sec. 5.2: interpolant at the deg+1 Ritz values of A
+                            (Newton form, Leja order)                             */
+  PP_HARMONIC_RITZ = 2,  /* Sec. 5.2: same at the deg+1 harmonic Ritz values      */
+  PP_LSQ_CONTOUR = 3,    /* Sec. 5.3 (not in this build)                              */
+  PP_NODES = 4           /* interpolant at caller-given nodes (pp_set_poly_nodes)     */
 } pp_poly_kind;
 
 typedef enum {
@@ -116,7 +118,16 @@ typedef struct pp_opts {
                            regenerates v_1..v_m from the stored coefficients and
                            accumulates x; twice the operator work, O(n) memory
                            instead of O(m n).  mvms counts both passes.            */
-  int32_t reserved[6];
+  int32_t clenshaw;     /* how q(A) v is evaluated, in deg q operator steps:
+                           0 (default): the Newton form of q at its Leja-ordered
+                           interpolation nodes x_i by a Horner scheme (Sec. 5.2's
+                           representation; for PP_CHEBYSHEV the first-kind nodes,
+                           the same q), each step w <- ((A - x_i)/cap) w + a_i
+                           cap^i v with cap = (max x_i - min x_i)/4: three vector
+                           streams per step.  1: for PP_CHEBYSHEV the matrix
+                           Clenshaw recurrence of the Chebyshev series (Sec. 5.1),
+                           four streams per step (ignored for the Ritz kinds).   */
+  int32_t reserved[5];
 } pp_opts;
 
 typedef struct pp_stats {
@@ -196,6 +207,24 @@ int pp_set_opts(pp_handle h, const pp_opts *opts);
  * i.e. plain Arnoldi/Lanczos.  The positivity of q on [a,b] is checked on a
  * dense grid (Sec. 5.1, last paragraph); PP_ERR_NONPRIMARY if it fails.
  * 0 <= degree <= 128.
+ *
+ * PP_RITZ_LEJA / PP_HARMONIC_RITZ (Sec. 5.2): degree + 1 Arnoldi steps on
+ * A itself (classical Gram-Schmidt twice, in the handle's precision;
+ * double-word for PP_PREC_MIXED) from a fixed pseudo-random start vector:
+ * entry i of the real view is (s_i >> 11) 2^-52 - 1, s_i the SplitMix64
+ * output for the state 0x5EED + (i + 1) 0x9E3779B97F4A7C15.  The nodes are
+ * the eigenvalues of H_d, or of H_d + h_{d+1,d}^2 H_d^{-T} e_d e_d^T for
+ * harmonic Ritz values.  Hermitian handles read H_d as the Lanczos matrix T
+ * (diagonal and sub-diagonal; eigenvalues by bisection, harmonic ones from
+ * the pencil (T^2 + h^2 e_d e_d^T, T)); other handles take the Hessenberg
+ * H_d (Francis QR; complex values come in conjugate pairs).  q is then built
+ * as by pp_set_poly_nodes from these nodes.  If the Krylov space of the
+ * start vector is invariant earlier (small n), fewer nodes are used and
+ * deg q drops accordingly (pp_get_poly reports it).  [a,b] (given, or the
+ * closed form, or the extreme real parts of the Ritz values lowered by 5 % /
+ * raised by 1 %) only serves the positivity check and the image interval.
+ * The node run costs degree + 1 operator applications and allocates a basis
+ * of degree + 2 vectors in the workspace.
  */
 int pp_build_poly(pp_handle h, int32_t degree, int32_t kind, const double *interval_ab_h);
 
@@ -218,13 +247,55 @@ int pp_build_poly(pp_handle h, int32_t degree, int32_t kind, const double *inter
 int pp_autotune(pp_handle h, double tol, int32_t max_degree, int32_t *degree_out);
 
 /*
- * Read back the polynomial: coeffs_h[0..*ncoeffs-1] (Chebyshev coefficients
- * c_i of q = sum c_i T_i((2z-a-b)/(b-a))), ab_h[2] = [a,b], image_h[2] =
+ * Read back the polynomial: coeffs_h[0..*ncoeffs-1] (PP_CHEBYSHEV: the
+ * coefficients c_i of q = sum c_i T_i((2z-a-b)/(b-a)); other kinds: the
+ * coefficients of q in the real basis R_i of pp_set_poly_nodes, for real
+ * nodes the Newton coefficients a_i; the nodes from pp_get_poly_nodes),
+ * ab_h[2] = [a,b], image_h[2] =
  * [min, max] of z q(z)^2 on [a,b] (the interval of Prop. 3.2).  Any output
- * pointer may be NULL; cap = capacity of coeffs_h.
+ * pointer may be NULL; cap = capacity of coeffs_h.  deg q = *ncoeffs - 1.
  */
 int pp_get_poly(pp_handle h, double *coeffs_h, int32_t cap, int32_t *ncoeffs, double *ab_h,
                 double *image_h);
+
+/*
+ * q = the interpolant of z^{-1/2} (principal branch) at caller-given nodes
+ * (Sec. 5.2 builds them from Ritz values; this call takes them from the
+ * caller, e.g. Ritz values of an Arnoldi run started from b): deg q =
+ * count - 1 <= 128.  nodes_re_h / nodes_im_h (host; nodes_im_h may be NULL
+ * for real nodes): real values or complex conjugate pairs, all with Re > 0
+ * (Hermitian handles: real only).  The nodes are put in Leja order (largest
+ * modulus first, then each time the node farthest from the taken ones in
+ * product distance; a pair is taken as its Im > 0 member followed by its
+ * conjugate) and q is written in the real basis R_0 = 1, R_{i+1} = (z - x_i)
+ * R_i for a real node, R_{i+1} = (z - Re x_i) R_i, R_{i+2} = |z - x_i|^2 R_i
+ * for a pair, which for real nodes is the Newton form q = sum_i a_i
+ * prod_{l<i} (z - x_l), a_i the divided differences.  q(A) v is evaluated by
+ * the matching backward (Horner) recurrence of deg q operator steps, each
+ * scaled by cap = a quarter of the diameter of the node set.  [a,b] =
+ * interval_ab_h, else the closed form of the stencils, else the extreme real
+ * parts of the nodes lowered by 5 % / raised by 1 %; Re q must be positive
+ * there and at the nodes (the condition of Sec. 5.2, checked on these
+ * points), and the image of |z q(z)^2| over them sets the quadrature of the
+ * small solve.  Host only (no device work).  Errors: PP_ERR_INVALID_ARG for
+ * count out of range, non-finite nodes, a complex node without its
+ * conjugate, complex nodes of a Hermitian handle, a bad interval;
+ * PP_ERR_NONPRIMARY for a node with Re <= 0, coincident nodes or Re q <= 0
+ * on the checked points.  The handle's kind becomes PP_NODES.
+ */
+int pp_set_poly_nodes(pp_handle h, const double *nodes_re_h, const double *nodes_im_h, int32_t count,
+                      const double *interval_ab_h);
+
+/*
+ * The interpolation nodes of q (host output): *kind = its pp_poly_kind,
+ * nodes_re_h / nodes_im_h [0..*nnodes-1] = the nodes in the Leja order of
+ * the Newton form the device evaluates (for PP_CHEBYSHEV its deg q + 1
+ * first-kind nodes of [a,b]), *scale = cap of pp_set_poly_nodes.  Any output
+ * pointer may be NULL; cap = capacity of the node arrays.
+ * Errors: PP_ERR_STATE before pp_build_poly.
+ */
+int pp_get_poly_nodes(pp_handle h, int32_t *kind, double *nodes_re_h, double *nodes_im_h, int32_t cap,
+                      int32_t *nnodes, double *scale);
 
 /*
  * x = f(A) b (Algorithm 1 or 2 by opts.side; Sec. 4 for PP_SQRT), iterating
@@ -268,7 +339,8 @@ int pp_apply_host(pp_handle h, int32_t f, const double *b_h, int64_t nrhs, int32
  * Krylov dimension over its right-hand sides, mvms / inner_products summed
  * over them, est_err the largest estimate; ms_total, launches and the
  * chain_* operator accounting of the whole batch (chain_ms with
- * handles[0]'s opts.profile = 1, summed over the groups' streams).  Returns
+ * handles[0]'s opts.profile = 1; the groups then run one after another
+ * instead of concurrently, so that the timed launches do not overlap).  Returns
  * PP_ERR_NOT_CONVERGED if any process reached m_max (1 <= m_max <= 1024).
  */
 int pp_apply_batch(const pp_handle *handles, int32_t count, const int32_t *f, const void *const *b_d,

@@ -4,7 +4,9 @@
 // handle's stream; all vector work, inner products, the projected matrix
 // and the small f(H_m) solve stay on the device.  The host reads back a
 // 48-byte status record at each stopping check.
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -91,13 +93,8 @@ int prof_end(pp_ctx *c) {
   return PP_OK;
 }
 
-// One operator launch of the chain: counted and its algorithmic bytes added.
-template <typename T>
-int run_op(pp_ctx *c, const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &k) {
-  int rc = op_step<T>(op, x, y, v, out, k, c->stream);
-  if (rc) return rc;
-  c->chain_launches += 1;
-  const double esz = (double)sizeof(T);
+// Algorithmic bytes of one operator step out = alpha A x + beta x [+ gamma y] [+ delta v].
+double step_bytes(const pp_ctx *c, const StepCoef &k, double esz) {
   double vecs = 2.0 + (k.sub_y ? 1.0 : 0.0) + (k.add_v ? 1.0 : 0.0);
   double bytes = vecs * esz * (double)c->n;
   if (c->op_kind == OPK_CSR) bytes += (esz + 4.0) * (double)c->nnz + 8.0 * (double)(c->n + 1);
@@ -107,7 +104,16 @@ int run_op(pp_ctx *c, const OpDesc &op, const T *x, const T *y, const T *v, T *o
     const double sites = (double)c->n / 24.0;
     bytes += (2.0 + (k.beta != 0.0 ? 1.0 : 0.0)) * esz * (double)c->n + 2.0 * 288.0 * sites;
   }
-  c->chain_bytes += bytes;
+  return bytes;
+}
+
+// One operator launch of the chain: counted and its algorithmic bytes added.
+template <typename T>
+int run_op(pp_ctx *c, const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &k) {
+  int rc = op_step<T>(op, x, y, v, out, k, c->stream);
+  if (rc) return rc;
+  c->chain_launches += 1;
+  c->chain_bytes += step_bytes(c, k, (double)sizeof(T));
   return PP_OK;
 }
 
@@ -264,28 +270,29 @@ OpDesc make_op(const pp_ctx *c, int arith) {
     if (_r != PP_OK) return _r; \
   } while (0)
 
-// y = q(A) x by the matrix Clenshaw recurrence with the first two steps
-// folded (b_{k+1} = 0, b_k = c_k x): deg q operator applications.
+// y = q(A) x in deg q operator applications: the Horner scheme of the Newton
+// form with its first step folded, or (opts.clenshaw, Chebyshev q) the matrix
+// Clenshaw recurrence with the first two steps folded (b_{k+1} = 0, b_k =
+// c_k x).  Horner steps read no second previous iterate; the same buffer
+// rotation serves both.
 template <typename T>
 int poly_apply_raw(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3]) {
-  const std::vector<double> &cf = c->coef;
-  const int k = (int)cf.size() - 1;
-  const double s1 = 4.0 / (c->b - c->a), s2 = -2.0 * (c->a + c->b) / (c->b - c->a);
+  const int k = (int)c->coef.size() - 1;
   cudaStream_t s = c->stream;
-  if (k == 0) return vec_scale<T>(in, out, c->n, cf[0], nullptr, s);
-  if (k == 1) return run_op<T>(c, op, in, nullptr, nullptr, out, clenshaw_coef(cf, s1, s2, 0));
+  if (k == 0) return vec_scale<T>(in, out, c->n, poly_const(c), nullptr, s);
+  if (k == 1) return run_op<T>(c, op, in, nullptr, nullptr, out, poly_step_coef(c, 0));
   int i2 = 0, i1 = 1, i0 = 2;  // buffer indices of b_{i+2}, b_{i+1}, free
-  RC(run_op<T>(c, op, in, nullptr, nullptr, bufs[i2], clenshaw_coef(cf, s1, s2, 0)));
-  if (k == 2) return run_op<T>(c, op, bufs[i2], nullptr, in, out, clenshaw_coef(cf, s1, s2, 1));
-  RC(run_op<T>(c, op, bufs[i2], nullptr, in, bufs[i1], clenshaw_coef(cf, s1, s2, 1)));
+  RC(run_op<T>(c, op, in, nullptr, nullptr, bufs[i2], poly_step_coef(c, 0)));
+  if (k == 2) return run_op<T>(c, op, bufs[i2], nullptr, in, out, poly_step_coef(c, 1));
+  RC(run_op<T>(c, op, bufs[i2], nullptr, in, bufs[i1], poly_step_coef(c, 1)));
   for (int t = 2; t <= k - 2; ++t) {
-    RC(run_op<T>(c, op, bufs[i1], bufs[i2], in, bufs[i0], clenshaw_coef(cf, s1, s2, t)));
+    RC(run_op<T>(c, op, bufs[i1], bufs[i2], in, bufs[i0], poly_step_coef(c, t)));
     const int tmp = i2;
     i2 = i1;
     i1 = i0;
     i0 = tmp;
   }
-  return run_op<T>(c, op, bufs[i1], bufs[i2], in, out, clenshaw_coef(cf, s1, s2, k - 1));
+  return run_op<T>(c, op, bufs[i1], bufs[i2], in, out, poly_step_coef(c, k - 1));
 }
 
 template <typename T>
@@ -311,6 +318,7 @@ struct Solve {
   double *H, *h1, *part, *X, *tri, *z, *zprev, *sig, *wt, *scal;
   int ldh, nb, K;
   bool right, lanczos;
+  bool plain = false;  // w = A v_j alone (the node run of Sec. 5.2)
   int deg;
   int64_t mvms, ip;
 };
@@ -327,17 +335,21 @@ int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double b
   T *pb[3] = {t[2], t[3], t[4]};
   T *vj = V + (size_t)j * ldv;
   T *wv = V + (size_t)(j + 1) * ldv;
-  if (!S.right) {  // Algorithm 1: u = A v_j, y = q(A) u, w = q(A) y
+  if (S.plain) {          // Arnoldi on A itself
+    RC(run_op<T>(c, op, vj, nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
+    S.mvms += 1;
+  } else if (!S.right) {  // Algorithm 1: u = A v_j, y = q(A) u, w = q(A) y
     RC(run_op_timed<T>(c, op, vj, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
     RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
     RC(poly_apply_t<T>(c, op, t[1], wv, pb));
-  } else {         // Algorithm 2: y_j = q(A) v_j, u = q(A) y_j, w = A u
+    S.mvms += 2 * S.deg + 1;
+  } else {                // Algorithm 2: y_j = q(A) v_j, u = q(A) y_j, w = A u
     T *yj = Y + (size_t)j * ldv;
     RC(poly_apply_t<T>(c, op, vj, yj, pb));
     RC(poly_apply_t<T>(c, op, yj, t[0], pb));
     RC(run_op_timed<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
+    S.mvms += 2 * S.deg + 1;
   }
-  S.mvms += 2 * S.deg + 1;
   double *hcol = S.H + (size_t)j * S.ldh;
   const int nb = S.nb;
   if (S.lanczos) {
@@ -989,6 +1001,239 @@ int lanczos_extremes(pp_ctx *c, int steps, double *lo, double *hi) {
   return rc;
 }
 
+// Node run of Sec. 5.2: d Arnoldi steps on A (classical Gram-Schmidt twice,
+// the kernels of the solve loop) from the fixed pseudo-random start vector,
+// in arithmetic T.  Returns the Hessenberg matrix (column j at Hh[j * ldh],
+// rows 0 .. j+1) and the number m <= d of steps before the Krylov space
+// became invariant.
+template <typename T>
+int ritz_arnoldi(pp_ctx *c, int d, std::vector<double> *Hh, int *ldh_out, int *m_out) {
+  if (c->qsig.empty()) {  // the workspace layout needs a quadrature size
+    c->qsig.assign(1, 1.0);
+    c->qwt.assign(1, 1.0);
+  }
+  RC(ensure_ws(c, c->opts.precision, d, false, LAYOUT_FULL));
+  Workspace &w = c->ws;
+  cudaStream_t s = c->stream;
+  const OpDesc op = make_op(c, arith_of<T>());
+  const DLayout L = dlayout(c, w.m_cap);
+  double *D = w.dmem;
+  Solve S;
+  S.c = c;
+  S.s = s;
+  S.n = c->n;
+  S.ldv = w.ldv;
+  S.H = D + L.H;
+  S.h1 = D + L.h1;
+  S.part = D + L.part;
+  S.X = D + L.X;
+  S.tri = D + L.tri;
+  S.z = D + L.z;
+  S.zprev = D + L.zprev;
+  S.sig = D + L.sig;
+  S.wt = D + L.wt;
+  S.scal = D + L.scal;
+  S.ldh = L.ldh;
+  S.nb = L.nb;
+  S.K = L.K;
+  S.right = false;
+  S.lanczos = false;
+  S.plain = true;
+  S.deg = 0;
+  S.mvms = 0;
+  S.ip = 0;
+  T *V = (T *)w.V;
+  T *t[6];
+  for (int i = 0; i < 6; ++i) t[i] = (T *)w.tmp + (size_t)i * w.ldv;
+  PP_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(DevStatus), s));
+  PP_CUDA_TRY(cudaMemsetAsync(S.H, 0, sizeof(double) * (size_t)L.ldh * w.m_cap, s));
+  RC(vec_fill_hash<T>(V, c->n, 0x5eedull, s));
+  RC(vec_dot_partials<T>(V, V, c->n, S.part, S.nb, s));
+  RC(norm_finalize(S.part, S.nb, &w.st->beta0, S.scal, nullptr, 0, 0.0, 0, w.st, s));
+  RC(vec_scale<T>(V, V, c->n, 1.0, S.scal, s));
+  for (int j = 0; j < d; ++j) RC(krylov_step<T>(S, op, V, nullptr, t, j, kBreakdownRel));
+  Hh->assign((size_t)L.ldh * d, 0.0);
+  PP_CUDA_TRY(cudaMemcpyAsync(Hh->data(), S.H, sizeof(double) * Hh->size(), cudaMemcpyDeviceToHost, s));
+  PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+  PP_CUDA_TRY(cudaStreamSynchronize(s));
+  if (w.st_host->bad) return pp_set_error(PP_ERR_CUDA, "non-finite values in the Ritz value run");
+  *m_out = w.st_host->breakdown ? std::max(1, w.st_host->m_bd) : d;
+  *ldh_out = L.ldh;
+  return PP_OK;
+}
+
+// Closed-form spectral interval of the 2D / 3D stencil operators.
+bool closed_form_interval(const pp_ctx *c, double *a, double *b) {
+  if (c->op_kind == OPK_ST2D) {
+    *a = *b = 0.0;
+    for (int i = 0; i < 2; ++i) {
+      const double N = (double)c->dims[i];
+      *a += 2.0 - 2.0 * std::cos(M_PI / (N + 1));
+      *b += 2.0 - 2.0 * std::cos(N * M_PI / (N + 1));
+    }
+    return true;
+  }
+  if (c->op_kind == OPK_ST3D) {
+    // Sec. 6, Example 1 for the Laplacian; convection-diffusion factors are
+    // diagonally similar to tridiag(-r, 2+ch, -r), r = sqrt(1+ch)
+    const double r = std::sqrt(1.0 + c->ch);
+    *a = *b = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      const double N = (double)c->dims[i];
+      *a += (2.0 + c->ch) - 2.0 * r * std::cos(M_PI / (N + 1));
+      *b += (2.0 + c->ch) - 2.0 * r * std::cos(N * M_PI / (N + 1));
+    }
+    return true;
+  }
+  return false;
+}
+
+// Polynomial-independent tail of pp_build_poly: the quadrature of the small
+// solve sized by the image [lo, hi] of z q(z)^2, and a fresh device layout.
+void finish_poly(pp_ctx *c) {
+  // real Ritz values for Hermitian A, |arg| <= pi/3 allowed otherwise;
+  // generous margins around the image
+  const double theta = c->hermitian ? 0.0 : M_PI / 3.0;
+  invsqrt_quadrature(c->img_lo * 1e-3, c->img_hi * 1e3, 1e-15, theta, &c->qsig, &c->qwt);
+  c->quad_uploaded = false;
+  if (c->ws.dmem) {  // K may have changed: re-layout on next use
+    cudaFree(c->ws.dmem);
+    c->ws.dmem = nullptr;
+  }
+  c->have_poly = true;
+}
+
+int read_nnz(pp_ctx *c) {
+  if (c->op_kind == OPK_CSR && c->nnz < 0) {
+    int64_t nnz = 0;
+    PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    c->nnz = nnz;
+  }
+  return PP_OK;
+}
+
+// q = the interpolant of z^{-1/2} at the nodes (real values or conjugate
+// pairs with Re > 0), in Newton form at their Leja order (Sec. 5.2); [lo, hi]
+// serves the positivity check and the image interval, which also covers the
+// nodes.  Host only.
+int set_poly_nodes(pp_ctx *c, int kind, const std::vector<std::complex<double>> &nodes, double lo, double hi) {
+  const int d = (int)nodes.size();
+  if (d < 1 || d > kMaxDegree + 1) return pp_set_error(PP_ERR_INVALID_ARG, "need 1 .. 129 nodes");
+  std::vector<char> used(d, 0);
+  for (int i = 0; i < d; ++i) {
+    const std::complex<double> z = nodes[i];
+    if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return pp_set_error(PP_ERR_INVALID_ARG, "non-finite node");
+    if (!(z.real() > 0.0))
+      return pp_set_error(PP_ERR_NONPRIMARY, "a node with Re <= 0 (A q(A)^2 would need a non-principal root)");
+    if (z.imag() != 0.0 && c->hermitian) return pp_set_error(PP_ERR_INVALID_ARG, "complex node for a Hermitian operator");
+    for (int j = 0; j < i; ++j)
+      if (nodes[j] == z) return pp_set_error(PP_ERR_NONPRIMARY, "coincident nodes");
+    if (z.imag() > 0.0) {  // its conjugate must be in the set
+      int m = -1;
+      for (int j = 0; j < d && m < 0; ++j)
+        if (!used[j] && nodes[j] == std::conj(z)) m = j;
+      if (m < 0) return pp_set_error(PP_ERR_INVALID_ARG, "complex node without its conjugate");
+      used[m] = 1;
+    }
+  }
+  for (int i = 0; i < d; ++i)
+    if (nodes[i].imag() < 0.0 && !used[i]) return pp_set_error(PP_ERR_INVALID_ARG, "complex node without its conjugate");
+  if (!(lo > 0.0) || !(hi > lo) || !std::isfinite(hi)) return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
+  NewtonForm F;
+  if (!newton_form(nodes, &F)) return pp_set_error(PP_ERR_NONPRIMARY, "non-finite Newton coefficient");
+  double qmin, img_lo, img_hi;
+  newton_scan(F, lo, hi, &qmin, &img_lo, &img_hi);
+  if (!(qmin > 0.0)) return pp_set_error(PP_ERR_NONPRIMARY, "Re q is not positive on [a,b] or at a node");
+  c->poly_kind = kind;
+  c->nf = F;
+  c->coef.resize(d);
+  double p = 1.0;
+  for (int i = 0; i < d; ++i) {
+    c->coef[i] = F.b[i] / p;
+    p *= F.cap;
+  }
+  c->degree = d - 1;
+  c->a = lo;
+  c->b = hi;
+  c->img_lo = img_lo;
+  c->img_hi = img_hi;
+  finish_poly(c);
+  return PP_OK;
+}
+
+// Default check interval of node-based kinds: the closed form of the
+// stencils, else the extreme real parts of the reference values lowered by
+// 5 % / raised by 1 % (as for the interval estimate).
+void node_interval(const pp_ctx *c, const double *ab, const std::vector<std::complex<double>> &ref, double *lo,
+                   double *hi) {
+  if (ab) {
+    *lo = ab[0];
+    *hi = ab[1];
+    return;
+  }
+  if (closed_form_interval(c, lo, hi)) return;
+  double mn = INFINITY, mx = -INFINITY;
+  for (const auto &z : ref) {
+    mn = std::fmin(mn, z.real());
+    mx = std::fmax(mx, z.real());
+  }
+  *lo = 0.95 * mn;
+  *hi = 1.01 * mx;
+  if (!(*hi > *lo)) *hi = *lo * 1.01 + 1e-300;
+}
+
+// pp_build_poly for PP_RITZ_LEJA / PP_HARMONIC_RITZ (Sec. 5.2): degree + 1
+// Arnoldi steps on A; the nodes are the eigenvalues of H_d, or of H_d +
+// h_{d+1,d}^2 H_d^{-T} e_d e_d^T (harmonic).  Hermitian A: H_d read as the
+// Lanczos matrix T (diagonal and sub-diagonal), eigenvalues by bisection,
+// harmonic ones from the symmetric pencil (T^2 + beta^2 e_d e_d^T, T).
+// Non-Hermitian A: the Hessenberg H_d, Francis QR.
+int build_ritz(pp_ctx *c, int degree, int kind, const double *ab) {
+  RC(read_nnz(c));
+  const int d = (int)std::min<int64_t>((int64_t)degree + 1, c->n);
+  std::vector<double> H;
+  int ldh = 0, m = 0;
+  const int rc = c->opts.precision == PP_PREC_F64 ? ritz_arnoldi<double>(c, d, &H, &ldh, &m)
+                                                  : ritz_arnoldi<dw>(c, d, &H, &ldh, &m);
+  if (rc != PP_OK) return rc;
+  const double beta = m < d ? 0.0 : H[(size_t)(m - 1) * ldh + m];  // h_{m+1,m}
+  std::vector<std::complex<double>> ritz, nodes;
+  if (c->hermitian) {
+    std::vector<double> al(m), be(m > 1 ? m - 1 : 0);
+    for (int j = 0; j < m; ++j) {
+      al[j] = H[(size_t)j * ldh + j];
+      if (j + 1 < m) be[j] = H[(size_t)j * ldh + j + 1];
+    }
+    for (int k = 0; k < m; ++k) ritz.emplace_back(tridiag_eig(al, be, k), 0.0);
+    if (kind == PP_HARMONIC_RITZ) {
+      std::vector<double> hv;
+      if (!harmonic_ritz(al, be, beta, &hv))
+        return pp_set_error(PP_ERR_NONPRIMARY, "Lanczos matrix not positive definite: A is not HPD");
+      for (double v : hv) nodes.emplace_back(v, 0.0);
+    } else {
+      nodes = ritz;
+    }
+  } else {
+    std::vector<double> Hd((size_t)m * m, 0.0), wr, wi;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i <= std::min(j + 1, m - 1); ++i) Hd[(size_t)i * m + j] = H[(size_t)j * ldh + i];
+    if (!hess_eigvals(Hd, m, &wr, &wi)) return pp_set_error(PP_ERR_NONPRIMARY, "Hessenberg QR did not converge");
+    for (int k = 0; k < m; ++k) ritz.emplace_back(wr[k], wi[k]);
+    if (kind == PP_HARMONIC_RITZ) {
+      std::vector<double> f;
+      if (!solve_transposed_last(Hd, m, &f)) return pp_set_error(PP_ERR_NONPRIMARY, "H_d is singular");
+      for (int i = 0; i < m; ++i) Hd[(size_t)i * m + m - 1] += beta * beta * f[i];
+      if (!hess_eigvals(Hd, m, &wr, &wi)) return pp_set_error(PP_ERR_NONPRIMARY, "Hessenberg QR did not converge");
+      for (int k = 0; k < m; ++k) nodes.emplace_back(wr[k], wi[k]);
+    } else {
+      nodes = ritz;
+    }
+  }
+  double lo, hi;
+  node_interval(c, ab, ritz, &lo, &hi);
+  return set_poly_nodes(c, kind, nodes, lo, hi);
+}
+
 pp_ctx *new_ctx(void *stream) {
   pp_ctx *c = new pp_ctx();
   pp_default_opts(&c->opts);
@@ -1109,46 +1354,31 @@ int pp_set_opts(pp_handle c, const pp_opts *o) {
   if (o->check_every < 0) return pp_set_error(PP_ERR_INVALID_ARG, "check_every < 0");
   if (o->profile != 0 && o->profile != 1) return pp_set_error(PP_ERR_INVALID_ARG, "profile must be 0 or 1");
   if (o->two_pass != 0 && o->two_pass != 1) return pp_set_error(PP_ERR_INVALID_ARG, "two_pass must be 0 or 1");
+  if (o->clenshaw != 0 && o->clenshaw != 1) return pp_set_error(PP_ERR_INVALID_ARG, "clenshaw must be 0 or 1");
   c->opts = *o;
   return PP_OK;
 }
 
 int pp_build_poly(pp_handle c, int32_t degree, int32_t kind, const double *ab) {
   if (!c) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle");
-  if (kind != PP_CHEBYSHEV) {
-    if (kind >= PP_RITZ_LEJA && kind <= PP_LSQ_CONTOUR) return pp_set_error(PP_ERR_UNSUPPORTED, "polynomial kind not in this build");
+  if (kind != PP_CHEBYSHEV && kind != PP_RITZ_LEJA && kind != PP_HARMONIC_RITZ) {
+    if (kind == PP_LSQ_CONTOUR) return pp_set_error(PP_ERR_UNSUPPORTED, "polynomial kind not in this build");
+    if (kind == PP_NODES) return pp_set_error(PP_ERR_INVALID_ARG, "PP_NODES is set by pp_set_poly_nodes");
     return pp_set_error(PP_ERR_INVALID_ARG, "unknown polynomial kind");
   }
   if (degree < 0 || degree > kMaxDegree) return pp_set_error(PP_ERR_INVALID_ARG, "degree out of [0, 128]");
+  if (ab && (!(ab[0] > 0.0) || !(ab[1] > ab[0]) || !std::isfinite(ab[1])))
+    return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
+  if (kind != PP_CHEBYSHEV) return build_ritz(c, degree, kind, ab);
   double a, b;
   if (ab) {
     a = ab[0];
     b = ab[1];
-  } else if (c->op_kind == OPK_ST2D) {
-    a = b = 0.0;
-    for (int i = 0; i < 2; ++i) {
-      const double N = (double)c->dims[i];
-      a += 2.0 - 2.0 * std::cos(M_PI / (N + 1));
-      b += 2.0 - 2.0 * std::cos(N * M_PI / (N + 1));
-    }
-  } else if (c->op_kind == OPK_ST3D) {
-    // Sec. 6, Example 1 for the Laplacian; convection-diffusion factors are
-    // diagonally similar to tridiag(-r, 2+ch, -r), r = sqrt(1+ch)
-    const double r = std::sqrt(1.0 + c->ch);
-    a = b = 0.0;
-    for (int i = 0; i < 3; ++i) {
-      const double N = (double)c->dims[i];
-      a += (2.0 + c->ch) - 2.0 * r * std::cos(M_PI / (N + 1));
-      b += (2.0 + c->ch) - 2.0 * r * std::cos(N * M_PI / (N + 1));
-    }
+  } else if (closed_form_interval(c, &a, &b)) {
   } else if (c->hermitian) {
     // no closed form: extreme Ritz values of kIntervalSteps Lanczos steps,
     // a lowered by 5 % and b raised by 1 %
-    if (c->op_kind == OPK_CSR && c->nnz < 0) {
-      int64_t nnz = 0;
-      PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
-      c->nnz = nnz;
-    }
+    RC(read_nnz(c));
     const int steps = (int)std::min<int64_t>(kIntervalSteps, c->n);
     double lo = 0.0, hi = 0.0;
     const int rc = c->opts.precision == PP_PREC_F64 ? lanczos_extremes<double>(c, steps, &lo, &hi)
@@ -1164,22 +1394,20 @@ int pp_build_poly(pp_handle c, int32_t degree, int32_t kind, const double *ab) {
   double qmin, lo, hi;
   cheb_scan(cf, a, b, &qmin, &lo, &hi);
   if (!(qmin > 0.0)) return pp_set_error(PP_ERR_NONPRIMARY, "q is not positive on [a,b]");
+  {  // the same q in Newton form at its d = degree + 1 first-kind nodes
+    const int d = degree + 1;
+    std::vector<std::complex<double>> xc(d);
+    for (int k = 0; k < d; ++k) xc[k] = 0.5 * (a + b) + 0.5 * (b - a) * std::cos(M_PI * (k + 0.5) / d);
+    if (!newton_form(xc, &c->nf)) return pp_set_error(PP_ERR_NONPRIMARY, "non-finite Newton coefficient");
+  }
+  c->poly_kind = PP_CHEBYSHEV;
   c->coef = cf;
   c->degree = degree;
   c->a = a;
   c->b = b;
   c->img_lo = lo;
   c->img_hi = hi;
-  // quadrature for the small solve: real Ritz values for Hermitian A,
-  // |arg| <= pi/3 allowed otherwise; generous margins around the image
-  const double theta = c->hermitian ? 0.0 : M_PI / 3.0;
-  invsqrt_quadrature(lo * 1e-3, hi * 1e3, 1e-15, theta, &c->qsig, &c->qwt);
-  c->quad_uploaded = false;
-  if (c->ws.dmem) {  // K may have changed: re-layout on next use
-    cudaFree(c->ws.dmem);
-    c->ws.dmem = nullptr;
-  }
-  c->have_poly = true;
+  finish_poly(c);
   return PP_OK;
 }
 
@@ -1198,6 +1426,34 @@ int pp_get_poly(pp_handle c, double *coeffs, int32_t cap, int32_t *ncoeffs, doub
     image[1] = c->img_hi;
   }
   return PP_OK;
+}
+
+int pp_get_poly_nodes(pp_handle c, int32_t *kind, double *nodes_re, double *nodes_im, int32_t cap,
+                      int32_t *nnodes, double *scale) {
+  if (!c) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle");
+  if (!c->have_poly) return pp_set_error(PP_ERR_STATE, "pp_build_poly has not been called");
+  if (kind) *kind = c->poly_kind;
+  const int d = (int)c->nf.re.size();
+  if (nnodes) *nnodes = d;
+  for (int i = 0; i < d && i < cap; ++i) {
+    if (nodes_re) nodes_re[i] = c->nf.re[i];
+    if (nodes_im) nodes_im[i] = c->nf.im[i];
+  }
+  if (scale) *scale = c->nf.cap;
+  return PP_OK;
+}
+
+int pp_set_poly_nodes(pp_handle c, const double *nodes_re, const double *nodes_im, int32_t count,
+                      const double *ab) {
+  if (!c) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle");
+  if (!nodes_re || count < 1 || count > kMaxDegree + 1) return pp_set_error(PP_ERR_INVALID_ARG, "need 1 .. 129 nodes");
+  if (ab && (!(ab[0] > 0.0) || !(ab[1] > ab[0]) || !std::isfinite(ab[1])))
+    return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
+  std::vector<std::complex<double>> z(count);
+  for (int i = 0; i < count; ++i) z[i] = {nodes_re[i], nodes_im ? nodes_im[i] : 0.0};
+  double lo, hi;
+  node_interval(c, ab, z, &lo, &hi);
+  return set_poly_nodes(c, PP_NODES, z, lo, hi);
 }
 
 int pp_get_quadrature(pp_handle c, double *sig, double *wt, int32_t cap, int32_t *K) {
@@ -1302,11 +1558,12 @@ int pp_autotune(pp_handle c, double tol, int32_t max_degree, int32_t *degree_out
   if (!c->have_poly) RC(pp_build_poly(c, 0, PP_CHEBYSHEV, nullptr));
   const double a = c->a, b = c->b;
   const bool lanczos = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
-  // operator pass cost in vector passes: Clenshaw step 4 (matrix-free) or 4 plus
-  // the matrix bytes in vector units (CSR), 2 for the Wilson pair of launches more
-  double op_cost = 4.0;
+  // operator pass cost in vector passes: Horner step 3 / Clenshaw step 4
+  // (matrix-free), plus the matrix bytes in vector units (CSR), 2 for the
+  // Wilson pair of launches more
+  double op_cost = c->opts.clenshaw ? 4.0 : 3.0;
   if (c->op_kind == OPK_CSR && c->nnz > 0) op_cost += (12.0 * (double)c->nnz) / (8.0 * (double)c->n);
-  if (c->op_kind == OPK_WILSON) op_cost = 10.0;
+  if (c->op_kind == OPK_WILSON) op_cost += 6.0;
   static const int cand[] = {0, 1, 2, 3, 4, 6, 8, 12, 16, 20, 24, 32, 40, 48, 64, 80, 96, 128};
   // model constants: sustained HBM bandwidth, launch-plus-gap time, cost of a check
   constexpr double kBW = 6.0e12, kLaunchS = 3.0e-6, kCheckS = 40.0e-6;

@@ -4,12 +4,14 @@
 // of one solve.
 //
 // Every (handle, right-hand side) pair is a segment.  Segments are grouped by
-// polynomial degree and orthogonalization (Lanczos or CGS2); a group's
+// polynomial degree, evaluation scheme of q (Horner or Clenshaw) and
+// orthogonalization (Lanczos or CGS2); a group's
 // vectors are the concatenation of its segments, each padded to whole
 // reduction chunks (padding stays zero), so the vector kernels find a
 // block's segment from a chunk table and read per-segment scalars from
 // per-segment FP64 scratch blocks (Seg in internal.h).  The stencil steps use
-// a per-segment geometry table and per-segment Clenshaw constants, uploaded
+// a per-segment geometry table and per-segment step constants (Horner or
+// Clenshaw steps of q), uploaded
 // once per call.  A segment that meets its stopping estimate (or breaks down)
 // is masked out of all later launches and keeps its iterate.  Groups run on
 // their own streams from their own host threads, concurrently.
@@ -196,7 +198,7 @@ struct ArithTabs {
   const BatchSeg *bseg = nullptr;  // geometry table
   unsigned nblk = 0;
   int P = 1;
-  const Konst<T> *K = nullptr;     // (deg + 1) x nseg: [0] = A, [1 + t] = Clenshaw step t
+  const Konst<T> *K = nullptr;     // (deg + 1) x nseg: [0] = A, [1 + t] = step t of q
 };
 
 struct GroupCtx {
@@ -204,6 +206,8 @@ struct GroupCtx {
   int64_t N = 0;
   BLayout L;
   bool lanczos = true, right = false;
+  bool horner = false;      // q by the backward recurrence of its Newton form
+  std::vector<char> ystep;  // step t of q reads w_{t-2} (any segment needs its y term)
   cudaStream_t s = nullptr;
   double *dmem = nullptr, *part = nullptr, *hess = nullptr;
   size_t hess_n = 0;
@@ -280,13 +284,13 @@ int poly_batch(GroupCtx &G, const ArithTabs<T> &A, const T *in, T *out, T *bufs[
   if (k == 2) return step(1, bufs[i2], nullptr, in, out, false, true);
   BRC(step(1, bufs[i2], nullptr, in, bufs[i1], false, true));
   for (int t = 2; t <= k - 2; ++t) {
-    BRC(step(t, bufs[i1], bufs[i2], in, bufs[i0], true, true));
+    BRC(step(t, bufs[i1], bufs[i2], in, bufs[i0], G.ystep[t] != 0, true));
     const int tmp = i2;
     i2 = i1;
     i1 = i0;
     i0 = tmp;
   }
-  return step(k - 1, bufs[i1], bufs[i2], in, out, true, true);
+  return step(k - 1, bufs[i1], bufs[i2], in, out, G.ystep[k - 1] != 0, true);
 }
 
 template <typename T>
@@ -378,7 +382,7 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
     nblk += (uint64_t)g[i].gx * g[i].gy * g[i].nz;
   }
   if (nblk > 0x7fffffffull) return pp_set_error(PP_ERR_INVALID_ARG, "batch too large for one launch");
-  // constants: [0] = A, [1 + t] = Clenshaw step t
+  // constants: [0] = A, [1 + t] = step t of q (Clenshaw or Horner)
   const int nt = G.deg + 1;
   std::vector<Konst<T>> Kh((size_t)nt * ns);
   std::vector<double> d(ns), cm(ns), cp(ns);
@@ -394,8 +398,7 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
       if (t == 0) {
         coefs[i] = {1.0, 0.0, 0.0, false, false};
       } else {
-        const double s1 = 4.0 / (c->b - c->a), s2 = -2.0 * (c->a + c->b) / (c->b - c->a);
-        coefs[i] = clenshaw_coef(c->coef, s1, s2, t - 1);
+        coefs[i] = poly_step_coef(c, t - 1);
       }
     }
     batch_konst<T>(d.data(), cm.data(), cp.data(), coefs.data(), ns, Kh.data() + (size_t)t * ns);
@@ -433,6 +436,10 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
   G.nseg = ns;
   G.deg = deg;
   G.lanczos = lanczos;
+  G.horner = poly_horner(segs[0].c);
+  G.ystep.assign(std::max(deg, 1), 0);
+  for (int t = 0; t < deg; ++t)
+    for (const SegIn &q : segs) G.ystep[t] |= poly_step_coef(q.c, t).sub_y ? 1 : 0;
   G.right = right;
   G.s = s;
   G.profile = profile;
@@ -503,7 +510,7 @@ int run_group(std::vector<SegIn> &segs, int deg, bool lanczos, bool right, int k
     sq[i] = segs[i].f == PP_SQRT ? 1 : 0;
     src[i] = segs[i].b;
     dst[i] = segs[i].x;
-    cf0[i] = segs[i].c->coef[0];
+    cf0[i] = poly_const(segs[i].c);
   }
   PP_CUDA_TRY(cudaMemcpyAsync(G.active, ones.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
   PP_CUDA_TRY(cudaMemcpyAsync(G.sqrt_mask, sq.data(), sizeof(int) * ns, cudaMemcpyHostToDevice, s));
@@ -733,9 +740,10 @@ extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int
     if (c->opts.precision != prec || c->opts.side != side)
       return pp_set_error(PP_ERR_INVALID_ARG, "all handles of a batch need the same precision and side");
   }
-  // groups: same degree and orthogonalization
+  // groups: same degree, form of q and orthogonalization
   struct Key {
     int deg;
+    bool horner;
     bool lanczos;
   };
   std::vector<Key> keys;
@@ -744,11 +752,12 @@ extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int
   for (int i = 0; i < count; ++i) {
     pp_ctx *c = handles[i];
     const bool lz = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
+    const bool hz = poly_horner(c);
     int g = -1;
     for (size_t q = 0; q < keys.size(); ++q)
-      if (keys[q].deg == c->degree && keys[q].lanczos == lz) g = (int)q;
+      if (keys[q].deg == c->degree && keys[q].horner == hz && keys[q].lanczos == lz) g = (int)q;
     if (g < 0) {
-      keys.push_back({c->degree, lz});
+      keys.push_back({c->degree, hz, lz});
       groups.emplace_back();
       where.emplace_back();
       g = (int)keys.size() - 1;
@@ -804,10 +813,17 @@ extern "C" int pp_apply_batch(const pp_handle *handles, int32_t count, const int
     rcs[g] = rc;
     if (rc != PP_OK) errs[g] = pp_last_error();
   };
-  std::vector<std::thread> th;
-  for (size_t g = 1; g < ng; ++g) th.emplace_back(work, g);
-  work(0);
-  for (std::thread &t : th) t.join();
+  if (profile) {  // groups one after another, so the timed launches do not overlap
+    for (size_t g = 0; g < ng; ++g) {
+      work(g);
+      cudaStreamSynchronize(streams[g]);
+    }
+  } else {
+    std::vector<std::thread> th;
+    for (size_t g = 1; g < ng; ++g) th.emplace_back(work, g);
+    work(0);
+    for (std::thread &t : th) t.join();
+  }
   int rc = PP_OK;
   for (size_t g = 0; g < ng; ++g) {
     cudaEvent_t eg;

@@ -52,7 +52,9 @@ struct pp_ctx {
   pp_opts opts;
   bool have_poly = false;
   int degree = 0;
-  std::vector<double> coef;
+  int poly_kind = 0;          // pp_poly_kind of q
+  std::vector<double> coef;   // as read back: Chebyshev coefficients, or b_i / cap^i (other kinds)
+  NewtonForm nf;              // q at its Leja-ordered nodes, the form the device chain evaluates
   double a = 0, b = 0, img_lo = 0, img_hi = 0;
   std::vector<double> qsig, qwt;
   int tile_bdx = 0;  // stencil block x-size chosen by pp_autotune (0 = default)
@@ -65,3 +67,16 @@ struct pp_ctx {
   size_t prof_used = 0;
 };
 
+// q(A) v by the Horner scheme of the Newton form (every kind of q unless
+// opts.clenshaw asks for the matrix Clenshaw recurrence of a Chebyshev q).
+inline bool poly_horner(const pp_ctx *c) { return c->poly_kind != 0 || !c->opts.clenshaw; }
+
+// Coefficients of step t (0 .. degree-1) of q(A) v.
+inline StepCoef poly_step_coef(const pp_ctx *c, int t) {
+  if (poly_horner(c)) return horner_step(c->nf.b, c->nf.c, c->nf.e, c->nf.cap, t);
+  const double s1 = 4.0 / (c->b - c->a), s2 = -2.0 * (c->a + c->b) / (c->b - c->a);
+  return clenshaw_coef(c->coef, s1, s2, t);
+}
+
+// Constant q of degree 0.
+inline double poly_const(const pp_ctx *c) { return poly_horner(c) ? c->nf.b[0] : c->coef[0]; }

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <complex>
 #include <string>
 #include <vector>
 
@@ -29,10 +30,12 @@ struct OpDesc {
   int tile_bdx;  // stencil kernels: threads per block in x (0 = sized to the row)
 };
 
-// out = alpha * (A x) + beta * x  [- y]  [+ delta * v]
+// out = alpha * (A x) + beta * x  [+ gamma * y]  [+ delta * v]; sub_y switches
+// the y term on (gamma = -1: the Clenshaw step subtracts y).
 struct StepCoef {
   double alpha, beta, delta;
   bool sub_y, add_v;
+  double gamma = -1.0;
 };
 
 template <typename T>
@@ -54,11 +57,30 @@ inline StepCoef clenshaw_coef(const std::vector<double> &cf, double s1, double s
   return {s1, s2, cf[k - 1 - t], true, true};
 }
 
+// Step t (0 .. k-1) of q(A) v for q = sum_{i<=k} b_i R_i in the basis of
+// NewtonForm, by the backward recurrence
+//   w_k = b_k v,  w_i = ((A - c_i)/cap) w_{i+1} + e_{i+1} w_{i+2} + b_i v,  q(A) v = w_0
+// (for real nodes the Horner scheme of the Newton form; the scaling by cap
+// keeps coefficients and vectors inside the FP32 range at high degree).  Step
+// t computes w_{k-1-t}; the first step folds w_k = b_k v, the second folds
+// e_k w_k into the v term, later steps read w_{i+2} (as y) only where
+// e_{i+1} != 0.  Real nodes: three vector streams per step, one fewer than
+// the Clenshaw step.
+inline StepCoef horner_step(const std::vector<double> &b, const std::vector<double> &c,
+                            const std::vector<double> &e, double cap, int t) {
+  const int k = (int)b.size() - 1;
+  const double r = 1.0 / cap;
+  if (t == 0) return {b[k] * r, b[k - 1] - c[k - 1] * b[k] * r, 0.0, false, false, 0.0};
+  const int i = k - 1 - t;
+  if (t == 1) return {r, -c[i] * r, b[i] + e[i + 1] * b[k], false, true, 0.0};
+  return {r, -c[i] * r, b[i], e[i + 1] != 0.0, true, e[i + 1]};
+}
+
 // Constants of one stencil row: K0 x_c + Km (sum of -1 neighbours) + Kp (sum
-// of +1 neighbours) [- y] [+ D v], in the vector arithmetic.
+// of +1 neighbours) [+ Y y] [+ D v], in the vector arithmetic.
 template <typename T>
 struct Konst {
-  T K0, Km, Kp, D;
+  T K0, Km, Kp, D, Y;
 };
 
 // One grid of a batched stencil launch: rows [off, off + nx ny nz) of the
@@ -193,6 +215,30 @@ double cheb_eval(const std::vector<double> &c, double a, double b, double z);
 // min/max of q over a dense grid of [a,b] and of z q(z)^2
 void cheb_scan(const std::vector<double> &c, double a, double b, double *qmin, double *img_lo,
                double *img_hi);
+// Interpolant q of z^{-1/2} at real nodes or conjugate pairs (Sec. 5.2) in
+// Newton form at the Leja-ordered nodes, written in a real scaled basis:
+// R_0 = 1, R_{i+1} = ((z - c_i)/cap) R_i + e_i R_{i-1}, q = sum b_i R_i (for
+// real nodes c_i = x_i, e_i = 0: the Newton basis scaled by cap^i; a
+// conjugate pair (x_i, conj x_i) has c_i = c_{i+1} = Re x_i, e_{i+1} =
+// (Im x_i/cap)^2).
+struct NewtonForm {
+  std::vector<double> re, im;  // Leja-ordered nodes, a pair as (Im > 0, conjugate)
+  double cap = 1.0;            // a quarter of the diameter of the node set
+  std::vector<double> b, c, e;
+};
+// false for an empty node set, a pair without its conjugate or a non-finite coefficient
+bool newton_form(const std::vector<std::complex<double>> &nodes, NewtonForm *F);
+std::complex<double> newton_form_eval(const NewtonForm &F, std::complex<double> z);
+// min Re q and the extremes of |z q(z)^2| on [lo, hi] and at the nodes
+void newton_scan(const NewtonForm &F, double lo, double hi, double *qmin, double *img_lo, double *img_hi);
+// eigenvalues of a real upper Hessenberg matrix (row-major); false if not converged
+bool hess_eigvals(std::vector<double> H, int n, std::vector<double> *wr, std::vector<double> *wi);
+// f = M^{-T} e_n for a dense row-major M; false if singular
+bool solve_transposed_last(const std::vector<double> &M, int n, std::vector<double> *f);
+// Harmonic Ritz values of SPD tridiagonal T (al, be) and beta = h_{m+1,m};
+// false if T is not positive definite.
+bool harmonic_ritz(const std::vector<double> &al, const std::vector<double> &be, double beta,
+                   std::vector<double> *out);
 // Trapezoid rule for z^{-1/2} = (2/pi) int_0^inf (t^2 + z)^{-1} dt, t = e^u.
 void invsqrt_quadrature(double lo, double hi, double tau, double theta_max, std::vector<double> *sig,
                         std::vector<double> *wt);

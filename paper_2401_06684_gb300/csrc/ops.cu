@@ -1,13 +1,16 @@
-// Operator kernels: one application of A fused with the vector update of the
-// matrix Clenshaw recurrence (Sec. 5.1),
-//     out = alpha (A x) + beta x  [- y]  [+ delta v],
-// which covers a plain product u = A x (alpha = 1, beta = 0) as well as
-// every step b_i = 2 sigma(A) b_{i+1} - b_{i+2} + c_i v, sigma(A) = (2A -
-// (a+b) I)/(b-a).  The stencil is folded into three constants
+// Operator kernels: one application of A fused with the vector update of a
+// step of q(A) v,
+//     out = alpha (A x) + beta x  [+ gamma y]  [+ delta v],
+// which covers a plain product u = A x (alpha = 1, beta = 0), every Horner
+// step of the Newton form w_i = ((A - x_i)/cap) w_{i+1} + a_i v (Sec. 5.2; no
+// y term for real nodes), its conjugate-pair steps (gamma = (Im x_i/cap)^2)
+// and every step b_i = 2 sigma(A) b_{i+1} - b_{i+2} + c_i v of the matrix
+// Clenshaw recurrence (Sec. 5.1, gamma = -1).  The stencil is folded into
+// three constants
 //     K0 = alpha d + beta, Km = alpha cm, Kp = alpha cp,
-// so one pass reads x (with its neighbours), y, v and writes out: 4 vectors
-// of HBM traffic per step for the matrix-free operators.  The arithmetic is
-// that of the vectors: FP64, double-word pairs or FP32.
+// so one pass reads x (with its neighbours) and v, [y,] and writes out: 3
+// (4 with y) vectors of HBM traffic per step for the matrix-free operators.
+// The arithmetic is that of the vectors: FP64, double-word pairs or FP32.
 #include "common.cuh"
 #include "internal.h"
 
@@ -24,7 +27,7 @@ __device__ __forceinline__ dw shfl_xor_t<dw>(dw v, int o, int width) {
 
 
 // One stencil row evaluated as a compensated linear combination
-//   K0 x_c + Km (x_w + x_s + x_d) + Kp (x_e + x_n + x_u) [- y] [+ D v].
+//   K0 x_c + Km (x_w + x_s + x_d) + Kp (x_e + x_n + x_u) [+ Y y] [+ D v].
 template <typename T, bool SUB_Y, bool ADD_V>
 __device__ __forceinline__ T stencil_row(T xc, T xw, T xe, T xs, T xn, T xd, T xu, T yy, T vv,
                                          const Konst<T> &K) {
@@ -39,7 +42,7 @@ __device__ __forceinline__ T stencil_row(T xc, T xw, T xe, T xs, T xn, T xd, T x
   acc_set_prod(r, K.K0, xc);
   acc_add_prod(r, K.Km, acc_raw(nm));
   acc_add_prod(r, K.Kp, acc_raw(np));
-  if (SUB_Y) acc_sub(r, yy);
+  if (SUB_Y) acc_add_prod(r, K.Y, yy);
   if (ADD_V) acc_add_prod(r, K.D, vv);
   return acc_get(r);
 }
@@ -176,7 +179,7 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
                                                 const T *__restrict__ val, const T *__restrict__ x,
                                                 const T *__restrict__ y, const T *__restrict__ v,
                                                 T *__restrict__ out, int64_t n, T alpha, T beta,
-                                                T delta) {
+                                                T gamma, T delta) {
   pdl_wait();
   pdl_trigger();
   using A = typename acc_of<T>::type;
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
     A r;
     acc_set_prod(r, alpha, sum);
     acc_add_prod(r, beta, ldg(x + row));
-    if (SUB_Y) acc_sub(r, ldg(y + row));
+    if (SUB_Y) acc_add_prod(r, gamma, ldg(y + row));
     if (ADD_V) acc_add_prod(r, delta, ldg(v + row));
     out[row] = acc_get(r);
   }
@@ -227,13 +230,15 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     const int64_t nb = (threads + bs - 1) / bs;
     PP_CUDA_TRY(pdl_launch(csr_step<T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col, (const T *)op.val, x, y, v,
                                                        out, op.n, host_const<T>(c.alpha),
-                                                       host_const<T>(c.beta), host_const<T>(c.delta)));
+                                                       host_const<T>(c.beta), host_const<T>(c.gamma),
+                                                       host_const<T>(c.delta)));
   } else {
     Konst<T> K;
     K.K0 = host_const<T>(c.alpha * op.d + c.beta);
     K.Km = host_const<T>(c.alpha * op.cm);
     K.Kp = host_const<T>(c.alpha * op.cp);
     K.D = host_const<T>(c.delta);
+    K.Y = host_const<T>(c.gamma);
     const int nz = op.kind == OPK_ST2D ? 1 : (int)op.nz;
     // widest vector access the row length and every pointer allow
     constexpr int PW = 16 / (int)sizeof(T);
@@ -282,6 +287,7 @@ void batch_konst(const double *d, const double *cm, const double *cp, const Step
     out[i].Km = host_const<T>(c[i].alpha * cm[i]);
     out[i].Kp = host_const<T>(c[i].alpha * cp[i]);
     out[i].D = host_const<T>(c[i].delta);
+    out[i].Y = host_const<T>(c[i].gamma);
   }
 }
 

@@ -1,6 +1,8 @@
 // Host-side FP64 construction of the preconditioning polynomial and of the
 // quadrature rule used by the small projected solve.
+#include <algorithm>
 #include <cmath>
+#include <complex>
 #include <vector>
 
 #include "internal.h"
@@ -81,4 +83,353 @@ void invsqrt_quadrature(double lo, double hi, double tau, double theta_max, std:
     (*sig)[k] = std::exp(2.0 * u);
     (*wt)[k] = (2.0 * h / M_PI) * std::exp(u);
   }
+}
+
+// ---- interpolation at (harmonic) Ritz values (Sec. 5.2) ----
+
+using cplx = std::complex<double>;
+
+// Leja order: a node of largest modulus first, then each time the remaining
+// node whose product of distances to the nodes already taken is largest
+// (compared as sums of logarithms; ties go to the earlier node).  Nodes of a
+// real problem come as real values or conjugate pairs: only the member with
+// Im > 0 of a pair is a candidate, and its conjugate follows it at once.
+static std::vector<cplx> leja_order(const std::vector<cplx> &nodes) {
+  std::vector<cplx> rest, out;
+  for (const cplx &z : nodes)
+    if (z.imag() >= 0.0) rest.push_back(z);
+  auto take = [&](size_t i) {
+    const cplx z = rest[i];
+    rest.erase(rest.begin() + (long)i);
+    out.push_back(z);
+    if (z.imag() > 0.0) out.push_back(std::conj(z));
+  };
+  size_t first = 0;
+  for (size_t i = 1; i < rest.size(); ++i)
+    if (std::abs(rest[i]) > std::abs(rest[first])) first = i;
+  take(first);
+  while (!rest.empty()) {
+    size_t best = 0;
+    double best_s = -INFINITY;
+    for (size_t i = 0; i < rest.size(); ++i) {
+      double s = 0.0;
+      for (const cplx &x : out) s += rest[i] == x ? -INFINITY : std::log(std::abs(rest[i] - x));
+      if (s > best_s) {
+        best_s = s;
+        best = i;
+      }
+    }
+    take(best);
+  }
+  return out;
+}
+
+bool newton_form(const std::vector<cplx> &nodes, NewtonForm *F) {
+  const std::vector<cplx> x = leja_order(nodes);
+  const size_t d = x.size();
+  if (d == 0 || d != nodes.size()) return false;  // a pair without its conjugate
+  // divided differences a_i = f[x_0, ..., x_i] of f(z) = z^{-1/2}, principal branch
+  std::vector<cplx> col(d), a(d);
+  for (size_t i = 0; i < d; ++i) col[i] = 1.0 / std::sqrt(x[i]);
+  a[0] = col[0];
+  for (size_t k = 1; k < d; ++k) {
+    for (size_t i = 0; i + k < d; ++i) col[i] = (col[i + 1] - col[i]) / (x[i + k] - x[i]);
+    a[k] = col[0];
+  }
+  // scaling: a quarter of the diameter of the node set (the capacity of an interval)
+  double diam = 0.0;
+  for (size_t i = 0; i < d; ++i)
+    for (size_t j = i + 1; j < d; ++j) diam = std::fmax(diam, std::abs(x[i] - x[j]));
+  F->cap = diam > 0.0 ? 0.25 * diam : 1.0;
+  // scaled Newton coefficients ah_i = a_i cap^i of the basis N_i = prod_{l<i} (z - x_l)/cap
+  std::vector<cplx> ah(d);
+  double p = 1.0;
+  for (size_t i = 0; i < d; ++i) {
+    ah[i] = a[i] * p;
+    p *= F->cap;
+  }
+  // real basis: R_0 = 1; a real node x_i: R_{i+1} = ((z - x_i)/cap) R_i; a pair
+  // (x_i, conj x_i): R_{i+1} = ((z - Re x_i)/cap) R_i and R_{i+2} = ((z - Re x_i)/cap)
+  // R_{i+1} + (Im x_i/cap)^2 R_i.  N_i = R_i at the start of a pair, N_{i+1} =
+  // R_{i+1} - i (Im x_i/cap) R_i, so q = sum b_i R_i with b_i = ah_i - i (Im x_i/cap)
+  // ah_{i+1}, b_{i+1} = ah_{i+1} (real for a conjugation-closed node set).
+  F->re.resize(d);
+  F->im.resize(d);
+  F->b.assign(d, 0.0);
+  F->c.assign(d, 0.0);
+  F->e.assign(d, 0.0);
+  for (size_t i = 0; i < d; ++i) {
+    F->re[i] = x[i].real();
+    F->im[i] = x[i].imag();
+  }
+  for (size_t i = 0; i < d;) {
+    F->c[i] = x[i].real();
+    if (x[i].imag() > 0.0) {
+      if (i + 1 >= d) return false;
+      const double s = x[i].imag() / F->cap;
+      F->b[i] = (ah[i] - cplx(0.0, s) * ah[i + 1]).real();
+      F->b[i + 1] = ah[i + 1].real();
+      F->c[i + 1] = x[i].real();
+      F->e[i + 1] = s * s;
+      i += 2;
+    } else {
+      F->b[i] = ah[i].real();
+      i += 1;
+    }
+  }
+  for (size_t i = 0; i < d; ++i)
+    if (!std::isfinite(F->b[i])) return false;
+  return true;
+}
+
+// q(z) by the backward recurrence of the basis: u_{k+1} = u_{k+2} = 0,
+// u_i = b_i + ((z - c_i)/cap) u_{i+1} + e_{i+1} u_{i+2}, q(z) = u_0.
+cplx newton_form_eval(const NewtonForm &F, cplx z) {
+  const int k = (int)F.b.size() - 1;
+  cplx u1 = 0.0, u2 = 0.0;
+  for (int i = k; i >= 0; --i) {
+    const cplx u0 = F.b[i] + (z - F.c[i]) / F.cap * u1 + (i + 1 <= k ? F.e[i + 1] : 0.0) * u2;
+    u2 = u1;
+    u1 = u0;
+  }
+  return u1;
+}
+
+// Positivity check and image of z q(z)^2 for a Newton-form q: the points of
+// cheb_scan on [lo, hi] (q real there) and the nodes themselves.  qmin is the
+// smallest real part of q over the points, img_lo / img_hi the extremes of
+// |z q(z)^2|.
+void newton_scan(const NewtonForm &F, double lo, double hi, double *qmin, double *img_lo, double *img_hi) {
+  const int N = 20001;
+  double qm = INFINITY, l = INFINITY, h = -INFINITY;
+  auto visit = [&](cplx z) {
+    const cplx q = newton_form_eval(F, z);
+    const double p = std::abs(z * q * q);
+    qm = std::fmin(qm, q.real());
+    l = std::fmin(l, p);
+    h = std::fmax(h, p);
+  };
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < N; ++k) {
+      const double f = (double)k / (N - 1);
+      visit(pass == 0 ? lo + (hi - lo) * f : lo * std::pow(hi / lo, f));
+    }
+  for (size_t i = 0; i < F.re.size(); ++i) visit(cplx(F.re[i], F.im[i]));
+  *qmin = qm;
+  *img_lo = l;
+  *img_hi = h;
+}
+
+// Eigenvalues of a real upper Hessenberg matrix (n x n, row-major, overwritten)
+// by the Francis double-shift QR iteration with deflation (Golub & Van Loan,
+// Sec. 7.5), transforming only the active diagonal block (eigenvalues only).
+// Complex eigenvalues come as exact conjugate pairs (Im > 0 first).  Returns
+// false if an eigenvalue has not converged after 60 n double steps.
+bool hess_eigvals(std::vector<double> H, int n, std::vector<double> *wr, std::vector<double> *wi) {
+  auto h = [&](int i, int j) -> double & { return H[(size_t)i * n + j]; };
+  wr->assign(n, 0.0);
+  wi->assign(n, 0.0);
+  int u = n - 1, iter = 0, total = 0;
+  while (u >= 0) {
+    int l = u;
+    for (; l > 0; --l) {
+      double s = std::fabs(h(l - 1, l - 1)) + std::fabs(h(l, l));
+      if (s == 0.0) s = 1.0;
+      if (std::fabs(h(l, l - 1)) <= 0x1p-53 * s) {
+        h(l, l - 1) = 0.0;
+        break;
+      }
+    }
+    if (l == u) {  // 1 x 1 block
+      (*wr)[u] = h(u, u);
+      --u;
+      iter = 0;
+      continue;
+    }
+    if (l == u - 1) {  // 2 x 2 block
+      const double a = h(u - 1, u - 1), b = h(u - 1, u), c = h(u, u - 1), d = h(u, u);
+      const double mid = 0.5 * (a + d), p = 0.5 * (a - d), disc = p * p + b * c;
+      if (disc >= 0.0) {
+        const double sq = std::sqrt(disc);
+        const double r1 = mid + (mid >= 0.0 ? sq : -sq);
+        const double r2 = r1 != 0.0 ? (a * d - b * c) / r1 : mid - sq;
+        (*wr)[u - 1] = r1;
+        (*wr)[u] = r2;
+      } else {
+        const double sq = std::sqrt(-disc);
+        (*wr)[u - 1] = (*wr)[u] = mid;
+        (*wi)[u - 1] = sq;
+        (*wi)[u] = -sq;
+      }
+      u -= 2;
+      iter = 0;
+      continue;
+    }
+    if (++total > 60 * n) return false;
+    ++iter;
+    double s, t;  // sum and product of the two shifts
+    if (iter % 11 == 10) {  // exceptional shift after a run without deflation
+      const double w = std::fabs(h(u, u - 1)) + std::fabs(h(u - 1, u - 2));
+      s = 1.5 * w + h(u, u);
+      t = s * s / 4.0 + w * w;
+    } else {
+      s = h(u - 1, u - 1) + h(u, u);
+      t = h(u - 1, u - 1) * h(u, u) - h(u - 1, u) * h(u, u - 1);
+    }
+    // first column of (H - s1 I)(H - s2 I) restricted to the block
+    double x = h(l, l) * h(l, l) + h(l, l + 1) * h(l + 1, l) - s * h(l, l) + t;
+    double y = h(l + 1, l) * (h(l, l) + h(l + 1, l + 1) - s);
+    double z = h(l + 1, l) * h(l + 2, l + 1);
+    for (int k = l; k <= u - 1; ++k) {
+      const int r = k <= u - 2 ? 3 : 2;  // reflector size
+      double v[3] = {x, y, r == 3 ? z : 0.0};
+      const double nrm = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+      if (nrm != 0.0) {
+        const double alpha = v[0] >= 0.0 ? -nrm : nrm;
+        v[0] -= alpha;
+        const double vv = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+        if (vv != 0.0) {
+          const double beta = 2.0 / vv;
+          for (int j = std::max(l, k - 1); j <= u; ++j) {  // rows k .. k+r-1 from the left
+            double sm = 0.0;
+            for (int q = 0; q < r; ++q) sm += v[q] * h(k + q, j);
+            sm *= beta;
+            for (int q = 0; q < r; ++q) h(k + q, j) -= sm * v[q];
+          }
+          for (int i = l; i <= std::min(k + 3, u); ++i) {  // columns k .. k+r-1 from the right
+            double sm = 0.0;
+            for (int q = 0; q < r; ++q) sm += h(i, k + q) * v[q];
+            sm *= beta;
+            for (int q = 0; q < r; ++q) h(i, k + q) -= sm * v[q];
+          }
+        }
+      }
+      if (k + 1 <= u - 1) {
+        x = h(k + 1, k);
+        y = h(k + 2, k);
+        z = k + 3 <= u ? h(k + 3, k) : 0.0;
+      }
+    }
+  }
+  return true;
+}
+
+// Solve M^T f = e_last for a dense n x n M (row-major) by Gaussian
+// elimination with partial pivoting; false if M is singular.
+bool solve_transposed_last(const std::vector<double> &M, int n, std::vector<double> *f) {
+  std::vector<double> T((size_t)n * n), rhs(n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) T[(size_t)i * n + j] = M[(size_t)j * n + i];
+  rhs[n - 1] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int pr = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(T[(size_t)i * n + k]) > std::fabs(T[(size_t)pr * n + k])) pr = i;
+    if (T[(size_t)pr * n + k] == 0.0) return false;
+    if (pr != k) {
+      for (int j = 0; j < n; ++j) std::swap(T[(size_t)k * n + j], T[(size_t)pr * n + j]);
+      std::swap(rhs[k], rhs[pr]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const double m = T[(size_t)i * n + k] / T[(size_t)k * n + k];
+      if (m == 0.0) continue;
+      for (int j = k; j < n; ++j) T[(size_t)i * n + j] -= m * T[(size_t)k * n + j];
+      rhs[i] -= m * rhs[k];
+    }
+  }
+  f->assign(n, 0.0);
+  for (int i = n - 1; i >= 0; --i) {
+    double sm = rhs[i];
+    for (int j = i + 1; j < n; ++j) sm -= T[(size_t)i * n + j] * (*f)[j];
+    (*f)[i] = sm / T[(size_t)i * n + i];
+  }
+  return true;
+}
+
+// Eigenvalues of a symmetric n x n matrix M (row-major, overwritten) by the
+// cyclic Jacobi method (Golub & Van Loan, Sec. 8.5), ascending.
+std::vector<double> sym_eigvals(std::vector<double> M, int n) {
+  auto at = [&](int i, int j) -> double & { return M[(size_t)i * n + j]; };
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        tot += at(i, j) * at(i, j);
+        if (i != j) off += at(i, j) * at(i, j);
+      }
+    if (off <= 1e-30 * tot) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = at(p, q);
+        if (apq == 0.0) continue;
+        // rotation that zeroes M[p][q]: tan of the angle t solves t^2 + 2 tau t - 1 = 0
+        const double tau = (at(q, q) - at(p, p)) / (2.0 * apq);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double mkp = at(k, p), mkq = at(k, q);
+          at(k, p) = cs * mkp - sn * mkq;
+          at(k, q) = sn * mkp + cs * mkq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double mpk = at(p, k), mqk = at(q, k);
+          at(p, k) = cs * mpk - sn * mqk;
+          at(q, k) = sn * mpk + cs * mqk;
+        }
+      }
+  }
+  std::vector<double> ev(n);
+  for (int i = 0; i < n; ++i) ev[i] = at(i, i);
+  std::sort(ev.begin(), ev.end());
+  return ev;
+}
+
+// Harmonic Ritz values of a symmetric positive definite tridiagonal T
+// (diagonal al, off-diagonal be[0..m-2]) with next coefficient beta = h_{m+1,m}:
+// the eigenvalues of T + beta^2 T^{-1} e_m e_m^T, i.e. of the symmetric pencil
+// (T^2 + beta^2 e_m e_m^T, T).  With T = L L^T (Cholesky, L lower bidiagonal)
+// they are the eigenvalues of the symmetric L^{-1} (T^2 + beta^2 e_m e_m^T) L^{-T}.
+// Returns false if T is not positive definite.
+bool harmonic_ritz(const std::vector<double> &al, const std::vector<double> &be, double beta,
+                   std::vector<double> *out) {
+  const int m = (int)al.size();
+  std::vector<double> ld(m), ls(m > 1 ? m - 1 : 0);  // diagonal and sub-diagonal of L
+  for (int i = 0; i < m; ++i) {
+    const double piv = al[i] - (i > 0 ? ls[i - 1] * ls[i - 1] : 0.0);
+    if (!(piv > 0.0)) return false;
+    ld[i] = std::sqrt(piv);
+    if (i + 1 < m) ls[i] = be[i] / ld[i];
+  }
+  // B = T^2 + beta^2 e_m e_m^T (dense, symmetric)
+  std::vector<double> T((size_t)m * m, 0.0), B((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    T[(size_t)i * m + i] = al[i];
+    if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = be[i];
+  }
+  for (int i = 0; i < m; ++i)
+    for (int j = std::max(0, i - 2); j <= std::min(m - 1, i + 2); ++j) {
+      double s = 0.0;
+      for (int k = std::max(0, i - 1); k <= std::min(m - 1, i + 1); ++k) s += T[(size_t)i * m + k] * T[(size_t)k * m + j];
+      B[(size_t)i * m + j] = s;
+    }
+  B[(size_t)(m - 1) * m + m - 1] += beta * beta;
+  // C = L^{-1} B (forward substitution on each column), then M = C L^{-T}
+  // (forward substitution on each row of C, i.e. on the columns of C^T)
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < m; ++i) {
+      double v = B[(size_t)i * m + j] - (i > 0 ? ls[i - 1] * B[(size_t)(i - 1) * m + j] : 0.0);
+      B[(size_t)i * m + j] = v / ld[i];
+    }
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < m; ++j) {
+      double v = B[(size_t)i * m + j] - (j > 0 ? ls[j - 1] * B[(size_t)i * m + j - 1] : 0.0);
+      B[(size_t)i * m + j] = v / ld[j];
+    }
+  for (int i = 0; i < m; ++i)  // symmetrize the rounding
+    for (int j = i + 1; j < m; ++j) {
+      const double s = 0.5 * (B[(size_t)i * m + j] + B[(size_t)j * m + i]);
+      B[(size_t)i * m + j] = B[(size_t)j * m + i] = s;
+    }
+  *out = sym_eigvals(B, m);
+  return true;
 }

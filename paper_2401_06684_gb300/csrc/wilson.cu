@@ -179,12 +179,12 @@ __device__ __forceinline__ void hop_pair(A *hs, const T *__restrict__ in, const 
   hop<MU, DAG ? -1 : 1, true>(hs, in + bwd * 24, U + (bwd * 4 + MU) * 9);
 }
 
-// out = Kd in + Kh (hop sum of in) [+ Kb x] [- y] [+ Kv v], one thread per site
+// out = Kd in + Kh (hop sum of in) [+ Kb x] [+ Ky y] [+ Kv v], one thread per site
 template <typename T, bool DAG, bool ADD_X, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(128) wilson_step(const T *__restrict__ in, const T *__restrict__ x,
                                                    const T *__restrict__ y, const T *__restrict__ v,
                                                    T *__restrict__ out, const float2 *__restrict__ U,
-                                                   Lat lat, T Kd, T Kh, T Kb, T Kv) {
+                                                   Lat lat, T Kd, T Kh, T Kb, T Ky, T Kv) {
   pdl_wait();
   pdl_trigger();
   using A = typename acc_of<T>::type;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(128) wilson_step(const T *__restrict__ in, con
     acc_set_prod(res, Kd, ldg(in + o + k));
     acc_add_prod(res, Kh, acc_raw(hs[k]));
     if (ADD_X) acc_add_prod(res, Kb, ldg(x + o + k));
-    if (SUB_Y) acc_sub(res, ldg(y + o + k));
+    if (SUB_Y) acc_add_prod(res, Ky, ldg(y + o + k));
     if (ADD_V) acc_add_prod(res, Kv, ldg(v + o + k));
     out[o + k] = acc_get(res);
   }
@@ -234,11 +234,12 @@ dw host_c<dw>(double v) {
 
 template <typename T, bool DAG, bool AX, bool SY, bool AV>
 int launch(const T *in, const T *x, const T *y, const T *v, T *out, const float2 *U, const Lat &lat,
-           double kd, double kh, double kb, double kv, cudaStream_t s) {
+           double kd, double kh, double kb, double ky, double kv, cudaStream_t s) {
   const int bs = 128;
   const int64_t nb = (lat.V + bs - 1) / bs;
   PP_CUDA_TRY(pdl_launch(wilson_step<T, DAG, AX, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, in, x, y, v, out, U, lat, host_c<T>(kd),
-                                                             host_c<T>(kh), host_c<T>(kb), host_c<T>(kv)));
+                                                             host_c<T>(kh), host_c<T>(kb), host_c<T>(ky),
+                                                             host_c<T>(kv)));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
@@ -261,26 +262,26 @@ int wilson_op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out,
   const double md = 4.0 + op.mass;
   // t = D x
   int rc = launch<T, false, false, false, false>(x, nullptr, nullptr, nullptr, t, U, lat, md, -0.5, 0.0,
-                                                 0.0, s);
+                                                 0.0, 0.0, s);
   if (rc) return rc;
-  // out = alpha D^H t + beta x [- y] [+ delta v]
+  // out = alpha D^H t + beta x [+ gamma y] [+ delta v]
   const double kd = c.alpha * md, kh = -0.5 * c.alpha;
   const bool ax = c.beta != 0.0;
   if (!ax && !c.sub_y && !c.add_v)
-    return launch<T, true, false, false, false>(t, x, y, v, out, U, lat, kd, kh, 0.0, 0.0, s);
+    return launch<T, true, false, false, false>(t, x, y, v, out, U, lat, kd, kh, 0.0, c.gamma, 0.0, s);
   if (ax && !c.sub_y && !c.add_v)
-    return launch<T, true, true, false, false>(t, x, y, v, out, U, lat, kd, kh, c.beta, 0.0, s);
+    return launch<T, true, true, false, false>(t, x, y, v, out, U, lat, kd, kh, c.beta, c.gamma, 0.0, s);
   if (ax && !c.sub_y && c.add_v)
-    return launch<T, true, true, false, true>(t, x, y, v, out, U, lat, kd, kh, c.beta, c.delta, s);
+    return launch<T, true, true, false, true>(t, x, y, v, out, U, lat, kd, kh, c.beta, c.gamma, c.delta, s);
   if (ax && c.sub_y && c.add_v)
-    return launch<T, true, true, true, true>(t, x, y, v, out, U, lat, kd, kh, c.beta, c.delta, s);
+    return launch<T, true, true, true, true>(t, x, y, v, out, U, lat, kd, kh, c.beta, c.gamma, c.delta, s);
   if (ax && c.sub_y && !c.add_v)
-    return launch<T, true, true, true, false>(t, x, y, v, out, U, lat, kd, kh, c.beta, 0.0, s);
+    return launch<T, true, true, true, false>(t, x, y, v, out, U, lat, kd, kh, c.beta, c.gamma, 0.0, s);
   if (!ax && c.add_v && !c.sub_y)
-    return launch<T, true, false, false, true>(t, x, y, v, out, U, lat, kd, kh, 0.0, c.delta, s);
+    return launch<T, true, false, false, true>(t, x, y, v, out, U, lat, kd, kh, 0.0, c.gamma, c.delta, s);
   if (!ax && c.sub_y && c.add_v)
-    return launch<T, true, false, true, true>(t, x, y, v, out, U, lat, kd, kh, 0.0, c.delta, s);
-  return launch<T, true, false, true, false>(t, x, y, v, out, U, lat, kd, kh, 0.0, 0.0, s);
+    return launch<T, true, false, true, true>(t, x, y, v, out, U, lat, kd, kh, 0.0, c.gamma, c.delta, s);
+  return launch<T, true, false, true, false>(t, x, y, v, out, U, lat, kd, kh, 0.0, c.gamma, 0.0, s);
 }
 
 template int wilson_op_step<double>(const OpDesc &, const double *, const double *, const double *, double *,

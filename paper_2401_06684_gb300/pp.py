@@ -24,7 +24,7 @@ PP_ERR_UNSUPPORTED = -9
 
 PP_F64, PP_F32, PP_C64, PP_C128 = 0, 1, 2, 3
 PP_INVSQRT, PP_SQRT = -1, 1
-PP_CHEBYSHEV, PP_RITZ_LEJA, PP_HARMONIC_RITZ, PP_LSQ_CONTOUR = 0, 1, 2, 3
+PP_CHEBYSHEV, PP_RITZ_LEJA, PP_HARMONIC_RITZ, PP_LSQ_CONTOUR, PP_NODES = 0, 1, 2, 3, 4
 PP_LAPLACE2D5, PP_LAPLACE3D7, PP_CONVDIFF3D7_UPWIND, PP_WILSON4D_DHD = 0, 1, 2, 3
 PP_LEFT, PP_RIGHT = 0, 1
 PP_PREC_F64, PP_PREC_DW, PP_PREC_MIXED = 0, 1, 2
@@ -36,7 +36,7 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 class pp_opts(ctypes.Structure):
     _fields_ = [("side", ctypes.c_int32), ("precision", ctypes.c_int32), ("orth", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("two_pass", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
+                ("two_pass", ctypes.c_int32), ("clenshaw", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class pp_stats(ctypes.Structure):
@@ -72,6 +72,11 @@ SYMBOLS = {
     "pp_get_poly": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
                                    ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_double)]),
+    "pp_get_poly_nodes": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.c_int32,
+                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
+    "pp_set_poly_nodes": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "pp_get_quadrature": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "pp_apply": (ctypes.c_int, [_h, ctypes.c_int32, _p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
@@ -190,6 +195,31 @@ def pp_get_poly(h):
     img = (ctypes.c_double * 2)()
     _check(lib().pp_get_poly(h, c, n.value, ctypes.byref(n), ab, img))
     return np.array(c[:]), (ab[0], ab[1]), (img[0], img[1])
+
+
+def pp_get_poly_nodes(h):
+    """(kind, nodes, cap): the pp_poly_kind of q, its interpolation nodes in
+    Leja order (complex array if any is complex) and the step scaling cap."""
+    n = ctypes.c_int32()
+    k = ctypes.c_int32()
+    cap = ctypes.c_double()
+    _check(lib().pp_get_poly_nodes(h, ctypes.byref(k), None, None, 0, ctypes.byref(n), None))
+    xr = (ctypes.c_double * n.value)()
+    xi = (ctypes.c_double * n.value)()
+    _check(lib().pp_get_poly_nodes(h, ctypes.byref(k), xr, xi, n.value, ctypes.byref(n), ctypes.byref(cap)))
+    re, im = np.array(xr[:]), np.array(xi[:])
+    return k.value, (re + 1j * im if np.any(im != 0) else re), cap.value
+
+
+def pp_set_poly_nodes(h, nodes, interval_ab=None):
+    z = np.asarray(nodes)
+    re = np.ascontiguousarray(np.real(z), dtype=np.float64)
+    im = np.ascontiguousarray(np.imag(z), dtype=np.float64) if np.iscomplexobj(z) else None
+    n = len(re)
+    ab = (ctypes.c_double * 2)(*interval_ab) if interval_ab is not None else None
+    _check(lib().pp_set_poly_nodes(h, re.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   im.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if im is not None else None,
+                                   n, ab))
 
 
 def pp_get_quadrature(h):

@@ -9,7 +9,7 @@ import subprocess
 import numpy as np
 import pytest
 
-from oracle import chebyshev as cheb, operators as ops
+from oracle import chebyshev as cheb, operators as ops, ritz
 from tests.libpp import load
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -129,12 +129,34 @@ def test_argument_validation():
             pp.pp_build_poly(h, -1)
         assert e.value.status == pp.PP_ERR_INVALID_ARG
         with pytest.raises(pp.PPError) as e:
-            pp.pp_build_poly(h, 4, pp.PP_RITZ_LEJA)
+            pp.pp_build_poly(h, 4, pp.PP_LSQ_CONTOUR)
         assert e.value.status == pp.PP_ERR_UNSUPPORTED
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_build_poly(h, 4, 9)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
         with pytest.raises(pp.PPError) as e:
             pp.pp_build_poly(h, 4, interval_ab=(2.0, 1.0))
         assert e.value.status == pp.PP_ERR_INVALID_ARG
+        with pytest.raises(pp.PPError) as e:  # checked before the node run
+            pp.pp_build_poly(h, 4, pp.PP_RITZ_LEJA, interval_ab=(0.0, 1.0))
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_get_poly_nodes(h)
+        assert e.value.status == pp.PP_ERR_STATE
         pp.pp_build_poly(h, 4)
+        # Chebyshev q: its nodes are the 5 first-kind Chebyshev nodes of [a,b],
+        # in Leja order (the order of its Newton form)
+        kind, x, _ = pp.pp_get_poly_nodes(h)
+        _, (a, b), _ = pp.pp_get_poly(h)
+        t = np.pi * (np.arange(5) + 0.5) / 5
+        assert kind == pp.PP_CHEBYSHEV
+        assert np.allclose(np.sort(x), np.sort(0.5 * (a + b) + 0.5 * (b - a) * np.cos(t)), rtol=1e-15)
+        assert x[0] == x.max() and x[1] == x.min()
+        o = pp.pp_default_opts()
+        o.clenshaw = 2
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_set_opts(h, o)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
         with pytest.raises(pp.PPError) as e:  # aliasing
             pp.pp_apply(h, pp.PP_INVSQRT, 1024, 1024)
         assert e.value.status == pp.PP_ERR_INVALID_ARG
@@ -159,6 +181,7 @@ def test_argument_validation():
         assert e.value.status == pp.PP_ERR_INVALID_ARG
     finally:
         pp.pp_destroy(h)
+
     pp.pp_destroy(None)
 
 
@@ -188,3 +211,96 @@ def test_autotune_degree_model():
     finally:
         for h in hs:
             pp.pp_destroy(h)
+
+
+def real_basis_eval(coef, x, z):
+    """q(z) = sum_i coef_i R_i(z) in the real basis of pp_set_poly_nodes:
+    R_0 = 1; a real node: R_{i+1} = (z - x_i) R_i; a pair (x_i, conj x_i):
+    R_{i+1} = (z - Re x_i) R_i, R_{i+2} = (z - Re x_i) R_{i+1} + (Im x_i)^2 R_i."""
+    z = np.asarray(z, dtype=complex)
+    R_prev, R = np.zeros_like(z), np.ones_like(z)
+    out = coef[0] * R
+    i = 0
+    while i + 1 < len(coef):
+        if np.imag(x[i]) > 0:
+            R1 = (z - x[i].real) * R
+            out = out + coef[i + 1] * R1
+            if i + 2 < len(coef):
+                R2 = (z - x[i].real) * R1 + x[i].imag ** 2 * R
+                out = out + coef[i + 2] * R2
+                R_prev, R = R1, R2
+            i += 2
+        else:
+            R_prev, R = R, (z - np.real(x[i])) * R
+            out = out + coef[i + 1] * R
+            i += 1
+    return out
+
+
+@pytest.mark.parametrize("nodes,ab", [
+    ([0.7, 2.5, 1.1, 6.0, 3.3], (0.2, 7.0)),
+    ([0.8, 1.5 + 0.7j, 1.5 - 0.7j, 3.0 + 1.2j, 3.0 - 1.2j, 5.0, 2.2], (0.2, 7.0)),
+    ([2.0 + 1.0j, 2.0 - 1.0j], (1.0, 3.0)),
+    ([4.0 - 0.5j, 1.0, 4.0 + 0.5j, 0.3 + 0.1j, 0.3 - 0.1j], (0.2, 7.0)),
+], ids=["real5", "pairs7", "pair2", "pairs5"])
+def test_set_poly_nodes_matches_oracle(nodes, ab):
+    # host-only construction of q from given nodes: Leja order, Newton form in
+    # the real basis, positivity, image; against the oracle's complex Newton form
+    pp = load()
+    z = np.array(nodes)
+    h = pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (5, 4, 3), [0.5])
+    try:
+        pp.pp_set_poly_nodes(h, z, interval_ab=ab)
+        kind, x, cap = pp.pp_get_poly_nodes(h)
+        coef, abr, img = pp.pp_get_poly(h)
+        assert kind == pp.PP_NODES and len(x) == len(z) and len(coef) == len(z)
+        xo = ritz.leja_order(z)
+        assert np.allclose(x, xo, rtol=0, atol=0)
+        ao = ritz.newton_coeffs(xo)
+        pts = np.concatenate([np.linspace(ab[0], ab[1], 41), z, [1 + 2j, 3 - 1j]])
+        assert np.allclose(real_basis_eval(coef, x, pts), ritz.newton_eval(ao, xo, pts), rtol=1e-12, atol=1e-14)
+        assert np.allclose(real_basis_eval(coef, x, z), z ** -0.5, rtol=1e-12)
+        # image of |z q(z)^2| on [a,b] and at the nodes
+        t = np.concatenate([np.linspace(ab[0], ab[1], 20001), np.geomspace(ab[0], ab[1], 20001), z])
+        qt = ritz.newton_eval(ao, xo, t)
+        p = np.abs(t * qt * qt)
+        assert img[0] == pytest.approx(p.min(), rel=1e-9) and img[1] == pytest.approx(p.max(), rel=1e-9)
+        assert abr == ab
+        assert cap == pytest.approx(0.25 * max(abs(a - b) for a in z for b in z), rel=1e-15)
+    finally:
+        pp.pp_destroy(h)
+
+
+def test_set_poly_nodes_validation():
+    pp = load()
+    hl = pp.pp_create_stencil(pp.PP_LAPLACE2D5, (6, 5))
+    hc = pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (5, 4, 3), [0.5])
+    try:
+        bad = [(hl, [1.0, 2.0 + 1j, 2.0 - 1j], pp.PP_ERR_INVALID_ARG),   # complex nodes, Hermitian handle
+               (hc, [1.0, 2.0 + 1j], pp.PP_ERR_INVALID_ARG),              # pair without conjugate
+               (hc, [1.0, 2.0 + 1j, 2.0 - 0.5j], pp.PP_ERR_INVALID_ARG),
+               (hc, [1.0, -0.5, 2.0], pp.PP_ERR_NONPRIMARY),              # Re <= 0
+               (hc, [1.0, 2.0, 1.0], pp.PP_ERR_NONPRIMARY),               # coincident
+               (hc, [], pp.PP_ERR_INVALID_ARG),
+               (hc, list(np.linspace(1, 2, 130)), pp.PP_ERR_INVALID_ARG),
+               (hc, [1.0, float("nan")], pp.PP_ERR_INVALID_ARG)]
+        for h, z, st in bad:
+            with pytest.raises(pp.PPError) as e:
+                pp.pp_set_poly_nodes(h, np.array(z, dtype=complex if np.iscomplexobj(np.array(z)) else float))
+            assert e.value.status == st, z
+        # a linear interpolant of z^{-1/2} at 1 and 2 turns negative near 5.8:
+        # positive on [0.5, 3], rejected on [0.5, 8]
+        pp.pp_set_poly_nodes(hl, np.array([1.0, 2.0]), interval_ab=(0.5, 3.0))
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_set_poly_nodes(hl, np.array([1.0, 2.0]), interval_ab=(0.5, 8.0))
+        assert e.value.status == pp.PP_ERR_NONPRIMARY
+        # default interval of a stencil handle: its closed form
+        pp.pp_set_poly_nodes(hl, np.array([0.5, 3.0, 7.0]))
+        _, ab, _ = pp.pp_get_poly(hl)
+        assert ab == pytest.approx(ops.laplace_interval((6, 5)), rel=1e-14)
+        with pytest.raises(pp.PPError) as e:
+            pp.pp_build_poly(hl, 3, pp.PP_NODES)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+    finally:
+        pp.pp_destroy(hl)
+        pp.pp_destroy(hc)

@@ -34,12 +34,13 @@ def host(t):
     return t.cpu().numpy()
 
 
-def set_prec(pp, h, prec, side=0, orth=0, check_every=0):
+def set_prec(pp, h, prec, side=0, orth=0, check_every=0, clenshaw=0):
     o = pp.pp_default_opts()
     o.precision = PRECS[prec]
     o.side = side
     o.orth = orth
     o.check_every = check_every
+    o.clenshaw = clenshaw
     pp.pp_set_opts(h, o)
 
 
@@ -110,35 +111,44 @@ def test_op_apply(case, prec):
         P.close()
 
 
+@pytest.mark.parametrize("scheme", ["horner", "clenshaw"])
 @pytest.mark.parametrize("prec", ["f64", "dw"])
-@pytest.mark.parametrize("degree", [0, 1, 2, 3, 8, 17])
+@pytest.mark.parametrize("degree", [0, 1, 2, 3, 8, 17, 64])
 @pytest.mark.parametrize("case", CASES[:3] + CASES[4:] + CASES_EVEN,
                          ids=lambda c: f"{c[0]}{c[1]}{'csr' if c[3] else ''}")
-def test_poly_apply(case, degree, prec):
+def test_poly_apply(case, degree, prec, scheme):
+    # the Chebyshev interpolant by either evaluation scheme against the
+    # oracle's three-term recurrence
     pp = load()
     P = Problem(pp, case[0], case[1], case[2], case[3], degree=degree)
     try:
-        set_prec(pp, P.h, prec)
+        set_prec(pp, P.h, prec, clenshaw=int(scheme == "clenshaw"))
         x = synth.rhs(P.n, 12)
         xd, yd = dev(x), torch.empty(P.n, dtype=torch.float64, device="cuda")
         pp.pp_poly_apply(P.h, xd, yd)
         ref = cheb.q_apply(P.A.dot, P.coef, P.ab[0], P.ab[1], x)
-        assert rel(host(yd), ref) < POLY_TOL[prec]
+        # the non-normal convection-diffusion operator amplifies rounding in
+        # any degree-64 evaluation, the oracle's three-term recurrence
+        # included (both schemes land 2e-11 .. 5e-11 from it); Laplacians keep
+        # the tight bound
+        tol = POLY_TOL[prec] * (100.0 if case[0] == "convdiff" and degree > 17 else 1.0)
+        assert rel(host(yd), ref) < tol
     finally:
         P.close()
 
 
+@pytest.mark.parametrize("scheme", ["horner", "clenshaw"])
 @pytest.mark.parametrize("prec", ["f64", "dw"])
 @pytest.mark.parametrize("f", [-1, 1], ids=["invsqrt", "sqrt"])
 @pytest.mark.parametrize("side", [0, 1], ids=["left", "right"])
 @pytest.mark.parametrize("degree", [0, 4, 9])
 @pytest.mark.parametrize("case", [CASES[0], CASES[1], CASES[2], CASES[3], CASES_EVEN[1]],
                          ids=lambda c: f"{c[0]}{c[1]}{'csr' if c[3] else ''}")
-def test_solve_parity(case, degree, side, f, prec):
+def test_solve_parity(case, degree, side, f, prec, scheme):
     pp = load()
     P = Problem(pp, case[0], case[1], case[2], case[3], degree=degree)
     try:
-        set_prec(pp, P.h, prec, side=side)
+        set_prec(pp, P.h, prec, side=side, clenshaw=int(scheme == "clenshaw"))
         b = synth.rhs(P.n, 0)
         bd, xd = dev(b), torch.empty(P.n, dtype=torch.float64, device="cuda")
         st = pp.pp_apply(P.h, f, bd, xd, m_max=600, tol=1e-12)

@@ -55,10 +55,11 @@ class Lattice:
             self.A = wilson.dhd_matrix(self.dims, self.links, M0)
         return self.A
 
-    def set(self, prec, side=0):
+    def set(self, prec, side=0, clenshaw=0):
         o = self.pp.pp_default_opts()
         o.precision = PREC[prec]
         o.side = side
+        o.clenshaw = clenshaw
         self.pp.pp_set_opts(self.h, o)
 
     def close(self):
@@ -88,16 +89,17 @@ def test_wilson_op_apply(dims, prec):
         L.close()
 
 
+@pytest.mark.parametrize("scheme", ["horner", "clenshaw"])
 @pytest.mark.parametrize("prec", ["f64", "dw", "mixed"])
 @pytest.mark.parametrize("degree", [1, 2, 8])
-def test_wilson_poly_apply(degree, prec):
+def test_wilson_poly_apply(degree, prec, scheme):
     pp = load()
     dims = (4, 4, 2, 6)
     links = synth.wilson_links(dims, 1)
     A = wilson.dhd_matrix(dims, links, M0)
     L = Lattice(pp, dims, links, degree=degree, interval=(0.05, 60.0))
     try:
-        L.set(prec)
+        L.set(prec, clenshaw=int(scheme == "clenshaw"))
         x = synth.spinor_field(dims, 12)
         yd = torch.empty(L.n, dtype=torch.complex128, device="cuda")
         pp.pp_poly_apply(L.h, dev(x), yd)
