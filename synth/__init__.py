@@ -139,3 +139,65 @@ def batch_problems(count=64, seed=2, n_lo=1e3, n_hi=1e6, max_rhs=16):
         out.append({"kind": kind, "dims": dims, "nrhs": int(rng.integers(1, max_rhs + 1)),
                     "f": int(1 if rng.integers(2) else -1)})
     return out
+
+
+# ---- directed graphs (in-degree graph Laplacian inputs) -------------------
+
+def directed_powerlaw_graph(n, m, seed=3, gamma_in=2.1, gamma_out=2.7):
+    """Edges (src, dst) of a directed graph with power-law degrees, no self
+    loops, no repeated edges, exactly m >= n edges (Chung-Lu style).
+
+    Node i has expected in-degree weight (r_in(i) + 1)^(-1/(gamma_in - 1)) and
+    out-degree weight (r_out(i) + 1)^(-1/(gamma_out - 1)), r_in and r_out two
+    independent random rankings.  Every node first receives one in-edge (as
+    every page of a crawl was reached by a link), its source drawn from the
+    out weights; the other edges draw their source from the out weights and
+    their target from the in weights.  The exponents are the in-/out-degree
+    exponents commonly reported for web graphs.
+    """
+    rng = np.random.default_rng(seed)
+    w_in = (rng.permutation(n) + 1.0) ** (-1.0 / (gamma_in - 1.0))
+    w_out = (rng.permutation(n) + 1.0) ** (-1.0 / (gamma_out - 1.0))
+    w_in /= w_in.sum()
+    w_out /= w_out.sum()
+    dst0 = np.arange(n, dtype=np.int64)
+    src0 = rng.choice(n, size=n, p=w_out)
+    while np.any(src0 == dst0):  # no self loops
+        bad = src0 == dst0
+        src0[bad] = rng.choice(n, size=int(bad.sum()), p=w_out)
+    first = src0 * n + dst0
+    keys = np.zeros(0, dtype=np.int64)
+    m_rest = m - n
+    while keys.shape[0] < m_rest:
+        k = int(1.2 * (m_rest - keys.shape[0])) + 1024
+        src = rng.choice(n, size=k, p=w_out)
+        dst = rng.choice(n, size=k, p=w_in)
+        ok = src != dst
+        new = src[ok].astype(np.int64) * n + dst[ok]
+        keys = np.setdiff1d(np.unique(np.concatenate([keys, new])), first, assume_unique=True)
+    keys = np.concatenate([first, keys[rng.permutation(keys.shape[0])[:m_rest]]])
+    return (keys // n).astype(np.int64), (keys % n).astype(np.int64)
+
+
+def graph_laplacian_csr(n, src, dst):
+    """CSR (rowptr int64, col int32, val float64) of the in-degree Laplacian
+    L = D_in - A, A[i, j] = 1 for an edge i -> j, D_in = diag(in-degrees) (the
+    column sums of A), so every column of L sums to zero.  Columns ascending
+    within a row; the diagonal is stored only where it is nonzero."""
+    indeg = np.bincount(dst, minlength=n).astype(np.float64)
+    diag = np.nonzero(indeg)[0]
+    rows = np.concatenate([src, diag])
+    cols = np.concatenate([dst, diag])
+    vals = np.concatenate([-np.ones(src.shape[0]), indeg[diag]])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(rowptr, rows + 1, 1)
+    return np.cumsum(rowptr), cols.astype(np.int32), vals
+
+
+def unit_vector(n, seed=4):
+    """A canonical unit vector e_i with i drawn from the seed (Sec. 6, Example 3 takes b = e_i)."""
+    b = np.zeros(n)
+    b[np.random.default_rng(seed).integers(n)] = 1.0
+    return b
