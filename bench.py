@@ -45,6 +45,11 @@ WORKLOADS = {
                 "n log-uniform in [1e3, 1e6], 1-16 right-hand sides each, mixed sqrt / inverse sqrt (problem "
                 "list seed 2); degree and stencil tile chosen by the autotuner; a solve = one right-hand side",
                 "batch", (), 0, 0, 1e-9, "mixed"),
+    "graph282k": ("L^(1/2) b, L = D_in - A the in-degree Laplacian of a synthetic directed power-law graph "
+                  "(n=281903, 2312497 edges, in/out-degree exponents 2.1/2.7, graph seed 3; the size of "
+                  "Example 3's web graph), non-Hermitian CSR, b = e_i (seed 4), Ritz polynomial of degree 15 "
+                  "(d = 16), Arnoldi CGS2, stopping check every 32/d = 2 iterations; 1e-7 target, estimate "
+                  "tolerance 1e-8", "graphcsr", (281903,), 1, 15, 1e-8, "cgs2"),
     "wilson16x32": ("A = D^H D, Wilson-type D on a periodic 16^3x32 lattice (n=1572864 complex), Haar "
                     "SU(3) links seed 1, m0=0.1, f=A^(-1/2), Lanczos; 1e-8 target, estimate tolerance 1e-9",
                     "wilson4d", (16, 16, 16, 32), -1, 16, 1e-9, "lanczos"),
@@ -67,6 +72,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--plain-m-max", type=int, default=1000)
+    p.add_argument("--poly", default=None, choices=["ritz", "harmonic", "lsq"],
+                   help="graph workload: the kind of q (default ritz)")
     p.add_argument("--probe", action="store_true",
                    help="per-launch timing of the operator kernels on the workload (no bench line)")
     p.add_argument("--clenshaw", action="store_true",
@@ -91,6 +98,18 @@ def parse():
     return a
 
 
+_GRAPH = {}
+
+
+def graph_csr(n):
+    """CSR arrays of the synthetic web-graph Laplacian (built once per process)."""
+    if n not in _GRAPH:
+        import synth
+        src, dst = synth.directed_powerlaw_graph(n, 2312497 if n == 281903 else 8 * n, seed=3)
+        _GRAPH[n] = synth.graph_laplacian_csr(n, src, dst)
+    return _GRAPH[n]
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -101,8 +120,11 @@ def config(args, ws):
             + (", two-pass Lanczos" if args.two_pass else ""),
             "grid": list(args.dims), "n": args.n,
             "ch": 0.5 if args.kind == "convdiff3d7" else 0.0,
-            "func": "sqrt" if args.func > 0 else "invsqrt", "poly": "chebyshev", "degree": args.degree,
-            "q_eval": "clenshaw" if args.clenshaw else "newton-horner at Leja-ordered Chebyshev nodes",
+            "func": "sqrt" if args.func > 0 else "invsqrt",
+            "poly": ({"ritz": "ritz (leja/newton)", "harmonic": "harmonic ritz (leja/newton)",
+                      "lsq": "least squares on the Ritz-value contour"}[args.poly or "ritz"]
+                     if args.kind == "graphcsr" else "chebyshev"), "degree": args.degree,
+            "q_eval": "clenshaw" if args.clenshaw else "newton-horner at Leja-ordered nodes",
             "side": "left", "orth": args.orth, "tol": args.tol, "rhs_per_rank": 1,
             "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MB write)"}
 
@@ -126,16 +148,39 @@ def oracle_timed(args, m_max, tol, seed=0):
         mv = lambda v: DH @ (D @ v)  # noqa: E731
         a, b = 0.01, 96.0  # interval only shapes q; the per-iteration cost does not depend on it
         rhs = synth.spinor_field(args.dims, seed)
+    elif args.kind == "graphcsr":
+        import scipy.sparse as sp
+        from oracle import ritz
+        rp, col, val = graph_csr(args.dims[0])
+        A = sp.csr_matrix((val, col, rp), shape=(args.dims[0], args.dims[0]))
+        mv, rhs = A.dot, synth.unit_vector(A.shape[0], 4 + seed)
     else:
         A = ops.laplace(args.dims)
         a, b = ops.laplace_interval(args.dims)
         mv, rhs = A.dot, synth.rhs(A.shape[0], seed)
-    c = cheb.interp_coeffs(a, b, args.degree + 1)
     stamps = []
     t0 = time.perf_counter()
-    r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, c, (a, b), side="left", m_max=m_max, tol=tol,
-                          k_chk=max(1, 64 // (args.degree + 1)), hermitian=args.orth == "lanczos",
-                          orth=args.orth, on_iter=lambda j: stamps.append(time.perf_counter()))
+    if args.kind == "graphcsr":  # Example 3: q from the oracle's own Ritz values (part of the set-up)
+        if args.poly == "lsq":
+            from oracle import lsq
+            H60, _ = ritz.arnoldi(mv, ritz.start_vector(A.shape[0]), max(60, args.degree + 1))
+            th = ritz.ritz_values(H60, hermitian=False)
+            th = th[np.abs(th) > 1e-4 * np.abs(th).max()]  # the null space of the singular L left out
+            z = lsq.contour(th, 0.5 * np.abs(th).min(), max(2000, 20 * (args.degree + 1)))
+            P, Hq = lsq.basis(z, args.degree + 1)
+            al = lsq.coeffs(P, z ** -0.5)
+            qf = (args.degree, lambda v: lsq.apply(mv, Hq, al, len(z), v))
+        else:
+            x, an = ritz.ritz_poly(mv, A.shape[0], args.degree, harmonic=args.poly == "harmonic", hermitian=False)
+            qf = (args.degree, lambda v: ritz.newton_apply(mv, an, x, v))
+        r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, q=qf, side="left", m_max=m_max, tol=tol,
+                              k_chk=max(1, 32 // (args.degree + 1)), orth=args.orth,
+                              on_iter=lambda j: stamps.append(time.perf_counter()))
+    else:
+        c = cheb.interp_coeffs(a, b, args.degree + 1)
+        r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, c, (a, b), side="left", m_max=m_max, tol=tol,
+                              k_chk=max(1, 64 // (args.degree + 1)), hermitian=args.orth == "lanczos",
+                              orth=args.orth, on_iter=lambda j: stamps.append(time.perf_counter()))
     t_end = time.perf_counter()
     setup = stamps[0] - t0
     iters = [b_ - a_ for a_, b_ in zip(stamps[:-1], stamps[1:])]
@@ -310,6 +355,12 @@ def run_ours(args):
             hh = pp.pp_create_stencil(pp.PP_WILSON4D_DHD, dims, [WILSON_M0], links=keep[-1],
                                       dtype=pp.PP_C128, stream=stream)
             pp.pp_build_poly(hh, degree)
+        elif args.kind == "graphcsr":  # Example 3: non-Hermitian CSR, q at Ritz values
+            rp, col, val = graph_csr(n)
+            keep.extend(torch.from_numpy(a).cuda() for a in (rp, col, val))
+            hh = pp.pp_create_csr(n, *keep[-3:], is_hermitian=False, stream=stream)
+            pp.pp_build_poly(hh, degree, {"ritz": pp.PP_RITZ_LEJA, "harmonic": pp.PP_HARMONIC_RITZ,
+                                          "lsq": pp.PP_LSQ_CONTOUR}[args.poly or "ritz"])
         else:  # 2D Laplacian in CSR: interval from the closed form of its eigenvalues
             rp, col, val = synth.stencil_csr("laplace2d5", dims)
             keep.extend(torch.from_numpy(a).cuda() for a in (rp, col, val))
@@ -326,6 +377,8 @@ def run_ours(args):
     if args.two_pass:  # O(n) basis memory: two-pass Lanczos
         o.two_pass = 1
     o.clenshaw = 1 if args.clenshaw else 0
+    if args.kind == "graphcsr":  # Example 3 checks every 32/d iterations
+        o.check_every = max(1, 32 // (args.degree + 1))
     pp.pp_set_opts(h, o)
     if args.autotune:
         args.degree = pp.pp_autotune(h, args.tol, 64)
@@ -333,6 +386,8 @@ def run_ours(args):
     esz = 16 if args.complex else 8
 
     def rhs_host():
+        if args.kind == "graphcsr":
+            return synth.unit_vector(n, 4 + rank)
         return synth.spinor_field(dims, rank) if args.complex else synth.rhs(n, rank)
 
     b = torch.from_numpy(rhs_host()).cuda()
@@ -409,7 +464,8 @@ def run_ours(args):
         peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    traffic = traffic_from_profile(os.path.join(ROOT, "paper_2401_06684_gb300", "csrc", "ops.cu"))
+    traffic = (traffic_from_profile(os.path.join(ROOT, "paper_2401_06684_gb300", "csrc", "ops.cu"))
+               if args.workload == "convdiff128" and not args.clenshaw else None)
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
     bh = torch.from_numpy(rhs_host()).pin_memory()
@@ -447,15 +503,22 @@ def run_ours(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+            "ms_per_step_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"dw": "f32x2-dw", "f64": "f64", "mixed": "f32x2-dw+f32"}[args.prec],
-            "precision": {"dw": "double-word FP32 pairs (FP64-grade)", "f64": "IEEE FP64",
-                          "mixed": "double-word start, FP32 after switch_iter"}[args.prec],
+            "dtype": ("f32x2-dw" if args.prec == "mixed" and stats[-1]["switch_iter"] < 0 else
+                      {"dw": "f32x2-dw", "f64": "f64", "mixed": "f32x2-dw+f32"}[args.prec]),
+            "precision": ("double-word FP32 pairs throughout (no FP32 switch: the image of q was taken at "
+                          "Ritz values only)" if args.prec == "mixed" and stats[-1]["switch_iter"] < 0 else
+                          {"dw": "double-word FP32 pairs (FP64-grade)", "f64": "IEEE FP64",
+                           "mixed": "double-word start, FP32 after switch_iter"}[args.prec]),
             "data": "synthetic (b ~ N(0,1), seed = rank)", "config": config(args, ws),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                         "kernel": "st_step (operator + %s update)" % ("Clenshaw" if args.clenshaw else "Horner"),
+                         "kernel": "%s (operator + %s update)" % (
+                             {"graphcsr": "csr_step", "laplace2d5csr": "csr_step", "wilson4d": "wilson_step"}.get(
+                                 args.kind, "st_step"), "Clenshaw" if args.clenshaw else "Horner"),
                          "peak_source": peak_src,
                          "timing": "CUDA events around each run of consecutive operator launches "
                                    "(one q(A) or one A product) during the timed steps",

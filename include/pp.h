@@ -64,7 +64,7 @@ typedef enum {
   PP_RITZ_LEJA = 1,      /* Sec. 5.2: interpolant at the deg+1 Ritz values of A
                             (Newton form, Leja order)                             */
   PP_HARMONIC_RITZ = 2,  /* Sec. 5.2: same at the deg+1 harmonic Ritz values      */
-  PP_LSQ_CONTOUR = 3,    /* Sec. 5.3 (not in this build)                              */
+  PP_LSQ_CONTOUR = 3,    /* Sec. 5.3: least-squares approximation on a contour     */
   PP_NODES = 4           /* interpolant at caller-given nodes (pp_set_poly_nodes)     */
 } pp_poly_kind;
 
@@ -221,8 +221,14 @@ int pp_set_opts(pp_handle h, const pp_opts *opts);
  * as by pp_set_poly_nodes from these nodes.  If the Krylov space of the
  * start vector is invariant earlier (small n), fewer nodes are used and
  * deg q drops accordingly (pp_get_poly reports it).  [a,b] (given, or the
- * closed form, or the extreme real parts of the Ritz values lowered by 5 % /
- * raised by 1 %) only serves the positivity check and the image interval.
+ * closed form, or for Hermitian handles the extreme Ritz values lowered by
+ * 5 % / raised by 1 %) only serves the positivity check and the image
+ * interval.  A non-Hermitian handle without either is checked at its Ritz
+ * values and the nodes only (the indication of Sec. 5.2: between them an
+ * interpolant may turn negative where A has no eigenvalues); the quadrature
+ * of the small solve then spans the image at those points widened by 1e6
+ * both ways, and PP_PREC_MIXED stays in double-word (the image does not
+ * bound the FP32 amplification).
  * The node run costs degree + 1 operator applications and allocates a basis
  * of degree + 2 vectors in the workspace.
  */
@@ -267,7 +273,10 @@ int pp_get_poly(pp_handle h, double *coeffs_h, int32_t cap, int32_t *ncoeffs, do
  * (Hermitian handles: real only).  The nodes are put in Leja order (largest
  * modulus first, then each time the node farthest from the taken ones in
  * product distance; a pair is taken as its Im > 0 member followed by its
- * conjugate) and q is written in the real basis R_0 = 1, R_{i+1} = (z - x_i)
+ * conjugate), and the Newton form takes them in the reverse of that order
+ * (pairs kept), so that the Horner scheme, which applies the factor of the
+ * last node first, applies the factors in Leja order; q is written in the
+ * real basis R_0 = 1, R_{i+1} = (z - x_i)
  * R_i for a real node, R_{i+1} = (z - Re x_i) R_i, R_{i+2} = |z - x_i|^2 R_i
  * for a pair, which for real nodes is the Newton form q = sum_i a_i
  * prod_{l<i} (z - x_l), a_i the divided differences.  q(A) v is evaluated by
@@ -287,9 +296,37 @@ int pp_set_poly_nodes(pp_handle h, const double *nodes_re_h, const double *nodes
                       const double *interval_ab_h);
 
 /*
+ * q = the least-squares approximation of z^{-1/2} of degree `degree` on the
+ * discretized contour z_1..z_N (Sec. 5.3): q minimizes sum_i |z_i^{-1/2} -
+ * q(z_i)|^2, computed through the orthonormal basis that the Arnoldi process
+ * on diag(z_1..z_N) from the vector of ones / sqrt(N) yields (alpha = P^*
+ * z^{-1/2}).  pts_re_h / pts_im_h (host; pts_im_h may be NULL): N >= degree +
+ * 1 points, none on (-inf, 0]; the set must be symmetric about the real axis
+ * (then q is real; PP_ERR_UNSUPPORTED otherwise), real for Hermitian
+ * handles.  Re q must be positive at every point (Sec. 5.3 takes this as the
+ * indication that q is in the right half-plane inside the contour;
+ * PP_ERR_NONPRIMARY otherwise).  The device evaluates q in the Newton form of
+ * pp_set_poly_nodes at degree + 1 Leja points chosen among the contour points
+ * (q interpolates its own values there, so it is the same polynomial; the
+ * call checks that the form reproduces q on all points to 1e-8 of max |q|).
+ * pp_build_poly(h, degree, PP_LSQ_CONTOUR, interval) builds the contour
+ * itself: the segment [a, b] when a real spectral interval is known (given,
+ * closed form, or the Hermitian estimate), else around the Ritz values of
+ * max(60, degree + 1) Arnoldi steps (as Example 3; Ritz values within 1e-4
+ * of the largest modulus of zero, the null space of a singular A, are left
+ * out): their convex hull made
+ * symmetric about the real axis, the part inside |z| < r_min (half the
+ * smallest Ritz modulus) replaced by the arc of that circle, max(2000,
+ * 20 (degree + 1)) points at equal arc length.  Host only (pp_set_poly_lsq).
+ * Errors: PP_ERR_INVALID_ARG for bad points or degree.
+ */
+int pp_set_poly_lsq(pp_handle h, int32_t degree, const double *pts_re_h, const double *pts_im_h, int32_t npts);
+
+/*
  * The interpolation nodes of q (host output): *kind = its pp_poly_kind,
- * nodes_re_h / nodes_im_h [0..*nnodes-1] = the nodes in the Leja order of
- * the Newton form the device evaluates (for PP_CHEBYSHEV its deg q + 1
+ * nodes_re_h / nodes_im_h [0..*nnodes-1] = the nodes in the order of the
+ * Newton form the device evaluates (reverse Leja order, see
+ * pp_set_poly_nodes; for PP_CHEBYSHEV its deg q + 1
  * first-kind nodes of [a,b]), *scale = cap of pp_set_poly_nodes.  Any output
  * pointer may be NULL; cap = capacity of the node arrays.
  * Errors: PP_ERR_STATE before pp_build_poly.

@@ -47,6 +47,8 @@ int pp_cuda_fail(cudaError_t e, const char *what) {
 namespace {
 
 constexpr int kMaxDegree = 128;
+// CSR rows with more entries than this get a block of their own
+constexpr int64_t kLongRow = 64;
 constexpr int kMaxM = 4096;
 constexpr double kBreakdownRel = 1e-12;
 constexpr int kIntervalSteps = 200;
@@ -62,6 +64,7 @@ void ws_free(Workspace &w) {
   if (w.io) cudaFree(w.io);
   if (w.val_dw) cudaFree(w.val_dw);
   if (w.val_f) cudaFree(w.val_f);
+  if (w.long_rows) cudaFree(w.long_rows);
   if (w.Vf) cudaFree(w.Vf);
   if (w.Yf) cudaFree(w.Yf);
   if (w.ev0) cudaEventDestroy(w.ev0);
@@ -221,6 +224,19 @@ int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y, int layout = LAYOUT_K
     PP_CUDA_TRY(cudaMemcpyAsync(w.dmem + L.wt, c->qwt.data(), L.K * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     c->quad_uploaded = true;
   }
+  if (c->op_kind == OPK_CSR && w.nlong < 0) {
+    // rows longer than kLongRow entries, listed once per handle (rowptr read back)
+    std::vector<int64_t> rp((size_t)c->n + 1);
+    PP_CUDA_TRY(cudaMemcpy(rp.data(), c->rowptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> lr;
+    for (int64_t i = 0; i < c->n; ++i)
+      if (rp[i + 1] - rp[i] > kLongRow) lr.push_back((int32_t)i);
+    if (!lr.empty()) {
+      PP_CUDA_TRY(cudaMalloc(&w.long_rows, sizeof(int32_t) * lr.size()));
+      PP_CUDA_TRY(cudaMemcpy(w.long_rows, lr.data(), sizeof(int32_t) * lr.size(), cudaMemcpyHostToDevice));
+    }
+    w.nlong = (int)lr.size();
+  }
   if ((prec == PP_PREC_DW || prec == PP_PREC_MIXED) && c->op_kind == OPK_CSR && !w.val_dw) {
     PP_CUDA_TRY(cudaMalloc(&w.val_dw, (size_t)c->nnz * sizeof(dw)));
     int rc = vec_from_f64<dw>(c->val, (dw *)w.val_dw, c->nnz, c->stream);
@@ -254,6 +270,9 @@ OpDesc make_op(const pp_ctx *c, int arith) {
   op.cp = c->st_cp;
   op.rowptr = c->rowptr;
   op.col = c->col;
+  op.long_rows = c->ws.long_rows;
+  op.nlong = c->ws.nlong > 0 ? c->ws.nlong : 0;
+  op.long_len = c->ws.nlong > 0 ? kLongRow : 0;
   op.val = arith == AR_DW ? c->ws.val_dw : (arith == AR_F32 ? c->ws.val_f : (const void *)c->val);
   for (int d = 0; d < 4; ++d) op.L[d] = c->dims[d];
   op.mass = c->mass;
@@ -491,7 +510,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   // Precision switch (PP_PREC_MIXED): columns [0, nv1) of V1 (and [0, ny1)
   // of Y1) hold the phase-1 basis; V2 / Y2 hold FP32 copies of them and the
   // FP32 columns after them.
-  const double kappa_pre = c->img_lo > 0.0 ? c->img_hi / c->img_lo : INFINITY;
+  const double kappa_pre = c->img_lo > 0.0 && !c->image_on_points ? c->img_hi / c->img_lo : INFINITY;
   const double amp = kMixedSafety * kU32 * kappa_pre;
   double est_prev = INFINITY;
   int phase = 1, nv1 = 0, ny1 = 0;
@@ -718,7 +737,7 @@ int solve_two_pass(pp_ctx *c, int f, const double *b_dev, int m_max, double tol,
     }
     return vec_scale<T>(wv, wv, n, 1.0, scal, s);
   };
-  const double kappa_pre = c->img_lo > 0.0 ? c->img_hi / c->img_lo : INFINITY;
+  const double kappa_pre = c->img_lo > 0.0 && !c->image_on_points ? c->img_hi / c->img_lo : INFINITY;
   const double amp = kMixedSafety * kU32 * kappa_pre;
   double est_prev = INFINITY;
   int phase = 1, sw = mixed ? -1 : 0;
@@ -1090,11 +1109,14 @@ bool closed_form_interval(const pp_ctx *c, double *a, double *b) {
 
 // Polynomial-independent tail of pp_build_poly: the quadrature of the small
 // solve sized by the image [lo, hi] of z q(z)^2, and a fresh device layout.
-void finish_poly(pp_ctx *c) {
-  // real Ritz values for Hermitian A, |arg| <= pi/3 allowed otherwise;
-  // generous margins around the image
-  const double theta = c->hermitian ? 0.0 : M_PI / 3.0;
-  invsqrt_quadrature(c->img_lo * 1e-3, c->img_hi * 1e3, 1e-15, theta, &c->qsig, &c->qwt);
+void finish_poly(pp_ctx *c, double margin = 1e3) {
+  // real Ritz values for Hermitian A, |arg| <= pi/3 allowed otherwise (more
+  // when q has complex nodes far from the real axis); margins around the image
+  double theta = c->hermitian ? 0.0 : M_PI / 3.0;
+  if (!c->hermitian)
+    for (size_t i = 0; i < c->nf.re.size(); ++i)
+      theta = std::fmax(theta, std::fmin(0.45 * M_PI, 1.5 * std::fabs(std::atan2(c->nf.im[i], c->nf.re[i]))));
+  invsqrt_quadrature(c->img_lo / margin, c->img_hi * margin, 1e-15, theta, &c->qsig, &c->qwt);
   c->quad_uploaded = false;
   if (c->ws.dmem) {  // K may have changed: re-layout on next use
     cudaFree(c->ws.dmem);
@@ -1116,7 +1138,8 @@ int read_nnz(pp_ctx *c) {
 // pairs with Re > 0), in Newton form at their Leja order (Sec. 5.2); [lo, hi]
 // serves the positivity check and the image interval, which also covers the
 // nodes.  Host only.
-int set_poly_nodes(pp_ctx *c, int kind, const std::vector<std::complex<double>> &nodes, double lo, double hi) {
+int set_poly_nodes(pp_ctx *c, int kind, const std::vector<std::complex<double>> &nodes, double lo, double hi,
+                   const std::vector<std::complex<double>> *check_pts = nullptr) {
   const int d = (int)nodes.size();
   if (d < 1 || d > kMaxDegree + 1) return pp_set_error(PP_ERR_INVALID_ARG, "need 1 .. 129 nodes");
   std::vector<char> used(d, 0);
@@ -1138,11 +1161,12 @@ int set_poly_nodes(pp_ctx *c, int kind, const std::vector<std::complex<double>> 
   }
   for (int i = 0; i < d; ++i)
     if (nodes[i].imag() < 0.0 && !used[i]) return pp_set_error(PP_ERR_INVALID_ARG, "complex node without its conjugate");
-  if (!(lo > 0.0) || !(hi > lo) || !std::isfinite(hi)) return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
+  if (!check_pts && (!(lo > 0.0) || !(hi > lo) || !std::isfinite(hi)))
+    return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
   NewtonForm F;
   if (!newton_form(nodes, &F)) return pp_set_error(PP_ERR_NONPRIMARY, "non-finite Newton coefficient");
   double qmin, img_lo, img_hi;
-  newton_scan(F, lo, hi, &qmin, &img_lo, &img_hi);
+  newton_scan(F, check_pts ? 0.0 : lo, check_pts ? 0.0 : hi, check_pts, &qmin, &img_lo, &img_hi);
   if (!(qmin > 0.0)) return pp_set_error(PP_ERR_NONPRIMARY, "Re q is not positive on [a,b] or at a node");
   c->poly_kind = kind;
   c->nf = F;
@@ -1157,7 +1181,8 @@ int set_poly_nodes(pp_ctx *c, int kind, const std::vector<std::complex<double>> 
   c->b = hi;
   c->img_lo = img_lo;
   c->img_hi = img_hi;
-  finish_poly(c);
+  c->image_on_points = check_pts != nullptr;
+  finish_poly(c, check_pts ? 1e6 : 1e3);
   return PP_OK;
 }
 
@@ -1230,8 +1255,163 @@ int build_ritz(pp_ctx *c, int degree, int kind, const double *ab) {
     }
   }
   double lo, hi;
+  if (!c->hermitian && !ab && !closed_form_interval(c, &lo, &hi)) {
+    // no spectral interval of a non-normal operator: q is checked at the
+    // Ritz values and the nodes, the indication of Sec. 5.2 (between them an
+    // interpolant may dip anywhere where A has no eigenvalues), and the
+    // quadrature gets a margin of 1e6 around the image of those points
+    lo = INFINITY;
+    hi = -INFINITY;
+    for (const auto &z : ritz) {
+      lo = std::fmin(lo, z.real());
+      hi = std::fmax(hi, z.real());
+    }
+    return set_poly_nodes(c, kind, nodes, lo, hi, &ritz);
+  }
   node_interval(c, ab, ritz, &lo, &hi);
   return set_poly_nodes(c, kind, nodes, lo, hi);
+}
+
+// The spectral interval [a, b] of the Chebyshev and least-squares kinds: the
+// given one, the closed form of the stencils, or for other Hermitian handles
+// the extreme Ritz values of kIntervalSteps Lanczos steps (a lowered by 5 %,
+// b raised by 1 %).  *have = false for a non-Hermitian CSR handle without one.
+int spectral_interval(pp_ctx *c, const double *ab, double *a, double *b, bool *have) {
+  *have = true;
+  if (ab) {
+    *a = ab[0];
+    *b = ab[1];
+    return PP_OK;
+  }
+  if (closed_form_interval(c, a, b)) return PP_OK;
+  if (c->hermitian) {
+    RC(read_nnz(c));
+    const int steps = (int)std::min<int64_t>(kIntervalSteps, c->n);
+    double lo = 0.0, hi = 0.0;
+    const int rc = c->opts.precision == PP_PREC_F64 ? lanczos_extremes<double>(c, steps, &lo, &hi)
+                                                    : lanczos_extremes<dw>(c, steps, &lo, &hi);
+    if (rc != PP_OK) return rc;
+    *a = 0.95 * lo;
+    *b = 1.01 * hi;
+    return PP_OK;
+  }
+  *have = false;
+  return PP_OK;
+}
+
+// q = the least-squares approximation of z^{-1/2} of degree `degree` on the
+// contour points (Sec. 5.3): orthonormal basis by Arnoldi on diag(z),
+// alpha = P^* z^{-1/2}; Re q > 0 required at every point; the device then
+// evaluates q in Newton form at degree + 1 Leja points of the contour (the
+// same polynomial: it interpolates its own values there), checked to
+// reproduce q on all points.
+int set_poly_lsq(pp_ctx *c, int degree, const std::vector<std::complex<double>> &pts) {
+  using cplx = std::complex<double>;
+  const int d = degree + 1;
+  const size_t N = pts.size();
+  if (degree < 0 || degree > kMaxDegree) return pp_set_error(PP_ERR_INVALID_ARG, "degree out of [0, 128]");
+  if (N < (size_t)d) return pp_set_error(PP_ERR_INVALID_ARG, "need at least degree + 1 contour points");
+  std::vector<std::pair<double, double>> up, lo;
+  double rmin = INFINITY, rmax = -INFINITY;
+  for (const cplx &z : pts) {
+    if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return pp_set_error(PP_ERR_INVALID_ARG, "non-finite point");
+    if (z.imag() == 0.0 && !(z.real() > 0.0))
+      return pp_set_error(PP_ERR_INVALID_ARG, "a contour point on (-inf, 0] (z^{-1/2} has its branch cut there)");
+    if (z.imag() != 0.0 && c->hermitian) return pp_set_error(PP_ERR_INVALID_ARG, "complex contour point for a Hermitian operator");
+    if (z.imag() > 0.0) up.emplace_back(z.real(), z.imag());
+    if (z.imag() < 0.0) lo.emplace_back(z.real(), -z.imag());
+    rmin = std::fmin(rmin, z.real());
+    rmax = std::fmax(rmax, z.real());
+  }
+  std::sort(up.begin(), up.end());
+  std::sort(lo.begin(), lo.end());
+  if (up != lo)
+    return pp_set_error(PP_ERR_UNSUPPORTED,
+                        "contour not symmetric about the real axis: q would be complex (no complex vectors for real A)");
+  std::vector<cplx> H, alpha;
+  if (!lsq_poly(pts, d, &H, &alpha)) return pp_set_error(PP_ERR_INVALID_ARG, "fewer distinct contour points than degree + 1");
+  double qmin = INFINITY, img_lo = INFINITY, img_hi = -INFINITY, qmax = 0.0;
+  std::vector<cplx> qv(N);
+  for (size_t i = 0; i < N; ++i) {
+    qv[i] = lsq_eval(H, alpha, N, pts[i]);
+    const double p = std::abs(pts[i] * qv[i] * qv[i]);
+    qmin = std::fmin(qmin, qv[i].real());
+    qmax = std::fmax(qmax, std::abs(qv[i]));
+    img_lo = std::fmin(img_lo, p);
+    img_hi = std::fmax(img_hi, p);
+  }
+  if (!(qmin > 0.0)) return pp_set_error(PP_ERR_NONPRIMARY, "Re q is not positive on the contour (Sec. 5.3)");
+  std::vector<cplx> nodes;
+  if (!leja_select(pts, d, &nodes)) return pp_set_error(PP_ERR_INVALID_ARG, "cannot pick interpolation points");
+  NewtonForm F;
+  if (!newton_form_fn(nodes, [&](cplx z) { return lsq_eval(H, alpha, N, z); }, &F))
+    return pp_set_error(PP_ERR_NONPRIMARY, "non-finite Newton coefficient");
+  double dev = 0.0;
+  for (size_t i = 0; i < N; ++i) dev = std::fmax(dev, std::abs(newton_form_eval(F, pts[i]) - qv[i]));
+  if (!(dev <= 1e-8 * qmax)) return pp_set_error(PP_ERR_NONPRIMARY, "Newton form does not reproduce q on the contour");
+  c->poly_kind = PP_LSQ_CONTOUR;
+  c->nf = F;
+  c->coef.resize(d);
+  double p = 1.0;
+  for (int i = 0; i < d; ++i) {
+    c->coef[i] = F.b[i] / p;
+    p *= F.cap;
+  }
+  c->degree = degree;
+  c->a = rmin;
+  c->b = rmax;
+  c->img_lo = img_lo;
+  c->img_hi = img_hi;
+  c->image_on_points = false;
+  finish_poly(c);
+  return PP_OK;
+}
+
+// pp_build_poly for PP_LSQ_CONTOUR: the segment [a, b] of a real spectral
+// interval, else (non-Hermitian CSR) the contour around the Ritz values of
+// max(60, degree + 1) Arnoldi steps (Example 3 uses 60), kept out of
+// |z| < half the smallest Ritz modulus; N = max(2000, 20 (degree + 1)) points.
+int build_lsq(pp_ctx *c, int degree, const double *ab) {
+  double a = 0.0, b = 0.0;
+  bool have = false;
+  RC(spectral_interval(c, ab, &a, &b, &have));
+  const int npts = std::max(2000, 20 * (degree + 1));
+  std::vector<std::complex<double>> pts;
+  if (have) {
+    if (!(a > 0.0) || !(b > a) || !std::isfinite(b)) return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
+    for (int i = 0; i < npts; ++i) pts.emplace_back(a + (b - a) * (double)i / (npts - 1), 0.0);
+  } else {
+    RC(read_nnz(c));
+    const int steps = (int)std::min<int64_t>(std::max(60, degree + 1), c->n);
+    std::vector<double> H;
+    int ldh = 0, m = 0;
+    const int rc = c->opts.precision == PP_PREC_F64 ? ritz_arnoldi<double>(c, steps, &H, &ldh, &m)
+                                                    : ritz_arnoldi<dw>(c, steps, &H, &ldh, &m);
+    if (rc != PP_OK) return rc;
+    std::vector<double> Hd((size_t)m * m, 0.0), wr, wi;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i <= std::min(j + 1, m - 1); ++i) Hd[(size_t)i * m + j] = H[(size_t)j * ldh + i];
+    if (!hess_eigvals(Hd, m, &wr, &wi)) return pp_set_error(PP_ERR_NONPRIMARY, "Hessenberg QR did not converge");
+    // Ritz values within 1e-4 of the largest modulus of zero approximate the
+    // null space of a singular A (60 steps bring a graph Laplacian's zero
+    // eigenvalue only to about -1e-6 of it; its square root is taken through
+    // A^{-1/2}(A b), Sec. 4, whose right-hand side has no component there):
+    // left out
+    double amax = 0.0;
+    for (int k = 0; k < m; ++k) amax = std::fmax(amax, std::abs(std::complex<double>(wr[k], wi[k])));
+    std::vector<std::complex<double>> ritz;
+    double rmin = INFINITY;
+    for (int k = 0; k < m; ++k) {
+      const std::complex<double> z(wr[k], wi[k]);
+      if (std::abs(z) <= 1e-4 * amax) continue;
+      if (!(z.real() > 0.0)) return pp_set_error(PP_ERR_NONPRIMARY, "a Ritz value with Re <= 0");
+      ritz.push_back(z);
+      rmin = std::fmin(rmin, std::abs(z));
+    }
+    if (ritz.empty()) return pp_set_error(PP_ERR_NONPRIMARY, "no nonzero Ritz value");
+    pts = lsq_contour(ritz, 0.5 * rmin, npts);
+  }
+  return set_poly_lsq(c, degree, pts);
 }
 
 pp_ctx *new_ctx(void *stream) {
@@ -1361,34 +1541,19 @@ int pp_set_opts(pp_handle c, const pp_opts *o) {
 
 int pp_build_poly(pp_handle c, int32_t degree, int32_t kind, const double *ab) {
   if (!c) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle");
-  if (kind != PP_CHEBYSHEV && kind != PP_RITZ_LEJA && kind != PP_HARMONIC_RITZ) {
-    if (kind == PP_LSQ_CONTOUR) return pp_set_error(PP_ERR_UNSUPPORTED, "polynomial kind not in this build");
+  if (kind != PP_CHEBYSHEV && kind != PP_RITZ_LEJA && kind != PP_HARMONIC_RITZ && kind != PP_LSQ_CONTOUR) {
     if (kind == PP_NODES) return pp_set_error(PP_ERR_INVALID_ARG, "PP_NODES is set by pp_set_poly_nodes");
     return pp_set_error(PP_ERR_INVALID_ARG, "unknown polynomial kind");
   }
   if (degree < 0 || degree > kMaxDegree) return pp_set_error(PP_ERR_INVALID_ARG, "degree out of [0, 128]");
   if (ab && (!(ab[0] > 0.0) || !(ab[1] > ab[0]) || !std::isfinite(ab[1])))
     return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
+  if (kind == PP_LSQ_CONTOUR) return build_lsq(c, degree, ab);
   if (kind != PP_CHEBYSHEV) return build_ritz(c, degree, kind, ab);
   double a, b;
-  if (ab) {
-    a = ab[0];
-    b = ab[1];
-  } else if (closed_form_interval(c, &a, &b)) {
-  } else if (c->hermitian) {
-    // no closed form: extreme Ritz values of kIntervalSteps Lanczos steps,
-    // a lowered by 5 % and b raised by 1 %
-    RC(read_nnz(c));
-    const int steps = (int)std::min<int64_t>(kIntervalSteps, c->n);
-    double lo = 0.0, hi = 0.0;
-    const int rc = c->opts.precision == PP_PREC_F64 ? lanczos_extremes<double>(c, steps, &lo, &hi)
-                                                    : lanczos_extremes<dw>(c, steps, &lo, &hi);
-    if (rc != PP_OK) return rc;
-    a = 0.95 * lo;
-    b = 1.01 * hi;
-  } else {
-    return pp_set_error(PP_ERR_INVALID_ARG, "non-Hermitian CSR handles need interval_ab");
-  }
+  bool have = false;
+  RC(spectral_interval(c, ab, &a, &b, &have));
+  if (!have) return pp_set_error(PP_ERR_INVALID_ARG, "non-Hermitian CSR handles need interval_ab");
   if (!(a > 0.0) || !(b > a) || !std::isfinite(b)) return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
   std::vector<double> cf = cheb_interp_coeffs(a, b, degree);
   double qmin, lo, hi;
@@ -1403,6 +1568,7 @@ int pp_build_poly(pp_handle c, int32_t degree, int32_t kind, const double *ab) {
   c->poly_kind = PP_CHEBYSHEV;
   c->coef = cf;
   c->degree = degree;
+  c->image_on_points = false;
   c->a = a;
   c->b = b;
   c->img_lo = lo;
@@ -1441,6 +1607,14 @@ int pp_get_poly_nodes(pp_handle c, int32_t *kind, double *nodes_re, double *node
   }
   if (scale) *scale = c->nf.cap;
   return PP_OK;
+}
+
+int pp_set_poly_lsq(pp_handle c, int32_t degree, const double *pts_re, const double *pts_im, int32_t npts) {
+  if (!c) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle");
+  if (!pts_re || npts < 1) return pp_set_error(PP_ERR_INVALID_ARG, "need contour points");
+  std::vector<std::complex<double>> z(npts);
+  for (int i = 0; i < npts; ++i) z[i] = {pts_re[i], pts_im ? pts_im[i] : 0.0};
+  return set_poly_lsq(c, degree, z);
 }
 
 int pp_set_poly_nodes(pp_handle c, const double *nodes_re, const double *nodes_im, int32_t count,

@@ -30,6 +30,8 @@ struct Workspace {
   double *io = nullptr;  // 2 n doubles for pp_apply_host
   void *val_dw = nullptr;
   void *val_f = nullptr;  // FP32 CSR values (PP_PREC_MIXED)
+  int32_t *long_rows = nullptr;  // CSR rows longer than kLongRow entries
+  int nlong = -1;                // -1: not scanned yet
   void *Vf = nullptr;     // FP32 basis of the second phase (PP_PREC_MIXED)
   void *Yf = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -56,6 +58,10 @@ struct pp_ctx {
   std::vector<double> coef;   // as read back: Chebyshev coefficients, or b_i / cap^i (other kinds)
   NewtonForm nf;              // q at its Leja-ordered nodes, the form the device chain evaluates
   double a = 0, b = 0, img_lo = 0, img_hi = 0;
+  // the image was taken at Ritz values only (no spectral interval of a
+  // non-normal operator): it does not bound the FP32 amplification, so
+  // PP_PREC_MIXED stays in double-word
+  bool image_on_points = false;
   std::vector<double> qsig, qwt;
   int tile_bdx = 0;  // stencil block x-size chosen by pp_autotune (0 = default)
   bool quad_uploaded = false;

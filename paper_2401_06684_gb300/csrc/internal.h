@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include <complex>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,11 @@ struct OpDesc {
   const int64_t *rowptr;
   const int32_t *col;
   const void *val;  // CSR values in the vector arithmetic (double, dw or float)
+  // CSR rows longer than long_len entries (device list of nlong row indices)
+  // get a block each; long_len = 0: every row takes the lane path
+  const int32_t *long_rows;
+  int nlong;
+  int64_t long_len;
   // Wilson D^H D: lattice extents, mass shift, complex64 links and one
   // scratch vector (in the vector arithmetic) for the intermediate D x
   int64_t L[4];
@@ -228,9 +234,24 @@ struct NewtonForm {
 };
 // false for an empty node set, a pair without its conjugate or a non-finite coefficient
 bool newton_form(const std::vector<std::complex<double>> &nodes, NewtonForm *F);
+// the same for the interpolant of f at the nodes (f(conj z) = conj f(z) for a real q)
+bool newton_form_fn(const std::vector<std::complex<double>> &nodes,
+                    const std::function<std::complex<double>(std::complex<double>)> &f, NewtonForm *F);
+// least-squares polynomial on contour points (Sec. 5.3): basis recurrence H
+// (d x (d-1), column-major) and coefficients alpha; its value at z
+bool lsq_poly(const std::vector<std::complex<double>> &z, int d, std::vector<std::complex<double>> *H,
+              std::vector<std::complex<double>> *alpha);
+std::complex<double> lsq_eval(const std::vector<std::complex<double>> &H,
+                              const std::vector<std::complex<double>> &alpha, size_t N, std::complex<double> z);
+// d points of a conjugation-symmetric set in Leja order (pairs adjacent)
+bool leja_select(const std::vector<std::complex<double>> &pts, int d, std::vector<std::complex<double>> *out);
+// discretized contour around Ritz values, kept out of |z| < r_min
+std::vector<std::complex<double>> lsq_contour(const std::vector<std::complex<double>> &ritz, double r_min, int npts);
 std::complex<double> newton_form_eval(const NewtonForm &F, std::complex<double> z);
-// min Re q and the extremes of |z q(z)^2| on [lo, hi] and at the nodes
-void newton_scan(const NewtonForm &F, double lo, double hi, double *qmin, double *img_lo, double *img_hi);
+// min Re q and the extremes of |z q(z)^2| on [lo, hi] (if hi > lo > 0), at
+// the nodes and at the extra points
+void newton_scan(const NewtonForm &F, double lo, double hi, const std::vector<std::complex<double>> *extra,
+                 double *qmin, double *img_lo, double *img_hi);
 // eigenvalues of a real upper Hessenberg matrix (row-major); false if not converged
 bool hess_eigvals(std::vector<double> H, int n, std::vector<double> *wr, std::vector<double> *wi);
 // f = M^{-T} e_n for a dense row-major M; false if singular

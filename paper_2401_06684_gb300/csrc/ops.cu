@@ -172,37 +172,68 @@ __global__ void __launch_bounds__(ST_THREADS) bst_step(const T *__restrict__ x, 
                                    g.nx, g.ny, g.nz, i0, j, k, K[lo]);
 }
 
-// CSR: L lanes per row, lane-strided over the row's entries, shuffle sum.
+// CSR.  Rows of up to long_len entries: L lanes per row, lane-strided over
+// the row, shuffle sum.  Longer rows (the nlong rows listed in long_rows,
+// long_len > 0; power-law graphs have a few rows thousands of entries long,
+// whose sequential lane loops would otherwise set the kernel's duration):
+// one block of 256 threads per row, thread-strided, then a fixed-order block
+// sum.  The first nlong blocks take the long rows, the others the short ones.
 template <typename T, int L, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowptr,
                                                 const int32_t *__restrict__ col,
                                                 const T *__restrict__ val, const T *__restrict__ x,
                                                 const T *__restrict__ y, const T *__restrict__ v,
                                                 T *__restrict__ out, int64_t n, T alpha, T beta,
-                                                T gamma, T delta) {
+                                                T gamma, T delta, const int32_t *__restrict__ long_rows,
+                                                int nlong, int64_t long_len) {
   pdl_wait();
   pdl_trigger();
   using A = typename acc_of<T>::type;
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t row = t / L;
-  const int lane = (int)(t % L);
-  A acc;
-  acc_set(acc, num<T>::zero());
-  if (row < n) {
-    const int64_t p1 = __ldg(rowptr + row + 1);
-    for (int64_t p = __ldg(rowptr + row) + lane; p < p1; p += L) acc_add_prod(acc, ldg(val + p), ldg(x + __ldg(col + p)));
-  }
-  T sum = acc_get(acc);
-#pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) sum = sum + shfl_xor_t(sum, o, L);
-  if (row < n && lane == 0) {
+  auto finish = [&](int64_t row, T sum) {
     A r;
     acc_set_prod(r, alpha, sum);
     acc_add_prod(r, beta, ldg(x + row));
     if (SUB_Y) acc_add_prod(r, gamma, ldg(y + row));
     if (ADD_V) acc_add_prod(r, delta, ldg(v + row));
     out[row] = acc_get(r);
+  };
+  if ((int)blockIdx.x < nlong) {
+    __shared__ T red[8];
+    const int64_t row = __ldg(long_rows + blockIdx.x);
+    const int64_t p1 = __ldg(rowptr + row + 1);
+    A acc;
+    acc_set(acc, num<T>::zero());
+    for (int64_t p = __ldg(rowptr + row) + threadIdx.x; p < p1; p += blockDim.x)
+      acc_add_prod(acc, ldg(val + p), ldg(x + __ldg(col + p)));
+    T sum = acc_get(acc);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum = sum + shfl_xor_t(sum, o, 32);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      T tot = red[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot = tot + red[w];
+      finish(row, tot);
+    }
+    return;
   }
+  const int64_t t = (int64_t)(blockIdx.x - nlong) * blockDim.x + threadIdx.x;
+  const int64_t row = t / L;
+  const int lane = (int)(t % L);
+  A acc;
+  acc_set(acc, num<T>::zero());
+  bool mine = row < n;
+  if (mine) {
+    const int64_t p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
+    if (long_len > 0 && p1 - p0 > long_len)
+      mine = false;  // a long row: its own block computes it
+    else
+      for (int64_t p = p0 + lane; p < p1; p += L) acc_add_prod(acc, ldg(val + p), ldg(x + __ldg(col + p)));
+  }
+  T sum = acc_get(acc);
+#pragma unroll
+  for (int o = L / 2; o > 0; o >>= 1) sum = sum + shfl_xor_t(sum, o, L);
+  if (mine && lane == 0) finish(row, sum);
 }
 
 template <typename T>
@@ -227,11 +258,12 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     const int L = 4;
     const int64_t threads = op.n * L;
     const int bs = 256;
-    const int64_t nb = (threads + bs - 1) / bs;
-    PP_CUDA_TRY(pdl_launch(csr_step<T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col, (const T *)op.val, x, y, v,
-                                                       out, op.n, host_const<T>(c.alpha),
-                                                       host_const<T>(c.beta), host_const<T>(c.gamma),
-                                                       host_const<T>(c.delta)));
+    const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong : 0);
+    if (nb > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "CSR grid too large for one launch");
+    PP_CUDA_TRY(pdl_launch(csr_step<T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,
+                           (const T *)op.val, x, y, v, out, op.n, host_const<T>(c.alpha), host_const<T>(c.beta),
+                           host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,
+                           op.long_len > 0 ? op.nlong : 0, op.long_len));
   } else {
     Konst<T> K;
     K.K0 = host_const<T>(c.alpha * op.d + c.beta);

@@ -77,6 +77,8 @@ SYMBOLS = {
                                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)]),
     "pp_set_poly_nodes": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "pp_set_poly_lsq": (ctypes.c_int, [_h, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double), ctypes.c_int32]),
     "pp_get_quadrature": (ctypes.c_int, [_h, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                                          ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "pp_apply": (ctypes.c_int, [_h, ctypes.c_int32, _p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
@@ -220,6 +222,15 @@ def pp_set_poly_nodes(h, nodes, interval_ab=None):
     _check(lib().pp_set_poly_nodes(h, re.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                    im.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if im is not None else None,
                                    n, ab))
+
+
+def pp_set_poly_lsq(h, degree, points):
+    z = np.asarray(points)
+    re = np.ascontiguousarray(np.real(z), dtype=np.float64)
+    im = np.ascontiguousarray(np.imag(z), dtype=np.float64) if np.iscomplexobj(z) else None
+    _check(lib().pp_set_poly_lsq(h, degree, re.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 im.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if im is not None else None,
+                                 len(re)))
 
 
 def pp_get_quadrature(h):

@@ -9,7 +9,7 @@ import subprocess
 import numpy as np
 import pytest
 
-from oracle import chebyshev as cheb, operators as ops, ritz
+from oracle import chebyshev as cheb, lsq, operators as ops, ritz
 from tests.libpp import load
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -129,9 +129,6 @@ def test_argument_validation():
             pp.pp_build_poly(h, -1)
         assert e.value.status == pp.PP_ERR_INVALID_ARG
         with pytest.raises(pp.PPError) as e:
-            pp.pp_build_poly(h, 4, pp.PP_LSQ_CONTOUR)
-        assert e.value.status == pp.PP_ERR_UNSUPPORTED
-        with pytest.raises(pp.PPError) as e:
             pp.pp_build_poly(h, 4, 9)
         assert e.value.status == pp.PP_ERR_INVALID_ARG
         with pytest.raises(pp.PPError) as e:
@@ -151,7 +148,8 @@ def test_argument_validation():
         t = np.pi * (np.arange(5) + 0.5) / 5
         assert kind == pp.PP_CHEBYSHEV
         assert np.allclose(np.sort(x), np.sort(0.5 * (a + b) + 0.5 * (b - a) * np.cos(t)), rtol=1e-15)
-        assert x[0] == x.max() and x[1] == x.min()
+        # reverse Leja order: the last node has the largest modulus, the one before the smallest
+        assert x[-1] == x.max() and x[-2] == x.min()
         o = pp.pp_default_opts()
         o.clenshaw = 2
         with pytest.raises(pp.PPError) as e:
@@ -213,6 +211,20 @@ def test_autotune_degree_model():
             pp.pp_destroy(h)
 
 
+def reverse_units(x):
+    """A node sequence reversed unit by unit: a conjugate pair (z, conj z) stays in that order."""
+    x = list(np.atleast_1d(x))
+    units, i = [], 0
+    while i < len(x):
+        if np.imag(x[i]) > 0:
+            units.append(x[i:i + 2])
+            i += 2
+        else:
+            units.append(x[i:i + 1])
+            i += 1
+    return np.array([z for u in units[::-1] for z in u])
+
+
 def real_basis_eval(coef, x, z):
     """q(z) = sum_i coef_i R_i(z) in the real basis of pp_set_poly_nodes:
     R_0 = 1; a real node: R_{i+1} = (z - x_i) R_i; a pair (x_i, conj x_i):
@@ -254,7 +266,8 @@ def test_set_poly_nodes_matches_oracle(nodes, ab):
         kind, x, cap = pp.pp_get_poly_nodes(h)
         coef, abr, img = pp.pp_get_poly(h)
         assert kind == pp.PP_NODES and len(x) == len(z) and len(coef) == len(z)
-        xo = ritz.leja_order(z)
+        # the Newton form takes the nodes in reverse Leja order (pairs kept, Im > 0 first)
+        xo = reverse_units(ritz.leja_order(z))
         assert np.allclose(x, xo, rtol=0, atol=0)
         ao = ritz.newton_coeffs(xo)
         pts = np.concatenate([np.linspace(ab[0], ab[1], 41), z, [1 + 2j, 3 - 1j]])
@@ -301,6 +314,68 @@ def test_set_poly_nodes_validation():
         with pytest.raises(pp.PPError) as e:
             pp.pp_build_poly(hl, 3, pp.PP_NODES)
         assert e.value.status == pp.PP_ERR_INVALID_ARG
+    finally:
+        pp.pp_destroy(hl)
+        pp.pp_destroy(hc)
+
+
+@pytest.mark.parametrize("degree", [0, 3, 8, 16])
+@pytest.mark.parametrize("ritz_values", [
+    [1 + 0.5j, 1 - 0.5j, 3.0, 4 + 1j, 4 - 1j, 6.0, 0.2 + 0.3j, 0.2 - 0.3j],
+    [2 + 3j, 2 - 3j, 10 + 0.1j, 10 - 0.1j, 5.0],
+    [0.05, 2.0, 9.0],
+], ids=["hull8", "hull5", "real3"])
+def test_set_poly_lsq_matches_oracle(ritz_values, degree):
+    # least-squares q on the oracle's contour points: the library's Newton
+    # form (at Leja points of the contour) against the oracle's orthonormal
+    # basis evaluation, on the contour and inside it
+    pp = load()
+    th = np.array(ritz_values, dtype=complex)
+    z = lsq.contour(th, 0.5 * np.abs(th).min() if np.any(th.imag != 0) else 0.1, 400)
+    P, H = lsq.basis(z, degree + 1)
+    al = lsq.coeffs(P, z ** -0.5)
+    h = pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (5, 4, 3), [0.5])
+    try:
+        pp.pp_set_poly_lsq(h, degree, z)
+        kind, x, cap = pp.pp_get_poly_nodes(h)
+        coef, ab, img = pp.pp_get_poly(h)
+        assert kind == pp.PP_LSQ_CONTOUR and len(x) == degree + 1
+        assert all(np.min(np.abs(z - xi)) == 0 for xi in np.atleast_1d(x))  # nodes are contour points
+        inside = np.array([z.real.mean(), 0.5 * (z.real.min() + z.real.max()) + 0.1j * np.abs(z.imag).max()])
+        pts = np.concatenate([z, inside])
+        qo = lsq.evaluate(H, al, len(z), pts)
+        ql = real_basis_eval(coef, np.atleast_1d(x), pts)
+        assert np.abs(ql - qo).max() < 1e-9 * np.abs(qo).max()
+        qz = qo[:len(z)]
+        assert img[0] == pytest.approx(np.abs(z * qz * qz).min(), rel=1e-9)
+        assert img[1] == pytest.approx(np.abs(z * qz * qz).max(), rel=1e-9)
+    finally:
+        pp.pp_destroy(h)
+
+
+def test_lsq_validation_and_segment():
+    pp = load()
+    hl = pp.pp_create_stencil(pp.PP_LAPLACE2D5, (6, 5))
+    hc = pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (5, 4, 3), [0.5])
+    try:
+        for h, z, st in [(hc, np.array([1.0 + 1j, 2.0, 3.0 - 0.5j]), pp.PP_ERR_UNSUPPORTED),  # not symmetric
+                         (hl, np.array([1.0 + 1j, 1.0 - 1j, 3.0]), pp.PP_ERR_INVALID_ARG),    # complex, Hermitian
+                         (hc, np.array([-1.0, 2.0, 3.0]), pp.PP_ERR_INVALID_ARG),             # on (-inf, 0]
+                         (hc, np.array([1.0, 2.0]), pp.PP_ERR_INVALID_ARG)]:                  # N < degree + 1
+            with pytest.raises(pp.PPError) as e:
+                pp.pp_set_poly_lsq(h, 2, z)
+            assert e.value.status == st
+        # pp_build_poly with a known real spectrum: the least-squares q on its segment
+        pp.pp_build_poly(hl, 6, pp.PP_LSQ_CONTOUR)
+        coef, (a, b), _ = pp.pp_get_poly(hl)
+        assert (a, b) == pytest.approx(ops.laplace_interval((6, 5)), rel=1e-14)
+        kind, x, _ = pp.pp_get_poly_nodes(hl)
+        seg = np.linspace(a, b, 2000)
+        P, H = lsq.basis(seg, 7)
+        al = lsq.coeffs(P, seg ** -0.5)
+        t = np.linspace(a, b, 37)
+        assert kind == pp.PP_LSQ_CONTOUR
+        assert np.allclose(real_basis_eval(coef, x, t), lsq.evaluate(H, al, 2000, t), rtol=1e-9)
     finally:
         pp.pp_destroy(hl)
         pp.pp_destroy(hc)

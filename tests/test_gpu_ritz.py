@@ -95,11 +95,12 @@ def test_nodes_match_oracle(case, degree, kind, prec):
         assert len(P.x) == degree + 1 and len(P.a) == degree + 1
         scale = np.abs(xo).max()
         assert np.abs(np.sort(P.x) - np.sort(xo)).max() < 1e-10 * scale
-        # the library's order is a Leja order of its nodes (greedy maximum, to rounding)
-        assert P.x[0] == np.abs(P.x).max()
-        for k in range(1, len(P.x)):
-            prods = [np.prod(np.abs(z - P.x[:k])) for z in P.x[k:]]
-            assert np.prod(np.abs(P.x[k] - P.x[:k])) >= max(prods) * (1 - 1e-9)
+        # the library's order reversed is a Leja order of its nodes (greedy maximum, to rounding)
+        xl = P.x[::-1]
+        assert xl[0] == np.abs(xl).max()
+        for k in range(1, len(xl)):
+            prods = [np.prod(np.abs(z - xl[:k])) for z in xl[k:]]
+            assert np.prod(np.abs(xl[k] - xl[:k])) >= max(prods) * (1 - 1e-9)
         # Newton coefficients = divided differences of the library's nodes: the
         # same interpolant (the high-order coefficients carry the rounding of
         # z^{-1/2} at the nodes amplified by the divided differences, so the
