@@ -305,7 +305,7 @@ class ClockSampler:
 
 def traffic_from_profile(kernel_src):
     """DRAM bytes per launch of the chain kernel from the committed ncu summary, if current."""
-    path = os.path.join(ROOT, "profiles", "ncu_st3d_step_convdiff128.txt")
+    path = os.path.join(ROOT, "profiles", "ncu_st_step_horner_convdiff128.txt")
     if not os.path.exists(path):
         return None
     h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
