@@ -98,6 +98,25 @@ def parse():
     return a
 
 
+def max_over_ranks(x, ws):
+    """The largest x over the ranks (an all-reduce MAX on the process group's
+    device: CUDA under NCCL, host under gloo); x itself for one rank."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(steps, ws, t_max):
+    """Whole-job solves/s of ws replicas that each ran `steps` solves, timed by
+    the slowest rank (weak scaling, no collective on the data path)."""
+    return ws * steps / t_max
+
+
 _GRAPH = {}
 
 
@@ -447,14 +466,10 @@ def run_ours(args):
     wall = time.perf_counter() - wall0
     clocks = clk.stop()
     step_ms = [a.elapsed_time(e) for a, e in ev]
-    t_total = sum(step_ms) / 1e3
-    if ws > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = max_over_ranks(sum(step_ms) / 1e3, ws)
     o.profile = 0
     pp.pp_set_opts(h, o)
-    value = ws * args.steps / t_total
+    value = replica_value(args.steps, ws, t_total)
     chain_ms = sum(s["chain_ms"] for s in stats)
     chain_bytes = sum(s["chain_bytes"] for s in stats)
     chain_launches = sum(s["chain_launches"] for s in stats)
@@ -478,11 +493,7 @@ def run_ours(args):
         pp.pp_apply_host(h, args.func, bh.data_ptr(), xh.data_ptr(), m_max=m_max, tol=args.tol)
         if i > 0:
             e2e_t.append(time.perf_counter() - t0)
-    e2e_val = ws * len(e2e_t) / sum(e2e_t)
-    if ws > 1:
-        t = torch.tensor([sum(e2e_t)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = ws * len(e2e_t) / float(t.item())
+    e2e_val = replica_value(len(e2e_t), ws, max_over_ranks(sum(e2e_t), ws))
 
     # in-GPU baseline: plain unpreconditioned Arnoldi (degree 0) in FP64 on the same problem
     plain = None

@@ -364,9 +364,7 @@ template <typename T>
 int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<int64_t> &off, ArithTabs<T> *out) {
   const int ns = G.nseg;
   constexpr int PW = 16 / (int)sizeof(T);
-  bool vec = true;
-  for (const SegIn &q : segs) vec = vec && (q.c->dims[0] % PW == 0);
-  const int P = vec ? PW : 1;
+  const int P = PW;  // entries per thread; each segment has its own load path
   const int bdy = 128 / kBatchBlockX;
   std::vector<BatchSeg> g(ns);
   uint64_t nblk = 0;
@@ -376,7 +374,8 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
     g[i].nx = (int)c->dims[0];
     g[i].ny = (int)c->dims[1];
     g[i].nz = c->op_kind == OPK_ST2D ? 1 : (int)c->dims[2];
-    g[i].gx = (unsigned)((g[i].nx / P + kBatchBlockX - 1) / kBatchBlockX);
+    g[i].gx = (unsigned)(((g[i].nx + P - 1) / P + kBatchBlockX - 1) / kBatchBlockX);
+    g[i].vec = g[i].nx % P == 0 ? 1 : 0;
     g[i].gy = (unsigned)((g[i].ny + bdy - 1) / bdy);
     g[i].blk0 = (unsigned)nblk;
     nblk += (uint64_t)g[i].gx * g[i].gy * g[i].nz;

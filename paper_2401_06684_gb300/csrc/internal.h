@@ -95,6 +95,7 @@ struct BatchSeg {
   int64_t off;
   int nx, ny, nz;
   unsigned gx, gy, blk0;
+  int vec;  // 16-byte loads (nx a multiple of the entries per 16 bytes)
 };
 // Threads in x of a batched stencil block (128 threads per block).
 constexpr int kBatchBlockX = 32;

@@ -87,42 +87,70 @@ __device__ __forceinline__ void zero_p(T (&r)[P]) {
 
 constexpr int ST_THREADS = 128;  // threads per block of the stencil kernels
 
+// Entries [i0, i0 + P) of a row by separate loads, those at or past nx as
+// zero (rows of any length and alignment).
+template <typename T, int P>
+__device__ __forceinline__ void ld_s(const T *p, int cnt, T (&r)[P]) {
+#pragma unroll
+  for (int q = 0; q < P; ++q) r[q] = q < cnt ? ldg(p + q) : num<T>::zero();
+}
+
 // 2D 5-point and 3D 7-point stencils (nz = 1 for 2D): one thread per P
-// consecutive x entries of one grid row, one block per blockDim.x * P x
-// blockDim.y tile of one plane (blockDim.x sized to the row so no thread is
-// idle on rows shorter than 64 P); the flat block index runs over (x tile,
-// y tile, plane).  Every load is a coalesced vector load: the row itself, its four
-// y/z neighbour rows, y and v; the two x neighbours outside the thread's P
-// entries are scalar loads.  Neighbour reuse between threads and planes is
-// left to L1/L2.  Requires nx % P == 0 and P * sizeof(T)-aligned pointers.
-template <typename T, int P, bool SUB_Y, bool ADD_V>
+// consecutive x entries of one grid row (P = 16 bytes of entries), one block
+// per blockDim.x * P x blockDim.y tile of one plane (blockDim.x sized to the
+// row so no thread is idle on rows shorter than 64 P); the flat block index
+// runs over (x tile, y tile, plane).  VEC (nx % P == 0 and 16-byte aligned
+// vectors): every load is a coalesced 16-byte load: the row itself, its four
+// y/z neighbour rows, y and v.  Otherwise the same P entries come through
+// separate loads, masked at the end of the row (several loads in flight per
+// thread either way).  The two x neighbours outside the thread's P entries
+// are scalar loads.  Neighbour reuse between threads and planes is left to
+// L1/L2.
+template <typename T, int P, bool VEC, bool SUB_Y, bool ADD_V>
 __device__ __forceinline__ void stencil_rows(const T *__restrict__ x, const T *__restrict__ y,
                                              const T *__restrict__ v, T *__restrict__ out, int nx, int ny,
                                              int nz, int i0, int j, int k, const Konst<T> &K) {
   const int64_t plane = (int64_t)nx * ny;
   const int64_t off = (int64_t)k * plane + (int64_t)j * nx + i0;
   const T zero = num<T>::zero();
+  const int cnt = nx - i0 < P ? nx - i0 : P;
   T xc[P], xs[P], xn[P], xd[P], xu[P], yy[P], vv[P];
-  ld_p<T, P>(x + off, xc);
-  if (j > 0) ld_p<T, P>(x + off - nx, xs); else zero_p<T, P>(xs);
-  if (j + 1 < ny) ld_p<T, P>(x + off + nx, xn); else zero_p<T, P>(xn);
-  if (k > 0) ld_p<T, P>(x + off - plane, xd); else zero_p<T, P>(xd);
-  if (k + 1 < nz) ld_p<T, P>(x + off + plane, xu); else zero_p<T, P>(xu);
-  if (SUB_Y) ld_p<T, P>(y + off, yy); else zero_p<T, P>(yy);
-  if (ADD_V) ld_p<T, P>(v + off, vv); else zero_p<T, P>(vv);
+  if constexpr (VEC) {
+    ld_p<T, P>(x + off, xc);
+    if (j > 0) ld_p<T, P>(x + off - nx, xs); else zero_p<T, P>(xs);
+    if (j + 1 < ny) ld_p<T, P>(x + off + nx, xn); else zero_p<T, P>(xn);
+    if (k > 0) ld_p<T, P>(x + off - plane, xd); else zero_p<T, P>(xd);
+    if (k + 1 < nz) ld_p<T, P>(x + off + plane, xu); else zero_p<T, P>(xu);
+    if (SUB_Y) ld_p<T, P>(y + off, yy); else zero_p<T, P>(yy);
+    if (ADD_V) ld_p<T, P>(v + off, vv); else zero_p<T, P>(vv);
+  } else {
+    ld_s<T, P>(x + off, cnt, xc);
+    if (j > 0) ld_s<T, P>(x + off - nx, cnt, xs); else zero_p<T, P>(xs);
+    if (j + 1 < ny) ld_s<T, P>(x + off + nx, cnt, xn); else zero_p<T, P>(xn);
+    if (k > 0) ld_s<T, P>(x + off - plane, cnt, xd); else zero_p<T, P>(xd);
+    if (k + 1 < nz) ld_s<T, P>(x + off + plane, cnt, xu); else zero_p<T, P>(xu);
+    if (SUB_Y) ld_s<T, P>(y + off, cnt, yy); else zero_p<T, P>(yy);
+    if (ADD_V) ld_s<T, P>(v + off, cnt, vv); else zero_p<T, P>(vv);
+  }
   const T xw0 = i0 > 0 ? ldg(x + off - 1) : zero;
   const T xeP = i0 + P < nx ? ldg(x + off + P) : zero;
   T o[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) {
     const T xw = q == 0 ? xw0 : xc[q - 1];
-    const T xe = q == P - 1 ? xeP : xc[q + 1];
+    const T xe = q == P - 1 ? xeP : xc[q + 1];  // past the row's end: zero (Dirichlet)
     o[q] = stencil_row<T, SUB_Y, ADD_V>(xc[q], xw, xe, xs[q], xn[q], xd[q], xu[q], yy[q], vv[q], K);
   }
-  st_p<T, P>(out + off, o);
+  if constexpr (VEC) {
+    st_p<T, P>(out + off, o);
+  } else {
+#pragma unroll
+    for (int q = 0; q < P; ++q)
+      if (q < cnt) out[off + q] = o[q];
+  }
 }
 
-template <typename T, int P, bool SUB_Y, bool ADD_V>
+template <typename T, int P, bool VEC, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(ST_THREADS) st_step(const T *__restrict__ x, const T *__restrict__ y,
                                                         const T *__restrict__ v, T *__restrict__ out,
                                                         int nx, int ny, int nz, unsigned gx, unsigned gy,
@@ -136,12 +164,13 @@ __global__ void __launch_bounds__(ST_THREADS) st_step(const T *__restrict__ x, c
   const int i0 = (int)(bx * blockDim.x + threadIdx.x) * P;
   const int j = (int)(by * blockDim.y + threadIdx.y);
   if (i0 >= nx || j >= ny) return;
-  stencil_rows<T, P, SUB_Y, ADD_V>(x, y, v, out, nx, ny, nz, i0, j, k, K);
+  stencil_rows<T, P, VEC, SUB_Y, ADD_V>(x, y, v, out, nx, ny, nz, i0, j, k, K);
 }
 
 // Batched form: many grids (segments of concatenated vectors) in one launch.
 // The flat block index is located in the segments' first-block table by
-// binary search; each segment has its own geometry and constants.
+// binary search; each segment has its own geometry, constants and load path
+// (16-byte loads where its row length allows them).
 template <typename T, int P, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(ST_THREADS) bst_step(const T *__restrict__ x, const T *__restrict__ y,
                                                          const T *__restrict__ v, T *__restrict__ out,
@@ -168,8 +197,12 @@ __global__ void __launch_bounds__(ST_THREADS) bst_step(const T *__restrict__ x, 
   const int i0 = (int)(bx * blockDim.x + threadIdx.x) * P;
   const int j = (int)(by * blockDim.y + threadIdx.y);
   if (i0 >= g.nx || j >= g.ny) return;
-  stencil_rows<T, P, SUB_Y, ADD_V>(x + g.off, SUB_Y ? y + g.off : y, ADD_V ? v + g.off : v, out + g.off,
-                                   g.nx, g.ny, g.nz, i0, j, k, K[lo]);
+  if (g.vec)
+    stencil_rows<T, P, true, SUB_Y, ADD_V>(x + g.off, SUB_Y ? y + g.off : y, ADD_V ? v + g.off : v, out + g.off,
+                                           g.nx, g.ny, g.nz, i0, j, k, K[lo]);
+  else
+    stencil_rows<T, P, false, SUB_Y, ADD_V>(x + g.off, SUB_Y ? y + g.off : y, ADD_V ? v + g.off : v,
+                                            out + g.off, g.nx, g.ny, g.nz, i0, j, k, K[lo]);
 }
 
 // CSR.  Rows of up to long_len entries: L lanes per row, lane-strided over
@@ -277,9 +310,9 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     const size_t align = (size_t)PW * sizeof(T);
     auto ok = [&](const void *p) { return p == nullptr || ((uintptr_t)p % align) == 0; };
     const bool vec = op.nx % PW == 0 && ok(x) && ok(out) && (!SY || ok(y)) && (!AV || ok(v));
-    const int P = vec ? PW : 1;
+    constexpr int P = PW;
     // threads in x: the row's thread count rounded up to a power of two, 8 .. 64
-    const int64_t tx = op.nx / P;
+    const int64_t tx = (op.nx + P - 1) / P;
     int bdx = 8;
     while (bdx < 64 && bdx < tx) bdx *= 2;
     if (op.tile_bdx >= 8 && op.tile_bdx <= 128 && (op.tile_bdx & (op.tile_bdx - 1)) == 0) bdx = op.tile_bdx;
@@ -290,9 +323,11 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     if (nblk > 0x7fffffffull) return pp_set_error(PP_ERR_INVALID_ARG, "grid too large for one launch");
     const dim3 blk(bdx, bdy);
     if (vec)
-      PP_CUDA_TRY(pdl_launch(st_step<T, PW, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out, (int)op.nx, (int)op.ny, nz, gx, gy, K));
+      PP_CUDA_TRY(pdl_launch(st_step<T, PW, true, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out,
+                             (int)op.nx, (int)op.ny, nz, gx, gy, K));
     else
-      PP_CUDA_TRY(pdl_launch(st_step<T, 1, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out, (int)op.nx, (int)op.ny, nz, gx, gy, K));
+      PP_CUDA_TRY(pdl_launch(st_step<T, PW, false, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out,
+                             (int)op.nx, (int)op.ny, nz, gx, gy, K));
   }
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
@@ -331,17 +366,11 @@ int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Ko
 #define PP_BST(PP, SY, AV) \
   e = pdl_launch(bst_step<T, PP, SY, AV>, dim3(nblk), blk, 0, s, x, y, v, out, segs, nseg, K, active)
   cudaError_t e;
-  if (P == PW) {
-    if (sub_y && add_v) PP_BST(PW, true, true);
-    else if (sub_y) PP_BST(PW, true, false);
-    else if (add_v) PP_BST(PW, false, true);
-    else PP_BST(PW, false, false);
-  } else {
-    if (sub_y && add_v) PP_BST(1, true, true);
-    else if (sub_y) PP_BST(1, true, false);
-    else if (add_v) PP_BST(1, false, true);
-    else PP_BST(1, false, false);
-  }
+  (void)P;  // always PW entries per thread; each segment picks its load path
+  if (sub_y && add_v) PP_BST(PW, true, true);
+  else if (sub_y) PP_BST(PW, true, false);
+  else if (add_v) PP_BST(PW, false, true);
+  else PP_BST(PW, false, false);
 #undef PP_BST
   PP_CUDA_TRY(e);
   ++pp_launch_count();
