@@ -246,7 +246,7 @@ int pp_build_poly(pp_handle h, int32_t degree, int32_t kind, const double *inter
  * passes at 6 TB/s, plus 3 us per kernel launch and 40 us per stopping check,
  * and the fastest degree is taken (*degree_out).
  * For stencil handles in PP_PREC_DW / PP_PREC_MIXED it then times the
- * operator kernel with block x-sizes 16, 32, 64, 128 on the handle's stream
+ * operator kernel with blocks of 64, 128, 256, 512 threads on the handle's stream
  * (CUDA events, synchronising) and keeps the fastest for later calls.
  * Errors: as pp_build_poly; PP_ERR_INVALID_ARG for tol outside (0, 1).
  */

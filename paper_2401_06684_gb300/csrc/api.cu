@@ -1777,7 +1777,7 @@ int pp_autotune(pp_handle c, double tol, int32_t max_degree, int32_t *degree_out
     cudaEvent_t e0 = c->ws.ev0, e1 = c->ws.ev1;
     float best_ms = INFINITY;
     int best_bdx = 0;
-    for (int bdx : {16, 32, 64, 128}) {
+    for (int bdx : {64, 128, 256, 512}) {
       c->tile_bdx = bdx;
       float ms = 0.f;
       for (int rep = 0; rep < 2; ++rep) {  // first pass warms up

@@ -365,7 +365,6 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
   const int ns = G.nseg;
   constexpr int PW = 16 / (int)sizeof(T);
   const int P = PW;  // entries per thread; each segment has its own load path
-  const int bdy = 128 / kBatchBlockX;
   std::vector<BatchSeg> g(ns);
   uint64_t nblk = 0;
   for (int i = 0; i < ns; ++i) {
@@ -374,11 +373,11 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
     g[i].nx = (int)c->dims[0];
     g[i].ny = (int)c->dims[1];
     g[i].nz = c->op_kind == OPK_ST2D ? 1 : (int)c->dims[2];
-    g[i].gx = (unsigned)(((g[i].nx + P - 1) / P + kBatchBlockX - 1) / kBatchBlockX);
+    g[i].txs = (g[i].nx + P - 1) / P;
+    g[i].units = (int64_t)g[i].txs * g[i].ny * g[i].nz;
     g[i].vec = g[i].nx % P == 0 ? 1 : 0;
-    g[i].gy = (unsigned)((g[i].ny + bdy - 1) / bdy);
     g[i].blk0 = (unsigned)nblk;
-    nblk += (uint64_t)g[i].gx * g[i].gy * g[i].nz;
+    nblk += (uint64_t)((g[i].units + kBatchBlock - 1) / kBatchBlock);
   }
   if (nblk > 0x7fffffffull) return pp_set_error(PP_ERR_INVALID_ARG, "batch too large for one launch");
   // constants: [0] = A, [1 + t] = step t of q (Clenshaw or Horner)

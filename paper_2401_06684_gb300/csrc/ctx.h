@@ -63,7 +63,7 @@ struct pp_ctx {
   // PP_PREC_MIXED stays in double-word
   bool image_on_points = false;
   std::vector<double> qsig, qwt;
-  int tile_bdx = 0;  // stencil block x-size chosen by pp_autotune (0 = default)
+  int tile_bdx = 0;  // stencil threads per block chosen by pp_autotune (0 = default)
   bool quad_uploaded = false;
   Workspace ws;
   // operator-launch accounting of the current call (pp_stats.chain_*)

@@ -33,7 +33,7 @@ struct OpDesc {
   double mass;
   const void *links;
   void *tmp;
-  int tile_bdx;  // stencil kernels: threads per block in x (0 = sized to the row)
+  int tile_bdx;  // stencil kernels: threads per block (0 = 128)
 };
 
 // out = alpha * (A x) + beta * x  [+ gamma * y]  [+ delta * v]; sub_y switches
@@ -94,11 +94,13 @@ struct Konst {
 struct BatchSeg {
   int64_t off;
   int nx, ny, nz;
-  unsigned gx, gy, blk0;
-  int vec;  // 16-byte loads (nx a multiple of the entries per 16 bytes)
+  int txs;        // units (16 bytes of entries) per row
+  int64_t units;  // txs * ny * nz
+  unsigned blk0;  // first block of the segment (blocks of 128 threads)
+  int vec;        // 16-byte loads (nx a multiple of the entries per 16 bytes)
 };
-// Threads in x of a batched stencil block (128 threads per block).
-constexpr int kBatchBlockX = 32;
+// Threads per block of the batched stencil kernel.
+constexpr int kBatchBlock = 128;
 
 // Host: Konst of out = alpha A x + beta x [- y] + delta v for every segment
 // (stencil diagonal d, neighbour weights cm / cp, coefficients c[i]).

@@ -85,7 +85,8 @@ __device__ __forceinline__ void zero_p(T (&r)[P]) {
   for (int q = 0; q < P; ++q) r[q] = num<T>::zero();
 }
 
-constexpr int ST_THREADS = 128;  // threads per block of the stencil kernels
+constexpr int ST_THREADS = 128;           // threads per block of the stencil kernels (default)
+constexpr int kStencilMaxThreads = 512;  // largest block the tile tuner may pick
 
 // Entries [i0, i0 + P) of a row by separate loads, those at or past nx as
 // zero (rows of any length and alignment).
@@ -96,10 +97,8 @@ __device__ __forceinline__ void ld_s(const T *p, int cnt, T (&r)[P]) {
 }
 
 // 2D 5-point and 3D 7-point stencils (nz = 1 for 2D): one thread per P
-// consecutive x entries of one grid row (P = 16 bytes of entries), one block
-// per blockDim.x * P x blockDim.y tile of one plane (blockDim.x sized to the
-// row so no thread is idle on rows shorter than 64 P); the flat block index
-// runs over (x tile, y tile, plane).  VEC (nx % P == 0 and 16-byte aligned
+// consecutive x entries of one grid row (P = 16 bytes of entries; the units
+// are spread over the threads by st_step / bst_step).  VEC (nx % P == 0 and 16-byte aligned
 // vectors): every load is a coalesced 16-byte load: the row itself, its four
 // y/z neighbour rows, y and v.  Otherwise the same P entries come through
 // separate loads, masked at the end of the row (several loads in flight per
@@ -150,33 +149,65 @@ __device__ __forceinline__ void stencil_rows(const T *__restrict__ x, const T *_
   }
 }
 
-template <typename T, int P, bool VEC, bool SUB_Y, bool ADD_V>
-__global__ void __launch_bounds__(ST_THREADS) st_step(const T *__restrict__ x, const T *__restrict__ y,
-                                                        const T *__restrict__ v, T *__restrict__ out,
-                                                        int nx, int ny, int nz, unsigned gx, unsigned gy,
-                                                        Konst<T> K) {
+// Unit u of a grid with txs units per row -> (first entry i0, row j, plane k);
+// 32-bit divisions where the grid allows them (64-bit ones are emulated).
+template <int P>
+__device__ __forceinline__ void unit_coords(int64_t u, int64_t units, int txs, int ny, int *i0, int *j, int *k) {
+  if (units <= 0x7fffffff) {
+    const unsigned uu = (unsigned)u, r = uu / (unsigned)txs;
+    *i0 = (int)(uu - r * (unsigned)txs) * P;
+    const unsigned kk = r / (unsigned)ny;
+    *j = (int)(r - kk * (unsigned)ny);
+    *k = (int)kk;
+  } else {
+    const int64_t r = u / txs;
+    *i0 = (int)(u - r * txs) * P;
+    *j = (int)(r % ny);
+    *k = (int)(r / ny);
+  }
+}
+
+// One thread per unit of P consecutive entries of a row.  FLAT: units
+// numbered x-fastest over the whole grid (txs units per row), so no thread
+// idles whatever the row length; otherwise (the row's unit count a multiple
+// of blockDim.x or blockDim.x a multiple of it) a 2D block of blockDim.x
+// units by blockDim.y rows of one plane, the flat block index running over
+// (x tile, y tile, plane), which needs no division per thread.
+template <typename T, int P, bool VEC, bool FLAT, bool SUB_Y, bool ADD_V>
+__global__ void __launch_bounds__(kStencilMaxThreads) st_step(const T *__restrict__ x, const T *__restrict__ y,
+                                                                const T *__restrict__ v, T *__restrict__ out,
+                                                                int nx, int ny, int nz, int txs, int64_t units,
+                                                                unsigned gx, unsigned gy, Konst<T> K) {
   pdl_wait();
   pdl_trigger();
-  const unsigned blk = blockIdx.x;
-  const unsigned bx = blk % gx, rest = blk / gx;
-  const unsigned by = rest % gy;
-  const int k = (int)(rest / gy);
-  const int i0 = (int)(bx * blockDim.x + threadIdx.x) * P;
-  const int j = (int)(by * blockDim.y + threadIdx.y);
-  if (i0 >= nx || j >= ny) return;
+  int i0, j, k;
+  if constexpr (FLAT) {
+    const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= units) return;
+    unit_coords<P>(u, units, txs, ny, &i0, &j, &k);
+  } else {
+    const unsigned blk = blockIdx.x;
+    const unsigned bx = blk % gx, rest = blk / gx;
+    const unsigned by = rest % gy;
+    k = (int)(rest / gy);
+    i0 = (int)(bx * blockDim.x + threadIdx.x) * P;
+    j = (int)(by * blockDim.y + threadIdx.y);
+    if (i0 >= nx || j >= ny) return;
+  }
   stencil_rows<T, P, VEC, SUB_Y, ADD_V>(x, y, v, out, nx, ny, nz, i0, j, k, K);
 }
 
 // Batched form: many grids (segments of concatenated vectors) in one launch.
 // The flat block index is located in the segments' first-block table by
 // binary search; each segment has its own geometry, constants and load path
-// (16-byte loads where its row length allows them).
+// (16-byte loads where its row length allows them), and its units are mapped
+// as in st_step.
 template <typename T, int P, bool SUB_Y, bool ADD_V>
-__global__ void __launch_bounds__(ST_THREADS) bst_step(const T *__restrict__ x, const T *__restrict__ y,
-                                                         const T *__restrict__ v, T *__restrict__ out,
-                                                         const BatchSeg *__restrict__ segs, int nseg,
-                                                         const Konst<T> *__restrict__ K,
-                                                         const int *__restrict__ active) {
+__global__ void __launch_bounds__(kStencilMaxThreads) bst_step(const T *__restrict__ x, const T *__restrict__ y,
+                                                                 const T *__restrict__ v, T *__restrict__ out,
+                                                                 const BatchSeg *__restrict__ segs, int nseg,
+                                                                 const Konst<T> *__restrict__ K,
+                                                                 const int *__restrict__ active) {
   pdl_wait();
   pdl_trigger();
   const unsigned blk = blockIdx.x;
@@ -190,13 +221,10 @@ __global__ void __launch_bounds__(ST_THREADS) bst_step(const T *__restrict__ x, 
   }
   if (active && !active[lo]) return;
   const BatchSeg g = segs[lo];
-  const unsigned b = blk - g.blk0;
-  const unsigned bx = b % g.gx, rest = b / g.gx;
-  const unsigned by = rest % g.gy;
-  const int k = (int)(rest / g.gy);
-  const int i0 = (int)(bx * blockDim.x + threadIdx.x) * P;
-  const int j = (int)(by * blockDim.y + threadIdx.y);
-  if (i0 >= g.nx || j >= g.ny) return;
+  const int64_t u = (int64_t)(blk - g.blk0) * blockDim.x + threadIdx.x;
+  if (u >= g.units) return;
+  int i0, j, k;
+  unit_coords<P>(u, g.units, g.txs, g.ny, &i0, &j, &k);
   if (g.vec)
     stencil_rows<T, P, true, SUB_Y, ADD_V>(x + g.off, SUB_Y ? y + g.off : y, ADD_V ? v + g.off : v, out + g.off,
                                            g.nx, g.ny, g.nz, i0, j, k, K[lo]);
@@ -311,23 +339,35 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     auto ok = [&](const void *p) { return p == nullptr || ((uintptr_t)p % align) == 0; };
     const bool vec = op.nx % PW == 0 && ok(x) && ok(out) && (!SY || ok(y)) && (!AV || ok(v));
     constexpr int P = PW;
-    // threads in x: the row's thread count rounded up to a power of two, 8 .. 64
-    const int64_t tx = (op.nx + P - 1) / P;
-    int bdx = 8;
-    while (bdx < 64 && bdx < tx) bdx *= 2;
-    if (op.tile_bdx >= 8 && op.tile_bdx <= 128 && (op.tile_bdx & (op.tile_bdx - 1)) == 0) bdx = op.tile_bdx;
-    const int bdy = ST_THREADS / bdx;
-    const unsigned gx = (unsigned)((tx + bdx - 1) / bdx);
-    const unsigned gy = (unsigned)((op.ny + bdy - 1) / bdy);
-    const uint64_t nblk = (uint64_t)gx * gy * (uint64_t)nz;
-    if (nblk > 0x7fffffffull) return pp_set_error(PP_ERR_INVALID_ARG, "grid too large for one launch");
-    const dim3 blk(bdx, bdy);
-    if (vec)
-      PP_CUDA_TRY(pdl_launch(st_step<T, PW, true, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out,
-                             (int)op.nx, (int)op.ny, nz, gx, gy, K));
+    const int txs = (int)((op.nx + P - 1) / P);
+    const int64_t units = (int64_t)txs * op.ny * nz;
+    int bs = ST_THREADS;
+    if (op.tile_bdx >= 64 && op.tile_bdx <= kStencilMaxThreads && (op.tile_bdx & (op.tile_bdx - 1)) == 0)
+      bs = op.tile_bdx;
+    // 2D blocks (bdx units by bs / bdx rows) when a row splits into whole x
+    // tiles of 64, 32, 16 or 8 units, else the flat mapping
+    int bdx = 0;
+    for (int c : {64, 32, 16, 8})
+      if (bdx == 0 && c <= bs && txs % c == 0) bdx = c;
+    const bool flat = bdx == 0;
+    const int bdy = flat ? 1 : bs / bdx;
+    const unsigned gx = flat ? 1u : (unsigned)(txs / bdx);
+    const unsigned gy = flat ? 1u : (unsigned)((op.ny + bdy - 1) / bdy);
+    const int64_t nblk = flat ? (units + bs - 1) / bs : (int64_t)gx * gy * nz;
+    if (nblk > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "grid too large for one launch");
+    const dim3 blk = flat ? dim3(bs) : dim3(bdx, bdy);
+#define PP_ST(V, F)                                                                                       \
+  PP_CUDA_TRY(pdl_launch(st_step<T, PW, V, F, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out,      \
+                         (int)op.nx, (int)op.ny, nz, txs, units, gx, gy, K))
+    if (vec && flat)
+      PP_ST(true, true);
+    else if (vec)
+      PP_ST(true, false);
+    else if (flat)
+      PP_ST(false, true);
     else
-      PP_CUDA_TRY(pdl_launch(st_step<T, PW, false, SY, AV>, dim3((unsigned)nblk), blk, 0, s, x, y, v, out,
-                             (int)op.nx, (int)op.ny, nz, gx, gy, K));
+      PP_ST(false, false);
+#undef PP_ST
   }
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
@@ -362,7 +402,7 @@ template <typename T>
 int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Konst<T> *K, const int *active,
                   const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v, cudaStream_t s) {
   constexpr int PW = 16 / (int)sizeof(T);
-  const dim3 blk(kBatchBlockX, ST_THREADS / kBatchBlockX);
+  const dim3 blk(ST_THREADS);
 #define PP_BST(PP, SY, AV) \
   e = pdl_launch(bst_step<T, PP, SY, AV>, dim3(nblk), blk, 0, s, x, y, v, out, segs, nseg, K, active)
   cudaError_t e;
