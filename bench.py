@@ -39,6 +39,10 @@ WORKLOADS = {
     "laplace2048": ("2D Laplacian 2048^2 5-point matrix-free (n=4194304), f=A^(-1/2), Lanczos; "
                     "1e-8 target, estimate tolerance 1e-9", "laplace2d5", (2048, 2048), -1, 16, 1e-9,
                     "lanczos"),
+    "laplace8192": ("2D Laplacian 8192^2 5-point matrix-free (n=67108864, vectors of 268 MB in FP32: out of "
+                    "L2), f=A^(-1/2), Lanczos, degree 16, two-pass (basis memory O(n)); the out-of-L2 roofline "
+                    "case of the 2048^2 configuration (use --probe for the per-step chain numbers)",
+                    "laplace2d5", (8192, 8192), -1, 16, 1e-9, "lanczos"),
     "laplace64csr": ("2D Laplacian 64^2 5-point CSR (n=4096), f=A^(-1/2), Lanczos, degree 8",
                      "laplace2d5csr", (64, 64), -1, 8, 1e-10, "lanczos"),
     "batch64": ("64 independent problems in one batched call: 2D/3D Laplacians and 3D convection-diffusion, "
@@ -393,7 +397,7 @@ def run_ours(args):
     o = pp.pp_default_opts()
     o.precision = {"dw": pp.PP_PREC_DW, "f64": pp.PP_PREC_F64, "mixed": pp.PP_PREC_MIXED}[args.prec]
     pp.pp_set_opts(h, o)
-    if args.two_pass:  # O(n) basis memory: two-pass Lanczos
+    if args.two_pass or args.workload == "laplace8192":  # O(n) basis memory: two-pass Lanczos
         o.two_pass = 1
     o.clenshaw = 1 if args.clenshaw else 0
     if args.kind == "graphcsr":  # Example 3 checks every 32/d iterations
@@ -706,15 +710,26 @@ def run_probe(args):
         torch.cuda.synchronize()
         return 1e3 * e0.elapsed_time(e1) / reps
 
-    res = {}
-    for name, prec in (("f32", pp.PP_PREC_MIXED), ("dw", pp.PP_PREC_DW)):
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6800.0
+    res = {"peak_GBs": peak, "peak_source": "measured" if os.path.exists(peaks_path) else "fallback"}
+    for name, prec, esz in (("f32", pp.PP_PREC_MIXED, 4), ("dw", pp.PP_PREC_DW, 8)):
         for scheme in ("horner", "clenshaw"):
             o = pp.pp_default_opts()
             o.precision = prec
             o.clenshaw = int(scheme == "clenshaw")
             pp.pp_set_opts(h, o)
+            k = max(args.degree, 1)
             us = timed(lambda: pp.pp_poly_apply(h, x, y))
-            res[f"{name}_{scheme}_us_per_step"] = us / max(args.degree, 1)
+            # algorithmic bytes of one q(A) x by pp_poly_apply: the FP64 input
+            # converted in and the result out (8 + s bytes per entry each way),
+            # then the chain: first step 2 vectors, Horner steps 3, Clenshaw
+            # steps 3 (the second) and 4 (the others)
+            chain = 2 + (3 * (k - 1) if scheme == "horner" else (3 + 4 * (k - 2) if k >= 2 else 0))
+            byt = (chain * esz + 2 * (8 + esz)) * n
+            res[f"{name}_{scheme}_us_per_step"] = us / k
+            res[f"{name}_{scheme}_GBs"] = byt / (us * 1e-6) / 1e9
+            res[f"{name}_{scheme}_frac"] = byt / (us * 1e-6) / 1e9 / peak
     for name, prec in (("f32", pp.PP_PREC_MIXED), ("dw", pp.PP_PREC_DW), ("f64", pp.PP_PREC_F64)):
         o = pp.pp_default_opts()
         o.precision = prec
