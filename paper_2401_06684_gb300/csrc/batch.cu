@@ -374,7 +374,7 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
     g[i].ny = (int)c->dims[1];
     g[i].nz = c->op_kind == OPK_ST2D ? 1 : (int)c->dims[2];
     g[i].txs = (g[i].nx + P - 1) / P;
-    g[i].units = (int64_t)g[i].txs * g[i].ny * g[i].nz;
+    g[i].units = (int64_t)g[i].txs * ((g[i].ny + 1) / 2) * g[i].nz;  // P entries x 2 rows each
     g[i].vec = g[i].nx % P == 0 ? 1 : 0;
     g[i].blk0 = (unsigned)nblk;
     nblk += (uint64_t)((g[i].units + kBatchBlock - 1) / kBatchBlock);

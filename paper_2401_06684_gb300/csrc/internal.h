@@ -94,8 +94,8 @@ struct Konst {
 struct BatchSeg {
   int64_t off;
   int nx, ny, nz;
-  int txs;        // units (16 bytes of entries) per row
-  int64_t units;  // txs * ny * nz
+  int txs;        // units (16 bytes of entries of two rows) per row pair
+  int64_t units;  // txs * ceil(ny / 2) * nz
   unsigned blk0;  // first block of the segment (blocks of 128 threads)
   int vec;        // 16-byte loads (nx a multiple of the entries per 16 bytes)
 };
