@@ -19,6 +19,13 @@ Layout
   krylov     Algorithm 1 (left) and Algorithm 2 (right) polynomially
              preconditioned Arnoldi / Lanczos, the stopping rule of Sec. 6,
              and plain unpreconditioned Arnoldi as a large-n reference.
+  ritz       interpolation at Ritz / harmonic Ritz values in Newton form at
+             Leja-ordered nodes (Sec. 5.2).
+  lsq        least-squares polynomials on a contour (Sec. 5.3).
+  wilson     the Wilson-type lattice operator D (with chemical potential),
+             A = D^H D, Q = Gamma_5 D and free-field closed forms.
+  sign       sign(Q) b = Q (Q^2)^{-1/2} b and the overlap operator (Sec. 6,
+             Example 2).
 
 Every function is FP64 (complex128 where the data is complex) and follows
 the paper passage named in its docstring.  Pins for all of it live in

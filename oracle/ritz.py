@@ -119,26 +119,29 @@ def harmonic_ritz_values(H, hermitian=True):
     return np.linalg.eigvals(Ht)
 
 
-def leja_order(nodes):
+def leja_order(nodes, pairs=True):
     """Leja order; real input gives a real array.
 
-    Complex nodes (conjugate pairs of a real problem): the candidates are the
-    nodes with Im >= 0; a chosen complex node is followed at once by its
-    conjugate, so every pair is adjacent (a conjugation-closed node set after
-    each pair).
+    Complex nodes with pairs=True (conjugate pairs of a real problem): the
+    candidates are the nodes with Im >= 0; a chosen complex node is followed
+    at once by its conjugate, so every pair is adjacent (a conjugation-closed
+    node set after each pair).  pairs=False (a complex problem, nodes without
+    that symmetry): every node is a candidate on its own.
     """
     arr = np.asarray(nodes)
     real = not np.iscomplexobj(arr) or np.all(arr.imag == 0)
     if real:
         rest = [complex(x) for x in np.real(arr).astype(np.float64)]
-    else:
+    elif pairs:
         rest = [complex(x) for x in arr if x.imag >= 0]
+    else:
+        rest = [complex(x) for x in arr]
     first = max(range(len(rest)), key=lambda i: (abs(rest[i]), -i))
     out = []
 
     def take(z):
         out.append(z)
-        if z.imag > 0:
+        if pairs and z.imag > 0:
             out.append(z.conjugate())
 
     take(rest.pop(first))
@@ -207,12 +210,16 @@ def ritz_poly(A_mv, n, degree, harmonic=False, complex_=False, hermitian=True):
     degree + 1 Arnoldi steps on the library's start vector.
 
     Hermitian A: real nodes.  Real non-Hermitian A: the eigenvalues of H_d
-    (or of the harmonic matrix), complex ones in conjugate pairs.
+    (or of the harmonic matrix), complex ones in conjugate pairs.  Complex
+    non-Hermitian A (complex_ and not hermitian): the eigenvalues of the
+    complex H_d, Leja-ordered one by one (no conjugate symmetry).
     Returns (nodes, coeffs); fewer nodes if the Krylov space became invariant.
     """
     H, _ = arnoldi(A_mv, start_vector(n, complex_), degree + 1)
     th = harmonic_ritz_values(H, hermitian) if harmonic else ritz_values(H, hermitian)
-    if hermitian or np.all(np.abs(np.imag(th)) == 0):
+    if complex_ and not hermitian:
+        x = leja_order(np.asarray(th, dtype=np.complex128), pairs=False)
+    elif hermitian or np.all(np.abs(np.imag(th)) == 0):
         x = leja_order(np.sort(np.real(th)))
     else:
         # snap the conjugate pairs of the real H_d exactly (eigvals returns them

@@ -60,8 +60,13 @@ def neighbours(dims, mu, sign):
     return idx
 
 
-def dirac_matrix(dims, links, m0):
-    """Sparse complex128 matrix of D (12 V x 12 V)."""
+def dirac_matrix(dims, links, m0, mu_c=0.0):
+    """Sparse complex128 matrix of D (12 V x 12 V).
+
+    mu_c: chemical potential (Sec. 6, Example 2): the hop to x + t carries the
+    factor e^{mu_c}, the hop to x - t the factor e^{-mu_c} (t = direction 3,
+    gamma_4); mu_c = 0 is the operator above.
+    """
     dims = tuple(int(L) for L in dims)
     V = int(np.prod(dims))
     U = np.asarray(links).astype(np.complex128).reshape(V, 4, 3, 3)
@@ -72,11 +77,12 @@ def dirac_matrix(dims, links, m0):
     for mu in range(4):
         for sign in (+1, -1):
             nb = neighbours(dims, mu, sign)
+            chem = np.exp(sign * mu_c) if mu == 3 else 1.0
             if sign > 0:
-                spin = -0.5 * (I4 - g[mu])
+                spin = -0.5 * chem * (I4 - g[mu])
                 col_mats = U[:, mu]                                  # U_mu(x)
             else:
-                spin = -0.5 * (I4 + g[mu])
+                spin = -0.5 * chem * (I4 + g[mu])
                 col_mats = np.conj(np.transpose(U[nb, mu], (0, 2, 1)))  # U_mu(x - mu)^H
             # block[s] = kron(spin, colour[s]) : 12 x 12
             blocks = np.einsum("ij,sab->siajb", spin, col_mats).reshape(V, 12, 12)
@@ -92,6 +98,14 @@ def dirac_matrix(dims, links, m0):
     D = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(12 * V, 12 * V))
     return D.tocsr()
+
+
+def q_matrix(dims, links, m_w, mu_c):
+    """Q = Gamma_5 D(m_w, mu_c) (Sec. 6, Example 2), sparse; Gamma_5 = diag(1, 1, -1, -1) on spin."""
+    D = dirac_matrix(dims, links, m_w, mu_c)
+    V = D.shape[0] // 12
+    g5 = np.tile(np.repeat([1.0, 1.0, -1.0, -1.0], 3), V)
+    return (sp.diags(g5) @ D).tocsr()
 
 
 def dhd_matrix(dims, links, m0):
@@ -147,3 +161,38 @@ def gamma5_apply(psi):
     P = np.asarray(psi).reshape(-1, 4, 3).copy()
     P[:, 2:] *= -1.0
     return P.reshape(-1)
+
+
+def free_q_symbol(dims, m_w, mu_c):
+    """Q(p) = gamma_5 D(p) for U = 1: the 4 x 4 spin matrix of Q at every FFT
+    momentum, shape (Lt, Lz, Ly, Lx, 4, 4).
+
+    A plane wave e^{i p.x} u is an eigenvector of the hops, with e^{+-i p_mu}
+    for the hop to x +- mu and, in direction t, the extra factors e^{+-mu_c}:
+    with p~_t = p_t - i mu_c (p~ = p otherwise),
+        D(p) = (m_w + sum_mu (1 - cos p~_mu)) I + i sum_mu gamma_mu sin p~_mu.
+    """
+    dims = tuple(int(L) for L in dims)
+    shape = tuple(reversed(dims))
+    g = gammas()
+    M = np.full(shape, complex(m_w))
+    S = [None] * 4
+    for mu, L in enumerate(dims):
+        p = (2.0 * np.pi * np.arange(L) / L).astype(np.complex128)
+        if mu == 3:
+            p = p - 1j * mu_c
+        sh = [1, 1, 1, 1]
+        sh[3 - mu] = L
+        M = M + (1.0 - np.cos(p)).reshape(sh)
+        S[mu] = np.broadcast_to(np.sin(p).reshape(sh), shape)
+    D = M[..., None, None] * np.eye(4) + 1j * sum(S[mu][..., None, None] * g[mu] for mu in range(4))
+    return g[4] @ D
+
+
+def free_spin_fun(dims, b, mats):
+    """(F b) for a per-momentum 4 x 4 spin matrix field mats (identity on colour) by the 4D FFT."""
+    dims = tuple(int(L) for L in dims)
+    X = np.asarray(b, dtype=np.complex128).reshape(tuple(reversed(dims)) + (4, 3))
+    F = np.fft.fftn(X, axes=(0, 1, 2, 3))
+    F = np.einsum("...ij,...jc->...ic", mats, F)
+    return np.fft.ifftn(F, axes=(0, 1, 2, 3)).reshape(-1)
