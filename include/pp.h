@@ -57,7 +57,12 @@ typedef enum {
 
 typedef enum { PP_F64 = 0, PP_F32 = 1, PP_C64 = 2, PP_C128 = 3 } pp_dtype;
 
-typedef enum { PP_INVSQRT = -1, PP_SQRT = 1 } pp_func;
+typedef enum {
+  PP_INVSQRT = -1,
+  PP_SQRT = 1,
+  PP_SIGN = 2  /* sign(Q) b = Q (Q^2)^{-1/2} b for a PP_WILSON4D_Q2 handle (A = Q^2)
+                  (Sec. 6, Example 2) */
+} pp_func;
 
 typedef enum {
   PP_CHEBYSHEV = 0,      /* Sec. 5.1: interpolant at deg+1 first-kind nodes of [a,b] */
@@ -74,9 +79,12 @@ typedef enum {
   PP_CONVDIFF3D7_UPWIND = 2, /* 7-point upwind -Lap u + c.grad u, c = (c,c,c)>0,
                                 params[0] = c*h; row: (6+3ch) u_c - (1+ch) (u at
                                 i-1, j-1, k-1) - (u at i+1, j+1, k+1)             */
-  PP_WILSON4D_DHD = 3        /* A = D^H D of a Wilson-type operator on a periodic
+  PP_WILSON4D_DHD = 3,       /* A = D^H D of a Wilson-type operator on a periodic
                                 4D lattice, dims = {L0, L1, L2, L3} (see
                                 pp_create_stencil)                                */
+  PP_WILSON4D_Q2 = 4         /* A = Q^2, Q = Gamma_5 D(m_w, mu), the kernel of the
+                                overlap operator's sign function (Sec. 6,
+                                Example 2); params = {m_w, mu}                    */
 } pp_stencil_kind;
 
 typedef enum { PP_LEFT = 0, PP_RIGHT = 1 } pp_side;
@@ -187,6 +195,19 @@ int pp_create_csr(pp_handle *h, int64_t n, const int64_t *rowptr_d, const int32_
  * the order spin * 3 + colour.  A is Hermitian positive definite, so
  * PP_ORTH_AUTO runs Lanczos; the vector work runs on the real view (24 V
  * reals), which is exact for real recurrence coefficients.
+ *
+ * PP_WILSON4D_Q2 (Sec. 6, Example 2): A = Q^2 with Q = Gamma_5 D(m_w, mu),
+ * D the operator above with m0 = m_w = params[0] and chemical potential
+ * mu = params[1] (|mu| <= 20): the hop to x + e_3 (direction 3, gamma_4)
+ * carries e^{mu}, the hop to x - e_3 carries e^{-mu}; Gamma_5 = diag(1, 1,
+ * -1, -1) on spin.  Same links, dims and vector layout.  For mu != 0, Q is
+ * non-Hermitian and the handle runs complex Arnoldi (classical Gram-Schmidt
+ * twice with complex coefficients, complex H_m and small solve, a q with
+ * complex coefficients): PP_ORTH_LANCZOS and two_pass are refused
+ * (PP_ERR_INVALID_ARG), pp_build_poly's PP_LSQ_CONTOUR is unsupported and
+ * PP_CHEBYSHEV needs interval_ab; PP_PREC_MIXED stays in double-word.  For
+ * mu = 0, Q^2 = Q^H Q is Hermitian positive definite and behaves like
+ * PP_WILSON4D_DHD.  pp_apply with PP_SIGN returns sign(Q) b.
  */
 int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const double *params,
                       const void *links_d, int32_t dtype, void *cuda_stream);
@@ -343,8 +364,12 @@ int pp_get_poly_nodes(pp_handle h, int32_t *kind, double *nodes_re_h, double *no
  * b_d.  On PP_ERR_NOT_CONVERGED x_d still holds the last
  * iterate.  stats (host, may be NULL) is filled on return.  Blocks the
  * calling thread at each stopping check (a few bytes read back).
+ * f = PP_SIGN (PP_WILSON4D_Q2 handles, nrhs = 1; Sec. 6, Example 2):
+ * x = sign(Q) b = Q (Q^2)^{-1/2} b, the solve for (Q^2)^{-1/2} b followed by
+ * one FP64 application of Q on the device (stats describe the solve).
  * Errors: PP_ERR_STATE before pp_build_poly, PP_ERR_INVALID_ARG for NULL or
- * aliasing pointers, m_max < 1 or > 4096, tol < 0, non-finite ||b||.
+ * aliasing pointers, m_max < 1 or > 4096, tol < 0, non-finite ||b||;
+ * PP_ERR_UNSUPPORTED for PP_SIGN on another handle kind.
  */
 int pp_apply(pp_handle h, int32_t f, const void *b_d, int64_t nrhs, int32_t m_max, double tol,
              void *x_d, pp_stats *stats);

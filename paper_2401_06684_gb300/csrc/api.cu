@@ -144,26 +144,29 @@ struct DLayout {
   int ldh, nb, K;
 };
 
+// Complex operators keep H, h, the partial sums, X, z and zprev as complex
+// (re, im) pairs: twice the doubles.
 DLayout dlayout(const pp_ctx *c, int m_cap) {
   DLayout L;
+  const size_t cw = c->cplx ? 2 : 1;
   L.ldh = m_cap + 1;
   L.nb = vec_nchunks(c->n);
   L.K = (int)c->qsig.size();
   size_t o = 0;
   L.H = o;
-  o += (size_t)(m_cap + 1) * m_cap;
+  o += cw * (m_cap + 1) * m_cap;
   L.h1 = o;
-  o += (size_t)m_cap + 1;
+  o += cw * (m_cap + 1);
   L.part = o;
-  o += (size_t)L.nb * (m_cap + 1);
+  o += cw * L.nb * (m_cap + 1);
   L.X = o;
-  o += (size_t)L.K * m_cap;
+  o += cw * L.K * m_cap;
   L.tri = o;
   o += (size_t)L.K * m_cap;
   L.z = o;
-  o += (size_t)m_cap;
+  o += cw * m_cap;
   L.zprev = o;
-  o += (size_t)m_cap;
+  o += cw * m_cap;
   L.sig = o;
   o += (size_t)L.K;
   L.wt = o;
@@ -277,6 +280,8 @@ OpDesc make_op(const pp_ctx *c, int arith) {
   for (int d = 0; d < 4; ++d) op.L[d] = c->dims[d];
   op.mass = c->mass;
   op.links = c->links;
+  op.q2 = c->stencil == PP_WILSON4D_Q2 ? 1 : 0;
+  op.mu_c = c->mu_c;
   const size_t esz = arith == AR_F32 ? sizeof(float) : sizeof(double);
   op.tmp = c->ws.tmp ? (void *)((char *)c->ws.tmp + (size_t)(kTmpVecs - 1) * c->ws.ldv * esz) : nullptr;
   op.tile_bdx = c->tile_bdx;
@@ -298,7 +303,10 @@ template <typename T>
 int poly_apply_raw(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3]) {
   const int k = (int)c->coef.size() - 1;
   cudaStream_t s = c->stream;
-  if (k == 0) return vec_scale<T>(in, out, c->n, poly_const(c), nullptr, s);
+  if (k == 0) {
+    if (c->nf.cx) return vec_scale_c<T>(in, out, c->n, c->nf.b[0], c->nf.bi[0], s);
+    return vec_scale<T>(in, out, c->n, poly_const(c), nullptr, s);
+  }
   if (k == 1) return run_op<T>(c, op, in, nullptr, nullptr, out, poly_step_coef(c, 0));
   int i2 = 0, i1 = 1, i0 = 2;  // buffer indices of b_{i+2}, b_{i+1}, free
   RC(run_op<T>(c, op, in, nullptr, nullptr, bufs[i2], poly_step_coef(c, 0)));
@@ -338,6 +346,7 @@ struct Solve {
   int ldh, nb, K;
   bool right, lanczos;
   bool plain = false;  // w = A v_j alone (the node run of Sec. 5.2)
+  bool cx = false;     // complex Gram-Schmidt, H complex (column j at H + 2 j ldh)
   int deg;
   int64_t mvms, ip;
 };
@@ -369,8 +378,22 @@ int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double b
     RC(run_op_timed<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
     S.mvms += 2 * S.deg + 1;
   }
-  double *hcol = S.H + (size_t)j * S.ldh;
   const int nb = S.nb;
+  if (S.cx) {  // complex CGS2: h = V^* w (conjugated), w -= V h, twice
+    double *hc = S.H + (size_t)2 * j * S.ldh;
+    const int J = j + 1;
+    RC(vec_multi_dot_c<T>(V, ldv, J, wv, n, S.part, s));
+    RC(reduce_cols(S.part, nb, 2 * J, 1, S.h1, hc, s));
+    RC(vec_multi_update_c<T>(V, ldv, J, S.h1, wv, n, nullptr, s));
+    RC(vec_multi_dot_c<T>(V, ldv, J, wv, n, S.part, s));
+    RC(reduce_cols(S.part, nb, 2 * J, 2, S.h1, hc, s));
+    RC(vec_multi_update_c<T>(V, ldv, J, S.h1, wv, n, S.part, s));
+    // h_{j+1,j} = ||w|| (real; its imaginary part stays 0)
+    RC(norm_finalize(S.part, nb, hc + 2 * (j + 1), S.scal, hc, 2 * J, bd_rel, J, c->ws.st, s));
+    S.ip += 2 * J + 1;
+    return vec_scale<T>(wv, wv, n, 1.0, S.scal, s);
+  }
+  double *hcol = S.H + (size_t)j * S.ldh;
   if (S.lanczos) {
     RC(vec_dot_partials<T>(wv, vj, n, S.part, nb, s));
     RC(reduce_cols(S.part, nb, 1, 0, hcol + j, nullptr, s));
@@ -444,10 +467,12 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   S.K = L.K;
   S.right = right;
   S.lanczos = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
+  S.cx = c->cplx;
   S.deg = c->degree;
   S.mvms = 0;
   S.ip = 0;
   const int ldh = L.ldh, nb = L.nb, K = L.K;
+  const size_t cw = S.cx ? 2 : 1;
   T1 *V1 = (T1 *)w.V, *Y1 = (T1 *)w.Y;
   T2 *V2 = (T2 *)(mixed ? w.Vf : w.V), *Y2 = (T2 *)(mixed ? w.Yf : w.Y);
   T1 *t1[6];
@@ -465,7 +490,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
 
   PP_CUDA_TRY(cudaEventRecord(w.ev0, s));
   PP_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(DevStatus), s));
-  PP_CUDA_TRY(cudaMemsetAsync(S.H, 0, sizeof(double) * (size_t)ldh * w.m_cap, s));
+  PP_CUDA_TRY(cudaMemsetAsync(S.H, 0, sizeof(double) * cw * ldh * w.m_cap, s));
 
   // right-hand side in the phase-1 arithmetic
   const T1 *rhs;
@@ -539,7 +564,18 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
       RC(krylov_step<T2>(S, op2, V2, Y2, t2, j, std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
     m = j + 1;
     if (m % kchk == 0 || m == m_max) {
-      if (S.lanczos)
+      if (S.cx) {
+        const size_t need = small_hess_scratch_doubles_c(m, K);
+        const size_t smem_bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * 2 * sizeof(double);
+        if (smem_bytes > 200 * 1024 && w.hess_n < need) {
+          if (w.hess) cudaFree(w.hess);
+          w.hess = nullptr;
+          w.hess_n = 0;
+          PP_CUDA_TRY(cudaMalloc(&w.hess, need * sizeof(double)));
+          w.hess_n = need;
+        }
+        RC(small_hess_quad_c(S.H, ldh, m, S.sig, S.wt, K, S.X, w.hess, s));
+      } else if (S.lanczos)
         RC(small_tridiag_quad(S.H, ldh, m, S.sig, S.wt, K, S.X, S.tri, s));
       else {
         const size_t need = small_hess_scratch_doubles(m, K);
@@ -553,7 +589,10 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
         }
         RC(small_hess_quad(S.H, ldh, m, S.sig, S.wt, K, S.X, w.hess, s));
       }
-      RC(small_combine(S.X, K, m, mprev, S.z, S.zprev, tol, w.st, s));
+      if (S.cx)
+        RC(small_combine_c(S.X, K, m, mprev, S.z, S.zprev, tol, w.st, s));
+      else
+        RC(small_combine(S.X, K, m, mprev, S.z, S.zprev, tol, w.st, s));
       mprev = m;
       ++checks;
       PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -582,7 +621,13 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   }
   // f_m = V_m z (left) or Y_m z (right); with a precision switch the leading
   // columns come from the phase-1 basis
-  if (phase == 1) {
+  if (S.cx) {
+    const int k1 = phase == 1 ? m : std::min(m, right ? ny1 : nv1);
+    if (k1 > 0) RC(vec_reconstruct_c<T1>(right ? Y1 : V1, ldv, k1, S.z, x_dev, n, 0, s));
+    if (m > k1)
+      RC(vec_reconstruct_c<T2>((right ? Y2 : V2) + (size_t)k1 * ldv, ldv, m - k1, S.z + 2 * k1, x_dev, n,
+                               k1 > 0 ? 1 : 0, s));
+  } else if (phase == 1) {
     RC(vec_reconstruct<T1>(right ? Y1 : V1, ldv, m, S.z, x_dev, n, 0, s));
   } else {
     const int k1 = std::min(m, right ? ny1 : nv1);
@@ -1058,20 +1103,22 @@ int ritz_arnoldi(pp_ctx *c, int d, std::vector<double> *Hh, int *ldh_out, int *m
   S.right = false;
   S.lanczos = false;
   S.plain = true;
+  S.cx = c->cplx;
   S.deg = 0;
   S.mvms = 0;
   S.ip = 0;
+  const size_t cw = S.cx ? 2 : 1;
   T *V = (T *)w.V;
   T *t[6];
   for (int i = 0; i < 6; ++i) t[i] = (T *)w.tmp + (size_t)i * w.ldv;
   PP_CUDA_TRY(cudaMemsetAsync(w.st, 0, sizeof(DevStatus), s));
-  PP_CUDA_TRY(cudaMemsetAsync(S.H, 0, sizeof(double) * (size_t)L.ldh * w.m_cap, s));
+  PP_CUDA_TRY(cudaMemsetAsync(S.H, 0, sizeof(double) * cw * L.ldh * w.m_cap, s));
   RC(vec_fill_hash<T>(V, c->n, 0x5eedull, s));
   RC(vec_dot_partials<T>(V, V, c->n, S.part, S.nb, s));
   RC(norm_finalize(S.part, S.nb, &w.st->beta0, S.scal, nullptr, 0, 0.0, 0, w.st, s));
   RC(vec_scale<T>(V, V, c->n, 1.0, S.scal, s));
   for (int j = 0; j < d; ++j) RC(krylov_step<T>(S, op, V, nullptr, t, j, kBreakdownRel));
-  Hh->assign((size_t)L.ldh * d, 0.0);
+  Hh->assign(cw * L.ldh * d, 0.0);  // complex operators: (re, im) pairs
   PP_CUDA_TRY(cudaMemcpyAsync(Hh->data(), S.H, sizeof(double) * Hh->size(), cudaMemcpyDeviceToHost, s));
   PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   PP_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1186,6 +1233,46 @@ int set_poly_nodes(pp_ctx *c, int kind, const std::vector<std::complex<double>> 
   return PP_OK;
 }
 
+// Complex operators: q = the interpolant of z^{-1/2} at complex nodes with
+// Re > 0 and no conjugate symmetry (Sec. 5.2 for a complex non-Hermitian A),
+// in Newton form at their Leja order.  Positivity (Re q > 0) is checked at
+// the nodes, the check points and, if hi > lo > 0, on [lo, hi].
+int set_poly_nodes_cx(pp_ctx *c, int kind, const std::vector<std::complex<double>> &nodes, double lo, double hi,
+                      const std::vector<std::complex<double>> *check_pts) {
+  const int d = (int)nodes.size();
+  if (d < 1 || d > kMaxDegree + 1) return pp_set_error(PP_ERR_INVALID_ARG, "need 1 .. 129 nodes");
+  for (int i = 0; i < d; ++i) {
+    const std::complex<double> z = nodes[i];
+    if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return pp_set_error(PP_ERR_INVALID_ARG, "non-finite node");
+    if (!(z.real() > 0.0))
+      return pp_set_error(PP_ERR_NONPRIMARY, "a node with Re <= 0 (A q(A)^2 would need a non-principal root)");
+    for (int j = 0; j < i; ++j)
+      if (nodes[j] == z) return pp_set_error(PP_ERR_NONPRIMARY, "coincident nodes");
+  }
+  NewtonForm F;
+  if (!newton_form_cx(nodes, &F)) return pp_set_error(PP_ERR_NONPRIMARY, "non-finite Newton coefficient");
+  std::vector<std::complex<double>> pts = check_pts ? *check_pts : nodes;
+  double qmin, img_lo, img_hi;
+  newton_scan(F, lo, hi, &pts, &qmin, &img_lo, &img_hi);
+  if (!(qmin > 0.0)) return pp_set_error(PP_ERR_NONPRIMARY, "Re q is not positive at a node or check point");
+  c->poly_kind = kind;
+  c->nf = F;
+  c->coef.resize(d);  // real parts of b_i / cap^i (pp_get_poly)
+  double p = 1.0;
+  for (int i = 0; i < d; ++i) {
+    c->coef[i] = F.b[i] / p;
+    p *= F.cap;
+  }
+  c->degree = d - 1;
+  c->a = lo;
+  c->b = hi;
+  c->img_lo = img_lo;
+  c->img_hi = img_hi;
+  c->image_on_points = true;
+  finish_poly(c, 1e6);
+  return PP_OK;
+}
+
 // Default check interval of node-based kinds: the closed form of the
 // stencils, else the extreme real parts of the reference values lowered by
 // 5 % / raised by 1 % (as for the interval estimate).
@@ -1221,6 +1308,28 @@ int build_ritz(pp_ctx *c, int degree, int kind, const double *ab) {
   const int rc = c->opts.precision == PP_PREC_F64 ? ritz_arnoldi<double>(c, d, &H, &ldh, &m)
                                                   : ritz_arnoldi<dw>(c, d, &H, &ldh, &m);
   if (rc != PP_OK) return rc;
+  if (c->cplx) {  // complex H_d (column j at 2 j ldh): complex QR, no conjugate pairs
+    const double beta = m < d ? 0.0 : H[2 * ((size_t)(m - 1) * ldh + m)];
+    std::vector<std::complex<double>> Hd((size_t)m * m, 0.0), ritz, nodes;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i <= std::min(j + 1, m - 1); ++i)
+        Hd[(size_t)i * m + j] = {H[2 * ((size_t)j * ldh + i)], H[2 * ((size_t)j * ldh + i) + 1]};
+    if (!zhess_eigvals(Hd, m, &ritz)) return pp_set_error(PP_ERR_NONPRIMARY, "Hessenberg QR did not converge");
+    if (kind == PP_HARMONIC_RITZ) {
+      std::vector<std::complex<double>> f;
+      if (!zsolve_adjoint_last(Hd, m, &f)) return pp_set_error(PP_ERR_NONPRIMARY, "H_d is singular");
+      for (int i = 0; i < m; ++i) Hd[(size_t)i * m + m - 1] += beta * beta * f[i];
+      if (!zhess_eigvals(Hd, m, &nodes)) return pp_set_error(PP_ERR_NONPRIMARY, "Hessenberg QR did not converge");
+    } else {
+      nodes = ritz;
+    }
+    double lo = 0.0, hi = 0.0;
+    if (ab) {
+      lo = ab[0];
+      hi = ab[1];
+    }
+    return set_poly_nodes_cx(c, kind, nodes, lo, hi, &ritz);
+  }
   const double beta = m < d ? 0.0 : H[(size_t)(m - 1) * ldh + m];  // h_{m+1,m}
   std::vector<std::complex<double>> ritz, nodes;
   if (c->hermitian) {
@@ -1459,10 +1568,12 @@ int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const d
   if (!h) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle pointer");
   *h = nullptr;
   if (!dims) return pp_set_error(PP_ERR_INVALID_ARG, "NULL dims");
-  if (kind == PP_WILSON4D_DHD) {
+  if (kind == PP_WILSON4D_DHD || kind == PP_WILSON4D_Q2) {
     if (dtype != PP_C128) return pp_set_error(PP_ERR_UNSUPPORTED, "Wilson vectors must be PP_C128");
     if (!links_d) return pp_set_error(PP_ERR_INVALID_ARG, "Wilson operator needs links_d");
     if (!params || !std::isfinite(params[0])) return pp_set_error(PP_ERR_INVALID_ARG, "params[0] = m0 must be finite");
+    if (kind == PP_WILSON4D_Q2 && !(std::isfinite(params[1]) && std::fabs(params[1]) <= 20.0))
+      return pp_set_error(PP_ERR_INVALID_ARG, "params[1] = mu must be finite, |mu| <= 20");
     int64_t V = 1;
     for (int i = 0; i < 4; ++i) {
       if (dims[i] < 1 || dims[i] > (1 << 16)) return pp_set_error(PP_ERR_INVALID_ARG, "bad 4D dims");
@@ -1475,6 +1586,11 @@ int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const d
     c->links = links_d;
     c->mass = params[0];
     c->hermitian = 1;
+    if (kind == PP_WILSON4D_Q2) {  // Q^2 is Hermitian only at mu = 0 (Q = Gamma_5 D(m, 0) is)
+      c->mu_c = params[1];
+      c->hermitian = params[1] == 0.0 ? 1 : 0;
+      c->cplx = params[1] != 0.0;
+    }
     c->stencil = kind;
     c->n = 24 * V;  // real view of 12 complex components per site
     *h = c;
@@ -1548,8 +1664,12 @@ int pp_build_poly(pp_handle c, int32_t degree, int32_t kind, const double *ab) {
   if (degree < 0 || degree > kMaxDegree) return pp_set_error(PP_ERR_INVALID_ARG, "degree out of [0, 128]");
   if (ab && (!(ab[0] > 0.0) || !(ab[1] > ab[0]) || !std::isfinite(ab[1])))
     return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
-  if (kind == PP_LSQ_CONTOUR) return build_lsq(c, degree, ab);
+  if (kind == PP_LSQ_CONTOUR) {
+    if (c->cplx) return pp_set_error(PP_ERR_UNSUPPORTED, "least-squares contours of complex operators");
+    return build_lsq(c, degree, ab);
+  }
   if (kind != PP_CHEBYSHEV) return build_ritz(c, degree, kind, ab);
+  if (c->cplx && !ab) return pp_set_error(PP_ERR_INVALID_ARG, "complex operators need interval_ab for PP_CHEBYSHEV");
   double a, b;
   bool have = false;
   RC(spectral_interval(c, ab, &a, &b, &have));
@@ -1568,7 +1688,8 @@ int pp_build_poly(pp_handle c, int32_t degree, int32_t kind, const double *ab) {
   c->poly_kind = PP_CHEBYSHEV;
   c->coef = cf;
   c->degree = degree;
-  c->image_on_points = false;
+  // a complex spectrum is not bounded by the image of [a,b]: no FP32 switch
+  c->image_on_points = c->cplx;
   c->a = a;
   c->b = b;
   c->img_lo = lo;
@@ -1625,6 +1746,7 @@ int pp_set_poly_nodes(pp_handle c, const double *nodes_re, const double *nodes_i
     return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
   std::vector<std::complex<double>> z(count);
   for (int i = 0; i < count; ++i) z[i] = {nodes_re[i], nodes_im ? nodes_im[i] : 0.0};
+  if (c->cplx) return set_poly_nodes_cx(c, PP_NODES, z, ab ? ab[0] : 0.0, ab ? ab[1] : 0.0, nullptr);
   double lo, hi;
   node_interval(c, ab, z, &lo, &hi);
   return set_poly_nodes(c, PP_NODES, z, lo, hi);
@@ -1644,10 +1766,31 @@ int pp_get_quadrature(pp_handle c, double *sig, double *wt, int32_t cap, int32_t
 int pp_apply(pp_handle c, int32_t f, const void *b_d, int64_t nrhs, int32_t m_max, double tol,
              void *x_d, pp_stats *stats) {
   RC(check_ready(c));
-  if (f != PP_SQRT && f != PP_INVSQRT) return pp_set_error(PP_ERR_INVALID_ARG, "f must be PP_SQRT or PP_INVSQRT");
+  if (f != PP_SQRT && f != PP_INVSQRT && f != PP_SIGN)
+    return pp_set_error(PP_ERR_INVALID_ARG, "f must be PP_SQRT, PP_INVSQRT or PP_SIGN");
+  if (f == PP_SIGN && c->stencil != PP_WILSON4D_Q2)
+    return pp_set_error(PP_ERR_UNSUPPORTED, "PP_SIGN needs a PP_WILSON4D_Q2 handle");
   if (!b_d || !x_d) return pp_set_error(PP_ERR_INVALID_ARG, "NULL vector");
   if (b_d == x_d) return pp_set_error(PP_ERR_INVALID_ARG, "x_d aliases b_d");
   if (nrhs < 1) return pp_set_error(PP_ERR_INVALID_ARG, "nrhs < 1");
+  if (c->cplx) {
+    if (c->opts.orth == PP_ORTH_LANCZOS || c->opts.two_pass)
+      return pp_set_error(PP_ERR_INVALID_ARG, "a non-Hermitian complex operator needs Arnoldi (CGS2)");
+    if (nrhs > 1) return pp_set_error(PP_ERR_UNSUPPORTED, "nrhs > 1 for complex operators");
+  }
+  if (f == PP_SIGN) {  // sign(Q) b = Q (Q^2)^{-1/2} b (Sec. 6, Example 2)
+    if (nrhs != 1) return pp_set_error(PP_ERR_UNSUPPORTED, "PP_SIGN with nrhs > 1");
+    // (Q^2)^{-1/2} b into x_d, then x_d -> scratch, Q scratch -> x_d (FP64)
+    const int rc = pp_apply(c, PP_INVSQRT, b_d, 1, m_max, tol, x_d, stats);
+    if (rc != PP_OK && rc != PP_ERR_NOT_CONVERGED) return rc;
+    double *tmp = (double *)c->ws.tmp;  // kTmpVecs scratch vectors of 8-byte entries, free after the solve
+    PP_CUDA_TRY(cudaMemcpyAsync(tmp, x_d, sizeof(double) * c->n, cudaMemcpyDeviceToDevice, c->stream));
+    const OpDesc op = make_op(c, AR_F64);
+    RC(wilson_q_apply<double>(op, tmp, (double *)x_d, c->stream));
+    PP_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (rc != PP_OK) pp_set_error(rc, "m_max reached before the stopping estimate fell below tol");
+    return rc;
+  }
   if (nrhs > 1) {
     if (c->op_kind != OPK_ST2D && c->op_kind != OPK_ST3D)
       return pp_set_error(PP_ERR_UNSUPPORTED, "nrhs > 1 is supported for the 2D/3D stencil operators");

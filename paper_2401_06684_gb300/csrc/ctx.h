@@ -49,7 +49,11 @@ struct pp_ctx {
   int64_t nnz = 0;
   const void *links = nullptr;  // Wilson: complex64 links (caller-owned)
   double mass = 0.0;
+  double mu_c = 0.0;  // Wilson Q^2: chemical potential
   int hermitian = 0;
+  // complex non-Hermitian operator (Wilson Q^2 with mu_c != 0): complex
+  // Arnoldi coefficients, complex H_m, a complex q
+  bool cplx = false;
   cudaStream_t stream = nullptr;
   pp_opts opts;
   bool have_poly = false;
@@ -74,11 +78,13 @@ struct pp_ctx {
 };
 
 // q(A) v by the Horner scheme of the Newton form (every kind of q unless
-// opts.clenshaw asks for the matrix Clenshaw recurrence of a Chebyshev q).
-inline bool poly_horner(const pp_ctx *c) { return c->poly_kind != 0 || !c->opts.clenshaw; }
+// opts.clenshaw asks for the matrix Clenshaw recurrence of a Chebyshev q;
+// always for complex operators).
+inline bool poly_horner(const pp_ctx *c) { return c->poly_kind != 0 || !c->opts.clenshaw || c->cplx; }
 
 // Coefficients of step t (0 .. degree-1) of q(A) v.
 inline StepCoef poly_step_coef(const pp_ctx *c, int t) {
+  if (c->nf.cx) return horner_step_cx(c->nf.b, c->nf.bi, c->nf.c, c->nf.ci, c->nf.cap, t);
   if (poly_horner(c)) return horner_step(c->nf.b, c->nf.c, c->nf.e, c->nf.cap, t);
   const double s1 = 4.0 / (c->b - c->a), s2 = -2.0 * (c->a + c->b) / (c->b - c->a);
   return clenshaw_coef(c->coef, s1, s2, t);

@@ -34,6 +34,10 @@ struct OpDesc {
   const void *links;
   void *tmp;
   int tile_bdx;  // stencil kernels: threads per block (0 = 128)
+  // Wilson Q^2 (q2 = 1): A = Q^2, Q = Gamma_5 D(mass, mu_c), chemical
+  // potential mu_c on the direction-3 hops
+  int q2 = 0;
+  double mu_c = 0.0;
 };
 
 // out = alpha * (A x) + beta * x  [+ gamma * y]  [+ delta * v]; sub_y switches
@@ -42,6 +46,9 @@ struct StepCoef {
   double alpha, beta, delta;
   bool sub_y, add_v;
   double gamma = -1.0;
+  // imaginary parts of alpha, beta, delta (complex operators only: a step of
+  // q(A) v for a q with complex coefficients)
+  double alpha_im = 0.0, beta_im = 0.0, delta_im = 0.0;
 };
 
 template <typename T>
@@ -82,6 +89,32 @@ inline StepCoef horner_step(const std::vector<double> &b, const std::vector<doub
   return {r, -c[i] * r, b[i], e[i + 1] != 0.0, true, e[i + 1]};
 }
 
+// Step t of q(A) v for a complex Newton form (complex nodes c_i without
+// conjugate symmetry, no e terms): w_k = b_k v, w_i = ((A - c_i)/cap) w_{i+1}
+// + b_i v; the first step folds w_k (complex alpha), later steps read x =
+// w_{i+1} and v.  bi, ci: imaginary parts of b, c.
+inline StepCoef horner_step_cx(const std::vector<double> &b, const std::vector<double> &bi,
+                               const std::vector<double> &c, const std::vector<double> &ci, double cap, int t) {
+  const int k = (int)b.size() - 1;
+  const double r = 1.0 / cap;
+  StepCoef s{r, 0.0, 0.0, false, false, 0.0};
+  if (t == 0) {
+    // alpha = b_k r, beta = b_{k-1} - c_{k-1} b_k r
+    s.alpha = b[k] * r;
+    s.alpha_im = bi[k] * r;
+    s.beta = b[k - 1] - (c[k - 1] * s.alpha - ci[k - 1] * s.alpha_im);
+    s.beta_im = bi[k - 1] - (c[k - 1] * s.alpha_im + ci[k - 1] * s.alpha);
+    return s;
+  }
+  const int i = k - 1 - t;
+  s.beta = -c[i] * r;
+  s.beta_im = -ci[i] * r;
+  s.delta = b[i];
+  s.delta_im = bi[i];
+  s.add_v = true;
+  return s;
+}
+
 // Constants of one stencil row: K0 x_c + Km (sum of -1 neighbours) + Kp (sum
 // of +1 neighbours) [+ Y y] [+ D v], in the vector arithmetic.
 template <typename T>
@@ -114,10 +147,14 @@ int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Ko
                   const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v, cudaStream_t s);
 
 // Wilson D^H D step (wilson.cu): t = D x into op.tmp, then
-// out = alpha D^H t + beta x [- y] [+ delta v]
+// out = alpha D^H t + beta x [- y] [+ delta v].  With op.q2: t = Q x, then
+// out = alpha Q t + beta x + delta v with complex alpha, beta, delta.
 template <typename T>
 int wilson_op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &c,
                    cudaStream_t s);
+// out = Q x, Q = Gamma_5 D(op.mass, op.mu_c) (one launch; op.q2 handles)
+template <typename T>
+int wilson_q_apply(const OpDesc &op, const T *x, T *out, cudaStream_t s);
 
 // ---- vector kernels (vec.cu) ----
 // A vector may be the concatenation of independent problems ("segments"),
@@ -173,6 +210,21 @@ int vec_update_dot(const T *V, int64_t ldv, int J, const double *h, T *w, int64_
 template <typename T>
 int vec_reconstruct(const T *V, int64_t ldv, int m, const double *z, double *x, int64_t n,
                     int accumulate, cudaStream_t s, const Seg &S = Seg(), const int *m_seg = nullptr);
+// ---- complex vectors: n reals = n/2 complex entries, (re, im) interleaved ----
+// partials[chunk*2J + 2c + {0,1}] = sum over the chunk of conj(V_c) w (re, im)
+template <typename T>
+int vec_multi_dot_c(const T *V, int64_t ldv, int J, const T *w, int64_t n, double *partials, cudaStream_t s);
+// w -= V h (h: J complex FP64 values, interleaved); ||w||^2 partials if partials != NULL
+template <typename T>
+int vec_multi_update_c(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n, double *partials,
+                       cudaStream_t s);
+// x = V z or x += V z (z: m complex FP64 values), FP64 output
+template <typename T>
+int vec_reconstruct_c(const T *V, int64_t ldv, int m, const double *z, double *x, int64_t n, int accumulate,
+                      cudaStream_t s);
+// out = (cr + i ci) in
+template <typename T>
+int vec_scale_c(const T *in, T *out, int64_t n, double cr, double ci, cudaStream_t s);
 // out[i] = fixed pseudo-random value in [-1, 1) (instantiated for double, dw)
 template <typename T>
 int vec_fill_hash(T *out, int64_t n, uint64_t seed, cudaStream_t s);
@@ -216,6 +268,13 @@ int small_hess_quad(const double *H, int ldh, int m, const double *sig, const do
 // z = beta0 * sum_k X[k] ; est = ||z - [zprev;0]|| / ||z||; conv = est < tol; zprev <- z
 int small_combine(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol,
                   DevStatus *st, cudaStream_t s, const Seg &S = Seg());
+// Complex Hessenberg H (column j at H + 2 j ldh, entries (re, im)); X, z and
+// zprev complex (2 m doubles per node / vector); one vector (no segments).
+int small_hess_quad_c(const double *H, int ldh, int m, const double *sig, const double *wt, int K, double *X,
+                      double *scratch, cudaStream_t s);
+size_t small_hess_scratch_doubles_c(int m, int K);
+int small_combine_c(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol, DevStatus *st,
+                    cudaStream_t s);
 
 // ---- host-side construction (poly.cpp) ----
 // Chebyshev interpolant of z^{-1/2} at d = degree+1 first-kind nodes of [a,b].
@@ -234,6 +293,10 @@ struct NewtonForm {
   std::vector<double> re, im;  // Leja-ordered nodes, a pair as (Im > 0, conjugate)
   double cap = 1.0;            // a quarter of the diameter of the node set
   std::vector<double> b, c, e;
+  // complex form (cx): nodes without conjugate symmetry, R_{i+1} = ((z -
+  // c_i)/cap) R_i with complex c_i = c + i ci, coefficients b + i bi, e = 0
+  bool cx = false;
+  std::vector<double> bi, ci;
 };
 // false for an empty node set, a pair without its conjugate or a non-finite coefficient
 bool newton_form(const std::vector<std::complex<double>> &nodes, NewtonForm *F);
@@ -250,6 +313,9 @@ std::complex<double> lsq_eval(const std::vector<std::complex<double>> &H,
 bool leja_select(const std::vector<std::complex<double>> &pts, int d, std::vector<std::complex<double>> *out);
 // discretized contour around Ritz values, kept out of |z| < r_min
 std::vector<std::complex<double>> lsq_contour(const std::vector<std::complex<double>> &ritz, double r_min, int npts);
+// complex nodes of a complex operator (no conjugate symmetry): Newton form of
+// the interpolant of z^{-1/2} in reverse Leja order, cx = true
+bool newton_form_cx(const std::vector<std::complex<double>> &nodes, NewtonForm *F);
 std::complex<double> newton_form_eval(const NewtonForm &F, std::complex<double> z);
 // min Re q and the extremes of |z q(z)^2| on [lo, hi] (if hi > lo > 0), at
 // the nodes and at the extra points
@@ -257,6 +323,10 @@ void newton_scan(const NewtonForm &F, double lo, double hi, const std::vector<st
                  double *qmin, double *img_lo, double *img_hi);
 // eigenvalues of a real upper Hessenberg matrix (row-major); false if not converged
 bool hess_eigvals(std::vector<double> H, int n, std::vector<double> *wr, std::vector<double> *wi);
+// eigenvalues of a complex upper Hessenberg matrix (row-major); false if not converged
+bool zhess_eigvals(std::vector<std::complex<double>> H, int n, std::vector<std::complex<double>> *w);
+// f = M^{-*} e_n for a dense complex row-major M; false if singular
+bool zsolve_adjoint_last(const std::vector<std::complex<double>> &M, int n, std::vector<std::complex<double>> *f);
 // f = M^{-T} e_n for a dense row-major M; false if singular
 bool solve_transposed_last(const std::vector<double> &M, int n, std::vector<double> *f);
 // Harmonic Ritz values of SPD tridiagonal T (al, be) and beta = h_{m+1,m};

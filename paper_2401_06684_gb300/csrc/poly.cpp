@@ -95,15 +95,16 @@ using cplx = std::complex<double>;
 // (compared as sums of logarithms; ties go to the earlier node).  Nodes of a
 // real problem come as real values or conjugate pairs: only the member with
 // Im > 0 of a pair is a candidate, and its conjugate follows it at once.
-static std::vector<cplx> leja_order(const std::vector<cplx> &nodes) {
+// pairs = false (a complex operator): every node is a candidate on its own.
+static std::vector<cplx> leja_order(const std::vector<cplx> &nodes, bool pairs = true) {
   std::vector<cplx> rest, out;
   for (const cplx &z : nodes)
-    if (z.imag() >= 0.0) rest.push_back(z);
+    if (!pairs || z.imag() >= 0.0) rest.push_back(z);
   auto take = [&](size_t i) {
     const cplx z = rest[i];
     rest.erase(rest.begin() + (long)i);
     out.push_back(z);
-    if (z.imag() > 0.0) out.push_back(std::conj(z));
+    if (pairs && z.imag() > 0.0) out.push_back(std::conj(z));
   };
   size_t first = 0;
   for (size_t i = 1; i < rest.size(); ++i)
@@ -204,11 +205,56 @@ bool newton_form_fn(const std::vector<cplx> &nodes, const std::function<cplx(cpl
   return true;
 }
 
+// Complex operator: the interpolant of z^{-1/2} at complex nodes with no
+// conjugate symmetry, in Newton form at the nodes in reverse Leja order (as
+// in newton_form_fn), basis N_i = prod_{l<i} (z - x_l)/cap, coefficients
+// b_i = f[x_0..x_i] cap^i.
+bool newton_form_cx(const std::vector<cplx> &nodes, NewtonForm *F) {
+  const std::vector<cplx> lj = leja_order(nodes, false);
+  if (lj.empty() || lj.size() != nodes.size()) return false;
+  const std::vector<cplx> x(lj.rbegin(), lj.rend());
+  const size_t d = x.size();
+  std::vector<cplx> col(d), a(d);
+  for (size_t i = 0; i < d; ++i) col[i] = 1.0 / std::sqrt(x[i]);
+  a[0] = col[0];
+  for (size_t k = 1; k < d; ++k) {
+    for (size_t i = 0; i + k < d; ++i) col[i] = (col[i + 1] - col[i]) / (x[i + k] - x[i]);
+    a[k] = col[0];
+  }
+  double diam = 0.0;
+  for (size_t i = 0; i < d; ++i)
+    for (size_t j = i + 1; j < d; ++j) diam = std::fmax(diam, std::abs(x[i] - x[j]));
+  F->cap = diam > 0.0 ? 0.25 * diam : 1.0;
+  F->cx = true;
+  F->re.resize(d);
+  F->im.resize(d);
+  F->b.resize(d);
+  F->bi.resize(d);
+  F->c.resize(d);
+  F->ci.resize(d);
+  F->e.assign(d, 0.0);
+  double p = 1.0;
+  for (size_t i = 0; i < d; ++i) {
+    const cplx bh = a[i] * p;
+    p *= F->cap;
+    F->re[i] = F->c[i] = x[i].real();
+    F->im[i] = F->ci[i] = x[i].imag();
+    F->b[i] = bh.real();
+    F->bi[i] = bh.imag();
+    if (!std::isfinite(F->b[i]) || !std::isfinite(F->bi[i])) return false;
+  }
+  return true;
+}
+
 // q(z) by the backward recurrence of the basis: u_{k+1} = u_{k+2} = 0,
 // u_i = b_i + ((z - c_i)/cap) u_{i+1} + e_{i+1} u_{i+2}, q(z) = u_0.
 cplx newton_form_eval(const NewtonForm &F, cplx z) {
   const int k = (int)F.b.size() - 1;
   cplx u1 = 0.0, u2 = 0.0;
+  if (F.cx) {
+    for (int i = k; i >= 0; --i) u1 = cplx(F.b[i], F.bi[i]) + (z - cplx(F.c[i], F.ci[i])) / F.cap * u1;
+    return u1;
+  }
   for (int i = k; i >= 0; --i) {
     const cplx u0 = F.b[i] + (z - F.c[i]) / F.cap * u1 + (i + 1 <= k ? F.e[i + 1] : 0.0) * u2;
     u2 = u1;
@@ -244,6 +290,106 @@ void newton_scan(const NewtonForm &F, double lo, double hi, const std::vector<cp
   *qmin = qm;
   *img_lo = l;
   *img_hi = h;
+}
+
+// Eigenvalues of a complex upper Hessenberg matrix (n x n, row-major) by the
+// shifted QR iteration with Givens rotations (Golub & Van Loan, Sec. 7.5,
+// the single-shift form for complex matrices): Wilkinson shift from the
+// trailing 2 x 2 block of the active window, an exceptional shift every 10
+// iterations without deflation, deflation when |h_{k,k-1}| <= eps (|h_kk| +
+// |h_{k-1,k-1}|).  Only the active window is transformed.  false if an
+// eigenvalue has not converged after 60 n iterations.
+bool zhess_eigvals(std::vector<cplx> H, int n, std::vector<cplx> *w) {
+  auto h = [&](int i, int j) -> cplx & { return H[(size_t)i * n + j]; };
+  w->assign(n, 0.0);
+  const double eps = 0x1p-52;
+  int hi = n - 1, iter = 0, total = 0;
+  std::vector<cplx> cs(n), sn(n);
+  while (hi >= 0) {
+    int l = hi;
+    while (l > 0) {
+      const double s = std::abs(h(l - 1, l - 1)) + std::abs(h(l, l));
+      if (std::abs(h(l, l - 1)) <= eps * (s > 0.0 ? s : 1.0)) break;
+      --l;
+    }
+    if (l > 0) h(l, l - 1) = 0.0;
+    if (l == hi) {
+      (*w)[hi] = h(hi, hi);
+      --hi;
+      iter = 0;
+      continue;
+    }
+    if (++total > 60 * n) return false;
+    ++iter;
+    cplx mu;
+    if (iter % 10 == 0) {
+      mu = h(hi, hi) + 0.75 * std::abs(h(hi, hi - 1));
+    } else {
+      const cplx a = h(hi - 1, hi - 1), b = h(hi - 1, hi), c = h(hi, hi - 1), d = h(hi, hi);
+      const cplx half = 0.5 * (a - d);
+      const cplx disc = std::sqrt(half * half + b * c);
+      const cplx m1 = 0.5 * (a + d) + disc, m2 = 0.5 * (a + d) - disc;
+      mu = std::abs(m1 - d) < std::abs(m2 - d) ? m1 : m2;
+    }
+    for (int k = l; k <= hi; ++k) h(k, k) -= mu;
+    // H - mu I = QR: rotations G_k = [[conj c, conj s], [-s, c]] on rows k, k+1
+    for (int k = l; k < hi; ++k) {
+      const cplx x = h(k, k), y = h(k + 1, k);
+      const double r = std::hypot(std::abs(x), std::abs(y));
+      cs[k] = r > 0.0 ? x / r : cplx(1.0);
+      sn[k] = r > 0.0 ? y / r : cplx(0.0);
+      for (int j = k; j <= hi; ++j) {
+        const cplx t1 = h(k, j), t2 = h(k + 1, j);
+        h(k, j) = std::conj(cs[k]) * t1 + std::conj(sn[k]) * t2;
+        h(k + 1, j) = -sn[k] * t1 + cs[k] * t2;
+      }
+    }
+    // RQ + mu I: G_k^* on columns k, k+1
+    for (int k = l; k < hi; ++k) {
+      const int rmax = std::min(k + 1, hi);
+      for (int i = l; i <= rmax; ++i) {
+        const cplx t1 = h(i, k), t2 = h(i, k + 1);
+        h(i, k) = t1 * cs[k] + t2 * sn[k];
+        h(i, k + 1) = -t1 * std::conj(sn[k]) + t2 * std::conj(cs[k]);
+      }
+    }
+    for (int k = l; k <= hi; ++k) h(k, k) += mu;
+  }
+  return true;
+}
+
+// f = M^{-*} e_n: Gaussian elimination with partial pivoting on M^* (complex).
+bool zsolve_adjoint_last(const std::vector<cplx> &M, int n, std::vector<cplx> *f) {
+  std::vector<cplx> A((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[(size_t)i * n + j] = std::conj(M[(size_t)j * n + i]);
+  std::vector<cplx> r(n, 0.0);
+  r[n - 1] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::abs(A[(size_t)i * n + k]) > std::abs(A[(size_t)p * n + k])) p = i;
+    if (!(std::abs(A[(size_t)p * n + k]) > 0.0)) return false;
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(A[(size_t)p * n + j], A[(size_t)k * n + j]);
+      std::swap(r[p], r[k]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      const cplx g = A[(size_t)i * n + k] / A[(size_t)k * n + k];
+      if (g == 0.0) continue;
+      for (int j = k; j < n; ++j) A[(size_t)i * n + j] -= g * A[(size_t)k * n + j];
+      r[i] -= g * r[k];
+    }
+  }
+  f->assign(n, 0.0);
+  for (int i = n - 1; i >= 0; --i) {
+    cplx t = r[i];
+    for (int j = i + 1; j < n; ++j) t -= A[(size_t)i * n + j] * (*f)[j];
+    (*f)[i] = t / A[(size_t)i * n + i];
+  }
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite((*f)[i].real()) || !std::isfinite((*f)[i].imag())) return false;
+  return true;
 }
 
 // Eigenvalues of a real upper Hessenberg matrix (n x n, row-major, overwritten)

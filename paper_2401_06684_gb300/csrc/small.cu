@@ -237,6 +237,131 @@ __global__ void __launch_bounds__(1024) k_combine(const double *__restrict__ X, 
   }
 }
 
+// ---- complex Hessenberg H (complex operators) ----
+struct zc {
+  double re, im;
+};
+__device__ __forceinline__ zc zadd(zc a, zc b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ zc zsub(zc a, zc b) { return {a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ zc zmul(zc a, zc b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+// conj(a) b
+__device__ __forceinline__ zc zcmul(zc a, zc b) { return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re}; }
+// a / b by Smith's algorithm (Smith, "Algorithm 116: Complex division",
+// CACM 5(8), 1962): scale by the larger part of b to avoid overflow
+__device__ __forceinline__ zc zdiv(zc a, zc b) {
+  if (fabs(b.re) >= fabs(b.im)) {
+    const double r = b.im / b.re, d = b.re + b.im * r;
+    return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+  }
+  const double r = b.re / b.im, d = b.re * r + b.im;
+  return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+}
+
+// One CTA per node: (H + s_k I) x = e_1 by complex Givens QR (rotation
+// [[conj c, conj s], [-s, c]] with c = a/r, s = b/r, r = sqrt(|a|^2 + |b|^2)),
+// then back substitution; the working matrix in shared memory or, for large
+// m, in global scratch (column-major, leading dimension m+1).
+__global__ void __launch_bounds__(128) k_hess_quad_c(const double *__restrict__ H, int ldh, int m,
+                                                     const double *__restrict__ sig, const double *__restrict__ wt,
+                                                     double *__restrict__ X, double *__restrict__ gscratch,
+                                                     int use_smem) {
+  pdl_wait();
+  pdl_trigger();
+  extern __shared__ double sm[];
+  const int k = blockIdx.x;
+  const int ld = m + 1;
+  zc *M = reinterpret_cast<zc *>(use_smem ? sm : gscratch + (int64_t)k * 2 * ((int64_t)ld * m + 2 * m));
+  zc *g = M + (int64_t)ld * m;
+  const double s = sig[k];
+  for (int c = 0; c < m; ++c)
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+      zc v = {0.0, 0.0};
+      if (r <= c + 1) v = {H[2 * ((int64_t)c * ldh + r)], H[2 * ((int64_t)c * ldh + r) + 1]};
+      if (r == c) v.re += s;
+      M[(int64_t)c * ld + r] = v;
+    }
+  for (int r = threadIdx.x; r < m; r += blockDim.x) g[r] = {r == 0 ? 1.0 : 0.0, 0.0};
+  __syncthreads();
+  for (int c = 0; c + 1 < m; ++c) {
+    const zc a = M[(int64_t)c * ld + c];
+    const zc b = M[(int64_t)c * ld + c + 1];
+    const double r = hypot(hypot(a.re, a.im), hypot(b.re, b.im));
+    const zc cs = r > 0.0 ? zc{a.re / r, a.im / r} : zc{1.0, 0.0};
+    const zc sn = r > 0.0 ? zc{b.re / r, b.im / r} : zc{0.0, 0.0};
+    __syncthreads();  // everyone has read the pivot pair
+    for (int cc = c + threadIdx.x; cc < m; cc += blockDim.x) {
+      const zc t1 = M[(int64_t)cc * ld + c];
+      const zc t2 = M[(int64_t)cc * ld + c + 1];
+      M[(int64_t)cc * ld + c] = zadd(zcmul(cs, t1), zcmul(sn, t2));
+      M[(int64_t)cc * ld + c + 1] = zsub(zmul(cs, t2), zmul(sn, t1));
+    }
+    if (threadIdx.x == 0) {
+      const zc g1 = g[c], g2 = g[c + 1];
+      g[c] = zadd(zcmul(cs, g1), zcmul(sn, g2));
+      g[c + 1] = zsub(zmul(cs, g2), zmul(sn, g1));
+    }
+    __syncthreads();
+  }
+  for (int c = m - 1; c >= 0; --c) {
+    if (threadIdx.x == 0) g[c] = zdiv(g[c], M[(int64_t)c * ld + c]);
+    __syncthreads();
+    const zc xc = g[c];
+    for (int r = threadIdx.x; r < c; r += blockDim.x) g[r] = zsub(g[r], zmul(M[(int64_t)c * ld + r], xc));
+    __syncthreads();
+  }
+  const double w = wt[k];
+  for (int r = threadIdx.x; r < m; r += blockDim.x) {
+    X[2 * ((int64_t)k * m + r)] = w * g[r].re;
+    X[2 * ((int64_t)k * m + r) + 1] = w * g[r].im;
+  }
+}
+
+// z_i = beta0 sum_k X[k][i] (complex), then the stopping estimate, as k_combine.
+__global__ void __launch_bounds__(1024) k_combine_c(const double *__restrict__ X, int K, int m, int mprev,
+                                                    double *__restrict__ z, double *__restrict__ zprev, double tol,
+                                                    DevStatus *st) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double rd[32], rz[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double beta0 = st->beta0;
+  double d2 = 0.0, z2 = 0.0;
+  for (int i = wid; i < m; i += 32) {
+    double sr = 0.0, si = 0.0;
+    for (int k = lane; k < K; k += 32) {
+      sr += X[2 * ((int64_t)k * m + i)];
+      si += X[2 * ((int64_t)k * m + i) + 1];
+    }
+    sr = warp_sum(sr) * beta0;
+    si = warp_sum(si) * beta0;
+    const double pr = (i < mprev) ? zprev[2 * i] : 0.0, pi = (i < mprev) ? zprev[2 * i + 1] : 0.0;
+    d2 += (sr - pr) * (sr - pr) + (si - pi) * (si - pi);
+    z2 += sr * sr + si * si;
+    if (lane == 0) {
+      z[2 * i] = sr;
+      z[2 * i + 1] = si;
+    }
+  }
+  if (lane == 0) {
+    rd[wid] = d2;
+    rz[wid] = z2;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 2 * m; i += blockDim.x) zprev[i] = z[i];
+  if (threadIdx.x == 0) {
+    double D = 0.0, Z = 0.0;
+    for (int q = 0; q < 32; ++q) {
+      D += rd[q];
+      Z += rz[q];
+    }
+    const double est = (mprev > 0 && Z > 0.0) ? sqrt(D / Z) : INFINITY;
+    st->est = est;
+    st->znorm = sqrt(Z);
+    if (!isfinite(Z)) st->bad = 1;
+    st->conv = (est < tol) ? 1 : 0;
+  }
+}
+
 }  // namespace
 
 int small_tridiag_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
@@ -278,6 +403,32 @@ size_t small_hess_scratch_doubles(int m, int K) {
 int small_combine(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol,
                   DevStatus *st, cudaStream_t s, const Seg &S) {
   PP_CUDA_TRY(pdl_launch(k_combine, dim3(S.nseg), dim3(1024), 0, s, X, K, m, mprev, z, zprev, tol, st, S));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
+int small_hess_quad_c(const double *H, int ldh, int m, const double *sig, const double *wt, int K, double *X,
+                      double *scratch, cudaStream_t s) {
+  const size_t bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * 2 * sizeof(double);
+  const size_t kSmemMax = 200 * 1024;
+  const int use_smem = bytes <= kSmemMax ? 1 : 0;
+  if (use_smem && bytes > 48 * 1024)
+    PP_CUDA_TRY(cudaFuncSetAttribute(k_hess_quad_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  PP_CUDA_TRY(pdl_launch(k_hess_quad_c, dim3(K), dim3(128), use_smem ? bytes : 0, s, H, ldh, m, sig, wt, X, scratch,
+                         use_smem));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
+size_t small_hess_scratch_doubles_c(int m, int K) {
+  return (size_t)K * 2 * ((size_t)(m + 1) * m + 2 * (size_t)m);
+}
+
+int small_combine_c(const double *X, int K, int m, int mprev, double *z, double *zprev, double tol, DevStatus *st,
+                    cudaStream_t s) {
+  PP_CUDA_TRY(pdl_launch(k_combine_c, dim3(1), dim3(1024), 0, s, X, K, m, mprev, z, zprev, tol, st));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;

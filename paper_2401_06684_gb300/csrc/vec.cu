@@ -502,6 +502,217 @@ constexpr int kMaxGrid = 152 * 8;
 
 inline unsigned nchunks(int64_t n) { return (unsigned)((n + CHUNK - 1) / CHUNK); }
 
+// ---- complex vectors ----
+// n reals = n/2 complex entries, (re, im) interleaved.  Same chunks as the
+// real kernels (CHUNK reals = CHUNK/2 entries per block, so the chunk
+// partials line up); thread t owns entries chunk/2 + t + TPB u, u < UC.
+constexpr int UC = U / 2;
+
+// partials[chunk*2J + 2c + {0,1}] = sum over the chunk of conj(V_c) w
+// (re: vr wr + vi wi, im: vr wi - vi wr), for the CG columns of this block.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_multi_dot_c(const T *__restrict__ V, int64_t ldv, int J,
+                                                     const T *__restrict__ w, int64_t n,
+                                                     double *__restrict__ partials) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename acc_of<T>::type;
+  __shared__ double red[2 * CG][TPB / 32];
+  const int c0 = blockIdx.y * CG;
+  const int ncol = min(CG, J - c0);
+  const int64_t e0 = (int64_t)blockIdx.x * (CHUNK / 2) + threadIdx.x;
+  T wr[UC], wi[UC];
+#pragma unroll
+  for (int u = 0; u < UC; ++u) {
+    const int64_t r = 2 * (e0 + (int64_t)u * TPB);
+    wr[u] = (r < n) ? ldg(w + r) : num<T>::zero();
+    wi[u] = (r < n) ? ldg(w + r + 1) : num<T>::zero();
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int CU = sizeof(T) == 4 ? 4 : 2;
+  for (int g0 = 0; g0 < ncol; g0 += CU) {
+    T vr[CU][UC], vi[CU][UC];
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      const T *col = V + (int64_t)(c0 + min(g0 + q, ncol - 1)) * ldv;
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        const int64_t r = 2 * (e0 + (int64_t)u * TPB);
+        const bool ok = r < n && g0 + q < ncol;
+        vr[q][u] = ok ? ldg(col + r) : num<T>::zero();
+        vi[q][u] = ok ? ldg(col + r + 1) : num<T>::zero();
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      if (g0 + q >= ncol) break;
+      A ar, ai;
+      acc_set(ar, num<T>::zero());
+      acc_set(ai, num<T>::zero());
+#pragma unroll
+      for (int u = 0; u < UC; ++u) {
+        acc_add_prod(ar, vr[q][u], wr[u]);
+        acc_add_prod(ar, vi[q][u], wi[u]);
+        acc_add_prod(ai, vr[q][u], wi[u]);
+        acc_add_prod(ai, -vi[q][u], wr[u]);
+      }
+      const T sr = warp_reduce_d(acc_get(ar));
+      const T si = warp_reduce_d(acc_get(ai));
+      if (lane == 0) {
+        red[2 * (g0 + q)][wid] = num<T>::to_d(sr);
+        red[2 * (g0 + q) + 1][wid] = num<T>::to_d(si);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 2 * ncol) {
+    double sum = 0.0;
+    for (int q = 0; q < TPB / 32; ++q) sum += red[threadIdx.x][q];
+    partials[(int64_t)blockIdx.x * 2 * J + 2 * c0 + threadIdx.x] = sum;
+  }
+}
+
+// w -= V h (h: J complex FP64 values); optional ||w||^2 partials
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_multi_update_c(const T *__restrict__ V, int64_t ldv, int J,
+                                                        const double *__restrict__ h, T *__restrict__ w,
+                                                        int64_t n, double *__restrict__ partials) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename acc_of<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  T *hr = reinterpret_cast<T *>(smem_raw);  // -Re h, -Im h, +Im h
+  T *hi = hr + J;
+  T *hni = hi + J;
+  __shared__ double red[TPB / 32];
+  for (int c = threadIdx.x; c < J; c += TPB) {
+    hr[c] = num<T>::from_d(-h[2 * c]);
+    hi[c] = num<T>::from_d(-h[2 * c + 1]);
+    hni[c] = num<T>::from_d(h[2 * c + 1]);
+  }
+  __syncthreads();
+  const int64_t e0 = (int64_t)blockIdx.x * (CHUNK / 2) + threadIdx.x;
+  A ar[UC], ai[UC];
+#pragma unroll
+  for (int u = 0; u < UC; ++u) {
+    const int64_t r = 2 * (e0 + (int64_t)u * TPB);
+    acc_set(ar[u], (r < n) ? w[r] : num<T>::zero());
+    acc_set(ai[u], (r < n) ? w[r + 1] : num<T>::zero());
+  }
+  // (-h)(v) = (-hr vr + hi vi) + i (-hr vi - hi vr) with hr, hi the parts of h
+  for (int c = 0; c < J; ++c) {
+    const T *col = V + (int64_t)c * ldv;
+    T vr[UC], vi[UC];
+#pragma unroll
+    for (int u = 0; u < UC; ++u) {
+      const int64_t r = 2 * (e0 + (int64_t)u * TPB);
+      vr[u] = (r < n) ? ldg(col + r) : num<T>::zero();
+      vi[u] = (r < n) ? ldg(col + r + 1) : num<T>::zero();
+    }
+    const T a = hr[c], b = hi[c], nb = hni[c];
+#pragma unroll
+    for (int u = 0; u < UC; ++u) {
+      acc_add_prod(ar[u], a, vr[u]);
+      acc_add_prod(ar[u], nb, vi[u]);
+      acc_add_prod(ai[u], a, vi[u]);
+      acc_add_prod(ai[u], b, vr[u]);
+    }
+  }
+  A nrm;
+  acc_set(nrm, num<T>::zero());
+#pragma unroll
+  for (int u = 0; u < UC; ++u) {
+    const int64_t r = 2 * (e0 + (int64_t)u * TPB);
+    if (r < n) {
+      const T xr = acc_get(ar[u]), xi = acc_get(ai[u]);
+      w[r] = xr;
+      w[r + 1] = xi;
+      acc_add_prod(nrm, xr, xr);
+      acc_add_prod(nrm, xi, xi);
+    }
+  }
+  if (partials) {
+    const double sum = block_reduce_to_d(acc_get(nrm), red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = sum;
+  }
+}
+
+// x = V z (x += V z with accumulate), z complex, FP64 output
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_reconstruct_c(const T *__restrict__ V, int64_t ldv, int m,
+                                                       const double *__restrict__ z, double *__restrict__ x,
+                                                       int64_t n, int accumulate) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename acc_of<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  T *zr = reinterpret_cast<T *>(smem_raw);
+  T *zi = zr + m;
+  T *zni = zi + m;
+  for (int c = threadIdx.x; c < m; c += TPB) {
+    zr[c] = num<T>::from_d(z[2 * c]);
+    zi[c] = num<T>::from_d(z[2 * c + 1]);
+    zni[c] = num<T>::from_d(-z[2 * c + 1]);
+  }
+  __syncthreads();
+  const int64_t e0 = (int64_t)blockIdx.x * (CHUNK / 2) + threadIdx.x;
+  A ar[UC], ai[UC];
+#pragma unroll
+  for (int u = 0; u < UC; ++u) {
+    acc_set(ar[u], num<T>::zero());
+    acc_set(ai[u], num<T>::zero());
+  }
+  for (int c = 0; c < m; ++c) {
+    const T *col = V + (int64_t)c * ldv;
+    const T a = zr[c], b = zi[c], nb = zni[c];
+#pragma unroll
+    for (int u = 0; u < UC; ++u) {
+      const int64_t r = 2 * (e0 + (int64_t)u * TPB);
+      if (r < n) {
+        const T vr = ldg(col + r), vi = ldg(col + r + 1);
+        acc_add_prod(ar[u], a, vr);
+        acc_add_prod(ar[u], nb, vi);
+        acc_add_prod(ai[u], a, vi);
+        acc_add_prod(ai[u], b, vr);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < UC; ++u) {
+    const int64_t r = 2 * (e0 + (int64_t)u * TPB);
+    if (r < n) {
+      const double pr = accumulate ? x[r] : 0.0, pi = accumulate ? x[r + 1] : 0.0;
+      x[r] = pr + num<T>::to_d(acc_get(ar[u]));
+      x[r + 1] = pi + num<T>::to_d(acc_get(ai[u]));
+    }
+  }
+}
+
+// out = (cr + i ci) in
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_scale_c(const T *__restrict__ in, T *__restrict__ out, int64_t n,
+                                                 double cr, double ci) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename acc_of<T>::type;
+  const T a = num<T>::from_d(cr), b = num<T>::from_d(ci), nb = num<T>::from_d(-ci);
+  const int64_t e0 = (int64_t)blockIdx.x * (CHUNK / 2) + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < UC; ++u) {
+    const int64_t r = 2 * (e0 + (int64_t)u * TPB);
+    if (r < n) {
+      const T xr = ldg(in + r), xi = ldg(in + r + 1);
+      A yr, yi;
+      acc_set_prod(yr, a, xr);
+      acc_add_prod(yr, nb, xi);
+      acc_set_prod(yi, a, xi);
+      acc_add_prod(yi, b, xr);
+      out[r] = acc_get(yr);
+      out[r + 1] = acc_get(yi);
+    }
+  }
+}
+
 }  // namespace
 
 int vec_nchunks(int64_t n) { return (int)nchunks(n); }
@@ -632,6 +843,44 @@ int norm_finalize(const double *partials, int nb, double *beta_out, double *inv_
   return PP_OK;
 }
 
+template <typename T>
+int vec_multi_dot_c(const T *V, int64_t ldv, int J, const T *w, int64_t n, double *partials, cudaStream_t s) {
+  PP_CUDA_TRY(pdl_launch(k_multi_dot_c<T>, dim3(nchunks(n), (J + CG - 1) / CG), dim3(TPB), 0, s, V, ldv, J, w, n,
+                         partials));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+template <typename T>
+int vec_multi_update_c(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n, double *partials,
+                       cudaStream_t s) {
+  const size_t sm = (size_t)3 * J * sizeof(T);
+  if (sm > 48 * 1024)
+    PP_CUDA_TRY(cudaFuncSetAttribute(k_multi_update_c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  PP_CUDA_TRY(pdl_launch(k_multi_update_c<T>, dim3(nchunks(n)), dim3(TPB), sm, s, V, ldv, J, h, w, n, partials));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+template <typename T>
+int vec_reconstruct_c(const T *V, int64_t ldv, int m, const double *z, double *x, int64_t n, int accumulate,
+                      cudaStream_t s) {
+  const size_t sm = (size_t)3 * m * sizeof(T);
+  if (sm > 48 * 1024)
+    PP_CUDA_TRY(cudaFuncSetAttribute(k_reconstruct_c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  PP_CUDA_TRY(pdl_launch(k_reconstruct_c<T>, dim3(nchunks(n)), dim3(TPB), sm, s, V, ldv, m, z, x, n, accumulate));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+template <typename T>
+int vec_scale_c(const T *in, T *out, int64_t n, double cr, double ci, cudaStream_t s) {
+  PP_CUDA_TRY(pdl_launch(k_scale_c<T>, dim3(nchunks(n)), dim3(TPB), 0, s, in, out, n, cr, ci));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
 #define PP_INST(T)                                                                                  \
   template int vec_from_f64<T>(const double *, T *, int64_t, cudaStream_t);                       \
   template int vec_to_f64<T>(const T *, double *, int64_t, cudaStream_t);                         \
@@ -649,7 +898,13 @@ int norm_finalize(const double *partials, int nb, double *beta_out, double *inv_
   template int vec_reconstruct<T>(const T *, int64_t, int, const double *, double *, int64_t, int, \
                                   cudaStream_t, const Seg &, const int *);                        \
   template int vec_update_dot<T>(const T *, int64_t, int, const double *, T *, int64_t, double *,  \
-                                 cudaStream_t, const Seg &);
+                                 cudaStream_t, const Seg &);                                      \
+  template int vec_multi_dot_c<T>(const T *, int64_t, int, const T *, int64_t, double *, cudaStream_t); \
+  template int vec_multi_update_c<T>(const T *, int64_t, int, const double *, T *, int64_t, double *, \
+                                     cudaStream_t);                                               \
+  template int vec_reconstruct_c<T>(const T *, int64_t, int, const double *, double *, int64_t, int, \
+                                    cudaStream_t);                                                \
+  template int vec_scale_c<T>(const T *, T *, int64_t, double, double, cudaStream_t);
 PP_INST(double)
 PP_INST(float)
 PP_INST(dw)

@@ -21,6 +21,13 @@
 //
 // A Clenshaw step out = alpha A x + beta x - y + delta v takes two launches:
 // t = D x, then out = alpha D^H t + beta x - y + delta v.
+//
+// A = Q^2 with Q = Gamma_5 D(m_w, mu) (Sec. 6, Example 2): the same D with
+// mass m_w and chemical potential mu, whose hop to x + 3 (direction 3, gamma_4)
+// carries e^{mu} and whose hop to x - 3 carries e^{-mu}; Gamma_5 =
+// diag(1, 1, -1, -1) on spin.  A step is t = Q x, then out = alpha Q t +
+// beta x + delta v with complex alpha, beta, delta (a q with complex
+// coefficients); Q is non-Hermitian for mu != 0.
 #include "common.cuh"
 #include "internal.h"
 
@@ -116,9 +123,10 @@ __device__ __forceinline__ void color_mul(const float2 (&u)[9], const cx<T> (&h)
   }
 }
 
-// One hop in direction MU: hs += (1 + S gamma_MU) M psi_nb, M = U or U^H.
-template <int MU, int S, bool ADJ, typename A, typename T>
-__device__ __forceinline__ void hop(A *hs, const T *__restrict__ psi, const float2 *__restrict__ link) {
+// One hop in direction MU: hs += (1 + S gamma_MU) M psi_nb, M = U or U^H,
+// times f when SCALE (the chemical-potential factor).
+template <int MU, int S, bool ADJ, bool SCALE, typename A, typename T>
+__device__ __forceinline__ void hop(A *hs, const T *__restrict__ psi, const float2 *__restrict__ link, T f) {
   float2 u[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) u[k] = __ldg(link + k);
@@ -144,6 +152,13 @@ __device__ __forceinline__ void hop(A *hs, const T *__restrict__ psi, const floa
   cx<T> c0[3], c1[3];
   color_mul<ADJ>(u, h0, c0);
   color_mul<ADJ>(u, h1, c1);
+  if constexpr (SCALE) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      c0[c] = {c0[c].re * f, c0[c].im * f};
+      c1[c] = {c1[c].re * f, c1[c].im * f};
+    }
+  }
   acc_row<1, false>(hs, 0, c0);
   acc_row<1, false>(hs, 1, c1);
   if (MU == 0) {  // row2 = S i chi1, row3 = S i chi0
@@ -167,16 +182,29 @@ struct Lat {
   int64_t V;
 };
 
-template <int MU, bool DAG, typename A, typename T>
+// CHEM: the direction-3 hops carry ef (forward) and eb (backward).
+template <int MU, bool DAG, bool CHEM, typename A, typename T>
 __device__ __forceinline__ void hop_pair(A *hs, const T *__restrict__ in, const float2 *__restrict__ U,
-                                         const Lat &lat, int64_t s, int coord) {
+                                         const Lat &lat, int64_t s, int coord, T ef, T eb) {
   const int L = lat.L[MU];
   const int64_t st = lat.st[MU];
   const int64_t fwd = s + (coord + 1 == L ? -(int64_t)(L - 1) * st : st);
   const int64_t bwd = s + (coord == 0 ? (int64_t)(L - 1) * st : -st);
+  constexpr bool SC = CHEM && MU == 3;
   // D: forward (1 - gamma), backward (1 + gamma); D^H: exchanged
-  hop<MU, DAG ? 1 : -1, false>(hs, in + fwd * 24, U + (s * 4 + MU) * 9);
-  hop<MU, DAG ? -1 : 1, true>(hs, in + bwd * 24, U + (bwd * 4 + MU) * 9);
+  hop<MU, DAG ? 1 : -1, false, SC>(hs, in + fwd * 24, U + (s * 4 + MU) * 9, ef);
+  hop<MU, DAG ? -1 : 1, true, SC>(hs, in + bwd * 24, U + (bwd * 4 + MU) * 9, eb);
+}
+
+// Lattice coordinates of site s.
+__device__ __forceinline__ void site_coords(const Lat &lat, int64_t s, int *c) {
+  int64_t r = s;
+  c[0] = (int)(r % lat.L[0]);
+  r /= lat.L[0];
+  c[1] = (int)(r % lat.L[1]);
+  r /= lat.L[1];
+  c[2] = (int)(r % lat.L[2]);
+  c[3] = (int)(r / lat.L[2]);
 }
 
 // out = Kd in + Kh (hop sum of in) [+ Kb x] [+ Ky y] [+ Kv v], one thread per site
@@ -200,10 +228,11 @@ __global__ void __launch_bounds__(128) wilson_step(const T *__restrict__ in, con
   A hs[24];
 #pragma unroll
   for (int k = 0; k < 24; ++k) acc_set(hs[k], num<T>::zero());
-  hop_pair<0, DAG>(hs, in, U, lat, s, c0);
-  hop_pair<1, DAG>(hs, in, U, lat, s, c1);
-  hop_pair<2, DAG>(hs, in, U, lat, s, c2);
-  hop_pair<3, DAG>(hs, in, U, lat, s, c3);
+  const T one = num<T>::from_d(1.0);
+  hop_pair<0, DAG, false>(hs, in, U, lat, s, c0, one, one);
+  hop_pair<1, DAG, false>(hs, in, U, lat, s, c1, one, one);
+  hop_pair<2, DAG, false>(hs, in, U, lat, s, c2, one, one);
+  hop_pair<3, DAG, false>(hs, in, U, lat, s, c3, one, one);
   const int64_t o = s * 24;
 #pragma unroll
   for (int k = 0; k < 24; ++k) {
@@ -214,6 +243,76 @@ __global__ void __launch_bounds__(128) wilson_step(const T *__restrict__ in, con
     if (SUB_Y) acc_add_prod(res, Ky, ldg(y + o + k));
     if (ADD_V) acc_add_prod(res, Kv, ldg(v + o + k));
     out[o + k] = acc_get(res);
+  }
+}
+
+// Complex coefficients of a Q^2 step, with the negated imaginary parts the
+// products need.
+template <typename T>
+struct QCoef {
+  T ar, ai, nai, br, bi, nbi, dr, di, ndi;
+};
+
+// Q = Gamma_5 D(m_w, mu): EPI = false: out = Q in; EPI: out = alpha (Q in)
+// [+ beta x] [+ delta v] with complex alpha, beta, delta.  One thread per site.
+template <typename T, bool EPI, bool AX, bool AV>
+__global__ void __launch_bounds__(128) wilson_q_step(const T *__restrict__ in, const T *__restrict__ x,
+                                                     const T *__restrict__ v, T *__restrict__ out,
+                                                     const float2 *__restrict__ U, Lat lat, T Kd, T Kh, T ef,
+                                                     T eb, QCoef<T> k) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename acc_of<T>::type;
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= lat.V) return;
+  int c[4];
+  site_coords(lat, s, c);
+  A hs[24];
+#pragma unroll
+  for (int q = 0; q < 24; ++q) acc_set(hs[q], num<T>::zero());
+  hop_pair<0, false, true>(hs, in, U, lat, s, c[0], ef, eb);
+  hop_pair<1, false, true>(hs, in, U, lat, s, c[1], ef, eb);
+  hop_pair<2, false, true>(hs, in, U, lat, s, c[2], ef, eb);
+  hop_pair<3, false, true>(hs, in, U, lat, s, c[3], ef, eb);
+  const int64_t o = s * 24;
+#pragma unroll
+  for (int q = 0; q < 12; ++q) {  // complex component q = spin * 3 + colour
+    A tr, ti;
+    acc_set_prod(tr, Kd, ldg(in + o + 2 * q));
+    acc_add_prod(tr, Kh, acc_raw(hs[2 * q]));
+    acc_set_prod(ti, Kd, ldg(in + o + 2 * q + 1));
+    acc_add_prod(ti, Kh, acc_raw(hs[2 * q + 1]));
+    T dr = acc_get(tr), di = acc_get(ti);
+    if (q >= 6) {  // Gamma_5: spins 2 and 3 change sign
+      dr = -dr;
+      di = -di;
+    }
+    if constexpr (!EPI) {
+      out[o + 2 * q] = dr;
+      out[o + 2 * q + 1] = di;
+    } else {
+      A rr, ri;
+      acc_set_prod(rr, k.ar, dr);
+      acc_add_prod(rr, k.nai, di);
+      acc_set_prod(ri, k.ar, di);
+      acc_add_prod(ri, k.ai, dr);
+      if constexpr (AX) {
+        const T xr = ldg(x + o + 2 * q), xi = ldg(x + o + 2 * q + 1);
+        acc_add_prod(rr, k.br, xr);
+        acc_add_prod(rr, k.nbi, xi);
+        acc_add_prod(ri, k.br, xi);
+        acc_add_prod(ri, k.bi, xr);
+      }
+      if constexpr (AV) {
+        const T vr = ldg(v + o + 2 * q), vi = ldg(v + o + 2 * q + 1);
+        acc_add_prod(rr, k.dr, vr);
+        acc_add_prod(rr, k.ndi, vi);
+        acc_add_prod(ri, k.dr, vi);
+        acc_add_prod(ri, k.di, vr);
+      }
+      out[o + 2 * q] = acc_get(rr);
+      out[o + 2 * q + 1] = acc_get(ri);
+    }
   }
 }
 
@@ -245,11 +344,7 @@ int launch(const T *in, const T *x, const T *y, const T *v, T *out, const float2
   return PP_OK;
 }
 
-}  // namespace
-
-template <typename T>
-int wilson_op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &c,
-                   cudaStream_t s) {
+Lat make_lat(const OpDesc &op) {
   Lat lat;
   lat.V = 1;
   for (int d = 0; d < 4; ++d) {
@@ -257,6 +352,62 @@ int wilson_op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out,
     lat.st[d] = lat.V;
     lat.V *= op.L[d];
   }
+  return lat;
+}
+
+template <typename T, bool EPI, bool AX, bool AV>
+int launch_q(const OpDesc &op, const T *in, const T *x, const T *v, T *out, const StepCoef &c, cudaStream_t s) {
+  const Lat lat = make_lat(op);
+  const int bs = 128;
+  const int64_t nb = (lat.V + bs - 1) / bs;
+  QCoef<T> k;
+  k.ar = host_c<T>(c.alpha);
+  k.ai = host_c<T>(c.alpha_im);
+  k.nai = host_c<T>(-c.alpha_im);
+  k.br = host_c<T>(c.beta);
+  k.bi = host_c<T>(c.beta_im);
+  k.nbi = host_c<T>(-c.beta_im);
+  k.dr = host_c<T>(c.delta);
+  k.di = host_c<T>(c.delta_im);
+  k.ndi = host_c<T>(-c.delta_im);
+  PP_CUDA_TRY(pdl_launch(wilson_q_step<T, EPI, AX, AV>, dim3((unsigned)nb), dim3(bs), 0, s, in, x, v, out,
+                         (const float2 *)op.links, lat, host_c<T>(4.0 + op.mass), host_c<T>(-0.5),
+                         host_c<T>(std::exp(op.mu_c)), host_c<T>(std::exp(-op.mu_c)), k));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
+// t = Q x, then out = alpha Q t [+ beta x] [+ delta v] (complex coefficients)
+template <typename T>
+int wilson_q2_step(const OpDesc &op, const T *x, const T *v, T *out, const StepCoef &c, cudaStream_t s) {
+  if (c.sub_y) return pp_set_error(PP_ERR_UNSUPPORTED, "Q^2 step with a y term");
+  T *t = (T *)op.tmp;
+  int rc = launch_q<T, false, false, false>(op, x, nullptr, nullptr, t, c, s);
+  if (rc) return rc;
+  const bool ax = c.beta != 0.0 || c.beta_im != 0.0;
+  if (ax && c.add_v) return launch_q<T, true, true, true>(op, t, x, v, out, c, s);
+  if (ax) return launch_q<T, true, true, false>(op, t, x, v, out, c, s);
+  if (c.add_v) return launch_q<T, true, false, true>(op, t, x, v, out, c, s);
+  return launch_q<T, true, false, false>(op, t, x, v, out, c, s);
+}
+
+}  // namespace
+
+template <typename T>
+int wilson_q_apply(const OpDesc &op, const T *x, T *out, cudaStream_t s) {
+  const StepCoef c{1.0, 0.0, 0.0, false, false};
+  return launch_q<T, false, false, false>(op, x, nullptr, nullptr, out, c, s);
+}
+template int wilson_q_apply<double>(const OpDesc &, const double *, double *, cudaStream_t);
+template int wilson_q_apply<float>(const OpDesc &, const float *, float *, cudaStream_t);
+template int wilson_q_apply<dw>(const OpDesc &, const dw *, dw *, cudaStream_t);
+
+template <typename T>
+int wilson_op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const StepCoef &c,
+                   cudaStream_t s) {
+  if (op.q2) return wilson_q2_step<T>(op, x, v, out, c, s);
+  const Lat lat = make_lat(op);
   const float2 *U = (const float2 *)op.links;
   T *t = (T *)op.tmp;
   const double md = 4.0 + op.mass;

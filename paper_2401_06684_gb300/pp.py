@@ -23,9 +23,9 @@ PP_ERR_STATE = -8
 PP_ERR_UNSUPPORTED = -9
 
 PP_F64, PP_F32, PP_C64, PP_C128 = 0, 1, 2, 3
-PP_INVSQRT, PP_SQRT = -1, 1
+PP_INVSQRT, PP_SQRT, PP_SIGN = -1, 1, 2
 PP_CHEBYSHEV, PP_RITZ_LEJA, PP_HARMONIC_RITZ, PP_LSQ_CONTOUR, PP_NODES = 0, 1, 2, 3, 4
-PP_LAPLACE2D5, PP_LAPLACE3D7, PP_CONVDIFF3D7_UPWIND, PP_WILSON4D_DHD = 0, 1, 2, 3
+PP_LAPLACE2D5, PP_LAPLACE3D7, PP_CONVDIFF3D7_UPWIND, PP_WILSON4D_DHD, PP_WILSON4D_Q2 = 0, 1, 2, 3, 4
 PP_LEFT, PP_RIGHT = 0, 1
 PP_PREC_F64, PP_PREC_DW, PP_PREC_MIXED = 0, 1, 2
 PP_ORTH_AUTO, PP_ORTH_LANCZOS, PP_ORTH_CGS2 = 0, 1, 2

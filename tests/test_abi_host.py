@@ -120,6 +120,27 @@ def test_argument_validation():
     assert e.value.status == pp.PP_ERR_INVALID_ARG
     hw = pp.pp_create_stencil(pp.PP_WILSON4D_DHD, (4, 4, 4, 4), [0.1], links=64, dtype=pp.PP_C128)
     pp.pp_destroy(hw)
+    # Wilson Q^2 (sign function): params = {m_w, mu}, mu finite
+    with pytest.raises(pp.PPError) as e:
+        pp.pp_create_stencil(pp.PP_WILSON4D_Q2, (4, 4, 4, 4), [-1.4, float("nan")], links=64, dtype=pp.PP_C128)
+    assert e.value.status == pp.PP_ERR_INVALID_ARG
+    hq = pp.pp_create_stencil(pp.PP_WILSON4D_Q2, (4, 4, 4, 4), [-1.4, 0.3], links=64, dtype=pp.PP_C128)
+    try:
+        with pytest.raises(pp.PPError) as e:  # no contours for complex operators
+            pp.pp_build_poly(hq, 4, pp.PP_LSQ_CONTOUR)
+        assert e.value.status == pp.PP_ERR_UNSUPPORTED
+        with pytest.raises(pp.PPError) as e:  # Chebyshev needs the interval
+            pp.pp_build_poly(hq, 4)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+        pp.pp_build_poly(hq, 4, interval_ab=(0.1, 30.0))  # host work only
+        o = pp.pp_default_opts()
+        o.orth = pp.PP_ORTH_LANCZOS
+        pp.pp_set_opts(hq, o)
+        with pytest.raises(pp.PPError) as e:  # non-Hermitian complex: Arnoldi only
+            pp.pp_apply(hq, pp.PP_SIGN, 1024, 2048)
+        assert e.value.status == pp.PP_ERR_INVALID_ARG
+    finally:
+        pp.pp_destroy(hq)
     h = pp.pp_create_stencil(pp.PP_LAPLACE3D7, (4, 4, 4))
     try:
         with pytest.raises(pp.PPError) as e:  # apply before build_poly
@@ -161,6 +182,9 @@ def test_argument_validation():
         with pytest.raises(pp.PPError) as e:
             pp.pp_apply(h, 3, 1024, 2048)
         assert e.value.status == pp.PP_ERR_INVALID_ARG
+        with pytest.raises(pp.PPError) as e:  # the sign function needs a Q^2 handle
+            pp.pp_apply(h, pp.PP_SIGN, 1024, 2048)
+        assert e.value.status == pp.PP_ERR_UNSUPPORTED
         with pytest.raises(pp.PPError) as e:
             pp.pp_apply(h, pp.PP_SQRT, 1024, 2048, m_max=0)
         assert e.value.status == pp.PP_ERR_INVALID_ARG
@@ -379,3 +403,27 @@ def test_lsq_validation_and_segment():
     finally:
         pp.pp_destroy(hl)
         pp.pp_destroy(hc)
+
+
+def test_complex_nodes_newton_form_matches_oracle():
+    # complex operator (Q^2 handle, host work only): unpaired complex nodes in
+    # reverse Leja order, and the Newton coefficients of the interpolant of
+    # z^{-1/2} at them (real parts b_i / cap^i = a_i) against the oracle
+    pp = load()
+    rng = np.random.default_rng(5)
+    z = rng.uniform(0.5, 6.0, 9) + 1j * rng.uniform(-1.5, 1.5, 9)
+    hq = pp.pp_create_stencil(pp.PP_WILSON4D_Q2, (4, 4, 4, 4), [-1.4, 0.3], links=64, dtype=pp.PP_C128)
+    try:
+        pp.pp_set_poly_nodes(hq, z)
+        kind, x, cap = pp.pp_get_poly_nodes(hq)
+        assert kind == pp.PP_NODES
+        ref = ritz.leja_order(z, pairs=False)[::-1]
+        assert np.array_equal(x, ref)
+        a = ritz.newton_coeffs(ref)
+        coef, _, _ = pp.pp_get_poly(hq)
+        assert np.max(np.abs(coef - a.real)) < 1e-12 * np.max(np.abs(a))
+        with pytest.raises(pp.PPError) as e:  # Re <= 0 is refused
+            pp.pp_set_poly_nodes(hq, np.array([1.0 + 1j, -0.5 + 0.2j]))
+        assert e.value.status == pp.PP_ERR_NONPRIMARY
+    finally:
+        pp.pp_destroy(hq)
