@@ -57,8 +57,17 @@ WORKLOADS = {
     "wilson16x32": ("A = D^H D, Wilson-type D on a periodic 16^3x32 lattice (n=1572864 complex), Haar "
                     "SU(3) links seed 1, m0=0.1, f=A^(-1/2), Lanczos; 1e-8 target, estimate tolerance 1e-9",
                     "wilson4d", (16, 16, 16, 32), -1, 16, 1e-9, "lanczos"),
+    "sign16x32": ("sign(Q) b = Q (Q^2)^(-1/2) b, Q = Gamma_5 D_w(m_w=-1.4, mu=0.3) non-Hermitian (chemical "
+                  "potential on the 32-site direction), periodic 16^3x32 lattice (n=1572864 complex), Haar SU(3) "
+                  "links seed 1; complex Arnoldi CGS2, Ritz polynomial of degree 31 (d = 32), stopping check "
+                  "every 64/d = 2 iterations; 1e-8 estimate tolerance", "wilsonq2", (16, 16, 16, 32), 2, 31,
+                  1e-8, "cgs2"),
+    "sign32x64": ("sign(Q) b as sign16x32 on the 32^3x64 lattice of Sec. 6, Example 2 (n=25165824 complex), "
+                  "Ritz polynomial of degree 63 (d = 64), stopping check every iteration; 1e-8 estimate "
+                  "tolerance", "wilsonq2", (32, 32, 32, 64), 2, 63, 1e-8, "cgs2"),
 }
 WILSON_M0 = 0.1
+SIGN_MW, SIGN_MU = -1.4, 0.3  # Sec. 6, Example 2
 
 
 def parse():
@@ -96,7 +105,7 @@ def parse():
         a.n *= d
     if a.kind == "batch":
         a.n = 0
-    a.complex = a.kind == "wilson4d"
+    a.complex = a.kind in ("wilson4d", "wilsonq2")
     if a.complex:
         a.n *= 12  # complex components per site
     return a
@@ -143,10 +152,10 @@ def config(args, ws):
             + (", two-pass Lanczos" if args.two_pass else ""),
             "grid": list(args.dims), "n": args.n,
             "ch": 0.5 if args.kind == "convdiff3d7" else 0.0,
-            "func": "sqrt" if args.func > 0 else "invsqrt",
+            "func": {1: "sqrt", -1: "invsqrt", 2: "sign"}[args.func],
             "poly": ({"ritz": "ritz (leja/newton)", "harmonic": "harmonic ritz (leja/newton)",
                       "lsq": "least squares on the Ritz-value contour"}[args.poly or "ritz"]
-                     if args.kind == "graphcsr" else "chebyshev"), "degree": args.degree,
+                     if args.kind in ("graphcsr", "wilsonq2") else "chebyshev"), "degree": args.degree,
             "q_eval": "clenshaw" if args.clenshaw else "newton-horner at Leja-ordered nodes",
             "side": "left", "orth": args.orth, "tol": args.tol, "rhs_per_rank": 1,
             "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MB write)"}
@@ -170,6 +179,11 @@ def oracle_timed(args, m_max, tol, seed=0):
         DH = D.conj().T.tocsr()
         mv = lambda v: DH @ (D @ v)  # noqa: E731
         a, b = 0.01, 96.0  # interval only shapes q; the per-iteration cost does not depend on it
+        rhs = synth.spinor_field(args.dims, seed)
+    elif args.kind == "wilsonq2":
+        from oracle import wilson
+        Q = wilson.q_matrix(args.dims, synth.wilson_links(args.dims, 1), SIGN_MW, SIGN_MU)
+        mv = lambda v: Q @ (Q @ v)  # noqa: E731
         rhs = synth.spinor_field(args.dims, seed)
     elif args.kind == "graphcsr":
         import scipy.sparse as sp
@@ -199,6 +213,13 @@ def oracle_timed(args, m_max, tol, seed=0):
         r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, q=qf, side="left", m_max=m_max, tol=tol,
                               k_chk=max(1, 32 // (args.degree + 1)), orth=args.orth,
                               on_iter=lambda j: stamps.append(time.perf_counter()))
+    elif args.kind == "wilsonq2":  # Example 2: complex Ritz q (set-up), (Q^2)^{-1/2} b, then Q
+        from oracle import ritz, sign
+        x, an = ritz.ritz_poly(mv, rhs.shape[0], args.degree, complex_=True, hermitian=False)
+        qf = (args.degree, lambda v: ritz.newton_apply(mv, an, x, v))
+        _, r = sign.sign_krylov(lambda v: Q @ v, rhs, q=qf, side="left", m_max=m_max, tol=tol,
+                                k_chk=max(1, 64 // (args.degree + 1)), orth=args.orth,
+                                on_iter=lambda j: stamps.append(time.perf_counter()))
     else:
         c = cheb.interp_coeffs(a, b, args.degree + 1)
         r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, c, (a, b), side="left", m_max=m_max, tol=tol,
@@ -213,7 +234,8 @@ def oracle_timed(args, m_max, tol, seed=0):
 
 def cpu_sample(args, m_full):
     """The oracle on the full workload for a few iterations, extrapolated to m_full iterations."""
-    k = max(1, args.cpu_iters)
+    # the sign workload's oracle iteration takes 2 d + 1 sparse Q^2 products (about a minute): one
+    k = 1 if args.kind == "wilsonq2" else max(1, args.cpu_iters)
     r, setup, iters = oracle_timed(args, k, 0.0)
     t_iter = statistics.mean(iters)
     t_solve = setup + m_full * t_iter
@@ -378,6 +400,11 @@ def run_ours(args):
             hh = pp.pp_create_stencil(pp.PP_WILSON4D_DHD, dims, [WILSON_M0], links=keep[-1],
                                       dtype=pp.PP_C128, stream=stream)
             pp.pp_build_poly(hh, degree)
+        elif args.kind == "wilsonq2":  # Example 2: Q^2 with the chemical potential, q at Ritz values
+            keep.append(torch.from_numpy(synth.wilson_links(dims, 1)).cuda())
+            hh = pp.pp_create_stencil(pp.PP_WILSON4D_Q2, dims, [SIGN_MW, SIGN_MU], links=keep[-1],
+                                      dtype=pp.PP_C128, stream=stream)
+            pp.pp_build_poly(hh, degree, pp.PP_RITZ_LEJA)
         elif args.kind == "graphcsr":  # Example 3: non-Hermitian CSR, q at Ritz values
             rp, col, val = graph_csr(n)
             keep.extend(torch.from_numpy(a).cuda() for a in (rp, col, val))
@@ -402,6 +429,8 @@ def run_ours(args):
     o.clenshaw = 1 if args.clenshaw else 0
     if args.kind == "graphcsr":  # Example 3 checks every 32/d iterations
         o.check_every = max(1, 32 // (args.degree + 1))
+    if args.kind == "wilsonq2":  # Example 2 checks every 64/d iterations
+        o.check_every = max(1, 64 // (args.degree + 1))
     pp.pp_set_opts(h, o)
     if args.autotune:
         args.degree = pp.pp_autotune(h, args.tol, 64)
@@ -429,7 +458,11 @@ def run_ours(args):
     # double-word solve with the stopping estimate below 1e-13
     s2 = torch.empty_like(x)
     solve()
-    if args.func > 0:
+    if args.func == pp.PP_SIGN:
+        ref_id = b
+        pp.pp_apply(h, pp.PP_SIGN, x, s2, m_max=m_max, tol=args.tol)
+        id_name = "identity_sign_sign_vs_b"
+    elif args.func > 0:
         ref_id = torch.empty_like(x)
         pp.pp_op_apply(h, b, ref_id)
         pp.pp_apply(h, pp.PP_SQRT, x, s2, m_max=m_max, tol=args.tol)
@@ -445,7 +478,9 @@ def run_ours(args):
     o_t.two_pass = o.two_pass
     o_t.clenshaw = o.clenshaw
     pp.pp_set_opts(h, o_t)
-    pp.pp_apply(h, args.func, b, s2, m_max=max(m_max, 1000), tol=1e-13)
+    # basis of at most ~100 GB for the tight solve (the paper-size lattice keeps the run's m_max)
+    tight_m = max(m_max, 1000) if esz * n * 1000 < 100e9 else m_max
+    pp.pp_apply(h, args.func, b, s2, m_max=tight_m, tol=1e-13)
     pp.pp_set_opts(h, o)
     solve()
     torch.cuda.synchronize()
@@ -532,7 +567,8 @@ def run_ours(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "kernel": "%s (operator + %s update)" % (
-                             {"graphcsr": "csr_step", "laplace2d5csr": "csr_step", "wilson4d": "wilson_step"}.get(
+                             {"graphcsr": "csr_step", "laplace2d5csr": "csr_step", "wilson4d": "wilson_step",
+                              "wilsonq2": "wilson_q_step"}.get(
                                  args.kind, "st_step"), "Clenshaw" if args.clenshaw else "Horner"),
                          "peak_source": peak_src,
                          "timing": "CUDA events around each run of consecutive operator launches "

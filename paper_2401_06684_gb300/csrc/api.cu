@@ -105,7 +105,7 @@ double step_bytes(const pp_ctx *c, const StepCoef &k, double esz) {
     // t = D x (read x, write t) and out = alpha D^H t + beta x ...: the second
     // launch reads t and x; both read the links (288 bytes per site)
     const double sites = (double)c->n / 24.0;
-    bytes += (2.0 + (k.beta != 0.0 ? 1.0 : 0.0)) * esz * (double)c->n + 2.0 * 288.0 * sites;
+    bytes += (2.0 + (k.beta != 0.0 || k.beta_im != 0.0 ? 1.0 : 0.0)) * esz * (double)c->n + 2.0 * 288.0 * sites;
   }
   return bytes;
 }
