@@ -19,6 +19,16 @@
 // ones with the constant factors of the projector.  The vector arithmetic is
 // FP64, double-word pairs or FP32 (the link entries are exact in all three).
 //
+// Two threads (adjacent lanes) share a site: the thread of parity `half`
+// forms h_half only (it reads the two neighbour spin rows that feed it),
+// accumulates its upper output row (spin half) and partial sums of both
+// lower rows, and the pair exchanges the partial lower rows once at the end
+// (one shuffle per entry).  The two threads run the same instructions (the
+// projector's signs and row choices are runtime values of `half`), and each
+// holds a third fewer accumulators than a thread owning the whole site
+// (double-word: 139 -> about 90 registers, so more warps per SM hide the
+// latency of the dependent double-word operations).
+//
 // A Clenshaw step out = alpha A x + beta x - y + delta v takes two launches:
 // t = D x, then out = alpha D^H t + beta x - y + delta v.
 //
@@ -71,33 +81,6 @@ __device__ __forceinline__ cx<T> ld_c(const T *p, int k) {
   return {ldg(p + 2 * k), ldg(p + 2 * k + 1)};
 }
 
-// hs[(row * 3 + col) * 2 + {0, 1}] += f * chi[col], f in {1, -1, i, -i} = (FI ? i : 1) * FS
-template <int FS, bool FI, typename A, typename T>
-__device__ __forceinline__ void acc_row(A *hs, int row, const cx<T> (&chi)[3]) {
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    A &r = hs[(row * 3 + c) * 2 + 0];
-    A &i = hs[(row * 3 + c) * 2 + 1];
-    if (!FI) {
-      if (FS > 0) {
-        acc_add(r, chi[c].re);
-        acc_add(i, chi[c].im);
-      } else {
-        acc_sub(r, chi[c].re);
-        acc_sub(i, chi[c].im);
-      }
-    } else {  // FS i (re + i im) = -FS im + i FS re
-      if (FS > 0) {
-        acc_sub(r, chi[c].im);
-        acc_add(i, chi[c].re);
-      } else {
-        acc_add(r, chi[c].im);
-        acc_sub(i, chi[c].re);
-      }
-    }
-  }
-}
-
 // chi[a] = sum_b M_ab h[b] with M = U (ADJ = false) or U^H (ADJ = true)
 template <bool ADJ, typename T>
 __device__ __forceinline__ void color_mul(const float2 (&u)[9], const cx<T> (&h)[3], cx<T> (&chi)[3]) {
@@ -123,57 +106,120 @@ __device__ __forceinline__ void color_mul(const float2 (&u)[9], const cx<T> (&h)
   }
 }
 
-// One hop in direction MU: hs += (1 + S gamma_MU) M psi_nb, M = U or U^H,
-// times f when SCALE (the chemical-potential factor).
+// (neg ? -a : a) by flipping sign bits (integer pipe, no floating-point
+// operation and no select between two computed values)
+__device__ __forceinline__ float neg_if(float a, bool neg) {
+  return __int_as_float(__float_as_int(a) ^ (neg ? 0x80000000u : 0u));
+}
+__device__ __forceinline__ double neg_if(double a, bool neg) {
+  const unsigned long long m = neg ? 0x8000000000000000ull : 0ull;
+  return __longlong_as_double((long long)((unsigned long long)__double_as_longlong(a) ^ m));
+}
+__device__ __forceinline__ dw neg_if(dw a, bool neg) {
+  const unsigned m = neg ? 0x80000000u : 0u;
+  return {__int_as_float(__float_as_int(a.hi) ^ m), __int_as_float(__float_as_int(a.lo) ^ m)};
+}
+
+// The rows the thread of parity `half` owns, [colour * 2 + {re, im}]: u the
+// upper row (spin half), p the lower row 2 + half, x the lower row 3 - half
+// (partial: its sum goes to the partner thread).
+template <typename A>
+struct Rows {
+  A u[6], p[6], x[6];
+};
+
+// dst += (neg ? -1 : 1) (IM ? i : 1) c
+template <bool IM, typename A, typename T>
+__device__ __forceinline__ void acc_c(A *dst, const cx<T> (&c)[3], bool neg) {
+#pragma unroll
+  for (int col = 0; col < 3; ++col) {
+    const T re = IM ? -c[col].im : c[col].re;  // i (re + i im) = -im + i re
+    const T im = IM ? c[col].re : c[col].im;
+    acc_add(dst[2 * col], neg_if(re, neg));
+    acc_add(dst[2 * col + 1], neg_if(im, neg));
+  }
+}
+
+// One hop in direction MU, the thread's half: with the projector
+// (1 + S gamma_MU) the half spinor is h_half = p_half + sg (i) p_lo of the
+// neighbour (MU 0: h0 = p0 - S i p3, h1 = p1 - S i p2; MU 1: h0 = p0 - S p3,
+// h1 = p1 + S p2; MU 2: h0 = p0 - S i p2, h1 = p1 + S i p3; MU 3: h0 = p0 +
+// S p2, h1 = p1 + S p3), chi = M h_half (M = U or U^H, times f when SCALE)
+// goes to the upper row, and the projector's lower rows get (MU 0: row 3 +=
+// S i chi0, row 2 += S i chi1; MU 1: row 3 -= S chi0, row 2 += S chi1; MU 2:
+// row 2 += S i chi0, row 3 -= S i chi1; MU 3: row 2 += S chi0, row 3 += S chi1).
 template <int MU, int S, bool ADJ, bool SCALE, typename A, typename T>
-__device__ __forceinline__ void hop(A *hs, const T *__restrict__ psi, const float2 *__restrict__ link, T f) {
+__device__ __forceinline__ void hop(Rows<A> &R, const T *__restrict__ psi, const float2 *__restrict__ link, T f,
+                                    int half) {
   float2 u[9];
 #pragma unroll
   for (int k = 0; k < 9; ++k) u[k] = __ldg(link + k);
-  cx<T> h0[3], h1[3];
+  constexpr bool IM = MU == 0 || MU == 2;
+  const int lo = MU <= 1 ? 3 - half : 2 + half;
+  const bool nsg = MU == 0 ? (S > 0) : MU == 3 ? (S < 0) : (half ? S < 0 : S > 0);
+  cx<T> h[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
-    const cx<T> p0 = ld_c(psi, 0 * 3 + c), p1 = ld_c(psi, 1 * 3 + c);
-    const cx<T> p2 = ld_c(psi, 2 * 3 + c), p3 = ld_c(psi, 3 * 3 + c);
-    if (MU == 0) {  // h0 = p0 - S i p3, h1 = p1 - S i p2
-      h0[c] = add_si<-S>(p0, p3);
-      h1[c] = add_si<-S>(p1, p2);
-    } else if (MU == 1) {  // h0 = p0 - S p3, h1 = p1 + S p2
-      h0[c] = add_s<-S>(p0, p3);
-      h1[c] = add_s<S>(p1, p2);
-    } else if (MU == 2) {  // h0 = p0 - S i p2, h1 = p1 + S i p3
-      h0[c] = add_si<-S>(p0, p2);
-      h1[c] = add_si<S>(p1, p3);
-    } else {  // h0 = p0 + S p2, h1 = p1 + S p3
-      h0[c] = add_s<S>(p0, p2);
-      h1[c] = add_s<S>(p1, p3);
-    }
+    const cx<T> pu = ld_c(psi, half * 3 + c), pl = ld_c(psi, lo * 3 + c);
+    const T are = IM ? -pl.im : pl.re, aim = IM ? pl.re : pl.im;
+    h[c] = {pu.re + neg_if(are, nsg), pu.im + neg_if(aim, nsg)};
   }
-  cx<T> c0[3], c1[3];
-  color_mul<ADJ>(u, h0, c0);
-  color_mul<ADJ>(u, h1, c1);
+  cx<T> chi[3];
+  color_mul<ADJ>(u, h, chi);
   if constexpr (SCALE) {
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      c0[c] = {c0[c].re * f, c0[c].im * f};
-      c1[c] = {c1[c].re * f, c1[c].im * f};
-    }
+    for (int c = 0; c < 3; ++c) chi[c] = {chi[c].re * f, chi[c].im * f};
   }
-  acc_row<1, false>(hs, 0, c0);
-  acc_row<1, false>(hs, 1, c1);
-  if (MU == 0) {  // row2 = S i chi1, row3 = S i chi0
-    acc_row<S, true>(hs, 2, c1);
-    acc_row<S, true>(hs, 3, c0);
-  } else if (MU == 1) {  // row2 = S chi1, row3 = -S chi0
-    acc_row<S, false>(hs, 2, c1);
-    acc_row<-S, false>(hs, 3, c0);
-  } else if (MU == 2) {  // row2 = S i chi0, row3 = -S i chi1
-    acc_row<S, true>(hs, 2, c0);
-    acc_row<-S, true>(hs, 3, c1);
-  } else {  // row2 = S chi0, row3 = S chi1
-    acc_row<S, false>(hs, 2, c0);
-    acc_row<S, false>(hs, 3, c1);
+  acc_c<false>(R.u, chi, false);
+  const bool ntg = MU == 0 ? (S < 0) : MU == 3 ? (S < 0) : MU == 1 ? (half ? S < 0 : S > 0) : (half ? S > 0 : S < 0);
+  if (MU <= 1)
+    acc_c<IM>(R.x, chi, ntg);
+  else
+    acc_c<IM>(R.p, chi, ntg);
+}
+
+template <typename T>
+__device__ __forceinline__ T shfl_partner(T v) {
+  return __shfl_xor_sync(0xffffffffu, v, 1);
+}
+template <>
+__device__ __forceinline__ dw shfl_partner<dw>(dw v) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, 1), __shfl_xor_sync(0xffffffffu, v.lo, 1)};
+}
+
+// Double-word and FP32 sites take a thread pair; FP64 (bound by the narrow
+// FP64 pipe, where the pair measured slower: 0.69 against 0.57 ms per D^H D
+// at 16^3 x 32) keeps one thread per site doing both halves.
+template <typename T>
+constexpr bool kPairSites = !std::is_same<T, double>::value;
+
+template <typename T, typename A>
+__device__ __forceinline__ void rows_zero(Rows<A> &R) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    acc_set(R.u[k], num<T>::zero());
+    acc_set(R.p[k], num<T>::zero());
+    acc_set(R.x[k], num<T>::zero());
   }
+}
+
+// One thread with both halves: row 2 = R0.p + R1.x, row 3 = R1.p + R0.x.
+template <typename T, typename A>
+__device__ __forceinline__ void rows_merge(Rows<A> &R0, Rows<A> &R1) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const T a = acc_get(R1.x[k]), b = acc_get(R0.x[k]);
+    acc_add(R0.p[k], a);
+    acc_add(R1.p[k], b);
+  }
+}
+
+// p += the partner's x: both lower rows complete (every lane of the warp
+// takes part)
+template <typename T, typename A>
+__device__ __forceinline__ void pair_exchange(Rows<A> &R) {
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc_add(R.p[k], shfl_partner<T>(acc_get(R.x[k])));
 }
 
 struct Lat {
@@ -184,16 +230,16 @@ struct Lat {
 
 // CHEM: the direction-3 hops carry ef (forward) and eb (backward).
 template <int MU, bool DAG, bool CHEM, typename A, typename T>
-__device__ __forceinline__ void hop_pair(A *hs, const T *__restrict__ in, const float2 *__restrict__ U,
-                                         const Lat &lat, int64_t s, int coord, T ef, T eb) {
+__device__ __forceinline__ void hop_pair(Rows<A> &R, const T *__restrict__ in, const float2 *__restrict__ U,
+                                         const Lat &lat, int64_t s, int coord, T ef, T eb, int half) {
   const int L = lat.L[MU];
   const int64_t st = lat.st[MU];
   const int64_t fwd = s + (coord + 1 == L ? -(int64_t)(L - 1) * st : st);
   const int64_t bwd = s + (coord == 0 ? (int64_t)(L - 1) * st : -st);
   constexpr bool SC = CHEM && MU == 3;
   // D: forward (1 - gamma), backward (1 + gamma); D^H: exchanged
-  hop<MU, DAG ? 1 : -1, false, SC>(hs, in + fwd * 24, U + (s * 4 + MU) * 9, ef);
-  hop<MU, DAG ? -1 : 1, true, SC>(hs, in + bwd * 24, U + (bwd * 4 + MU) * 9, eb);
+  hop<MU, DAG ? 1 : -1, false, SC>(R, in + fwd * 24, U + (s * 4 + MU) * 9, ef, half);
+  hop<MU, DAG ? -1 : 1, true, SC>(R, in + bwd * 24, U + (bwd * 4 + MU) * 9, eb, half);
 }
 
 // Lattice coordinates of site s.
@@ -207,7 +253,8 @@ __device__ __forceinline__ void site_coords(const Lat &lat, int64_t s, int *c) {
   c[3] = (int)(r / lat.L[2]);
 }
 
-// out = Kd in + Kh (hop sum of in) [+ Kb x] [+ Ky y] [+ Kv v], one thread per site
+// out = Kd in + Kh (hop sum of in) [+ Kb x] [+ Ky y] [+ Kv v], two threads
+// per site (thread 2 s + half writes spin rows half and 2 + half).
 template <typename T, bool DAG, bool ADD_X, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(128) wilson_step(const T *__restrict__ in, const T *__restrict__ x,
                                                    const T *__restrict__ y, const T *__restrict__ v,
@@ -216,33 +263,56 @@ __global__ void __launch_bounds__(128) wilson_step(const T *__restrict__ in, con
   pdl_wait();
   pdl_trigger();
   using A = typename acc_of<T>::type;
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= lat.V) return;
-  int64_t r = s;
-  const int c0 = (int)(r % lat.L[0]);
-  r /= lat.L[0];
-  const int c1 = (int)(r % lat.L[1]);
-  r /= lat.L[1];
-  const int c2 = (int)(r % lat.L[2]);
-  const int c3 = (int)(r / lat.L[2]);
-  A hs[24];
-#pragma unroll
-  for (int k = 0; k < 24; ++k) acc_set(hs[k], num<T>::zero());
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const T one = num<T>::from_d(1.0);
-  hop_pair<0, DAG, false>(hs, in, U, lat, s, c0, one, one);
-  hop_pair<1, DAG, false>(hs, in, U, lat, s, c1, one, one);
-  hop_pair<2, DAG, false>(hs, in, U, lat, s, c2, one, one);
-  hop_pair<3, DAG, false>(hs, in, U, lat, s, c3, one, one);
-  const int64_t o = s * 24;
+  // rows half and 2 + half of site s from R (u: upper, p: lower)
+  auto epi = [&](const Rows<A> &R, int64_t s, int half) {
+    const int64_t o = s * 24;
 #pragma unroll
-  for (int k = 0; k < 24; ++k) {
-    A res;
-    acc_set_prod(res, Kd, ldg(in + o + k));
-    acc_add_prod(res, Kh, acc_raw(hs[k]));
-    if (ADD_X) acc_add_prod(res, Kb, ldg(x + o + k));
-    if (SUB_Y) acc_add_prod(res, Ky, ldg(y + o + k));
-    if (ADD_V) acc_add_prod(res, Kv, ldg(v + o + k));
-    out[o + k] = acc_get(res);
+    for (int k = 0; k < 12; ++k) {  // the upper row's 6 entries, then the lower row's
+      const int64_t g = o + (k < 6 ? 6 * half + k : 12 + 6 * half + (k - 6));
+      A res;
+      acc_set_prod(res, Kd, ldg(in + g));
+      acc_add_prod(res, Kh, acc_raw(k < 6 ? R.u[k] : R.p[k - 6]));
+      if (ADD_X) acc_add_prod(res, Kb, ldg(x + g));
+      if (SUB_Y) acc_add_prod(res, Ky, ldg(y + g));
+      if (ADD_V) acc_add_prod(res, Kv, ldg(v + g));
+      out[g] = acc_get(res);
+    }
+  };
+  if constexpr (kPairSites<T>) {
+    const int half = (int)(tid & 1);
+    const bool valid = (tid >> 1) < lat.V;
+    const int64_t s = valid ? (tid >> 1) : lat.V - 1;  // lanes past the end compute a site, store nothing
+    int c[4];
+    site_coords(lat, s, c);
+    Rows<A> R;
+    rows_zero<T>(R);
+    hop_pair<0, DAG, false>(R, in, U, lat, s, c[0], one, one, half);
+    hop_pair<1, DAG, false>(R, in, U, lat, s, c[1], one, one, half);
+    hop_pair<2, DAG, false>(R, in, U, lat, s, c[2], one, one, half);
+    hop_pair<3, DAG, false>(R, in, U, lat, s, c[3], one, one, half);
+    pair_exchange<T>(R);
+    if (valid) epi(R, s, half);
+  } else {  // one thread, both halves (compile-time signs)
+    const int64_t s = tid;
+    if (s >= lat.V) return;
+    int c[4];
+    site_coords(lat, s, c);
+    Rows<A> R0, R1;
+    rows_zero<T>(R0);
+    rows_zero<T>(R1);
+    hop_pair<0, DAG, false>(R0, in, U, lat, s, c[0], one, one, 0);
+    hop_pair<0, DAG, false>(R1, in, U, lat, s, c[0], one, one, 1);
+    hop_pair<1, DAG, false>(R0, in, U, lat, s, c[1], one, one, 0);
+    hop_pair<1, DAG, false>(R1, in, U, lat, s, c[1], one, one, 1);
+    hop_pair<2, DAG, false>(R0, in, U, lat, s, c[2], one, one, 0);
+    hop_pair<2, DAG, false>(R1, in, U, lat, s, c[2], one, one, 1);
+    hop_pair<3, DAG, false>(R0, in, U, lat, s, c[3], one, one, 0);
+    hop_pair<3, DAG, false>(R1, in, U, lat, s, c[3], one, one, 1);
+    rows_merge<T>(R0, R1);
+    epi(R0, s, 0);
+    epi(R1, s, 1);
   }
 }
 
@@ -253,8 +323,59 @@ struct QCoef {
   T ar, ai, nai, br, bi, nbi, dr, di, ndi;
 };
 
+// Output rows half and 2 + half of site s for wilson_q_step.
+template <typename T, bool EPI, bool AX, bool AV, typename A>
+__device__ __forceinline__ void q_epi(const Rows<A> &R, int64_t s, int half, const T *__restrict__ in,
+                                      const T *__restrict__ x, const T *__restrict__ v, T *__restrict__ out, T Kd,
+                                      T Kh, const QCoef<T> &k) {
+  const int64_t o = s * 24;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {  // (re, im) pairs: 3 of the upper row, 3 of the lower row
+    const bool lower = q >= 3;
+    const int col = lower ? q - 3 : q;
+    const int64_t g = o + (lower ? 12 : 0) + 6 * half + 2 * col;
+    A tr, ti;
+    acc_set_prod(tr, Kd, ldg(in + g));
+    acc_add_prod(tr, Kh, acc_raw(lower ? R.p[2 * col] : R.u[2 * col]));
+    acc_set_prod(ti, Kd, ldg(in + g + 1));
+    acc_add_prod(ti, Kh, acc_raw(lower ? R.p[2 * col + 1] : R.u[2 * col + 1]));
+    T dr = acc_get(tr), di = acc_get(ti);
+    if (lower) {  // Gamma_5: spins 2 and 3 change sign
+      dr = -dr;
+      di = -di;
+    }
+    if constexpr (!EPI) {
+      out[g] = dr;
+      out[g + 1] = di;
+    } else {
+      A rr, ri;
+      acc_set_prod(rr, k.ar, dr);
+      acc_add_prod(rr, k.nai, di);
+      acc_set_prod(ri, k.ar, di);
+      acc_add_prod(ri, k.ai, dr);
+      if constexpr (AX) {
+        const T xr = ldg(x + g), xi = ldg(x + g + 1);
+        acc_add_prod(rr, k.br, xr);
+        acc_add_prod(rr, k.nbi, xi);
+        acc_add_prod(ri, k.br, xi);
+        acc_add_prod(ri, k.bi, xr);
+      }
+      if constexpr (AV) {
+        const T vr = ldg(v + g), vi = ldg(v + g + 1);
+        acc_add_prod(rr, k.dr, vr);
+        acc_add_prod(rr, k.ndi, vi);
+        acc_add_prod(ri, k.dr, vi);
+        acc_add_prod(ri, k.di, vr);
+      }
+      out[g] = acc_get(rr);
+      out[g + 1] = acc_get(ri);
+    }
+  }
+}
+
 // Q = Gamma_5 D(m_w, mu): EPI = false: out = Q in; EPI: out = alpha (Q in)
-// [+ beta x] [+ delta v] with complex alpha, beta, delta.  One thread per site.
+// [+ beta x] [+ delta v] with complex alpha, beta, delta.  Two threads per
+// site as in wilson_step.
 template <typename T, bool EPI, bool AX, bool AV>
 __global__ void __launch_bounds__(128) wilson_q_step(const T *__restrict__ in, const T *__restrict__ x,
                                                      const T *__restrict__ v, T *__restrict__ out,
@@ -263,56 +384,40 @@ __global__ void __launch_bounds__(128) wilson_q_step(const T *__restrict__ in, c
   pdl_wait();
   pdl_trigger();
   using A = typename acc_of<T>::type;
-  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (s >= lat.V) return;
-  int c[4];
-  site_coords(lat, s, c);
-  A hs[24];
-#pragma unroll
-  for (int q = 0; q < 24; ++q) acc_set(hs[q], num<T>::zero());
-  hop_pair<0, false, true>(hs, in, U, lat, s, c[0], ef, eb);
-  hop_pair<1, false, true>(hs, in, U, lat, s, c[1], ef, eb);
-  hop_pair<2, false, true>(hs, in, U, lat, s, c[2], ef, eb);
-  hop_pair<3, false, true>(hs, in, U, lat, s, c[3], ef, eb);
-  const int64_t o = s * 24;
-#pragma unroll
-  for (int q = 0; q < 12; ++q) {  // complex component q = spin * 3 + colour
-    A tr, ti;
-    acc_set_prod(tr, Kd, ldg(in + o + 2 * q));
-    acc_add_prod(tr, Kh, acc_raw(hs[2 * q]));
-    acc_set_prod(ti, Kd, ldg(in + o + 2 * q + 1));
-    acc_add_prod(ti, Kh, acc_raw(hs[2 * q + 1]));
-    T dr = acc_get(tr), di = acc_get(ti);
-    if (q >= 6) {  // Gamma_5: spins 2 and 3 change sign
-      dr = -dr;
-      di = -di;
-    }
-    if constexpr (!EPI) {
-      out[o + 2 * q] = dr;
-      out[o + 2 * q + 1] = di;
-    } else {
-      A rr, ri;
-      acc_set_prod(rr, k.ar, dr);
-      acc_add_prod(rr, k.nai, di);
-      acc_set_prod(ri, k.ar, di);
-      acc_add_prod(ri, k.ai, dr);
-      if constexpr (AX) {
-        const T xr = ldg(x + o + 2 * q), xi = ldg(x + o + 2 * q + 1);
-        acc_add_prod(rr, k.br, xr);
-        acc_add_prod(rr, k.nbi, xi);
-        acc_add_prod(ri, k.br, xi);
-        acc_add_prod(ri, k.bi, xr);
-      }
-      if constexpr (AV) {
-        const T vr = ldg(v + o + 2 * q), vi = ldg(v + o + 2 * q + 1);
-        acc_add_prod(rr, k.dr, vr);
-        acc_add_prod(rr, k.ndi, vi);
-        acc_add_prod(ri, k.dr, vi);
-        acc_add_prod(ri, k.di, vr);
-      }
-      out[o + 2 * q] = acc_get(rr);
-      out[o + 2 * q + 1] = acc_get(ri);
-    }
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if constexpr (kPairSites<T>) {
+    const int half = (int)(tid & 1);
+    const bool valid = (tid >> 1) < lat.V;
+    const int64_t s = valid ? (tid >> 1) : lat.V - 1;
+    int c[4];
+    site_coords(lat, s, c);
+    Rows<A> R;
+    rows_zero<T>(R);
+    hop_pair<0, false, true>(R, in, U, lat, s, c[0], ef, eb, half);
+    hop_pair<1, false, true>(R, in, U, lat, s, c[1], ef, eb, half);
+    hop_pair<2, false, true>(R, in, U, lat, s, c[2], ef, eb, half);
+    hop_pair<3, false, true>(R, in, U, lat, s, c[3], ef, eb, half);
+    pair_exchange<T>(R);
+    if (valid) q_epi<T, EPI, AX, AV>(R, s, half, in, x, v, out, Kd, Kh, k);
+  } else {
+    const int64_t s = tid;
+    if (s >= lat.V) return;
+    int c[4];
+    site_coords(lat, s, c);
+    Rows<A> R0, R1;
+    rows_zero<T>(R0);
+    rows_zero<T>(R1);
+    hop_pair<0, false, true>(R0, in, U, lat, s, c[0], ef, eb, 0);
+    hop_pair<0, false, true>(R1, in, U, lat, s, c[0], ef, eb, 1);
+    hop_pair<1, false, true>(R0, in, U, lat, s, c[1], ef, eb, 0);
+    hop_pair<1, false, true>(R1, in, U, lat, s, c[1], ef, eb, 1);
+    hop_pair<2, false, true>(R0, in, U, lat, s, c[2], ef, eb, 0);
+    hop_pair<2, false, true>(R1, in, U, lat, s, c[2], ef, eb, 1);
+    hop_pair<3, false, true>(R0, in, U, lat, s, c[3], ef, eb, 0);
+    hop_pair<3, false, true>(R1, in, U, lat, s, c[3], ef, eb, 1);
+    rows_merge<T>(R0, R1);
+    q_epi<T, EPI, AX, AV>(R0, s, 0, in, x, v, out, Kd, Kh, k);
+    q_epi<T, EPI, AX, AV>(R1, s, 1, in, x, v, out, Kd, Kh, k);
   }
 }
 
@@ -335,7 +440,7 @@ template <typename T, bool DAG, bool AX, bool SY, bool AV>
 int launch(const T *in, const T *x, const T *y, const T *v, T *out, const float2 *U, const Lat &lat,
            double kd, double kh, double kb, double ky, double kv, cudaStream_t s) {
   const int bs = 128;
-  const int64_t nb = (lat.V + bs - 1) / bs;
+  const int64_t nb = ((kPairSites<T> ? 2 : 1) * lat.V + bs - 1) / bs;  // threads per site
   PP_CUDA_TRY(pdl_launch(wilson_step<T, DAG, AX, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, in, x, y, v, out, U, lat, host_c<T>(kd),
                                                              host_c<T>(kh), host_c<T>(kb), host_c<T>(ky),
                                                              host_c<T>(kv)));
@@ -359,7 +464,7 @@ template <typename T, bool EPI, bool AX, bool AV>
 int launch_q(const OpDesc &op, const T *in, const T *x, const T *v, T *out, const StepCoef &c, cudaStream_t s) {
   const Lat lat = make_lat(op);
   const int bs = 128;
-  const int64_t nb = (lat.V + bs - 1) / bs;
+  const int64_t nb = ((kPairSites<T> ? 2 : 1) * lat.V + bs - 1) / bs;  // threads per site
   QCoef<T> k;
   k.ar = host_c<T>(c.alpha);
   k.ai = host_c<T>(c.alpha_im);
