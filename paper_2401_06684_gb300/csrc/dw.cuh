@@ -125,6 +125,17 @@ __device__ __forceinline__ void acc_add_prod(dwacc &a, dw c, dw x) {
   a.e = __fadd_rn(a.e, __fadd_rn(t.lo, p.lo));
 }
 
+// float coefficient c (exact in FP32, e.g. a link entry): c*x with one FMA
+// fewer than the double-word product
+__device__ __forceinline__ void acc_add_prod(dwacc &a, float c, dw x) {
+  const float p = __fmul_rn(c, x.hi);
+  float e = __fmaf_rn(c, x.hi, -p);
+  e = __fmaf_rn(c, x.lo, e);
+  dw t = dw_two_sum(a.s, p);
+  a.s = t.hi;
+  a.e = __fadd_rn(a.e, __fadd_rn(t.lo, e));
+}
+
 __device__ __forceinline__ dw acc_get(const dwacc &a) { return dw_fast_two_sum(a.s, a.e); }
 // the unnormalised pair, usable as a product operand
 __device__ __forceinline__ dw acc_raw(const dwacc &a) { return {a.s, a.e}; }

@@ -81,10 +81,23 @@ __device__ __forceinline__ cx<T> ld_c(const T *p, int k) {
   return {ldg(p + 2 * k), ldg(p + 2 * k + 1)};
 }
 
+// The arithmetic a link entry enters the products in: FP32 for double-word
+// vectors (the entries are floats; a dw x float product is one FMA
+// shorter), the vector arithmetic otherwise.
+template <typename T>
+struct link_arith {
+  using type = T;
+};
+template <>
+struct link_arith<dw> {
+  using type = float;
+};
+
 // chi[a] = sum_b M_ab h[b] with M = U (ADJ = false) or U^H (ADJ = true)
 template <bool ADJ, typename T>
 __device__ __forceinline__ void color_mul(const float2 (&u)[9], const cx<T> (&h)[3], cx<T> (&chi)[3]) {
   using A = typename acc_of<T>::type;
+  using C = typename link_arith<T>::type;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     A re, im;
@@ -93,9 +106,9 @@ __device__ __forceinline__ void color_mul(const float2 (&u)[9], const cx<T> (&h)
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const float2 m = ADJ ? u[b * 3 + a] : u[a * 3 + b];
-      const T mr = from_f<T>(m.x);
-      const T mi = from_f<T>(ADJ ? -m.y : m.y);
-      const T nmi = from_f<T>(ADJ ? m.y : -m.y);
+      const C mr = from_f<C>(m.x);
+      const C mi = from_f<C>(ADJ ? -m.y : m.y);
+      const C nmi = from_f<C>(ADJ ? m.y : -m.y);
       // (mr + i mi)(hr + i hi) = (mr hr - mi hi) + i (mr hi + mi hr)
       acc_add_prod(re, mr, h[b].re);
       acc_add_prod(re, nmi, h[b].im);
