@@ -205,7 +205,9 @@ int pp_create_csr(pp_handle *h, int64_t n, const int64_t *rowptr_d, const int32_
  * twice with complex coefficients, complex H_m and small solve, a q with
  * complex coefficients): PP_ORTH_LANCZOS and two_pass are refused
  * (PP_ERR_INVALID_ARG), pp_build_poly's PP_LSQ_CONTOUR is unsupported and
- * PP_CHEBYSHEV needs interval_ab; PP_PREC_MIXED stays in double-word.  For
+ * PP_CHEBYSHEV needs interval_ab; under PP_PREC_MIXED the switch rule's
+ * kappa_pre is estimated at each stopping check from the eigenvalues of H_m
+ * (the Ritz values of A q(A)^2: ratio of the extreme moduli, times 4).  For
  * mu = 0, Q^2 = Q^H Q is Hermitian positive definite and behaves like
  * PP_WILSON4D_DHD.  pp_apply with PP_SIGN returns sign(Q) b.
  */

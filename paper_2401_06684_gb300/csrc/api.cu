@@ -421,6 +421,52 @@ int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double b
   return vec_scale<T>(wv, wv, n, 1.0, S.scal, s);
 }
 
+// Extra factor on a kappa_pre estimated from H_m rather than bounded by an
+// image interval.
+constexpr double kKappaEstSafety = 4.0;
+
+// Ratio of the extreme moduli of the eigenvalues of H_m (the Ritz values of
+// the preconditioned operator A q(A)^2; its extreme eigenvalues are the first
+// to converge), read back after a stopping check.  INFINITY if an eigenvalue
+// is zero or the QR does not converge.
+double tridiag_eig(const std::vector<double> &al, const std::vector<double> &be, int k);
+int hm_kappa(const Solve &S, int m, double *kappa) {
+  const size_t cw = S.cx ? 2 : 1;
+  std::vector<double> h(cw * (size_t)S.ldh * m);
+  PP_CUDA_TRY(cudaMemcpyAsync(h.data(), S.H, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, S.s));
+  PP_CUDA_TRY(cudaStreamSynchronize(S.s));
+  std::vector<double> mod;
+  if (S.cx) {
+    std::vector<std::complex<double>> Hd((size_t)m * m, 0.0), w;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i <= std::min(j + 1, m - 1); ++i)
+        Hd[(size_t)i * m + j] = {h[2 * ((size_t)j * S.ldh + i)], h[2 * ((size_t)j * S.ldh + i) + 1]};
+    if (zhess_eigvals(Hd, m, &w))
+      for (const auto &z : w) mod.push_back(std::abs(z));
+  } else if (S.lanczos) {
+    std::vector<double> al(m), be(m > 1 ? m - 1 : 0);
+    for (int j = 0; j < m; ++j) {
+      al[j] = h[(size_t)j * S.ldh + j];
+      if (j + 1 < m) be[j] = h[(size_t)j * S.ldh + j + 1];
+    }
+    mod.push_back(std::fabs(tridiag_eig(al, be, 0)));
+    mod.push_back(std::fabs(tridiag_eig(al, be, m - 1)));
+  } else {
+    std::vector<double> Hd((size_t)m * m, 0.0), wr, wi;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i <= std::min(j + 1, m - 1); ++i) Hd[(size_t)i * m + j] = h[(size_t)j * S.ldh + i];
+    if (hess_eigvals(Hd, m, &wr, &wi))
+      for (int k = 0; k < m; ++k) mod.push_back(std::hypot(wr[k], wi[k]));
+  }
+  double lo = INFINITY, hi = 0.0;
+  for (double v : mod) {
+    lo = std::fmin(lo, v);
+    hi = std::fmax(hi, v);
+  }
+  *kappa = mod.empty() || !(lo > 0.0) || !std::isfinite(hi) ? INFINITY : hi / lo;
+  return PP_OK;
+}
+
 // Solve in arithmetic T1; with PP_PREC_MIXED (T1 = dw, T2 = float) the loop
 // may move to FP32 at a stopping check.  A perturbation of relative size u
 // in a later step changes f_m by about u * kappa_pre times the part of the
@@ -433,7 +479,9 @@ int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double b
 //     est_m rho / (1 - rho) * 4 u_32 * kappa_pre <= tol.
 // The start vector, the leading basis vectors and the result stay at
 // FP64-grade accuracy; H_m, its coefficients and the small solve are FP64
-// throughout.
+// throughout.  For complex operators, whose q's image is known only at Ritz
+// values, kappa_pre is estimated at each check from the eigenvalues of H_m
+// (hm_kappa), times kKappaEstSafety.
 template <typename T1, typename T2>
 int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *x_dev, pp_stats *out) {
   const int prec = c->opts.precision;
@@ -536,7 +584,12 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   // of Y1) hold the phase-1 basis; V2 / Y2 hold FP32 copies of them and the
   // FP32 columns after them.
   const double kappa_pre = c->img_lo > 0.0 && !c->image_on_points ? c->img_hi / c->img_lo : INFINITY;
-  const double amp = kMixedSafety * kU32 * kappa_pre;
+  // Complex operators only: on the real non-normal graph Laplacian the FP32
+  // Horner chain of a Ritz interpolant that is huge between its nodes lost
+  // its accuracy (a false FP32 breakdown after the switch, error 4e-6), which
+  // no eigenvalue estimate of A q(A)^2 sees; those handles stay in double-word.
+  const bool kappa_from_hm = mixed && c->image_on_points && c->cplx;
+  double amp = kMixedSafety * kU32 * kappa_pre;
   double est_prev = INFINITY;
   int phase = 1, nv1 = 0, ny1 = 0;
   auto switch_phase = [&](int m_now) -> int {
@@ -609,6 +662,11 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
         break;
       }
       if (mixed && phase == 1 && std::isfinite(est_prev) && std::isfinite(hs.est) && est_prev > 0.0) {
+        if (kappa_from_hm) {
+          double kap;
+          RC(hm_kappa(S, m, &kap));
+          amp = kMixedSafety * kKappaEstSafety * kU32 * kap;
+        }
         double rho = std::pow(hs.est / est_prev, 1.0 / kchk);
         if (!(rho < 0.999)) rho = 0.999;
         if (hs.est * rho / (1.0 - rho) * amp <= tol) {
