@@ -467,6 +467,109 @@ int hm_kappa(const Solve &S, int m, double *kappa) {
   return PP_OK;
 }
 
+// ---- segment graphs ----
+// The kernels of the Krylov steps between two stopping checks (and the
+// small solve at the check) depend only on the step range, the precision
+// phase and the handle's state, not on b or x; their launches are captured
+// once as a CUDA graph and replayed by later solves (one graph launch per
+// segment instead of hundreds of kernel launches; the host still reads the
+// status record at every check).  Direct launches when profiling (the chain
+// events) or if a capture ever failed.
+void segs_clear(pp_ctx *c) {
+  for (auto &kv : c->segs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  c->segs.clear();
+}
+
+// Everything a captured segment bakes in: workspace pointers, q, options, tol.
+void segs_validate(pp_ctx *c, double tol) {
+  const Workspace &w = c->ws;
+  uint64_t tb;
+  memcpy(&tb, &tol, sizeof tb);
+  std::vector<uint64_t> sig = {(uint64_t)(uintptr_t)w.V,   (uint64_t)(uintptr_t)w.Y,
+                               (uint64_t)(uintptr_t)w.tmp, (uint64_t)(uintptr_t)w.dmem,
+                               (uint64_t)(uintptr_t)w.Vf,  (uint64_t)(uintptr_t)w.Yf,
+                               (uint64_t)(uintptr_t)w.hess, (uint64_t)(uintptr_t)w.st,
+                               (uint64_t)(uintptr_t)w.val_dw, (uint64_t)(uintptr_t)w.val_f,
+                               (uint64_t)(uintptr_t)w.long_rows, (uint64_t)w.ldv,
+                               c->poly_gen, (uint64_t)c->degree, (uint64_t)c->opts.side,
+                               (uint64_t)c->opts.precision, (uint64_t)c->opts.orth,
+                               (uint64_t)c->opts.check_every, (uint64_t)c->opts.clenshaw,
+                               (uint64_t)c->tile_bdx, tb};
+  if (sig != c->seg_sig) {
+    segs_clear(c);
+    c->seg_sig = sig;
+  }
+}
+
+// Run body() for the segment `key`: replay its graph, or capture it (the
+// captured launches run once by launching the new graph), or run directly.
+int run_segment(pp_ctx *c, Solve &S, uint64_t key, const std::function<int()> &body) {
+  if (c->opts.profile || c->graphs_off) return body();
+  cudaStream_t s = c->stream;
+  auto it = c->segs.find(key);
+  if (it != c->segs.end()) {
+    PP_CUDA_TRY(cudaGraphLaunch(it->second.exec, s));
+    pp_launch_count() += it->second.launches;
+    c->chain_launches += it->second.chain_launches;
+    c->chain_bytes += it->second.chain_bytes;
+    S.mvms += it->second.mvms;
+    S.ip += it->second.ip;
+    return PP_OK;
+  }
+  const int64_t l0 = pp_launch_count(), cl0 = c->chain_launches, mv0 = S.mvms, ip0 = S.ip;
+  const double cb0 = c->chain_bytes;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    c->graphs_off = true;
+    return body();
+  }
+  const int rc = body();
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  cudaGraphExec_t exec = nullptr;
+  const bool ok = rc == PP_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
+  if (g) cudaGraphDestroy(g);
+  if (!ok) {  // nothing of the segment ran: undo the counts and run it directly
+    cudaGetLastError();
+    pp_launch_count() = l0;
+    c->chain_launches = cl0;
+    c->chain_bytes = cb0;
+    S.mvms = mv0;
+    S.ip = ip0;
+    if (rc != PP_OK) return rc;
+    c->graphs_off = true;
+    return body();
+  }
+  SegGraph sg;
+  sg.exec = exec;
+  sg.launches = pp_launch_count() - l0;
+  sg.chain_launches = c->chain_launches - cl0;
+  sg.chain_bytes = c->chain_bytes - cb0;
+  sg.mvms = S.mvms - mv0;
+  sg.ip = S.ip - ip0;
+  c->segs[key] = sg;
+  PP_CUDA_TRY(cudaGraphLaunch(exec, s));
+  return PP_OK;
+}
+
+// Scratch of the global-memory Hessenberg solves for m (grows only; a new
+// allocation invalidates the captured segments that use the old one).
+int ensure_hess(pp_ctx *c, bool cx, int m, int K) {
+  Workspace &w = c->ws;
+  const size_t need = cx ? small_hess_scratch_doubles_c(m, K) : small_hess_scratch_doubles(m, K);
+  const size_t smem_bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * (cx ? 2 : 1) * sizeof(double);
+  if (smem_bytes > 200 * 1024 && w.hess_n < need) {
+    segs_clear(c);
+    if (w.hess) cudaFree(w.hess);
+    w.hess = nullptr;
+    w.hess_n = 0;
+    PP_CUDA_TRY(cudaMalloc(&w.hess, need * sizeof(double)));
+    w.hess_n = need;
+  }
+  return PP_OK;
+}
+
 // Solve in arithmetic T1; with PP_PREC_MIXED (T1 = dw, T2 = float) the loop
 // may move to FP32 at a stopping check.  A perturbation of relative size u
 // in a later step changes f_m by about u * kappa_pre times the part of the
@@ -610,42 +713,37 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
 
   int m = 0, mprev = 0, checks = 0, status = PP_ERR_NOT_CONVERGED, switched_at = mixed ? (phase == 2 ? 0 : -1) : 0;
   bool bd = false;
-  for (int j = 0; j < m_max; ++j) {
-    if (phase == 1)
-      RC(krylov_step<T1>(S, op1, V1, Y1, t1, j, kBreakdownRel));
-    else
-      RC(krylov_step<T2>(S, op2, V2, Y2, t2, j, std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
-    m = j + 1;
-    if (m % kchk == 0 || m == m_max) {
-      if (S.cx) {
-        const size_t need = small_hess_scratch_doubles_c(m, K);
-        const size_t smem_bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * 2 * sizeof(double);
-        if (smem_bytes > 200 * 1024 && w.hess_n < need) {
-          if (w.hess) cudaFree(w.hess);
-          w.hess = nullptr;
-          w.hess_n = 0;
-          PP_CUDA_TRY(cudaMalloc(&w.hess, need * sizeof(double)));
-          w.hess_n = need;
-        }
-        RC(small_hess_quad_c(S.H, ldh, m, S.sig, S.wt, K, S.X, w.hess, s));
-      } else if (S.lanczos)
-        RC(small_tridiag_quad(S.H, ldh, m, S.sig, S.wt, K, S.X, S.tri, s));
-      else {
-        const size_t need = small_hess_scratch_doubles(m, K);
-        const size_t smem_bytes = ((size_t)(m + 1) * m + 2 * (size_t)m) * sizeof(double);
-        if (smem_bytes > 200 * 1024 && w.hess_n < need) {
-          if (w.hess) cudaFree(w.hess);
-          w.hess = nullptr;
-          w.hess_n = 0;
-          PP_CUDA_TRY(cudaMalloc(&w.hess, need * sizeof(double)));
-          w.hess_n = need;
-        }
-        RC(small_hess_quad(S.H, ldh, m, S.sig, S.wt, K, S.X, w.hess, s));
+  // Segments of steps [j0, j1) ending at a stopping check (every kchk steps
+  // and at m_max), each with the check's small solve.
+  for (int j0 = 0; j0 < m_max;) {
+    const int j1 = std::min((j0 / kchk + 1) * kchk, m_max);
+    if (!S.lanczos) RC(ensure_hess(c, S.cx, j1, K));
+    segs_validate(c, tol);
+    const int mp = mprev, ph = phase;
+    auto body = [&]() -> int {
+      for (int j = j0; j < j1; ++j) {
+        if (ph == 1)
+          RC(krylov_step<T1>(S, op1, V1, Y1, t1, j, kBreakdownRel));
+        else
+          RC(krylov_step<T2>(S, op2, V2, Y2, t2, j,
+                             std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
       }
       if (S.cx)
-        RC(small_combine_c(S.X, K, m, mprev, S.z, S.zprev, tol, w.st, s));
+        RC(small_hess_quad_c(S.H, ldh, j1, S.sig, S.wt, K, S.X, w.hess, s));
+      else if (S.lanczos)
+        RC(small_tridiag_quad(S.H, ldh, j1, S.sig, S.wt, K, S.X, S.tri, s));
       else
-        RC(small_combine(S.X, K, m, mprev, S.z, S.zprev, tol, w.st, s));
+        RC(small_hess_quad(S.H, ldh, j1, S.sig, S.wt, K, S.X, w.hess, s));
+      if (S.cx)
+        RC(small_combine_c(S.X, K, j1, mp, S.z, S.zprev, tol, w.st, s));
+      else
+        RC(small_combine(S.X, K, j1, mp, S.z, S.zprev, tol, w.st, s));
+      return PP_OK;
+    };
+    RC(run_segment(c, S, ((uint64_t)j0 << 34) | ((uint64_t)j1 << 2) | (uint64_t)ph, body));
+    m = j1;
+    j0 = j1;
+    {
       mprev = m;
       ++checks;
       PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
@@ -1223,6 +1321,7 @@ void finish_poly(pp_ctx *c, double margin = 1e3) {
       theta = std::fmax(theta, std::fmin(0.45 * M_PI, 1.5 * std::fabs(std::atan2(c->nf.im[i], c->nf.re[i]))));
   invsqrt_quadrature(c->img_lo / margin, c->img_hi * margin, 1e-15, theta, &c->qsig, &c->qwt);
   c->quad_uploaded = false;
+  ++c->poly_gen;
   if (c->ws.dmem) {  // K may have changed: re-layout on next use
     cudaFree(c->ws.dmem);
     c->ws.dmem = nullptr;
@@ -2037,6 +2136,7 @@ int pp_poly_apply_static(pp_handle c, const void *x_d, void *y_d) {
 
 void pp_destroy(pp_handle c) {
   if (!c) return;
+  segs_clear(c);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   ws_free(c->ws);
   delete c;

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <vector>
 
 #include "internal.h"
@@ -35,6 +36,14 @@ struct Workspace {
   void *Vf = nullptr;     // FP32 basis of the second phase (PP_PREC_MIXED)
   void *Yf = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// A captured run of Krylov steps up to a stopping check (CUDA graph) and
+// the counters its launches add.
+struct SegGraph {
+  cudaGraphExec_t exec = nullptr;
+  int64_t launches = 0, chain_launches = 0, mvms = 0, ip = 0;
+  double chain_bytes = 0.0;
 };
 
 struct pp_ctx {
@@ -75,6 +84,12 @@ struct pp_ctx {
   double chain_bytes = 0.0;
   std::vector<cudaEvent_t> prof_ev;  // start/stop pairs, grown on demand
   size_t prof_used = 0;
+  // segment graphs of pp_apply, keyed by (first step, end step, phase); valid
+  // while seg_sig (workspace pointers, q, options, tol) is unchanged
+  std::map<uint64_t, SegGraph> segs;
+  std::vector<uint64_t> seg_sig;
+  uint64_t poly_gen = 0;    // bumped whenever q or its quadrature changes
+  bool graphs_off = false;  // capture failed once: direct launches
 };
 
 // q(A) v by the Horner scheme of the Newton form (every kind of q unless
