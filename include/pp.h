@@ -366,6 +366,11 @@ int pp_get_poly_nodes(pp_handle h, int32_t *kind, double *nodes_re_h, double *no
  * b_d.  On PP_ERR_NOT_CONVERGED x_d still holds the last
  * iterate.  stats (host, may be NULL) is filled on return.  Blocks the
  * calling thread at each stopping check (a few bytes read back).
+ * The kernels of the steps between two stopping checks are captured once
+ * as a CUDA graph per (step range, precision phase) and replayed by later
+ * calls on the handle (results bitwise equal to direct launches); the
+ * graphs are held by the handle and dropped when its workspace, q, options
+ * or tol change; opts.profile = 1 launches the kernels directly.
  * f = PP_SIGN (PP_WILSON4D_Q2 handles, nrhs = 1; Sec. 6, Example 2):
  * x = sign(Q) b = Q (Q^2)^{-1/2} b, the solve for (Q^2)^{-1/2} b followed by
  * one FP64 application of Q on the device (stats describe the solve).
