@@ -196,6 +196,7 @@ struct Allocs {
 template <typename T>
 struct ArithTabs {
   const BatchSeg *bseg = nullptr;  // geometry table
+  const int *blkseg = nullptr;     // segment of every block
   unsigned nblk = 0;
   int P = 1;
   const Konst<T> *K = nullptr;     // (deg + 1) x nseg: [0] = A, [1 + t] = step t of q
@@ -275,7 +276,8 @@ int poly_batch(GroupCtx &G, const ArithTabs<T> &A, const T *in, T *out, T *bufs[
   cudaStream_t s = G.s;
   auto step = [&](int t, const T *x, const T *y, const T *v, T *o, bool sy, bool av) {
     G.count<T>(sy, av);
-    return op_step_batch<T>(A.bseg, ns, A.nblk, A.P, A.K + (size_t)(1 + t) * ns, G.active, x, y, v, o, sy, av, s);
+    return op_step_batch<T>(A.bseg, A.blkseg, A.nblk, A.P, A.K + (size_t)(1 + t) * ns, G.active, x, y, v, o, sy, av,
+                            s);
   };
   if (k == 0) return vec_scale<T>(in, out, G.N, 1.0, G.dmem + G.L.qc0, s, G.seg(true));
   if (k == 1) return step(0, in, nullptr, nullptr, out, false, false);
@@ -297,7 +299,7 @@ template <typename T>
 int aop_batch(GroupCtx &G, const ArithTabs<T> &A, const int *mask, const T *x, T *out) {
   G.count<T>(false, false);
   BRC(G.prof_begin());
-  BRC(op_step_batch<T>(A.bseg, G.nseg, A.nblk, A.P, A.K, mask, x, nullptr, nullptr, out, false, false, G.s));
+  BRC(op_step_batch<T>(A.bseg, A.blkseg, A.nblk, A.P, A.K, mask, x, nullptr, nullptr, out, false, false, G.s));
   return G.prof_end();
 }
 
@@ -401,13 +403,22 @@ int build_tabs(GroupCtx &G, const std::vector<SegIn> &segs, const std::vector<in
     }
     batch_konst<T>(d.data(), cm.data(), cp.data(), coefs.data(), ns, Kh.data() + (size_t)t * ns);
   }
+  std::vector<int> bs((size_t)nblk);
+  for (int i = 0; i < ns; ++i) {
+    const unsigned e = i + 1 < ns ? g[i + 1].blk0 : (unsigned)nblk;
+    for (unsigned b = g[i].blk0; b < e; ++b) bs[b] = i;
+  }
   BatchSeg *gd = nullptr;
   Konst<T> *Kd = nullptr;
+  int *bsd = nullptr;
   BRC(G.alloc->get(&gd, sizeof(BatchSeg) * ns));
   BRC(G.alloc->get(&Kd, sizeof(Konst<T>) * Kh.size()));
+  BRC(G.alloc->get(&bsd, sizeof(int) * std::max<size_t>(bs.size(), 1)));
   PP_CUDA_TRY(cudaMemcpyAsync(gd, g.data(), sizeof(BatchSeg) * ns, cudaMemcpyHostToDevice, G.s));
   PP_CUDA_TRY(cudaMemcpyAsync(Kd, Kh.data(), sizeof(Konst<T>) * Kh.size(), cudaMemcpyHostToDevice, G.s));
+  if (!bs.empty()) PP_CUDA_TRY(cudaMemcpyAsync(bsd, bs.data(), sizeof(int) * bs.size(), cudaMemcpyHostToDevice, G.s));
   out->bseg = gd;
+  out->blkseg = bsd;
   out->nblk = (unsigned)nblk;
   out->P = P;
   out->K = Kd;

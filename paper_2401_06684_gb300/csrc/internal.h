@@ -141,10 +141,12 @@ template <typename T>
 void batch_konst(const double *d, const double *cm, const double *cp, const StepCoef *c, int nseg,
                  Konst<T> *out);
 // Batched stencil step over all segments (P entries per thread: 1, or the
-// 16-byte width when every segment's nx allows it); inactive segments skipped.
+// 16-byte width when every segment's nx allows it); blkseg[b] = the segment
+// of block b; inactive segments skipped.
 template <typename T>
-int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Konst<T> *K, const int *active,
-                  const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v, cudaStream_t s);
+int op_step_batch(const BatchSeg *segs, const int *blkseg, unsigned nblk, int P, const Konst<T> *K,
+                  const int *active, const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v,
+                  cudaStream_t s);
 
 // Wilson D^H D step (wilson.cu): t = D x into op.tmp, then
 // out = alpha D^H t + beta x [- y] [+ delta v].  With op.q2: t = Q x, then

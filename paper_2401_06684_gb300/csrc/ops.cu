@@ -289,27 +289,23 @@ __global__ void __launch_bounds__(kStencilMaxThreads) st_step(const T *__restric
 }
 
 // Batched form: many grids (segments of concatenated vectors) in one launch.
-// The flat block index is located in the segments' first-block table by
-// binary search; each segment has its own geometry, constants and load path
+// The flat block index is mapped to its segment by a per-block table (one
+// load instead of a binary search over the segments' first blocks, whose
+// dependent loads came before any of the block's work); each segment has
+// its own geometry, constants and load path
 // (16-byte loads where its row length allows them), and its units are mapped
 // as in st_step.
 template <typename T, int P, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(kStencilMaxThreads) bst_step(const T *__restrict__ x, const T *__restrict__ y,
                                                                  const T *__restrict__ v, T *__restrict__ out,
-                                                                 const BatchSeg *__restrict__ segs, int nseg,
+                                                                 const BatchSeg *__restrict__ segs,
+                                                                 const int *__restrict__ blkseg,
                                                                  const Konst<T> *__restrict__ K,
                                                                  const int *__restrict__ active) {
   pdl_wait();
   pdl_trigger();
   const unsigned blk = blockIdx.x;
-  int lo = 0, hi = nseg - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (segs[mid].blk0 <= blk)
-      lo = mid;
-    else
-      hi = mid - 1;
-  }
+  const int lo = __ldg(blkseg + blk);
   if (active && !active[lo]) return;
   const BatchSeg g = segs[lo];
   const int64_t u = (int64_t)(blk - g.blk0) * blockDim.x + threadIdx.x;
@@ -490,12 +486,13 @@ void batch_konst(const double *d, const double *cm, const double *cp, const Step
 }
 
 template <typename T>
-int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Konst<T> *K, const int *active,
-                  const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v, cudaStream_t s) {
+int op_step_batch(const BatchSeg *segs, const int *blkseg, unsigned nblk, int P, const Konst<T> *K,
+                  const int *active, const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v,
+                  cudaStream_t s) {
   constexpr int PW = 16 / (int)sizeof(T);
   const dim3 blk(ST_THREADS);
 #define PP_BST(PP, SY, AV) \
-  e = pdl_launch(bst_step<T, PP, SY, AV>, dim3(nblk), blk, 0, s, x, y, v, out, segs, nseg, K, active)
+  e = pdl_launch(bst_step<T, PP, SY, AV>, dim3(nblk), blk, 0, s, x, y, v, out, segs, blkseg, K, active)
   cudaError_t e;
   (void)P;  // always PW entries per thread; each segment picks its load path
   if (sub_y && add_v) PP_BST(PW, true, true);
@@ -512,7 +509,7 @@ int op_step_batch(const BatchSeg *segs, int nseg, unsigned nblk, int P, const Ko
 #define PP_BINST(T)                                                                                   \
   template void batch_konst<T>(const double *, const double *, const double *, const StepCoef *, int, \
                                Konst<T> *);                                                          \
-  template int op_step_batch<T>(const BatchSeg *, int, unsigned, int, const Konst<T> *, const int *,  \
+  template int op_step_batch<T>(const BatchSeg *, const int *, unsigned, int, const Konst<T> *, const int *, \
                                 const T *, const T *, const T *, T *, bool, bool, cudaStream_t);
 PP_BINST(double)
 PP_BINST(float)
