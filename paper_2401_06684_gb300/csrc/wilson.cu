@@ -162,11 +162,8 @@ __device__ __forceinline__ void acc_c(A *dst, const cx<T> (&c)[3], bool neg) {
 // S i chi0, row 2 += S i chi1; MU 1: row 3 -= S chi0, row 2 += S chi1; MU 2:
 // row 2 += S i chi0, row 3 -= S i chi1; MU 3: row 2 += S chi0, row 3 += S chi1).
 template <int MU, int S, bool ADJ, bool SCALE, typename A, typename T>
-__device__ __forceinline__ void hop(Rows<A> &R, const T *__restrict__ psi, const float2 *__restrict__ link, T f,
-                                    int half) {
-  float2 u[9];
-#pragma unroll
-  for (int k = 0; k < 9; ++k) u[k] = __ldg(link + k);
+__device__ __forceinline__ void hop_body(Rows<A> &R, const T *__restrict__ psi, const float2 (&u)[9], T f,
+                                         int half) {
   constexpr bool IM = MU == 0 || MU == 2;
   const int lo = MU <= 1 ? 3 - half : 2 + half;
   const bool nsg = MU == 0 ? (S > 0) : MU == 3 ? (S < 0) : (half ? S < 0 : S > 0);
@@ -191,6 +188,27 @@ __device__ __forceinline__ void hop(Rows<A> &R, const T *__restrict__ psi, const
     acc_c<IM>(R.p, chi, ntg);
 }
 
+// The thread's half of a hop (thread pair per site).
+template <int MU, int S, bool ADJ, bool SCALE, typename A, typename T>
+__device__ __forceinline__ void hop(Rows<A> &R, const T *__restrict__ psi, const float2 *__restrict__ link, T f,
+                                    int half) {
+  float2 u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = __ldg(link + k);
+  hop_body<MU, S, ADJ, SCALE>(R, psi, u, f, half);
+}
+
+// Both halves of a hop in one thread (the link loaded once).
+template <int MU, int S, bool ADJ, bool SCALE, typename A, typename T>
+__device__ __forceinline__ void hop2(Rows<A> &R0, Rows<A> &R1, const T *__restrict__ psi,
+                                     const float2 *__restrict__ link, T f) {
+  float2 u[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) u[k] = __ldg(link + k);
+  hop_body<MU, S, ADJ, SCALE>(R0, psi, u, f, 0);
+  hop_body<MU, S, ADJ, SCALE>(R1, psi, u, f, 1);
+}
+
 template <typename T>
 __device__ __forceinline__ T shfl_partner(T v) {
   return __shfl_xor_sync(0xffffffffu, v, 1);
@@ -202,7 +220,7 @@ __device__ __forceinline__ dw shfl_partner<dw>(dw v) {
 
 // Double-word and FP32 sites take a thread pair; FP64 (bound by the narrow
 // FP64 pipe, where the pair measured slower: 0.69 against 0.57 ms per D^H D
-// at 16^3 x 32) keeps one thread per site doing both halves.
+// at 16^3 x 32) keeps one thread per site doing both halves (0.58 ms).
 template <typename T>
 constexpr bool kPairSites = !std::is_same<T, double>::value;
 
@@ -253,6 +271,20 @@ __device__ __forceinline__ void hop_pair(Rows<A> &R, const T *__restrict__ in, c
   // D: forward (1 - gamma), backward (1 + gamma); D^H: exchanged
   hop<MU, DAG ? 1 : -1, false, SC>(R, in + fwd * 24, U + (s * 4 + MU) * 9, ef, half);
   hop<MU, DAG ? -1 : 1, true, SC>(R, in + bwd * 24, U + (bwd * 4 + MU) * 9, eb, half);
+}
+
+// hop_pair for one thread doing both halves of the site.
+template <int MU, bool DAG, bool CHEM, typename A, typename T>
+__device__ __forceinline__ void hop_pair2(Rows<A> &R0, Rows<A> &R1, const T *__restrict__ in,
+                                          const float2 *__restrict__ U, const Lat &lat, int64_t s, int coord, T ef,
+                                          T eb) {
+  const int L = lat.L[MU];
+  const int64_t st = lat.st[MU];
+  const int64_t fwd = s + (coord + 1 == L ? -(int64_t)(L - 1) * st : st);
+  const int64_t bwd = s + (coord == 0 ? (int64_t)(L - 1) * st : -st);
+  constexpr bool SC = CHEM && MU == 3;
+  hop2<MU, DAG ? 1 : -1, false, SC>(R0, R1, in + fwd * 24, U + (s * 4 + MU) * 9, ef);
+  hop2<MU, DAG ? -1 : 1, true, SC>(R0, R1, in + bwd * 24, U + (bwd * 4 + MU) * 9, eb);
 }
 
 // Lattice coordinates of site s.
@@ -315,14 +347,10 @@ __global__ void __launch_bounds__(128) wilson_step(const T *__restrict__ in, con
     Rows<A> R0, R1;
     rows_zero<T>(R0);
     rows_zero<T>(R1);
-    hop_pair<0, DAG, false>(R0, in, U, lat, s, c[0], one, one, 0);
-    hop_pair<0, DAG, false>(R1, in, U, lat, s, c[0], one, one, 1);
-    hop_pair<1, DAG, false>(R0, in, U, lat, s, c[1], one, one, 0);
-    hop_pair<1, DAG, false>(R1, in, U, lat, s, c[1], one, one, 1);
-    hop_pair<2, DAG, false>(R0, in, U, lat, s, c[2], one, one, 0);
-    hop_pair<2, DAG, false>(R1, in, U, lat, s, c[2], one, one, 1);
-    hop_pair<3, DAG, false>(R0, in, U, lat, s, c[3], one, one, 0);
-    hop_pair<3, DAG, false>(R1, in, U, lat, s, c[3], one, one, 1);
+    hop_pair2<0, DAG, false>(R0, R1, in, U, lat, s, c[0], one, one);
+    hop_pair2<1, DAG, false>(R0, R1, in, U, lat, s, c[1], one, one);
+    hop_pair2<2, DAG, false>(R0, R1, in, U, lat, s, c[2], one, one);
+    hop_pair2<3, DAG, false>(R0, R1, in, U, lat, s, c[3], one, one);
     rows_merge<T>(R0, R1);
     epi(R0, s, 0);
     epi(R1, s, 1);
@@ -420,14 +448,10 @@ __global__ void __launch_bounds__(128) wilson_q_step(const T *__restrict__ in, c
     Rows<A> R0, R1;
     rows_zero<T>(R0);
     rows_zero<T>(R1);
-    hop_pair<0, false, true>(R0, in, U, lat, s, c[0], ef, eb, 0);
-    hop_pair<0, false, true>(R1, in, U, lat, s, c[0], ef, eb, 1);
-    hop_pair<1, false, true>(R0, in, U, lat, s, c[1], ef, eb, 0);
-    hop_pair<1, false, true>(R1, in, U, lat, s, c[1], ef, eb, 1);
-    hop_pair<2, false, true>(R0, in, U, lat, s, c[2], ef, eb, 0);
-    hop_pair<2, false, true>(R1, in, U, lat, s, c[2], ef, eb, 1);
-    hop_pair<3, false, true>(R0, in, U, lat, s, c[3], ef, eb, 0);
-    hop_pair<3, false, true>(R1, in, U, lat, s, c[3], ef, eb, 1);
+    hop_pair2<0, false, true>(R0, R1, in, U, lat, s, c[0], ef, eb);
+    hop_pair2<1, false, true>(R0, R1, in, U, lat, s, c[1], ef, eb);
+    hop_pair2<2, false, true>(R0, R1, in, U, lat, s, c[2], ef, eb);
+    hop_pair2<3, false, true>(R0, R1, in, U, lat, s, c[3], ef, eb);
     rows_merge<T>(R0, R1);
     q_epi<T, EPI, AX, AV>(R0, s, 0, in, x, v, out, Kd, Kh, k);
     q_epi<T, EPI, AX, AV>(R1, s, 1, in, x, v, out, Kd, Kh, k);
