@@ -52,7 +52,7 @@ typedef enum {
   PP_ERR_TIMEOUT = -7,       /* a bounded device wait ran out                   */
   PP_ERR_STATE = -8,         /* call out of order (e.g. pp_apply before
                                 pp_build_poly)                                  */
-  PP_ERR_UNSUPPORTED = -9    /* valid request this build does not implement     */
+  PP_ERR_UNSUPPORTED = -9    /* valid request this library does not implement   */
 } pp_status;
 
 typedef enum { PP_F64 = 0, PP_F32 = 1, PP_C64 = 2, PP_C128 = 3 } pp_dtype;
@@ -165,7 +165,7 @@ void pp_default_opts(pp_opts *opts);
 /*
  * Create a handle for a CSR matrix (Sec. 1: A sparse).  n rows/columns;
  * rowptr_d[n+1] (int64, rowptr_d[0] = 0), col_d[nnz] (int32, 0-based),
- * val_d[nnz] of dtype PP_F64 (PP_C128 not in this build).  The arrays are
+ * val_d[nnz] of dtype PP_F64 (PP_C128 is not supported).  The arrays are
  * referenced, not copied (PP_PREC_DW keeps a converted copy of val), and must
  * stay alive and unchanged for the handle's lifetime.  is_hermitian selects
  * Lanczos under PP_ORTH_AUTO.  Errors: PP_ERR_INVALID_ARG for n <= 0 or NULL

@@ -1705,7 +1705,7 @@ int pp_create_csr(pp_handle *h, int64_t n, const int64_t *rowptr_d, const int32_
   if (!h) return pp_set_error(PP_ERR_INVALID_ARG, "NULL handle pointer");
   *h = nullptr;
   if (n <= 0 || !rowptr_d || !col_d || !val_d) return pp_set_error(PP_ERR_INVALID_ARG, "n <= 0 or NULL CSR array");
-  if (dtype != PP_F64) return pp_set_error(PP_ERR_UNSUPPORTED, "CSR values must be PP_F64 in this build");
+  if (dtype != PP_F64) return pp_set_error(PP_ERR_UNSUPPORTED, "CSR values must be PP_F64");
   if (n > INT32_MAX) return pp_set_error(PP_ERR_INVALID_ARG, "n > 2^31 - 1 (column indices are int32)");
   pp_ctx *c = new_ctx(cuda_stream);
   c->op_kind = OPK_CSR;
@@ -1753,7 +1753,7 @@ int pp_create_stencil(pp_handle *h, int32_t kind, const int64_t dims[4], const d
     *h = c;
     return PP_OK;
   }
-  if (dtype != PP_F64) return pp_set_error(PP_ERR_UNSUPPORTED, "stencil vectors must be PP_F64 in this build");
+  if (dtype != PP_F64) return pp_set_error(PP_ERR_UNSUPPORTED, "stencil vectors must be PP_F64");
   if (links_d) return pp_set_error(PP_ERR_INVALID_ARG, "links_d must be NULL for this stencil kind");
   pp_ctx *c = nullptr;
   if (kind == PP_LAPLACE2D5) {
@@ -1984,7 +1984,7 @@ int pp_apply_host(pp_handle c, int32_t f, const double *b_h, int64_t nrhs, int32
                   double *x_h, pp_stats *stats) {
   RC(check_ready(c));
   if (!b_h || !x_h) return pp_set_error(PP_ERR_INVALID_ARG, "NULL vector");
-  if (nrhs != 1) return pp_set_error(PP_ERR_UNSUPPORTED, "nrhs != 1 not in this build");
+  if (nrhs != 1) return pp_set_error(PP_ERR_UNSUPPORTED, "pp_apply_host takes nrhs = 1");
   if (!c->ws.io) PP_CUDA_TRY(cudaMalloc(&c->ws.io, 2 * sizeof(double) * (size_t)c->n));
   double *bd = c->ws.io, *xd = c->ws.io + c->n;
   PP_CUDA_TRY(cudaMemcpyAsync(bd, b_h, sizeof(double) * c->n, cudaMemcpyHostToDevice, c->stream));
