@@ -27,6 +27,7 @@ constexpr int TPB = 256;
 constexpr int U = 8;
 constexpr int CHUNK = TPB * U;
 constexpr int CG = 8;  // columns per block in the multi-dot
+constexpr int kUpdateDotTileMaxJ = 32;  // widest J of the shared-memory fused sweep
 
 __device__ __forceinline__ double warp_reduce_d(double v) { return warp_sum(v); }
 __device__ __forceinline__ float warp_reduce_d(float v) {
@@ -387,6 +388,71 @@ __global__ void __launch_bounds__(TPB) k_update_dot(const T *__restrict__ V, int
     double sum = 0.0;
     for (int q = 0; q < TPB / 32; ++q) sum += red[threadIdx.x][q];
     partials[(int64_t)blockIdx.x * J + threadIdx.x] = sum;
+  }
+}
+
+// The same fused sweep for wider J: the chunk's rows go through shared
+// memory in tiles of TPB rows (one row per thread): the tile of V (J
+// columns) is loaded once, each thread updates its row of w from it, and
+// the block then forms the J inner products of the tile with the updated w
+// from shared memory (warp g takes columns g, g + 8, ...; lane l rows
+// l + 32 k), accumulated over the chunk's tiles in a fixed order.  V is read
+// from HBM once instead of twice.
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_update_dot_tile(const T *__restrict__ V, int64_t ldv, int J,
+                                                         const double *__restrict__ h, T *__restrict__ w,
+                                                         int64_t n, double *__restrict__ partials, Seg S) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename acc_of<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  T *hs = reinterpret_cast<T *>(smem_raw);  // -h, J entries
+  T *wn = hs + J;                            // the tile's updated w, TPB entries
+  T *vt = wn + TPB;                          // V tile, [column][row], J x TPB
+  const int seg = chunk_seg(S, blockIdx.x);
+  if (!seg_active(S, seg)) {
+    for (int c = threadIdx.x; c < J; c += TPB) partials[(int64_t)blockIdx.x * J + c] = 0.0;
+    return;
+  }
+  const double *hseg = h + seg * S.dstride;
+  for (int c = threadIdx.x; c < J; c += TPB) hs[c] = num<T>::from_d(-hseg[c]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int NW = TPB / 32;
+  constexpr int CMAX = kUpdateDotTileMaxJ / NW;  // columns per warp
+  A dacc[CMAX];
+#pragma unroll
+  for (int q = 0; q < CMAX; ++q) acc_set(dacc[q], num<T>::zero());
+  const int64_t base = (int64_t)blockIdx.x * CHUNK;
+  for (int u = 0; u < U; ++u) {
+    const int64_t r = base + (int64_t)u * TPB + threadIdx.x;
+    const bool ok = r < n;
+    for (int c = 0; c < J; ++c) vt[c * TPB + threadIdx.x] = ok ? ldg(V + (int64_t)c * ldv + r) : num<T>::zero();
+    A acc;
+    acc_set(acc, ok ? w[r] : num<T>::zero());
+    for (int c = 0; c < J; ++c) acc_add_prod(acc, hs[c], vt[c * TPB + threadIdx.x]);
+    const T wr = acc_get(acc);
+    if (ok) w[r] = wr;
+    wn[threadIdx.x] = wr;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < CMAX; ++q) {
+      const int c = wid + q * NW;
+      if (c < J) {
+#pragma unroll
+        for (int k = 0; k < TPB / 32; ++k)
+          acc_add_prod(dacc[q], vt[c * TPB + lane + 32 * k], wn[lane + 32 * k]);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int q = 0; q < CMAX; ++q) {
+    const int c = wid + q * NW;
+    if (c < J) {
+      const T sc = warp_reduce_d(acc_get(dacc[q]));
+      if (lane == 0) partials[(int64_t)blockIdx.x * J + c] = num<T>::to_d(sc);
+    }
   }
 }
 
@@ -807,12 +873,22 @@ int vec_multi_update(const T *V, int64_t ldv, int J, const double *h, T *w, int6
 template <typename T>
 int vec_update_dot(const T *V, int64_t ldv, int J, const double *h, T *w, int64_t n, double *partials,
                    cudaStream_t s, const Seg &S) {
-  // measured on GB300 at n = 2M: a win up to 8 columns (40 us against 65 us
-  // for the two sweeps in double-word); wider, the per-thread register
-  // arrays cut the occupancy below what the separate sweeps reach
-  if (J > 8) return PP_ERR_UNSUPPORTED;
-  PP_CUDA_TRY(pdl_launch(k_update_dot<T, 8>, dim3(nchunks(n)), dim3(TPB), 0, s, V, ldv, J, h, w, n, partials, S));
+  // measured on GB300 at n = 2M: registers hold the row's columns up to 8
+  // (40 us against 65 us for the two sweeps in double-word); wider, the
+  // register arrays cut the occupancy, and a shared-memory tile of the
+  // columns takes over up to kUpdateDotTileMaxJ
+  if (J <= 8) {
+    PP_CUDA_TRY(pdl_launch(k_update_dot<T, 8>, dim3(nchunks(n)), dim3(TPB), 0, s, V, ldv, J, h, w, n, partials, S));
+    ++pp_launch_count();
+    return PP_OK;
+  }
+  if (J > kUpdateDotTileMaxJ) return PP_ERR_UNSUPPORTED;
+  const size_t sm = ((size_t)J + TPB + (size_t)J * TPB) * sizeof(T);
+  if (sm > 48 * 1024)
+    PP_CUDA_TRY(cudaFuncSetAttribute(k_update_dot_tile<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  PP_CUDA_TRY(pdl_launch(k_update_dot_tile<T>, dim3(nchunks(n)), dim3(TPB), sm, s, V, ldv, J, h, w, n, partials, S));
   ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
 template <typename T>
