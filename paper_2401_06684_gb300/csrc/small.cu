@@ -89,12 +89,14 @@ __global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H,
                        : gscratch + ((int64_t)seg * gridDim.x + k) * ((int64_t)ld * m + 2 * m);
   double *g = M + (int64_t)ld * m;  // rhs / solution, m entries
   const double s = sig[k];
-  for (int c = 0; c < m; ++c)
-    for (int r = threadIdx.x; r < m; r += blockDim.x) {
-      double v = (r <= c + 1) ? H[(int64_t)c * ldh + r] : 0.0;
-      if (r == c) v += s;
-      M[(int64_t)c * ld + r] = v;
-    }
+  // one flat loop over the m x m entries (loads issued back to back, not one
+  // column at a time)
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int c = idx / m, r = idx - c * m;
+    double v = (r <= c + 1) ? H[(int64_t)c * ldh + r] : 0.0;
+    if (r == c) v += s;
+    M[(int64_t)c * ld + r] = v;
+  }
   for (int r = threadIdx.x; r < m; r += blockDim.x) g[r] = (r == 0) ? 1.0 : 0.0;
   __syncthreads();
   for (int c = 0; c + 1 < m; ++c) {
@@ -151,12 +153,12 @@ __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict
   double *M = sm + (int64_t)wid * ((int64_t)ld * m + m);
   double *g = M + (int64_t)ld * m;
   const double s = sig[k];
-  for (int c = 0; c < m; ++c)
-    for (int r = lane; r < m; r += 32) {
-      double v = (r <= c + 1) ? H[(int64_t)c * ldh + r] : 0.0;
-      if (r == c) v += s;
-      M[(int64_t)c * ld + r] = v;
-    }
+  for (int idx = lane; idx < m * m; idx += 32) {
+    const int c = idx / m, r = idx - c * m;
+    double v = (r <= c + 1) ? H[(int64_t)c * ldh + r] : 0.0;
+    if (r == c) v += s;
+    M[(int64_t)c * ld + r] = v;
+  }
   for (int r = lane; r < m; r += 32) g[r] = (r == 0) ? 1.0 : 0.0;
   __syncwarp();
   for (int c = 0; c + 1 < m; ++c) {
@@ -273,13 +275,13 @@ __global__ void __launch_bounds__(128) k_hess_quad_c(const double *__restrict__ 
   zc *M = reinterpret_cast<zc *>(use_smem ? sm : gscratch + (int64_t)k * 2 * ((int64_t)ld * m + 2 * m));
   zc *g = M + (int64_t)ld * m;
   const double s = sig[k];
-  for (int c = 0; c < m; ++c)
-    for (int r = threadIdx.x; r < m; r += blockDim.x) {
-      zc v = {0.0, 0.0};
-      if (r <= c + 1) v = {H[2 * ((int64_t)c * ldh + r)], H[2 * ((int64_t)c * ldh + r) + 1]};
-      if (r == c) v.re += s;
-      M[(int64_t)c * ld + r] = v;
-    }
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) {
+    const int c = idx / m, r = idx - c * m;
+    zc v = {0.0, 0.0};
+    if (r <= c + 1) v = {H[2 * ((int64_t)c * ldh + r)], H[2 * ((int64_t)c * ldh + r) + 1]};
+    if (r == c) v.re += s;
+    M[(int64_t)c * ld + r] = v;
+  }
   for (int r = threadIdx.x; r < m; r += blockDim.x) g[r] = {r == 0 ? 1.0 : 0.0, 0.0};
   __syncthreads();
   for (int c = 0; c + 1 < m; ++c) {
