@@ -361,9 +361,10 @@ int pp_get_poly_nodes(pp_handle h, int32_t *kind, double *nodes_re_h, double *no
  * x = f(A) b (Algorithm 1 or 2 by opts.side; Sec. 4 for PP_SQRT), iterating
  * until the stopping estimate is below tol or m = m_max.  b_d, x_d: device
  * vectors of n entries of the handle's vector dtype (nrhs > 1: n x nrhs,
- * column-major, solved as independent processes in lockstep through
- * pp_apply_batch; stencil handles only, m_max <= 1024); x_d must not alias
- * b_d.  On PP_ERR_NOT_CONVERGED x_d still holds the last
+ * column-major; stencil handles solve them as independent processes in
+ * lockstep through pp_apply_batch, m_max <= 1024; CSR and Wilson handles
+ * one after another, stats summed, iters and est_err the largest); x_d must
+ * not alias b_d.  On PP_ERR_NOT_CONVERGED x_d still holds the last
  * iterate.  stats (host, may be NULL) is filled on return.  Blocks the
  * calling thread at each stopping check (a few bytes read back).
  * The kernels of the steps between two stopping checks are captured once

@@ -1933,10 +1933,41 @@ int pp_apply(pp_handle c, int32_t f, const void *b_d, int64_t nrhs, int32_t m_ma
   if (c->cplx) {
     if (c->opts.orth == PP_ORTH_LANCZOS || c->opts.two_pass)
       return pp_set_error(PP_ERR_INVALID_ARG, "a non-Hermitian complex operator needs Arnoldi (CGS2)");
-    if (nrhs > 1) return pp_set_error(PP_ERR_UNSUPPORTED, "nrhs > 1 for complex operators");
+  }
+  if (nrhs > 1 && c->op_kind != OPK_ST2D && c->op_kind != OPK_ST3D) {
+    // CSR and Wilson handles: the columns one after another on the handle
+    // (the later ones replay the captured segment graphs)
+    const size_t esz = c->op_kind == OPK_WILSON ? 16 : 8;  // complex128 / float64 entries per row
+    const int64_t rows = c->op_kind == OPK_WILSON ? c->n / 2 : c->n;
+    pp_stats tot;
+    memset(&tot, 0, sizeof tot);
+    int worst = PP_OK;
+    for (int64_t r = 0; r < nrhs; ++r) {
+      pp_stats st;
+      const int rc = pp_apply(c, f, (const char *)b_d + (size_t)r * rows * esz, 1, m_max, tol,
+                              (char *)x_d + (size_t)r * rows * esz, &st);
+      if (rc != PP_OK && rc != PP_ERR_NOT_CONVERGED) return rc;
+      if (rc != PP_OK) worst = rc;
+      tot.iters = std::max(tot.iters, st.iters);
+      tot.checks += st.checks;
+      tot.breakdown |= st.breakdown;
+      tot.mvms += st.mvms;
+      tot.inner_products += st.inner_products;
+      tot.est_err = std::max(tot.est_err, st.est_err);
+      tot.beta0 = std::max(tot.beta0, st.beta0);
+      tot.ms_total += st.ms_total;
+      tot.launches += st.launches;
+      tot.chain_launches += st.chain_launches;
+      tot.chain_bytes += st.chain_bytes;
+      tot.chain_ms += st.chain_ms;
+      tot.switch_iter = r == 0 ? st.switch_iter : std::max(tot.switch_iter, st.switch_iter);
+    }
+    tot.status = worst;
+    if (stats) *stats = tot;
+    if (worst != PP_OK) pp_set_error(worst, "m_max reached before the stopping estimate fell below tol");
+    return worst;
   }
   if (f == PP_SIGN) {  // sign(Q) b = Q (Q^2)^{-1/2} b (Sec. 6, Example 2)
-    if (nrhs != 1) return pp_set_error(PP_ERR_UNSUPPORTED, "PP_SIGN with nrhs > 1");
     // (Q^2)^{-1/2} b into x_d, then x_d -> scratch, Q scratch -> x_d (FP64)
     const int rc = pp_apply(c, PP_INVSQRT, b_d, 1, m_max, tol, x_d, stats);
     if (rc != PP_OK && rc != PP_ERR_NOT_CONVERGED) return rc;
@@ -1949,8 +1980,6 @@ int pp_apply(pp_handle c, int32_t f, const void *b_d, int64_t nrhs, int32_t m_ma
     return rc;
   }
   if (nrhs > 1) {
-    if (c->op_kind != OPK_ST2D && c->op_kind != OPK_ST3D)
-      return pp_set_error(PP_ERR_UNSUPPORTED, "nrhs > 1 is supported for the 2D/3D stencil operators");
     pp_handle hs[1] = {c};
     const int32_t fs[1] = {f};
     const void *bs[1] = {b_d};
