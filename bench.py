@@ -578,7 +578,12 @@ def run_ours(args):
                                    "(those replay the library's CUDA graphs of the steps between stopping "
                                    "checks)",
                          "launches": chain_launches,
-                         "bytes_per_launch": chain_bytes / max(chain_launches, 1)},
+                         "bytes_per_launch": chain_bytes / max(chain_launches, 1),
+                         **({"note": "the double-word Wilson kernel is bound by the FP32 pipe, not HBM: FMA "
+                                     "pipe 51 % active, issue 56 %, DRAM 11-19 % busy (ncu, "
+                                     "profiles/ncu_wilson_q_step_dw_sign16x32.txt); frac is the HBM fraction "
+                                     "of the metric"}
+                            if args.kind in ("wilson4d", "wilsonq2") and args.prec != "f64" else {})},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": "solves/s", "h2d_bytes_per_step": esz * n,
                     "d2h_bytes_per_step": esz * n},
