@@ -43,23 +43,24 @@ def host(t):
 
 
 class Q2:
-    def __init__(self, pp, dims, links, mu=MU):
+    def __init__(self, pp, dims, links, mu=MU, matrix=True):
         self.pp, self.dims = pp, tuple(dims)
         self.V = int(np.prod(dims))
         self.n = 12 * self.V
         self.links_d = dev(links.astype(np.complex64))
         self.h = pp.pp_create_stencil(pp.PP_WILSON4D_Q2, self.dims, [MW, mu], links=self.links_d,
                                       dtype=pp.PP_C128)
-        self.Q = wilson.q_matrix(self.dims, links, MW, mu)
+        self.Q = wilson.q_matrix(self.dims, links, MW, mu) if matrix else None
 
     def q2(self, v):
         return self.Q @ (self.Q @ v)
 
-    def set(self, prec, side=0, orth=0):
+    def set(self, prec, side=0, orth=0, check_every=0):
         o = self.pp.pp_default_opts()
         o.precision = PREC[prec]
         o.side = side
         o.orth = orth
+        o.check_every = check_every
         self.pp.pp_set_opts(self.h, o)
 
     def close(self):
@@ -300,5 +301,51 @@ def test_sign_zero_rhs_and_overlap():
         st = pp.pp_apply(L.h, pp.PP_SIGN, dev(b), xd, m_max=800, tol=1e-12)
         rho = 0.9
         assert rel(sign.overlap_apply(b, host(xd), rho), sign.overlap_apply(b, xs, rho)) < 1e-10
+    finally:
+        L.close()
+
+
+FULL = (16, 16, 16, 32)  # the lattice of the sign16x32 bench workload
+
+
+@pytest.mark.parametrize("prec", ["dw", "mixed"])
+def test_sign_free_field_full_size(prec):
+    # U = 1 on 16^3 x 32 (n = 1,572,864 complex): the library's sign(Q) b with
+    # the bench's q (Ritz, degree 31) against the per-momentum Fourier form
+    pp = load()
+    L = Q2(pp, FULL, synth.unit_links(FULL), matrix=False)
+    try:
+        b = synth.spinor_field(FULL, 7)
+        sym = wilson.free_q_symbol(FULL, MW, MU)
+        lam, X = np.linalg.eig(sym)
+        S = X @ (np.sign(lam.real)[..., None] * np.linalg.inv(X))
+        ref = wilson.free_spin_fun(FULL, b, S)
+        L.set(prec, check_every=2)
+        pp.pp_build_poly(L.h, 31, pp.PP_RITZ_LEJA)
+        xd = torch.empty(L.n, dtype=torch.complex128, device="cuda")
+        st = pp.pp_apply(L.h, pp.PP_SIGN, dev(b), xd, m_max=300, tol=1e-11)
+        assert st.status == pp.PP_OK
+        assert rel(host(xd), ref) < 1e-9
+    finally:
+        L.close()
+
+
+def test_sign_identities_full_size():
+    # random SU(3) links on 16^3 x 32: sign(Q)^2 b = b and
+    # (Q^2)^{-1/2} (Q^2)^{1/2} b = b through the library alone
+    pp = load()
+    L = Q2(pp, FULL, synth.wilson_links(FULL, 1), matrix=False)
+    try:
+        L.set("dw", check_every=2)
+        pp.pp_build_poly(L.h, 31, pp.PP_RITZ_LEJA)
+        b = dev(synth.spinor_field(FULL, 0))
+        x1 = torch.empty(L.n, dtype=torch.complex128, device="cuda")
+        x2 = torch.empty_like(x1)
+        assert pp.pp_apply(L.h, pp.PP_SIGN, b, x1, m_max=300, tol=1e-12).status == pp.PP_OK
+        assert pp.pp_apply(L.h, pp.PP_SIGN, x1, x2, m_max=300, tol=1e-12).status == pp.PP_OK
+        assert rel(host(x2), host(b)) < 1e-10
+        assert pp.pp_apply(L.h, pp.PP_SQRT, b, x1, m_max=300, tol=1e-12).status == pp.PP_OK
+        assert pp.pp_apply(L.h, pp.PP_INVSQRT, x1, x2, m_max=300, tol=1e-12).status == pp.PP_OK
+        assert rel(host(x2), host(b)) < 1e-10
     finally:
         L.close()
