@@ -39,18 +39,18 @@ __global__ void k_tri_quad(const double *__restrict__ H, int ldh, int m, const d
   const double s = sig[k];
   double *cp = scratch + (int64_t)k * m;  // modified super-diagonal
   double *x = X + (int64_t)k * m;         // modified rhs, then solution
-  // forward elimination of (T + sI) x = e_1
-  double den = H[0] + s;
-  double cprev = (m > 1) ? H[1] / den : 0.0;
-  double dprev = 1.0 / den;
+  // forward elimination of (T + sI) x = e_1 (one FP64 division per row)
+  double iden = 1.0 / (H[0] + s);
+  double cprev = (m > 1) ? H[1] * iden : 0.0;
+  double dprev = iden;
   cp[0] = cprev;
   x[0] = dprev;
   for (int i = 1; i < m; ++i) {
     const double bsub = H[(int64_t)(i - 1) * ldh + i];  // beta_{i-1}
-    den = (H[(int64_t)i * ldh + i] + s) - bsub * cprev;
+    iden = 1.0 / ((H[(int64_t)i * ldh + i] + s) - bsub * cprev);
     const double bsup = (i + 1 < m) ? H[(int64_t)i * ldh + i + 1] : 0.0;
-    cprev = bsup / den;
-    dprev = (-bsub * dprev) / den;
+    cprev = bsup * iden;
+    dprev = (-bsub * dprev) * iden;
     cp[i] = cprev;
     x[i] = dprev;
   }
@@ -103,8 +103,9 @@ __global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H,
     const double a = M[(int64_t)c * ld + c];
     const double b = M[(int64_t)c * ld + c + 1];
     const double r = hypot(a, b);
-    const double cs = (r > 0.0) ? a / r : 1.0;
-    const double sn = (r > 0.0) ? b / r : 0.0;
+    const double ir = (r > 0.0) ? 1.0 / r : 0.0;  // one FP64 division per rotation
+    const double cs = (r > 0.0) ? a * ir : 1.0;
+    const double sn = b * ir;
     __syncthreads();  // everyone has read the pivot pair
     for (int cc = c + threadIdx.x; cc < m; cc += blockDim.x) {
       const double t1 = M[(int64_t)cc * ld + c];
@@ -119,9 +120,13 @@ __global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H,
     }
     __syncthreads();
   }
-  // back substitution R x = g, column oriented
+  // back substitution R x = g, column oriented; the diagonal's reciprocals
+  // first, in parallel, so that the sequential steps only multiply
+  double *rd = g + m;
+  for (int c = threadIdx.x; c < m; c += blockDim.x) rd[c] = 1.0 / M[(int64_t)c * ld + c];
+  __syncthreads();
   for (int c = m - 1; c >= 0; --c) {
-    if (threadIdx.x == 0) g[c] = g[c] / M[(int64_t)c * ld + c];
+    if (threadIdx.x == 0) g[c] = g[c] * rd[c];
     __syncthreads();
     const double xc = g[c];
     for (int r = threadIdx.x; r < c; r += blockDim.x) g[r] -= M[(int64_t)c * ld + r] * xc;
@@ -150,8 +155,9 @@ __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict
   wt += so;
   X += so;
   const int ld = m + 1;
-  double *M = sm + (int64_t)wid * ((int64_t)ld * m + m);
+  double *M = sm + (int64_t)wid * ((int64_t)ld * m + 2 * m);
   double *g = M + (int64_t)ld * m;
+  double *rd = g + m;
   const double s = sig[k];
   for (int idx = lane; idx < m * m; idx += 32) {
     const int c = idx / m, r = idx - c * m;
@@ -165,8 +171,9 @@ __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict
     const double a = M[(int64_t)c * ld + c];
     const double b = M[(int64_t)c * ld + c + 1];
     const double r = hypot(a, b);
-    const double cs = (r > 0.0) ? a / r : 1.0;
-    const double sn = (r > 0.0) ? b / r : 0.0;
+    const double ir = (r > 0.0) ? 1.0 / r : 0.0;
+    const double cs = (r > 0.0) ? a * ir : 1.0;
+    const double sn = b * ir;
     __syncwarp();
     for (int cc = c + lane; cc < m; cc += 32) {
       const double t1 = M[(int64_t)cc * ld + c];
@@ -181,8 +188,10 @@ __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict
     }
     __syncwarp();
   }
+  for (int c = lane; c < m; c += 32) rd[c] = 1.0 / M[(int64_t)c * ld + c];
+  __syncwarp();
   for (int c = m - 1; c >= 0; --c) {
-    const double xc = g[c] / M[(int64_t)c * ld + c];
+    const double xc = g[c] * rd[c];
     __syncwarp();
     for (int r = lane; r < c; r += 32) g[r] -= M[(int64_t)c * ld + r] * xc;
     if (lane == 0) g[c] = xc;
@@ -288,8 +297,9 @@ __global__ void __launch_bounds__(128) k_hess_quad_c(const double *__restrict__ 
     const zc a = M[(int64_t)c * ld + c];
     const zc b = M[(int64_t)c * ld + c + 1];
     const double r = hypot(hypot(a.re, a.im), hypot(b.re, b.im));
-    const zc cs = r > 0.0 ? zc{a.re / r, a.im / r} : zc{1.0, 0.0};
-    const zc sn = r > 0.0 ? zc{b.re / r, b.im / r} : zc{0.0, 0.0};
+    const double ir = r > 0.0 ? 1.0 / r : 0.0;
+    const zc cs = r > 0.0 ? zc{a.re * ir, a.im * ir} : zc{1.0, 0.0};
+    const zc sn = {b.re * ir, b.im * ir};
     __syncthreads();  // everyone has read the pivot pair
     for (int cc = c + threadIdx.x; cc < m; cc += blockDim.x) {
       const zc t1 = M[(int64_t)cc * ld + c];
@@ -304,8 +314,11 @@ __global__ void __launch_bounds__(128) k_hess_quad_c(const double *__restrict__ 
     }
     __syncthreads();
   }
+  zc *rd = g + m;  // reciprocals of the diagonal, in parallel first
+  for (int c = threadIdx.x; c < m; c += blockDim.x) rd[c] = zdiv(zc{1.0, 0.0}, M[(int64_t)c * ld + c]);
+  __syncthreads();
   for (int c = m - 1; c >= 0; --c) {
-    if (threadIdx.x == 0) g[c] = zdiv(g[c], M[(int64_t)c * ld + c]);
+    if (threadIdx.x == 0) g[c] = zmul(g[c], rd[c]);
     __syncthreads();
     const zc xc = g[c];
     for (int r = threadIdx.x; r < c; r += blockDim.x) g[r] = zsub(g[r], zmul(M[(int64_t)c * ld + r], xc));
@@ -377,7 +390,7 @@ int small_tridiag_quad(const double *H, int ldh, int m, const double *sig, const
 int small_hess_quad(const double *H, int ldh, int m, const double *sig, const double *wt, int K,
                     double *X, double *scratch, cudaStream_t s, const Seg &S) {
   if (m <= 64) {
-    const size_t per_warp = ((size_t)(m + 1) * m + m) * sizeof(double);
+    const size_t per_warp = ((size_t)(m + 1) * m + 2 * (size_t)m) * sizeof(double);
     int wpb = (int)((48 * 1024) / per_warp);
     if (wpb > 8) wpb = 8;
     if (wpb < 1) wpb = 1;
