@@ -102,9 +102,9 @@ __global__ void __launch_bounds__(128) k_hess_quad(const double *__restrict__ H,
   for (int c = 0; c + 1 < m; ++c) {
     const double a = M[(int64_t)c * ld + c];
     const double b = M[(int64_t)c * ld + c + 1];
-    const double r = hypot(a, b);
-    const double ir = (r > 0.0) ? 1.0 / r : 0.0;  // one FP64 division per rotation
-    const double cs = (r > 0.0) ? a * ir : 1.0;
+    const bool nz = a != 0.0 || b != 0.0;
+    const double ir = nz ? rhypot(a, b) : 0.0;  // 1 / sqrt(a^2 + b^2) in one call
+    const double cs = nz ? a * ir : 1.0;
     const double sn = b * ir;
     __syncthreads();  // everyone has read the pivot pair
     for (int cc = c + threadIdx.x; cc < m; cc += blockDim.x) {
@@ -170,9 +170,9 @@ __global__ void __launch_bounds__(256) k_hess_quad_warp(const double *__restrict
   for (int c = 0; c + 1 < m; ++c) {
     const double a = M[(int64_t)c * ld + c];
     const double b = M[(int64_t)c * ld + c + 1];
-    const double r = hypot(a, b);
-    const double ir = (r > 0.0) ? 1.0 / r : 0.0;
-    const double cs = (r > 0.0) ? a * ir : 1.0;
+    const bool nz = a != 0.0 || b != 0.0;
+    const double ir = nz ? rhypot(a, b) : 0.0;
+    const double cs = nz ? a * ir : 1.0;
     const double sn = b * ir;
     __syncwarp();
     for (int cc = c + lane; cc < m; cc += 32) {
@@ -296,9 +296,9 @@ __global__ void __launch_bounds__(128) k_hess_quad_c(const double *__restrict__ 
   for (int c = 0; c + 1 < m; ++c) {
     const zc a = M[(int64_t)c * ld + c];
     const zc b = M[(int64_t)c * ld + c + 1];
-    const double r = hypot(hypot(a.re, a.im), hypot(b.re, b.im));
-    const double ir = r > 0.0 ? 1.0 / r : 0.0;
-    const zc cs = r > 0.0 ? zc{a.re * ir, a.im * ir} : zc{1.0, 0.0};
+    const bool nz = a.re != 0.0 || a.im != 0.0 || b.re != 0.0 || b.im != 0.0;
+    const double ir = nz ? rnorm4d(a.re, a.im, b.re, b.im) : 0.0;
+    const zc cs = nz ? zc{a.re * ir, a.im * ir} : zc{1.0, 0.0};
     const zc sn = {b.re * ir, b.im * ir};
     __syncthreads();  // everyone has read the pivot pair
     for (int cc = c + threadIdx.x; cc < m; cc += blockDim.x) {
