@@ -250,8 +250,9 @@ int pp_set_opts(pp_handle h, const pp_opts *opts);
  * values and the nodes only (the indication of Sec. 5.2: between them an
  * interpolant may turn negative where A has no eigenvalues); the quadrature
  * of the small solve then spans the image at those points widened by 1e6
- * both ways, and PP_PREC_MIXED stays in double-word (the image does not
- * bound the FP32 amplification).
+ * both ways, and PP_PREC_MIXED stays in double-word for real handles (the
+ * image does not bound the FP32 amplification; complex handles estimate it
+ * from H_m, see PP_WILSON4D_Q2).
  * The node run costs degree + 1 operator applications and allocates a basis
  * of degree + 2 vectors in the workspace.
  */

@@ -73,7 +73,8 @@ struct pp_ctx {
   double a = 0, b = 0, img_lo = 0, img_hi = 0;
   // the image was taken at Ritz values only (no spectral interval of a
   // non-normal operator): it does not bound the FP32 amplification, so
-  // PP_PREC_MIXED stays in double-word
+  // PP_PREC_MIXED stays in double-word (complex operators estimate that
+  // amplification from H_m at each check instead)
   bool image_on_points = false;
   std::vector<double> qsig, qwt;
   int tile_bdx = 0;  // stencil threads per block chosen by pp_autotune (0 = default)
