@@ -81,7 +81,8 @@ def parse():
     p.add_argument("--prec", default="mixed", choices=["dw", "f64", "mixed"])
     p.add_argument("--tol", type=float, default=None, help="default: the workload's")
     p.add_argument("--cpu-iters", type=int, default=3)
-    p.add_argument("--m-max", type=int, default=1000)
+    p.add_argument("--m-max", type=int, default=None,
+                   help="basis size cap (default 1000; 200 for sign32x64, whose vectors are 403 MB)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--plain-m-max", type=int, default=1000)
@@ -99,6 +100,8 @@ def parse():
     a.desc, a.kind, a.dims, a.func = w[0], w[1], w[2], w[3]
     a.degree = w[4] if a.degree is None else a.degree
     a.tol = w[5] if a.tol is None else a.tol
+    if a.m_max is None:
+        a.m_max = 200 if a.workload == "sign32x64" else 1000
     a.orth = w[6]
     a.n = 1
     for d in a.dims:
