@@ -481,6 +481,12 @@ void segs_clear(pp_ctx *c) {
   c->segs.clear();
 }
 
+void segs_destroy(pp_ctx *c) {
+  segs_clear(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  c->cap_stream = nullptr;
+}
+
 // Everything a captured segment bakes in: workspace pointers, q, options, tol.
 void segs_validate(pp_ctx *c, double tol) {
   const Workspace &w = c->ws;
@@ -519,14 +525,26 @@ int run_segment(pp_ctx *c, Solve &S, uint64_t key, const std::function<int()> &b
   }
   const int64_t l0 = pp_launch_count(), cl0 = c->chain_launches, mv0 = S.mvms, ip0 = S.ip;
   const double cb0 = c->chain_bytes;
-  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+  if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+    c->graphs_off = true;
+    return body();
+  }
+  // the segment's launches go to the capture stream while it records
+  cudaStream_t cs = c->cap_stream;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
     c->graphs_off = true;
     return body();
   }
+  c->stream = cs;
+  S.s = cs;
   const int rc = body();
+  c->stream = s;
+  S.s = s;
   cudaGraph_t g = nullptr;
-  const cudaError_t e = cudaStreamEndCapture(s, &g);
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
   cudaGraphExec_t exec = nullptr;
   const bool ok = rc == PP_OK && e == cudaSuccess && g && cudaGraphInstantiate(&exec, g, 0) == cudaSuccess;
   if (g) cudaGraphDestroy(g);
@@ -728,16 +746,16 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
           RC(krylov_step<T2>(S, op2, V2, Y2, t2, j,
                              std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
       }
-      if (S.cx)
-        RC(small_hess_quad_c(S.H, ldh, j1, S.sig, S.wt, K, S.X, w.hess, s));
+      if (S.cx)  // S.s: the capture stream while a segment records
+        RC(small_hess_quad_c(S.H, ldh, j1, S.sig, S.wt, K, S.X, w.hess, S.s));
       else if (S.lanczos)
-        RC(small_tridiag_quad(S.H, ldh, j1, S.sig, S.wt, K, S.X, S.tri, s));
+        RC(small_tridiag_quad(S.H, ldh, j1, S.sig, S.wt, K, S.X, S.tri, S.s));
       else
-        RC(small_hess_quad(S.H, ldh, j1, S.sig, S.wt, K, S.X, w.hess, s));
+        RC(small_hess_quad(S.H, ldh, j1, S.sig, S.wt, K, S.X, w.hess, S.s));
       if (S.cx)
-        RC(small_combine_c(S.X, K, j1, mp, S.z, S.zprev, tol, w.st, s));
+        RC(small_combine_c(S.X, K, j1, mp, S.z, S.zprev, tol, w.st, S.s));
       else
-        RC(small_combine(S.X, K, j1, mp, S.z, S.zprev, tol, w.st, s));
+        RC(small_combine(S.X, K, j1, mp, S.z, S.zprev, tol, w.st, S.s));
       return PP_OK;
     };
     RC(run_segment(c, S, ((uint64_t)j0 << 34) | ((uint64_t)j1 << 2) | (uint64_t)ph, body));
@@ -2165,7 +2183,7 @@ int pp_poly_apply_static(pp_handle c, const void *x_d, void *y_d) {
 
 void pp_destroy(pp_handle c) {
   if (!c) return;
-  segs_clear(c);
+  segs_destroy(c);
   for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
   ws_free(c->ws);
   delete c;

@@ -91,6 +91,10 @@ struct pp_ctx {
   std::vector<uint64_t> seg_sig;
   uint64_t poly_gen = 0;    // bumped whenever q or its quadrature changes
   bool graphs_off = false;  // capture failed once: direct launches
+  // private stream the segments are captured on (capture is not allowed on
+  // the legacy default stream a handle may run on); the graphs are launched
+  // on the handle's stream
+  cudaStream_t cap_stream = nullptr;
 };
 
 // q(A) v by the Horner scheme of the Newton form (every kind of q unless
