@@ -371,8 +371,10 @@ int pp_get_poly_nodes(pp_handle h, int32_t *kind, double *nodes_re_h, double *no
  * The kernels of the steps between two stopping checks are captured once
  * as a CUDA graph per (step range, precision phase) and replayed by later
  * calls on the handle (results bitwise equal to direct launches); the
- * graphs are held by the handle and dropped when its workspace, q, options
- * or tol change; opts.profile = 1 launches the kernels directly.
+ * graphs are recorded on a private non-blocking stream the handle creates
+ * on first use, launched on the handle's stream, held by the handle (freed
+ * by pp_destroy) and dropped when its workspace, q, options or tol change;
+ * opts.profile = 1 launches the kernels directly.
  * f = PP_SIGN (PP_WILSON4D_Q2 handles, nrhs = 1; Sec. 6, Example 2):
  * x = sign(Q) b = Q (Q^2)^{-1/2} b, the solve for (Q^2)^{-1/2} b followed by
  * one FP64 application of Q on the device (stats describe the solve).
