@@ -280,10 +280,13 @@ int pp_autotune(pp_handle h, double tol, int32_t max_degree, int32_t *degree_out
  * Read back the polynomial: coeffs_h[0..*ncoeffs-1] (PP_CHEBYSHEV: the
  * coefficients c_i of q = sum c_i T_i((2z-a-b)/(b-a)); other kinds: the
  * coefficients of q in the real basis R_i of pp_set_poly_nodes, for real
- * nodes the Newton coefficients a_i; the nodes from pp_get_poly_nodes),
- * ab_h[2] = [a,b], image_h[2] =
- * [min, max] of z q(z)^2 on [a,b] (the interval of Prop. 3.2).  Any output
- * pointer may be NULL; cap = capacity of coeffs_h.  deg q = *ncoeffs - 1.
+ * nodes the Newton coefficients a_i; the nodes from pp_get_poly_nodes;
+ * for the complex q of a complex operator (PP_WILSON4D_Q2 with mu != 0) the
+ * real parts of its Newton coefficients), ab_h[2] = [a,b], image_h[2] =
+ * [min, max] of z q(z)^2 on [a,b] (the interval of Prop. 3.2; at the
+ * nodes and Ritz values where q was built from them without an interval).
+ * Any output pointer may be NULL; cap = capacity of coeffs_h.  deg q =
+ * *ncoeffs - 1.
  */
 int pp_get_poly(pp_handle h, double *coeffs_h, int32_t cap, int32_t *ncoeffs, double *ab_h,
                 double *image_h);
