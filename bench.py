@@ -282,6 +282,24 @@ def run_reference(args):
     rank, ws, _ = dist_env()
     if rank != 0:
         return
+    if args.kind == "batch":  # the oracle on one right-hand side of each problem, in list order
+        import synth
+        probs = synth.batch_problems(64, seed=2)
+        cpu_sample_batch(args, probs, budget_s=5.0)  # warm-up
+        cb = cpu_sample_batch(args, probs, budget_s=15.0)
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "solves/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (problem list seed 2, b ~ N(0,1) seed 1000 + i)",
+                "config": {"workload": args.desc, "problems": len(probs),
+                           "right_hand_sides": sum(p["nrhs"] for p in probs),
+                           "rows_total": sum(int(np.prod(p["dims"])) * p["nrhs"] for p in probs),
+                           "tol": args.tol, "parallelism": "replicas1",
+                           "l2": "flushed between timed steps (256 MB write)"},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
     # Steps are oracle iterations on the full workload; full solves run until
     # warmup + steps iterations have been seen.  value = 1 / (set-up + m * mean
     # iteration time), m = the oracle's own iteration count.
