@@ -376,18 +376,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+ST_STEP_END = b"// The flat block index is mapped"  # ops.cu: the batched kernel starts here
+
+
+def st_step_source_hash(kernel_src):
+    """Hash of ops.cu up to the batched kernel: the stencil helpers and st_step."""
+    data = open(kernel_src, "rb").read()
+    cut = data.find(ST_STEP_END)
+    return hashlib.sha256(data[:cut] if cut >= 0 else data).hexdigest()[:16]
+
+
 def traffic_from_profile(kernel_src):
-    """DRAM bytes per launch of the chain kernel from the committed ncu summary, if current."""
+    """DRAM bytes per launch of the chain kernel from the committed ncu summary, if its
+    source (ops.cu up to the batched kernel) is the one the counters were taken on."""
     path = os.path.join(ROOT, "profiles", "ncu_st_step_horner_convdiff128.txt")
     if not os.path.exists(path):
         return None
-    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
     vals = {}
     for line in open(path):
         parts = line.split()
         if len(parts) >= 2 and parts[0].endswith(":"):
             vals[parts[0][:-1]] = parts[1]
-    if vals.get("ops_cu_sha256_16") != h:
+    if vals.get("st_step_src_sha256_16") != st_step_source_hash(kernel_src):
         return None
     try:
         return float(vals["traffic_bytes_per_launch"])
