@@ -7,10 +7,17 @@ convection-diffusion operator on a 128^3 grid (n = 2,097,152, c*h = 0.5,
 non-Hermitian, so Arnoldi with CGS2), Chebyshev q of degree 16 on the exact
 spectral interval, stopping estimate < 1e-10, mixed precision (double-word
 start, FP32 once its rounding is below the tolerance).  --workload selects
-the other single-GPU workloads (2D Laplacian 2048^2 with A^{-1/2}, Lanczos;
-2D Laplacian 64^2 in CSR).  The metric is solves per
-second over all ranks; ranks solve independent right-hand sides (seed 0 +
-rank), no collective on the data path.
+the other single-GPU workloads.  The metric is solves per second over all
+ranks; ranks solve independent right-hand sides (seed 0 + rank), no
+collective on the data path.
+
+Besides the timed value the line carries, measured outside the timed region:
+accuracy.rel_err_vs_oracle (the timed solve's x against the FP64 oracle's
+x*), the same configuration in the other arithmetics (companions: double-word
+and IEEE FP64, each with its own oracle error), the degree-0 in-GPU baselines
+(plain_gpu), the chain's roofline (live, and out of L2 on an 8192^2 grid),
+the oracle's own whole solve on the host cores (cpu_baseline) and an
+end-to-end figure through pp_apply_host.
 
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
 on the same workload instead.
@@ -80,11 +87,14 @@ def parse():
     p.add_argument("--degree", type=int, default=None, help="default: the workload's")
     p.add_argument("--prec", default="mixed", choices=["dw", "f64", "mixed"])
     p.add_argument("--tol", type=float, default=None, help="default: the workload's")
-    p.add_argument("--cpu-iters", type=int, default=3)
     p.add_argument("--m-max", type=int, default=None,
                    help="basis size cap (default 1000; 200 for sign32x64, whose vectors are 403 MB)")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-plain", action="store_true", help="skip the degree-0 in-GPU baselines")
+    p.add_argument("--no-companions", action="store_true",
+                   help="skip the double-word / FP64 solves of the same configuration")
+    p.add_argument("--no-oracle-err", action="store_true", help="skip the error against the FP64 oracle")
+    p.add_argument("--no-out-of-l2", action="store_true", help="skip the 8192^2 out-of-L2 chain timing")
     p.add_argument("--plain-m-max", type=int, default=1000)
     p.add_argument("--poly", default=None, choices=["ritz", "harmonic", "lsq"],
                    help="graph workload: the kind of q (default ritz)")
@@ -166,93 +176,177 @@ def config(args, ws):
 
 # ---------------------------------------------------------------- oracle (CPU)
 
-def oracle_timed(args, m_max, tol, seed=0):
-    """Run the FP64 oracle (Algorithm 1, as it stands) and time its set-up and iterations.
+class _OutOfBudget(Exception):
+    pass
 
-    Returns (result, setup seconds, list of per-iteration seconds)."""
-    from oracle import chebyshev as cheb, krylov, operators as ops
+
+def oracle_problem(args, seed=0):
+    """The oracle's operator (x -> A x on all host cores through the oracle's
+    OpenMP CSR product) and right-hand side for the workload."""
+    from oracle import operators as ops, spmv
     import synth
+    P = {}
     if args.kind == "convdiff3d7":
         A = ops.convdiff(args.dims, 0.5)
-        a, b = ops.convdiff_interval(args.dims, 0.5)
-        mv, rhs = A.dot, synth.rhs(A.shape[0], seed)
+        P["ab"] = ops.convdiff_interval(args.dims, 0.5)
+        P["mv"], P["rhs"] = spmv.CsrMv(A), synth.rhs(A.shape[0], seed)
     elif args.kind == "wilson4d":
         from oracle import wilson
         D = wilson.dirac_matrix(args.dims, synth.wilson_links(args.dims, 1), WILSON_M0)
-        DH = D.conj().T.tocsr()
-        mv = lambda v: DH @ (D @ v)  # noqa: E731
-        a, b = 0.01, 96.0  # interval only shapes q; the per-iteration cost does not depend on it
-        rhs = synth.spinor_field(args.dims, seed)
+        mD, mDH = spmv.CsrMv(D), spmv.CsrMv(D.conj().T.tocsr())
+        P["mv"] = lambda v: mDH(mD(v))  # noqa: E731
+        P["ab"] = (0.01, 96.0)  # shapes q only; the cost per iteration does not depend on it
+        P["rhs"] = synth.spinor_field(args.dims, seed)
     elif args.kind == "wilsonq2":
         from oracle import wilson
-        Q = wilson.q_matrix(args.dims, synth.wilson_links(args.dims, 1), SIGN_MW, SIGN_MU)
-        mv = lambda v: Q @ (Q @ v)  # noqa: E731
-        rhs = synth.spinor_field(args.dims, seed)
+        mQ = spmv.CsrMv(wilson.q_matrix(args.dims, synth.wilson_links(args.dims, 1), SIGN_MW, SIGN_MU))
+        P["Q"] = mQ
+        P["mv"] = lambda v: mQ(mQ(v))  # noqa: E731
+        P["rhs"] = synth.spinor_field(args.dims, seed)
     elif args.kind == "graphcsr":
         import scipy.sparse as sp
-        from oracle import ritz
         rp, col, val = graph_csr(args.dims[0])
         A = sp.csr_matrix((val, col, rp), shape=(args.dims[0], args.dims[0]))
-        mv, rhs = A.dot, synth.unit_vector(A.shape[0], 4 + seed)
+        P["mv"], P["rhs"] = spmv.CsrMv(A), synth.unit_vector(A.shape[0], 4 + seed)
     else:
         A = ops.laplace(args.dims)
-        a, b = ops.laplace_interval(args.dims)
-        mv, rhs = A.dot, synth.rhs(A.shape[0], seed)
+        P["ab"] = ops.laplace_interval(args.dims)
+        P["mv"], P["rhs"] = spmv.CsrMv(A), synth.rhs(A.shape[0], seed)
+    return P
+
+
+def oracle_timed(args, m_max, tol, seed=0, budget_s=None, P=None, max_iters=None):
+    """Run the FP64 oracle (Algorithm 1, as it stands) on the workload and time it.
+
+    Returns (result or None, set-up seconds, per-iteration seconds).  With
+    budget_s the run is abandoned (result None) once it has taken longer."""
+    from oracle import chebyshev as cheb, krylov
+    if P is None:
+        P = oracle_problem(args, seed)
+    mv, rhs = P["mv"], P["rhs"]
     stamps = []
     t0 = time.perf_counter()
-    if args.kind == "graphcsr":  # Example 3: q from the oracle's own Ritz values (part of the set-up)
-        if args.poly == "lsq":
-            from oracle import lsq
-            H60, _ = ritz.arnoldi(mv, ritz.start_vector(A.shape[0]), max(60, args.degree + 1))
-            th = ritz.ritz_values(H60, hermitian=False)
-            th = th[np.abs(th) > 1e-4 * np.abs(th).max()]  # the null space of the singular L left out
-            z = lsq.contour(th, 0.5 * np.abs(th).min(), max(2000, 20 * (args.degree + 1)))
-            P, Hq = lsq.basis(z, args.degree + 1)
-            al = lsq.coeffs(P, z ** -0.5)
-            qf = (args.degree, lambda v: lsq.apply(mv, Hq, al, len(z), v))
-        else:
-            x, an = ritz.ritz_poly(mv, A.shape[0], args.degree, harmonic=args.poly == "harmonic", hermitian=False)
+
+    def hook(j):
+        stamps.append(time.perf_counter())
+        if budget_s is not None and stamps[-1] - t0 > budget_s:
+            raise _OutOfBudget()
+        if max_iters is not None and len(stamps) > max_iters:
+            raise _OutOfBudget()
+
+    r = None
+    try:
+        if args.kind == "graphcsr":  # Example 3: q from the oracle's own Ritz values (part of the set-up)
+            from oracle import ritz
+            n = rhs.shape[0]
+            if args.poly == "lsq":
+                from oracle import lsq
+                H60, _ = ritz.arnoldi(mv, ritz.start_vector(n), max(60, args.degree + 1))
+                th = ritz.ritz_values(H60, hermitian=False)
+                th = th[np.abs(th) > 1e-4 * np.abs(th).max()]  # the null space of the singular L left out
+                z = lsq.contour(th, 0.5 * np.abs(th).min(), max(2000, 20 * (args.degree + 1)))
+                Pz, Hq = lsq.basis(z, args.degree + 1)
+                al = lsq.coeffs(Pz, z ** -0.5)
+                qf = (args.degree, lambda v: lsq.apply(mv, Hq, al, len(z), v))
+            else:
+                x, an = ritz.ritz_poly(mv, n, args.degree, harmonic=args.poly == "harmonic", hermitian=False)
+                qf = (args.degree, lambda v: ritz.newton_apply(mv, an, x, v))
+            r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, q=qf, side="left", m_max=m_max, tol=tol,
+                                  k_chk=max(1, 32 // (args.degree + 1)), orth=args.orth, on_iter=hook)
+        elif args.kind == "wilsonq2":  # Example 2: complex Ritz q (set-up), (Q^2)^{-1/2} b, then Q
+            from oracle import ritz, sign
+            x, an = ritz.ritz_poly(mv, rhs.shape[0], args.degree, complex_=True, hermitian=False)
             qf = (args.degree, lambda v: ritz.newton_apply(mv, an, x, v))
-        r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, q=qf, side="left", m_max=m_max, tol=tol,
-                              k_chk=max(1, 32 // (args.degree + 1)), orth=args.orth,
-                              on_iter=lambda j: stamps.append(time.perf_counter()))
-    elif args.kind == "wilsonq2":  # Example 2: complex Ritz q (set-up), (Q^2)^{-1/2} b, then Q
-        from oracle import ritz, sign
-        x, an = ritz.ritz_poly(mv, rhs.shape[0], args.degree, complex_=True, hermitian=False)
-        qf = (args.degree, lambda v: ritz.newton_apply(mv, an, x, v))
-        _, r = sign.sign_krylov(lambda v: Q @ v, rhs, q=qf, side="left", m_max=m_max, tol=tol,
-                                k_chk=max(1, 64 // (args.degree + 1)), orth=args.orth,
-                                on_iter=lambda j: stamps.append(time.perf_counter()))
-    else:
-        c = cheb.interp_coeffs(a, b, args.degree + 1)
-        r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, c, (a, b), side="left", m_max=m_max, tol=tol,
-                              k_chk=max(1, 64 // (args.degree + 1)), hermitian=args.orth == "lanczos",
-                              orth=args.orth, on_iter=lambda j: stamps.append(time.perf_counter()))
+            xs, r = sign.sign_krylov(P["Q"], rhs, q=qf, side="left", m_max=m_max, tol=tol,
+                                     k_chk=max(1, 64 // (args.degree + 1)), orth=args.orth, on_iter=hook)
+            r = dict(r, x=xs)
+        else:
+            a, b = P["ab"]
+            c = cheb.interp_coeffs(a, b, args.degree + 1)
+            r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, c, (a, b), side="left", m_max=m_max, tol=tol,
+                                  k_chk=max(1, 64 // (args.degree + 1)), hermitian=args.orth == "lanczos",
+                                  orth=args.orth, on_iter=hook)
+    except _OutOfBudget:
+        r = None
     t_end = time.perf_counter()
-    setup = stamps[0] - t0
+    setup = stamps[0] - t0 if stamps else t_end - t0
     iters = [b_ - a_ for a_, b_ in zip(stamps[:-1], stamps[1:])]
-    r["tail_s"] = t_end - stamps[-1]
+    if r is not None:
+        r["solve_s"] = t_end - t0
     return r, setup, iters
 
 
-def cpu_sample(args, m_full):
-    """The oracle on the full workload for a few iterations, extrapolated to m_full iterations."""
-    # the sign workload's oracle iteration takes 2 d + 1 sparse Q^2 products (about a minute): one
-    k = 1 if args.kind == "wilsonq2" else max(1, args.cpu_iters)
-    r, setup, iters = oracle_timed(args, k, 0.0)
-    t_iter = statistics.mean(iters)
+def oracle_threads():
+    from oracle import spmv
+    return spmv.threads()
+
+
+# iterations of the GPU solve of the workloads whose oracle solve takes minutes
+# (measured), to extrapolate the oracle's solve time from its iteration time
+GPU_ITERS = {"laplace2048": 300, "wilson16x32": 6, "sign16x32": 8}
+
+ORACLE_SAMPLE_NOTE = ("numpy/scipy FP64; CSR products on {t} OpenMP threads (the oracle's own kernel), "
+                      "Gram-Schmidt products in OpenBLAS, vector updates in numpy")
+
+
+def cpu_sample(args, m_full, budget_s=45.0):
+    """The oracle on the full workload: whole solves at the bench's tolerance
+    when one fits in budget_s, else the iterations run by then, extrapolated
+    to m_full iterations.  Returns (cpu_baseline dict, the last whole run or None)."""
+    t = oracle_threads()
+    note = ORACLE_SAMPLE_NOTE.format(t=t)
+    P = oracle_problem(args, 0)
+    r, setup, iters = oracle_timed(args, 1000 if args.kind != "wilsonq2" else args.m_max, args.tol,
+                                   budget_s=budget_s, P=P)
+    if r is not None:
+        return ({"value": 1.0 / r["solve_s"], "unit": "solves/s", "cores": t, "kind": "oracle",
+                 "sample": f"one whole oracle solve of the full workload (Algorithm 1, {note}) to the "
+                           f"bench's tolerance: set-up {setup:.2f}s + {r['iters']} iterations = "
+                           f"{r['solve_s']:.1f}s"}, r)
+    t_iter = statistics.mean(iters) if iters else float("nan")
     t_solve = setup + m_full * t_iter
-    return {"value": 1.0 / t_solve, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle Algorithm 1 (numpy/scipy FP64; SpMV single-threaded, OpenBLAS for the "
-                      f"Gram-Schmidt products) run for {k} iterations on the full workload: set-up "
-                      f"{setup:.2f}s + {t_iter:.2f}s/iteration, extrapolated to the {m_full} iterations "
-                      f"of a solve = {t_solve:.1f}s"}
+    return ({"value": 1.0 / t_solve, "unit": "solves/s", "cores": t, "kind": "oracle",
+             "sample": f"oracle Algorithm 1 ({note}) on the full workload, stopped after {budget_s:.0f}s: "
+                       f"set-up {setup:.2f}s + {len(iters)} iterations of {t_iter:.2f}s, extrapolated to the "
+                       f"{m_full} iterations of the GPU solve = {t_solve:.1f}s"}, None)
+
+
+def oracle_reference(args, seed=0, run=None):
+    """The FP64 oracle's x* for the workload's right-hand side (seed), or None.
+
+    Laplacians: the closed form (sine basis).  Convection-diffusion and the
+    graph Laplacian: the oracle's Algorithm 1 run to a tight stopping estimate
+    (run, the cpu_baseline's whole solve, is reused when its estimate already
+    met that).  Returns (x or None, description)."""
+    import synth
+    from oracle import exact
+    if args.kind in ("laplace2d5", "laplace2d5csr"):
+        if args.n > 5_000_000:
+            return None, "not computed: the closed form needs dense 1D transforms of the 8192-point axes"
+        b = synth.rhs(args.n, seed)
+        return exact.separable_fun(args.dims, b, 0.5 * args.func, "laplace"), \
+            "closed form (Kronecker product of 1D sine transforms)"
+    tight = {"convdiff3d7": 1e-13, "graphcsr": 1e-11}.get(args.kind)
+    if tight is None:
+        return None, ("not computed by the bench (the oracle takes minutes per solve on the lattice); "
+                      "the GPU tests compare this size with the free-field closed form")
+    if run is not None and run.get("history") and run["history"][-1][1] < tight and seed == 0:
+        r = run
+    else:
+        r, _, _ = oracle_timed(args, 1000, tight, seed)
+    return r["x"], (f"oracle Algorithm 1 (FP64, {'Ritz' if args.kind == 'graphcsr' else 'Chebyshev'} q of "
+                    f"degree {args.degree}, {args.orth}) to a stopping estimate of "
+                    f"{r['history'][-1][1]:.1e} < {tight:g} ({r['iters']} iterations)")
+
+
+def rel_err(x, ref):
+    return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
 
 
 def cpu_sample_batch(args, probs, budget_s=15.0):
     """The oracle (Algorithm 1, FP64) on one right-hand side of each problem of
     the batch's list, in list order, until about budget_s seconds of work."""
-    from oracle import chebyshev as cheb, krylov, operators as ops
+    from oracle import chebyshev as cheb, krylov, operators as ops, spmv
     import synth
     solved, t_used, used = 0, 0.0, []
     for i, p in enumerate(probs):
@@ -264,8 +358,9 @@ def cpu_sample_batch(args, probs, budget_s=15.0):
         deg = 16
         c = cheb.interp_coeffs(ab[0], ab[1], deg + 1)
         b = synth.rhs(A.shape[0], 1000 + i, nrhs=p["nrhs"]) if p["nrhs"] > 1 else synth.rhs(A.shape[0], 1000 + i)[None, :]
+        mv = spmv.CsrMv(A)
         t0 = time.perf_counter()
-        krylov.pp_arnoldi(A.dot, b[0], 0.5 * p["f"], c, ab, side="left", m_max=1000, tol=args.tol,
+        krylov.pp_arnoldi(mv, b[0], 0.5 * p["f"], c, ab, side="left", m_max=1000, tol=args.tol,
                           k_chk=max(1, 64 // (deg + 1)), hermitian=p["kind"] != "convdiff3d7",
                           orth="lanczos" if p["kind"] != "convdiff3d7" else "cgs2")
         t_used += time.perf_counter() - t0
@@ -273,12 +368,18 @@ def cpu_sample_batch(args, probs, budget_s=15.0):
         used.append(i)
         if t_used > budget_s:
             break
-    return {"value": solved / t_used, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"oracle Algorithm 1 (numpy/scipy FP64, degree 16) on one right-hand side of each of "
-                      f"problems {used[0]}..{used[-1]} of the batch's list ({solved} solves, {t_used:.1f}s)"}
+    t = oracle_threads()
+    return {"value": solved / t_used, "unit": "solves/s", "cores": t, "kind": "oracle", "solves": solved,
+            "sample": f"oracle Algorithm 1 ({ORACLE_SAMPLE_NOTE.format(t=t)}, degree 16) on one right-hand side "
+                      f"of each of problems {used[0]}..{used[-1]} of the batch's list ({solved} solves, "
+                      f"{t_used:.1f}s)"}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores.
+
+    A step is one whole oracle solve where one takes at most a minute, else
+    one oracle iteration (step_unit says which); warm-up: one step."""
     rank, ws, _ = dist_env()
     if rank != 0:
         return
@@ -289,13 +390,17 @@ def run_reference(args):
     if args.workload in why:
         print(json.dumps({"impl": "reference", "unavailable": why[args.workload]}), flush=True)
         return
+    t = oracle_threads()
+    note = ORACLE_SAMPLE_NOTE.format(t=t)
+    budget = 150.0  # seconds of timed oracle work
     if args.kind == "batch":  # the oracle on one right-hand side of each problem, in list order
         import synth
         probs = synth.batch_problems(64, seed=2)
         cpu_sample_batch(args, probs, budget_s=5.0)  # warm-up
         cb = cpu_sample_batch(args, probs, budget_s=15.0)
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "solves/s", "n_gpus": ws,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / cb["value"],
+                "steps": cb["solves"], "warmup": 1, "ms_per_step": 1e3 / cb["value"],
+                "step_unit": "one oracle solve of one right-hand side of a problem of the list",
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic (problem list seed 2, b ~ N(0,1) seed 1000 + i)",
                 "config": {"workload": args.desc, "problems": len(probs),
@@ -307,29 +412,37 @@ def run_reference(args):
                 "e2e": {"value": cb["value"], "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(line), flush=True)
         return
-    # Steps are oracle iterations on the full workload; full solves run until
-    # warmup + steps iterations have been seen.  value = 1 / (set-up + m * mean
-    # iteration time), m = the oracle's own iteration count.
-    need = args.warmup + args.steps
-    setups, iters, m = [], [], None
-    while len(iters) < need:
-        r, setup, its = oracle_timed(args, 1000, args.tol)
-        setups.append(setup)
-        iters += its
-        m = r["iters"]
-    timed = iters[args.warmup:need]
-    t_solve = statistics.mean(setups) + m * statistics.mean(timed)
-    value = 1.0 / t_solve
+    P = oracle_problem(args, 0)
+    t_run0 = time.perf_counter()
+    # warm-up: one whole solve if it ends within a minute
+    r, setup, its = oracle_timed(args, 1000, args.tol, budget_s=60.0, P=P)
+    if r is not None:  # steps are whole solves, until the budget or --steps is reached
+        times, m = [], r["iters"]
+        while len(times) < max(1, args.steps) and (not times or sum(times) + statistics.mean(times) <= budget):
+            r, _, _ = oracle_timed(args, 1000, args.tol, P=P)
+            times.append(r["solve_s"])
+        step_s, steps = statistics.mean(times), len(times)
+        value = 1.0 / step_s
+        unit = f"one whole oracle solve (set-up + {m} iterations)"
+        sample = f"{steps} whole oracle solves of the full workload (Algorithm 1, {note}), one warm-up solve before"
+    else:  # steps are oracle iterations: one run, stopped once warm-up + steps iterations are seen
+        r, setup, its = oracle_timed(args, 1000, args.tol, budget_s=budget, P=P,
+                                     max_iters=1 + max(1, args.steps))
+        times = its[1:] or its
+        step_s, steps = statistics.mean(times), len(times)
+        m = GPU_ITERS.get(args.workload, r["iters"] if r is not None else None)
+        value = 1.0 / (setup + m * step_s)
+        unit = "one oracle iteration"
+        sample = (f"{steps} oracle iterations (after one warm-up iteration) on the full workload (Algorithm 1, "
+                  f"{note}); value = 1 / (set-up {setup:.1f}s + {m} iterations of {step_s:.2f}s), {m} being "
+                  f"the GPU solve's iteration count")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_solve,
+            "steps": steps, "warmup": 1, "ms_per_step": 1e3 * step_s, "step_unit": unit,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (b ~ N(0,1), seed 0)", "config": config(args, 1),
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} timed oracle iterations (after {args.warmup} warm-up "
-                                       f"iterations) of full solves of this workload; a solve is set-up + "
-                                       f"{m} iterations = {t_solve:.1f}s"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": t, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "oracle_iters": m}
+            "oracle_iters": m, "run_s": time.perf_counter() - t_run0}
     print(json.dumps(line), flush=True)
 
 
@@ -405,6 +518,65 @@ def traffic_from_profile(kernel_src):
         return None
 
 
+def load_peak():
+    """(HBM GB/s, source): the measured copy bandwidth, else the 6.8 TB/s fallback."""
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        return float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def events_time(fn, reps, stream, flush=None):
+    """Mean milliseconds of fn() over reps calls, CUDA events on `stream`
+    around each call (after a flush of L2 when given), synchronised."""
+    import torch
+    ms = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return statistics.mean(ms)
+
+
+def chain_out_of_l2(pp, torch, degree=16, reps=5):
+    """The stencil chain out of L2: q(A) x by pp_poly_apply on the 2D Laplacian
+    8192^2 (vectors of 268 MB in FP32), Horner form, FP32 and double-word.
+    Algorithmic bytes of one call: the FP64 input converted in and the result
+    converted out ((8 + s) bytes per entry each way), the first step (2
+    vectors) and deg - 1 Horner steps (3 vectors each), s = 4 (FP32) or 8."""
+    peak, src = load_peak()
+    dims = (8192, 8192)
+    n = dims[0] * dims[1]
+    stream = torch.cuda.current_stream()
+    h = pp.pp_create_stencil(pp.PP_LAPLACE2D5, dims, stream=stream)
+    out = {"workload": "2D Laplacian 8192^2 (n=67108864), q(A) x by pp_poly_apply, Chebyshev degree %d "
+                       "in Newton/Horner form" % degree, "peak": peak, "peak_source": src, "unit": "GB/s"}
+    try:
+        pp.pp_build_poly(h, degree)
+        x = torch.randn(n, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
+        y = torch.empty_like(x)
+        for name, prec, esz in (("f32", pp.PP_PREC_MIXED, 4), ("dw", pp.PP_PREC_DW, 8)):
+            o = pp.pp_default_opts()
+            o.precision = prec
+            pp.pp_set_opts(h, o)
+            for _ in range(2):
+                pp.pp_poly_apply(h, x, y)
+            ms = events_time(lambda: pp.pp_poly_apply(h, x, y), reps, stream)
+            byt = ((2 + 3 * (degree - 1)) * esz + 2 * (8 + esz)) * n
+            gbs = byt / (ms * 1e-3) / 1e9
+            out[name] = {"achieved": gbs, "frac": gbs / peak, "us_per_step": 1e3 * ms / degree,
+                         "bytes_per_call": byt, "ms_per_call": ms}
+        del x, y
+    finally:
+        pp.pp_destroy(h)
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -425,6 +597,7 @@ def run_ours(args):
     dims = args.dims
     n = args.n
     keep = []
+    PREC = {"dw": pp.PP_PREC_DW, "f64": pp.PP_PREC_F64, "mixed": pp.PP_PREC_MIXED}
 
     def make_handle(degree):
         if args.kind == "convdiff3d7":
@@ -458,73 +631,46 @@ def run_ours(args):
             pp.pp_build_poly(hh, degree, interval_ab=(lo, hi))
         return hh
 
+    def opts_for(prec, profile=0):
+        o = pp.pp_default_opts()
+        o.precision = PREC[prec]
+        if args.two_pass or args.workload == "laplace8192":  # O(n) basis memory: two-pass Lanczos
+            o.two_pass = 1
+        o.clenshaw = 1 if args.clenshaw else 0
+        if args.kind == "graphcsr":  # Example 3 checks every 32/d iterations
+            o.check_every = max(1, 32 // (args.degree + 1))
+        if args.kind == "wilsonq2":  # Example 2 checks every 64/d iterations
+            o.check_every = max(1, 64 // (args.degree + 1))
+        o.profile = profile
+        return o
+
     h = make_handle(args.degree)
-    o = pp.pp_default_opts()
-    o.precision = {"dw": pp.PP_PREC_DW, "f64": pp.PP_PREC_F64, "mixed": pp.PP_PREC_MIXED}[args.prec]
-    pp.pp_set_opts(h, o)
-    if args.two_pass or args.workload == "laplace8192":  # O(n) basis memory: two-pass Lanczos
-        o.two_pass = 1
-    o.clenshaw = 1 if args.clenshaw else 0
-    if args.kind == "graphcsr":  # Example 3 checks every 32/d iterations
-        o.check_every = max(1, 32 // (args.degree + 1))
-    if args.kind == "wilsonq2":  # Example 2 checks every 64/d iterations
-        o.check_every = max(1, 64 // (args.degree + 1))
+    o = opts_for(args.prec)
     pp.pp_set_opts(h, o)
     if args.autotune:
         args.degree = pp.pp_autotune(h, args.tol, 64)
     vdt = torch.complex128 if args.complex else torch.float64
     esz = 16 if args.complex else 8
 
-    def rhs_host():
+    def rhs_host(seed):
         if args.kind == "graphcsr":
-            return synth.unit_vector(n, 4 + rank)
-        return synth.spinor_field(dims, rank) if args.complex else synth.rhs(n, rank)
+            return synth.unit_vector(n, 4 + seed)
+        return synth.spinor_field(dims, seed) if args.complex else synth.rhs(n, seed)
 
-    b = torch.from_numpy(rhs_host()).cuda()
+    b = torch.from_numpy(rhs_host(rank)).cuda()
     x = torch.empty(n, dtype=vdt, device="cuda")
+    s2 = torch.empty_like(x)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     m_max = args.m_max
 
-    def solve():
-        return pp.pp_apply(h, args.func, b, x, m_max=m_max, tol=args.tol)
+    def solve(hh=h, out=x, m=m_max):
+        return pp.pp_apply(hh, args.func, b, out, m_max=m, tol=args.tol)
 
     for _ in range(args.warmup):
         st = solve()
         assert st.status == pp.PP_OK, st.as_dict()
-    # accuracy of this configuration, outside the timed region, through the library only:
-    # SQRT: (A^{1/2})^2 b = A b;  INVSQRT: A^{1/2} (A^{-1/2} b) = b; and the distance to a
-    # double-word solve with the stopping estimate below 1e-13
-    s2 = torch.empty_like(x)
-    solve()
-    if args.func == pp.PP_SIGN:
-        ref_id = b
-        pp.pp_apply(h, pp.PP_SIGN, x, s2, m_max=m_max, tol=args.tol)
-        id_name = "identity_sign_sign_vs_b"
-    elif args.func > 0:
-        ref_id = torch.empty_like(x)
-        pp.pp_op_apply(h, b, ref_id)
-        pp.pp_apply(h, pp.PP_SQRT, x, s2, m_max=m_max, tol=args.tol)
-        id_name = "identity_sqrt_sqrt_vs_Ab"
-    else:
-        ref_id = b
-        pp.pp_apply(h, pp.PP_SQRT, x, s2, m_max=m_max, tol=args.tol)
-        id_name = "identity_sqrt_of_invsqrt_vs_b"
-    torch.cuda.synchronize()
-    ident = float(torch.linalg.norm(s2 - ref_id) / torch.linalg.norm(ref_id))
-    o_t = pp.pp_default_opts()
-    o_t.precision = pp.PP_PREC_DW
-    o_t.two_pass = o.two_pass
-    o_t.clenshaw = o.clenshaw
-    pp.pp_set_opts(h, o_t)
-    # basis of at most ~100 GB for the tight solve (the paper-size lattice keeps the run's m_max)
-    tight_m = max(m_max, 1000) if esz * n * 1000 < 100e9 else m_max
-    pp.pp_apply(h, args.func, b, s2, m_max=tight_m, tol=1e-13)
-    pp.pp_set_opts(h, o)
-    solve()
-    torch.cuda.synchronize()
-    diff_tight = float(torch.linalg.norm(x - s2) / torch.linalg.norm(s2))
 
-    # timed solves without per-run events: they replay the library's captured segment graphs
+    # ---- timed solves (they replay the library's captured segment graphs; no per-run events inside)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     stats = []
     clk = ClockSampler(local)
@@ -544,25 +690,21 @@ def run_ours(args):
     step_ms = [a.elapsed_time(e) for a, e in ev]
     t_total = max_over_ranks(sum(step_ms) / 1e3, ws)
     value = replica_value(args.steps, ws, t_total)
-    # the chain's roofline: one untimed solve with CUDA events around every run of operator launches
-    o.profile = 1
-    pp.pp_set_opts(h, o)
+    x_timed = x.cpu().numpy().copy()  # the result of the last timed solve
+
+    # ---- the chain's roofline: one untimed solve with CUDA events around every run of operator launches
+    pp.pp_set_opts(h, opts_for(args.prec, profile=1))
     flush.zero_()
     pst = solve().as_dict()
-    o.profile = 0
     pp.pp_set_opts(h, o)
     chain_ms, chain_bytes, chain_launches = pst["chain_ms"], pst["chain_bytes"], pst["chain_launches"]
     achieved = chain_bytes / (chain_ms / 1e3) / 1e9 if chain_ms > 0 else None
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(peaks_path):
-        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-    else:
-        peak, peak_src = 6800.0, "fallback"
+    peak, peak_src = load_peak()
     traffic = (traffic_from_profile(os.path.join(ROOT, "paper_2401_06684_gb300", "csrc", "ops.cu"))
                if args.workload == "convdiff128" and not args.clenshaw else None)
 
-    # end to end through the C ABI with host buffers (copies inside the timed region)
-    bh = torch.from_numpy(rhs_host()).pin_memory()
+    # ---- end to end through the C ABI with host buffers (copies inside the timed region)
+    bh = torch.from_numpy(rhs_host(rank)).pin_memory()
     xh = torch.empty(n, dtype=vdt).pin_memory()
     e2e_t = []
     for i in range(args.steps + 1):
@@ -574,36 +716,93 @@ def run_ours(args):
             e2e_t.append(time.perf_counter() - t0)
     e2e_val = replica_value(len(e2e_t), ws, max_over_ranks(sum(e2e_t), ws))
 
-    # in-GPU baseline: plain unpreconditioned Arnoldi (degree 0) in FP64 on the same problem
-    plain = None
+    # ---- accuracy, outside the timed region.  The identity's reference (A b for SQRT, b for
+    # INVSQRT / SIGN) comes from a double-word (FP64-grade) operator application, never from
+    # the FP32 one of mixed precision.
+    if args.func == pp.PP_SIGN:
+        ref_id, id_name = b, "identity_sign_sign_vs_b"
+        pp.pp_apply(h, pp.PP_SIGN, x, s2, m_max=m_max, tol=args.tol)
+    elif args.func > 0:
+        ref_id, id_name = torch.empty_like(x), "identity_sqrt_sqrt_vs_Ab"
+        pp.pp_set_opts(h, opts_for("dw"))
+        pp.pp_op_apply(h, b, ref_id)
+        pp.pp_set_opts(h, o)
+        pp.pp_apply(h, pp.PP_SQRT, x, s2, m_max=m_max, tol=args.tol)
+    else:
+        ref_id, id_name = b, "identity_sqrt_of_invsqrt_vs_b"
+        pp.pp_apply(h, pp.PP_SQRT, x, s2, m_max=m_max, tol=args.tol)
+    torch.cuda.synchronize()
+    ident = float(torch.linalg.norm(s2 - ref_id) / torch.linalg.norm(ref_id))
+
+    # ---- companions in the other arithmetics on the same handle and b, and the in-GPU
+    # baselines: plain unpreconditioned Arnoldi / Lanczos (degree 0) in FP64 and double-word
+    comp = {}
+    if not args.no_companions and rank == 0:
+        for prec in ("dw", "f64"):
+            if prec == args.prec:
+                continue
+            pp.pp_set_opts(h, opts_for(prec))
+            for _ in range(2):
+                solve(out=s2)
+            reps = max(3, min(args.steps, 10))
+            ms = events_time(lambda: solve(out=s2), reps, stream, flush)
+            stc = solve(out=s2)
+            torch.cuda.synchronize()
+            comp[prec] = {"value": 1e3 / ms, "unit": "solves/s", "ms_per_solve": ms, "solves_timed": reps,
+                          "iters": stc.iters, "mvms": stc.mvms, "status": pp.pp_strerror(stc.status),
+                          "x": s2.cpu().numpy().copy()}
+        pp.pp_set_opts(h, o)
+    plain = {}
     if not args.no_plain and rank == 0:
         hp = make_handle(0)
-        st0 = pp.pp_apply(hp, args.func, b, s2, m_max=args.plain_m_max, tol=args.tol)
-        torch.cuda.synchronize()
-        err0 = float(torch.linalg.norm(s2 - x) / torch.linalg.norm(x))
-        plain = {"value": 1e3 / st0.ms_total, "unit": "solves/s", "iters": st0.iters, "prec": "f64",
-                 "status": pp.pp_strerror(st0.status), "rel_diff_vs_preconditioned": err0}
+        for prec in ("f64", "dw"):
+            pp.pp_set_opts(hp, opts_for(prec))
+            st0 = pp.pp_apply(hp, args.func, b, s2, m_max=args.plain_m_max, tol=args.tol)
+            torch.cuda.synchronize()
+            plain[prec] = {"value": 1e3 / st0.ms_total, "unit": "solves/s", "iters": st0.iters,
+                           "status": pp.pp_strerror(st0.status), "x": s2.cpu().numpy().copy()}
         pp.pp_destroy(hp)
 
+    # ---- the stencil chain out of L2 (8192^2), and the 128^3 chain counted in DRAM bytes
+    out_l2 = None
+    if not args.no_out_of_l2 and rank == 0 and args.kind in ("convdiff3d7", "laplace2d5"):
+        out_l2 = chain_out_of_l2(pp, torch)
+
     m_full = stats[-1]["iters"]
-    cpu = None
+    pp.pp_destroy(h)
+    del flush
+
+    # ---- host work: the oracle's whole solve (cpu_baseline) and its x* (accuracy)
+    cpu, ref, ref_how = None, None, "not computed"
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_sample(args, m_full)
+        cpu, run = cpu_sample(args, m_full)
+        if not args.no_oracle_err:
+            ref, ref_how = oracle_reference(args, rank, run)
+    elif rank == 0 and not args.no_oracle_err:
+        ref, ref_how = oracle_reference(args, rank, None)
+
+    def err_or_none(xv):
+        return rel_err(xv, ref) if ref is not None else None
 
     if rank == 0:
+        for d in list(comp.values()) + list(plain.values()):
+            d["rel_err_vs_oracle"] = err_or_none(d.pop("x"))
+        mixed_dtype = args.prec == "mixed" and stats[-1]["switch_iter"] >= 0
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
             "ms_per_step_min_median_max": [min(step_ms), statistics.median(step_ms), max(step_ms)],
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": ("f32x2-dw" if args.prec == "mixed" and stats[-1]["switch_iter"] < 0 else
-                      {"dw": "f32x2-dw", "f64": "f64", "mixed": "f32x2-dw+f32"}[args.prec]),
-            "precision": ("double-word FP32 pairs throughout (no FP32 switch: the image of q was taken at "
-                          "Ritz values only)" if args.prec == "mixed" and stats[-1]["switch_iter"] < 0 else
-                          {"dw": "double-word FP32 pairs (FP64-grade)", "f64": "IEEE FP64",
-                           "mixed": "double-word start, FP32 after switch_iter"}[args.prec]),
+            "dtype": ("f32x2-dw+f32" if mixed_dtype else {"dw": "f32x2-dw", "f64": "f64", "mixed": "f32x2-dw"}[args.prec]),
+            "precision": ("double-word start, FP32 chain/basis/updates after switch_iter, FP64 coefficients and "
+                          "small solve" if mixed_dtype else
+                          "double-word FP32 pairs throughout (the switch rule never allowed FP32)" if args.prec == "mixed"
+                          else {"dw": "double-word FP32 pairs (FP64-grade)", "f64": "IEEE FP64"}[args.prec]),
             "data": "synthetic (b ~ N(0,1), seed = rank)", "config": config(args, ws),
+            "accuracy": {"rel_err_vs_oracle": err_or_none(x_timed), "oracle": ref_how,
+                         "target": 1e-8 if args.prec == "mixed" else 1e-10,
+                         id_name: ident, "est_err_last": stats[-1]["est_err"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "kernel": "%s (operator + %s update)" % (
@@ -617,6 +816,9 @@ def run_ours(args):
                                    "checks)",
                          "launches": chain_launches,
                          "bytes_per_launch": chain_bytes / max(chain_launches, 1),
+                         "dram_frac": (traffic * chain_launches / (chain_ms / 1e3) / 1e9 / peak
+                                       if traffic and chain_ms > 0 else None),
+                         "out_of_l2": out_l2,
                          **({"note": "the double-word Wilson kernel is bound by the FP32 pipe, not HBM: FMA "
                                      "pipe 51 % active, issue 56 %, DRAM 11-19 % busy (ncu, "
                                      "profiles/ncu_wilson_q_step_dw_sign16x32.txt); frac is the HBM fraction "
@@ -627,14 +829,12 @@ def run_ours(args):
                     "d2h_bytes_per_step": esz * n},
             "gpu_launches": int(sum(s["launches"] for s in stats)),
             "clocks": clocks,
-            "accuracy": {id_name: ident, "rel_diff_vs_dw_solve_tol1e-13": diff_tight,
-                         "est_err_last": stats[-1]["est_err"]},
             "switch_iter": stats[-1]["switch_iter"],
             "iters": m_full, "mvms": stats[-1]["mvms"], "wall_s": wall,
-            "plain_arnoldi_gpu": plain,
+            "companions": comp or None,
+            "plain_gpu": plain or None,
         }
         print(json.dumps(line), flush=True)
-    pp.pp_destroy(h)
     if ws > 1:
         dist.destroy_process_group()
 
@@ -708,11 +908,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     o.profile = 0
     pp.pp_set_opts(hs[0], o)
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(peaks_path):
-        peak, peak_src = float(json.load(open(peaks_path))["hbm_gbs"]), "measured"
-    else:
-        peak, peak_src = 6800.0, "fallback"
+    peak, peak_src = load_peak()
     cb, cms, cl = stats[0].chain_bytes, stats[0].chain_ms, stats[0].chain_launches
     achieved = cb / (cms / 1e3) / 1e9 if cms > 0 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -793,9 +989,8 @@ def run_probe(args):
         torch.cuda.synchronize()
         return 1e3 * e0.elapsed_time(e1) / reps
 
-    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    peak = float(json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6800.0
-    res = {"peak_GBs": peak, "peak_source": "measured" if os.path.exists(peaks_path) else "fallback"}
+    peak, src = load_peak()
+    res = {"peak_GBs": peak, "peak_source": src}
     for name, prec, esz in (("f32", pp.PP_PREC_MIXED, 4), ("dw", pp.PP_PREC_DW, 8)):
         for scheme in ("horner", "clenshaw"):
             o = pp.pp_default_opts()
