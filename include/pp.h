@@ -453,9 +453,14 @@ int pp_poly_apply(pp_handle h, const void *x_d, void *y_d);
  * pointers; PP_ERR_STATE before pp_build_poly; PP_ERR_UNSUPPORTED for CSR
  * handles in PP_PREC_DW or PP_PREC_MIXED (their converted values would need
  * an allocation) and for Wilson handles (they need a sixth vector).
+ * Device: the handle's kernels use the copy of the array on the device that
+ * was current when the handle was created; a call made while another device
+ * is current is refused (PP_ERR_INVALID_ARG).
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current).  Make that first call
- * before any stream capture.
+ * before any stream capture.  The call makes no other synchronising request
+ * (for a CSR handle the algorithmic byte count of its statistics leaves the
+ * matrix entries out until another entry point has read nnz).
  * Sharing: all calls in the process use the same array.  Every scratch entry
  * a call reads was written earlier in the same call, so nothing left by a
  * previous call affects the result; but calls whose work overlaps on the GPU

@@ -100,7 +100,7 @@ int prof_end(pp_ctx *c) {
 double step_bytes(const pp_ctx *c, const StepCoef &k, double esz) {
   double vecs = 2.0 + (k.sub_y ? 1.0 : 0.0) + (k.add_v ? 1.0 : 0.0);
   double bytes = vecs * esz * (double)c->n;
-  if (c->op_kind == OPK_CSR) bytes += (esz + 4.0) * (double)c->nnz + 8.0 * (double)(c->n + 1);
+  if (c->op_kind == OPK_CSR) bytes += (esz + 4.0) * (double)(c->nnz > 0 ? c->nnz : 0) + 8.0 * (double)(c->n + 1);
   if (c->op_kind == OPK_WILSON) {
     // t = D x (read x, write t) and out = alpha D^H t + beta x ...: the second
     // launch reads t and x; both read the links (288 bytes per site)
@@ -1111,11 +1111,17 @@ namespace {
 std::mutex g_static_mu;
 void *g_static_addr[kStaticMaxDevices] = {};
 
-// Device address of pp_static_scratch on the current device (looked up on the
-// first call per device).
-int static_scratch_addr(void **out) {
+// Device address of pp_static_scratch on the handle's device (looked up on
+// the first call per device).  The handle's kernels run on the device that
+// was current when it was created; the lookup needs that device current, so
+// a call from a thread whose current device differs is refused instead of
+// handing the kernels another GPU's copy of the array.
+int static_scratch_addr(const pp_ctx *c, void **out) {
   int dev = 0;
   PP_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev != c->device)
+    return pp_set_error(PP_ERR_INVALID_ARG, "the current CUDA device (" + std::to_string(dev) +
+                                                ") is not the handle's device (" + std::to_string(c->device) + ")");
   if (dev < 0 || dev >= kStaticMaxDevices) return pp_set_error(PP_ERR_UNSUPPORTED, "device ordinal >= 64");
   std::lock_guard<std::mutex> lock(g_static_mu);
   if (!g_static_addr[dev]) {
@@ -1702,6 +1708,7 @@ pp_ctx *new_ctx(void *stream) {
   pp_ctx *c = new pp_ctx();
   pp_default_opts(&c->opts);
   c->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) c->device = 0;
   return c;
 }
 
@@ -2169,13 +2176,10 @@ int pp_poly_apply_static(pp_handle c, const void *x_d, void *y_d) {
   if (c->op_kind == OPK_CSR && c->opts.precision != PP_PREC_F64)
     return pp_set_error(PP_ERR_UNSUPPORTED,
                         "CSR handles in PP_PREC_DW / PP_PREC_MIXED need a converted copy of the values; use PP_PREC_F64");
-  if (c->op_kind == OPK_CSR && c->nnz < 0) {
-    int64_t nnz = 0;
-    PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
-    c->nnz = nnz;
-  }
+  // (no read-back of a CSR handle's nnz here: it only feeds the byte
+  // statistics, and a blocking copy would synchronise the device)
   void *base = nullptr;
-  RC(static_scratch_addr(&base));
+  RC(static_scratch_addr(c, &base));
   if (c->opts.precision == PP_PREC_MIXED) return poly_apply_static_t<float>(c, (const double *)x_d, (double *)y_d, base);
   if (c->opts.precision == PP_PREC_DW) return poly_apply_static_t<dw>(c, (const double *)x_d, (double *)y_d, base);
   return poly_apply_static_t<double>(c, (const double *)x_d, (double *)y_d, base);

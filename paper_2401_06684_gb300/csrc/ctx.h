@@ -64,6 +64,7 @@ struct pp_ctx {
   // Arnoldi coefficients, complex H_m, a complex q
   bool cplx = false;
   cudaStream_t stream = nullptr;
+  int device = 0;  // the CUDA device current when the handle was created
   pp_opts opts;
   bool have_poly = false;
   int degree = 0;
