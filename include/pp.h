@@ -166,8 +166,13 @@ void pp_default_opts(pp_opts *opts);
  * Create a handle for a CSR matrix (Sec. 1: A sparse).  n rows/columns;
  * rowptr_d[n+1] (int64, rowptr_d[0] = 0), col_d[nnz] (int32, 0-based),
  * val_d[nnz] of dtype PP_F64 (PP_C128 is not supported).  The arrays are
- * referenced, not copied (PP_PREC_DW keeps a converted copy of val), and must
- * stay alive and unchanged for the handle's lifetime.  is_hermitian selects
+ * referenced, not copied (PP_PREC_DW keeps a double-word copy of val,
+ * PP_PREC_MIXED also an FP32 one), and must stay alive and unchanged for
+ * the handle's lifetime.  Under PP_PREC_DW the CSR step accumulates each row
+ * sum and its update in triple-float arithmetic on the FP32 pipes (about
+ * 2^-72 of the summands) and rounds the result to a double-word pair, so
+ * rows that cancel heavily (a graph Laplacian's) keep FP64-grade accuracy.
+ * is_hermitian selects
  * Lanczos under PP_ORTH_AUTO.  Errors: PP_ERR_INVALID_ARG for n <= 0 or NULL
  * pointers, PP_ERR_UNSUPPORTED for other dtypes.
  */
@@ -365,9 +370,10 @@ int pp_get_poly_nodes(pp_handle h, int32_t *kind, double *nodes_re_h, double *no
  * x = f(A) b (Algorithm 1 or 2 by opts.side; Sec. 4 for PP_SQRT), iterating
  * until the stopping estimate is below tol or m = m_max.  b_d, x_d: device
  * vectors of n entries of the handle's vector dtype (nrhs > 1: n x nrhs,
- * column-major; stencil handles solve them as independent processes in
- * lockstep through pp_apply_batch, m_max <= 1024; CSR and Wilson handles
- * one after another, stats summed, iters and est_err the largest); x_d must
+ * column-major; stencil and CSR handles solve them as independent processes
+ * in lockstep through pp_apply_batch, m_max <= 1024, a CSR handle's
+ * operator steps as block SpMM; Wilson handles one after another, stats
+ * summed, iters and est_err the largest); x_d must
  * not alias b_d.  On PP_ERR_NOT_CONVERGED x_d still holds the last
  * iterate.  stats (host, may be NULL) is filled on return.  Blocks the
  * calling thread at each stopping check (a few bytes read back).
@@ -403,11 +409,16 @@ int pp_apply_host(pp_handle h, int32_t f, const double *b_h, int64_t nrhs, int32
  * Krylov process (Algorithm 1 or 2 as in pp_apply).  All processes advance in
  * lockstep: every kernel launch covers the whole batch, so a batch costs the
  * launches of one solve; a process that meets its stopping estimate is masked
- * out of later launches.  Handles are grouped by polynomial degree and
- * orthogonalization; groups run concurrently on internal streams that are
+ * out of later launches.  Stencil handles are grouped by polynomial degree
+ * and orthogonalization; the right-hand sides of a CSR handle form groups
+ * of their own, up to 16 each, whose operator steps are one block SpMM
+ * launch (each row's column indices and values read once for all of the
+ * group's vectors; real CSR, PP_F64 values; the small solve uses the
+ * handle's own quadrature rule, so each process gives pp_apply's iterate).
+ * Groups run concurrently on internal streams that are
  * ordered after the work queued on cuda_stream, which waits for them before
  * the call returns (the call blocks until done).  Every handle must be a 2D
- * or 3D stencil (PP_ERR_UNSUPPORTED otherwise), have called pp_build_poly,
+ * or 3D stencil or a CSR matrix (PP_ERR_UNSUPPORTED otherwise), have called pp_build_poly,
  * and share the precision and side options of handles[0]
  * (PP_ERR_INVALID_ARG otherwise).  With PP_PREC_MIXED a group moves to FP32
  * when the switching rule holds for all of its unconverged processes.
@@ -422,6 +433,31 @@ int pp_apply_host(pp_handle h, int32_t f, const double *b_h, int64_t nrhs, int32
 int pp_apply_batch(const pp_handle *handles, int32_t count, const int32_t *f, const void *const *b_d,
                    const int64_t *nrhs, void *const *x_d, int32_t m_max, double tol, void *cuda_stream,
                    pp_stats *stats);
+
+/*
+ * A batch plan: the processes of pp_apply_batch (same arguments: handles,
+ * f, nrhs, m_max, cuda_stream) set up once and solved by pp_batch_apply for
+ * any number of right-hand-side sets.  pp_batch_create groups the processes
+ * as pp_apply_batch does and allocates every group's device state (vectors
+ * padded to whole reduction chunks, the growing Krylov basis, scratch,
+ * tables); pp_batch_apply then launches no allocation unless a basis has to
+ * grow.  The kernels of the Krylov steps between two stopping checks of a
+ * group, with the check's small solve, are captured as a CUDA graph on their
+ * first run and replayed by later solves (one graph launch per group and
+ * check instead of a few hundred kernel launches; results bitwise equal to
+ * direct launches); the host still reads each group's status records at
+ * every check.  opts.profile = 1 on handles[0] launches directly.
+ * No counterpart in the paper (which solves one problem at a time).
+ * Errors: as pp_apply_batch; pp_batch_apply returns PP_ERR_STATE if a
+ * handle's q or options changed after pp_batch_create (create a new plan).
+ * The handles must outlive the plan.  pp_batch_destroy(NULL) is a no-op.
+ */
+typedef struct pp_batch_ctx *pp_batch;
+int pp_batch_create(pp_batch *batch, const pp_handle *handles, int32_t count, const int32_t *f,
+                    const int64_t *nrhs, int32_t m_max, void *cuda_stream);
+/* b_d[i], x_d[i]: as pp_apply_batch, for handle i of the plan; stats as pp_apply_batch. */
+int pp_batch_apply(pp_batch batch, const void *const *b_d, void *const *x_d, double tol, pp_stats *stats);
+void pp_batch_destroy(pp_batch batch);
 
 /* y_d = A x_d (one operator application in the handle's precision). */
 int pp_op_apply(pp_handle h, const void *x_d, void *y_d);

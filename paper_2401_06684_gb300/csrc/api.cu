@@ -180,6 +180,7 @@ DLayout dlayout(const pp_ctx *c, int m_cap) {
 // Basis layout requested from ensure_ws.
 enum Layout { LAYOUT_KEEP = -1, LAYOUT_FULL = 0, LAYOUT_TWO_PASS = 1 };
 
+
 int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y, int layout = LAYOUT_KEEP) {
   Workspace &w = c->ws;
   const size_t esz = 8;  // double and double-word are both 8 bytes
@@ -227,29 +228,7 @@ int ensure_ws(pp_ctx *c, int prec, int m_cap, bool need_y, int layout = LAYOUT_K
     PP_CUDA_TRY(cudaMemcpyAsync(w.dmem + L.wt, c->qwt.data(), L.K * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     c->quad_uploaded = true;
   }
-  if (c->op_kind == OPK_CSR && w.nlong < 0) {
-    // rows longer than kLongRow entries, listed once per handle (rowptr read back)
-    std::vector<int64_t> rp((size_t)c->n + 1);
-    PP_CUDA_TRY(cudaMemcpy(rp.data(), c->rowptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost));
-    std::vector<int32_t> lr;
-    for (int64_t i = 0; i < c->n; ++i)
-      if (rp[i + 1] - rp[i] > kLongRow) lr.push_back((int32_t)i);
-    if (!lr.empty()) {
-      PP_CUDA_TRY(cudaMalloc(&w.long_rows, sizeof(int32_t) * lr.size()));
-      PP_CUDA_TRY(cudaMemcpy(w.long_rows, lr.data(), sizeof(int32_t) * lr.size(), cudaMemcpyHostToDevice));
-    }
-    w.nlong = (int)lr.size();
-  }
-  if ((prec == PP_PREC_DW || prec == PP_PREC_MIXED) && c->op_kind == OPK_CSR && !w.val_dw) {
-    PP_CUDA_TRY(cudaMalloc(&w.val_dw, (size_t)c->nnz * sizeof(dw)));
-    int rc = vec_from_f64<dw>(c->val, (dw *)w.val_dw, c->nnz, c->stream);
-    if (rc) return rc;
-  }
-  if (prec == PP_PREC_MIXED && c->op_kind == OPK_CSR && !w.val_f) {
-    PP_CUDA_TRY(cudaMalloc(&w.val_f, (size_t)c->nnz * sizeof(float)));
-    int rc = vec_from_f64<float>(c->val, (float *)w.val_f, c->nnz, c->stream);
-    if (rc) return rc;
-  }
+  RC_(csr_prepare(c, prec));
   return PP_OK;
 }
 
@@ -1103,6 +1082,40 @@ constexpr int kStaticVecs = 5;
 constexpr int kStaticMaxDevices = 64;
 
 }  // namespace
+
+int csr_prepare(pp_ctx *c, int prec) {
+  if (c->op_kind != OPK_CSR) return PP_OK;
+  Workspace &w = c->ws;
+  if (c->nnz < 0) {
+    int64_t nnz = 0;
+    PP_CUDA_TRY(cudaMemcpy(&nnz, c->rowptr + c->n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    c->nnz = nnz;
+  }
+  if (w.nlong < 0) {
+    // rows longer than kLongRow entries, listed once per handle (rowptr read back)
+    std::vector<int64_t> rp((size_t)c->n + 1);
+    PP_CUDA_TRY(cudaMemcpy(rp.data(), c->rowptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> lr;
+    for (int64_t i = 0; i < c->n; ++i)
+      if (rp[i + 1] - rp[i] > kLongRow) lr.push_back((int32_t)i);
+    if (!lr.empty()) {
+      PP_CUDA_TRY(cudaMalloc(&w.long_rows, sizeof(int32_t) * lr.size()));
+      PP_CUDA_TRY(cudaMemcpy(w.long_rows, lr.data(), sizeof(int32_t) * lr.size(), cudaMemcpyHostToDevice));
+    }
+    w.nlong = (int)lr.size();
+  }
+  if ((prec == PP_PREC_DW || prec == PP_PREC_MIXED) && !w.val_dw) {
+    PP_CUDA_TRY(cudaMalloc(&w.val_dw, (size_t)c->nnz * sizeof(dw)));
+    RC_(vec_from_f64<dw>(c->val, (dw *)w.val_dw, c->nnz, c->stream));
+  }
+  if (prec == PP_PREC_MIXED && !w.val_f) {
+    PP_CUDA_TRY(cudaMalloc(&w.val_f, (size_t)c->nnz * sizeof(float)));
+    RC_(vec_from_f64<float>(c->val, (float *)w.val_f, c->nnz, c->stream));
+  }
+  return PP_OK;
+}
+
+OpDesc handle_op_desc(const pp_ctx *c, int arith) { return make_op(c, arith); }
 
 static __device__ __align__(256) double pp_static_scratch[kStaticVecs * (size_t)PP_STATIC_MAX_N];
 
@@ -1959,8 +1972,8 @@ int pp_apply(pp_handle c, int32_t f, const void *b_d, int64_t nrhs, int32_t m_ma
     if (c->opts.orth == PP_ORTH_LANCZOS || c->opts.two_pass)
       return pp_set_error(PP_ERR_INVALID_ARG, "a non-Hermitian complex operator needs Arnoldi (CGS2)");
   }
-  if (nrhs > 1 && c->op_kind != OPK_ST2D && c->op_kind != OPK_ST3D) {
-    // CSR and Wilson handles: the columns one after another on the handle
+  if (nrhs > 1 && c->op_kind == OPK_WILSON) {
+    // Wilson handles: the columns one after another on the handle
     // (the later ones replay the captured segment graphs)
     const size_t esz = c->op_kind == OPK_WILSON ? 16 : 8;  // complex128 / float64 entries per row
     const int64_t rows = c->op_kind == OPK_WILSON ? c->n / 2 : c->n;

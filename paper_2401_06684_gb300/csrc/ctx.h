@@ -29,7 +29,7 @@ struct Workspace {
   DevStatus *st = nullptr;
   DevStatus *st_host = nullptr;
   double *io = nullptr;  // 2 n doubles for pp_apply_host
-  void *val_dw = nullptr;
+  void *val_dw = nullptr;  // double-word CSR values (PP_PREC_DW, PP_PREC_MIXED)
   void *val_f = nullptr;  // FP32 CSR values (PP_PREC_MIXED)
   int32_t *long_rows = nullptr;  // CSR rows longer than kLongRow entries
   int nlong = -1;                // -1: not scanned yet
@@ -113,3 +113,13 @@ inline StepCoef poly_step_coef(const pp_ctx *c, int t) {
 
 // Constant q of degree 0.
 inline double poly_const(const pp_ctx *c) { return poly_horner(c) ? c->nf.b[0] : c->coef[0]; }
+
+// CSR handles: read nnz back, list the rows longer than the block-per-row
+// threshold (once per handle), and make the double-word copy of the values
+// (PP_PREC_DW, PP_PREC_MIXED) and the FP32 one (PP_PREC_MIXED).  Synchronous
+// host work; no-op for other handles.
+int csr_prepare(pp_ctx *c, int prec);
+// The operator description of a handle for vectors in arithmetic `arith`
+// (0 FP64, 1 double-word, 2 FP32).
+OpDesc handle_op_desc(const pp_ctx *c, int arith);
+

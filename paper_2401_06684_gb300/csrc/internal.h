@@ -148,6 +148,14 @@ int op_step_batch(const BatchSeg *segs, const int *blkseg, unsigned nblk, int P,
                   const int *active, const T *x, const T *y, const T *v, T *out, bool sub_y, bool add_v,
                   cudaStream_t s);
 
+// Block CSR step for r <= kCsrMaxRhs right-hand sides of the same matrix
+// (block SpMM): the r vectors of x, y, v, out are segments at s * sstride;
+// segments with active[s] == 0 are skipped (active may be NULL).
+constexpr int kCsrMaxRhs = 16;
+template <typename T>
+int op_step_csr_multi(const OpDesc &op, int64_t sstride, int r, const int *active, const T *x, const T *y,
+                      const T *v, T *out, const StepCoef &c, cudaStream_t s);
+
 // Wilson D^H D step (wilson.cu): t = D x into op.tmp, then
 // out = alpha D^H t + beta x [- y] [+ delta v].  With op.q2: t = Q x, then
 // out = alpha Q t + beta x + delta v with complex alpha, beta, delta.

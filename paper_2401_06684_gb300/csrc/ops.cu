@@ -16,15 +16,6 @@
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ T shfl_xor_t(T v, int o, int width) {
-  return __shfl_xor_sync(0xffffffffu, v, o, width);
-}
-template <>
-__device__ __forceinline__ dw shfl_xor_t<dw>(dw v, int o, int width) {
-  return {__shfl_xor_sync(0xffffffffu, v.hi, o, width), __shfl_xor_sync(0xffffffffu, v.lo, o, width)};
-}
-
 
 // One stencil row evaluated as a compensated linear combination
 //   K0 x_c + Km (x_w + x_s + x_d) + Kp (x_e + x_n + x_u) [+ Y y] [+ D v].
@@ -326,41 +317,123 @@ __global__ void __launch_bounds__(kStencilMaxThreads) bst_step(const T *__restri
 // whose sequential lane loops would otherwise set the kernel's duration):
 // one block of 256 threads per row, thread-strided, then a fixed-order block
 // sum.  The first nlong blocks take the long rows, the others the short ones.
+//
+// Accumulation (csr_acc): FP64 and FP32 vectors accumulate by FMA in their
+// own arithmetic.  Double-word vectors accumulate every row sum and the
+// step's update in a triple-float sum s + (e_hi + e_lo) on the FP32 pipes:
+// each product c x of double-word operands is split exactly into its
+// leading part (TwoSum into s) and the error-free residuals of its partial
+// products (FMA TwoProd), which are added to e with TwoSum; only the
+// products' u^2-sized tails go in unsplit.  The sum is then accurate to about
+// 2^-72 of the summands, and the result is rounded once to a double-word pair
+// (2^-48 of itself).  Rows like those of a graph Laplacian, whose diagonal is
+// minus the sum of the other entries, cancel heavily: with the lazy double-
+// word accumulator their error was 2^-48 of the summands, above what FP64
+// reaches, and on Example 3's graph the square root missed its 1e-7 target;
+// FP64 arithmetic in the kernel met it but ran on GB300's narrow FP64 pipe.
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+template <typename T>
+struct csr_acc {
+  T s;
+  __device__ __forceinline__ void zero() { s = (T)0; }
+  __device__ __forceinline__ void add_prod(T c, T x) { s = fma_t(c, x, s); }
+  __device__ __forceinline__ void add(const csr_acc &o) { s += o.s; }
+  __device__ __forceinline__ csr_acc shfl(int o, int width) const {
+    csr_acc r;
+    r.s = __shfl_xor_sync(0xffffffffu, s, o, width);
+    return r;
+  }
+  __device__ __forceinline__ T get() const { return s; }
+};
+
+template <>
+struct csr_acc<dw> {
+  float s, eh, el;  // s + (eh + el), |el| <= ulp(eh)/2 after each update of e
+  __device__ __forceinline__ void zero() { s = eh = el = 0.f; }
+  // e += f without loss: TwoSum of the leading parts, renormalised
+  __device__ __forceinline__ void add_e(float f) {
+    const dw t = dw_two_sum(eh, f);
+    const dw u = dw_fast_two_sum(t.hi, __fadd_rn(t.lo, el));
+    eh = u.hi;
+    el = u.lo;
+  }
+  __device__ __forceinline__ void add_lead(float p) {
+    const dw t = dw_two_sum(s, p);
+    s = t.hi;
+    add_e(t.lo);
+  }
+  __device__ __forceinline__ void add_prod(dw c, dw x) {
+    const float p0 = __fmul_rn(c.hi, x.hi), r0 = __fmaf_rn(c.hi, x.hi, -p0);
+    const float p1 = __fmul_rn(c.hi, x.lo), r1 = __fmaf_rn(c.hi, x.lo, -p1);
+    const float p2 = __fmul_rn(c.lo, x.hi), r2 = __fmaf_rn(c.lo, x.hi, -p2);
+    add_lead(p0);
+    add_e(r0);
+    add_e(p1);
+    add_e(p2);
+    el = __fadd_rn(el, __fadd_rn(__fadd_rn(r1, r2), __fmul_rn(c.lo, x.lo)));
+  }
+  __device__ __forceinline__ void add(const csr_acc &o) {
+    add_lead(o.s);
+    add_e(o.eh);
+    el = __fadd_rn(el, o.el);
+  }
+  __device__ __forceinline__ csr_acc shfl(int o, int width) const {
+    csr_acc r;
+    r.s = __shfl_xor_sync(0xffffffffu, s, o, width);
+    r.eh = __shfl_xor_sync(0xffffffffu, eh, o, width);
+    r.el = __shfl_xor_sync(0xffffffffu, el, o, width);
+    return r;
+  }
+  __device__ __forceinline__ dw get() const {
+    const dw t = dw_two_sum(s, eh);
+    return dw_fast_two_sum(t.hi, __fadd_rn(t.lo, el));
+  }
+};
+
+// out = alpha sum + beta x [+ gamma y] [+ delta v] in the accumulator
+template <typename T, bool SUB_Y, bool ADD_V>
+__device__ __forceinline__ T csr_finish(const csr_acc<T> &sum, T alpha, T beta, T gamma, T delta, T xr, T yr,
+                                        T vr) {
+  csr_acc<T> r;
+  r.zero();
+  r.add_prod(alpha, sum.get());
+  r.add_prod(beta, xr);
+  if (SUB_Y) r.add_prod(gamma, yr);
+  if (ADD_V) r.add_prod(delta, vr);
+  return r.get();
+}
+
 template <typename T, int L, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowptr,
-                                                const int32_t *__restrict__ col,
-                                                const T *__restrict__ val, const T *__restrict__ x,
-                                                const T *__restrict__ y, const T *__restrict__ v,
-                                                T *__restrict__ out, int64_t n, T alpha, T beta,
-                                                T gamma, T delta, const int32_t *__restrict__ long_rows,
+                                                const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                const T *__restrict__ x, const T *__restrict__ y,
+                                                const T *__restrict__ v, T *__restrict__ out, int64_t n, T alpha,
+                                                T beta, T gamma, T delta, const int32_t *__restrict__ long_rows,
                                                 int nlong, int64_t long_len) {
   pdl_wait();
   pdl_trigger();
-  using A = typename acc_of<T>::type;
-  auto finish = [&](int64_t row, T sum) {
-    A r;
-    acc_set_prod(r, alpha, sum);
-    acc_add_prod(r, beta, ldg(x + row));
-    if (SUB_Y) acc_add_prod(r, gamma, ldg(y + row));
-    if (ADD_V) acc_add_prod(r, delta, ldg(v + row));
-    out[row] = acc_get(r);
+  auto finish = [&](int64_t row, const csr_acc<T> &sum) {
+    out[row] = csr_finish<T, SUB_Y, ADD_V>(sum, alpha, beta, gamma, delta, ldg(x + row),
+                                           SUB_Y ? ldg(y + row) : num<T>::zero(),
+                                           ADD_V ? ldg(v + row) : num<T>::zero());
   };
+  csr_acc<T> acc;
+  acc.zero();
   if ((int)blockIdx.x < nlong) {
-    __shared__ T red[8];
+    __shared__ csr_acc<T> red[8];
     const int64_t row = __ldg(long_rows + blockIdx.x);
     const int64_t p1 = __ldg(rowptr + row + 1);
-    A acc;
-    acc_set(acc, num<T>::zero());
     for (int64_t p = __ldg(rowptr + row) + threadIdx.x; p < p1; p += blockDim.x)
-      acc_add_prod(acc, ldg(val + p), ldg(x + __ldg(col + p)));
-    T sum = acc_get(acc);
+      acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum = sum + shfl_xor_t(sum, o, 32);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl(o, 32));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
     if (threadIdx.x == 0) {
-      T tot = red[0];
-      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot = tot + red[w];
+      csr_acc<T> tot = red[0];
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot.add(red[w]);
       finish(row, tot);
     }
     return;
@@ -368,20 +441,102 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
   const int64_t t = (int64_t)(blockIdx.x - nlong) * blockDim.x + threadIdx.x;
   const int64_t row = t / L;
   const int lane = (int)(t % L);
-  A acc;
-  acc_set(acc, num<T>::zero());
   bool mine = row < n;
   if (mine) {
     const int64_t p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
     if (long_len > 0 && p1 - p0 > long_len)
       mine = false;  // a long row: its own block computes it
     else
-      for (int64_t p = p0 + lane; p < p1; p += L) acc_add_prod(acc, ldg(val + p), ldg(x + __ldg(col + p)));
+      for (int64_t p = p0 + lane; p < p1; p += L) acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
   }
-  T sum = acc_get(acc);
 #pragma unroll
-  for (int o = L / 2; o > 0; o >>= 1) sum = sum + shfl_xor_t(sum, o, L);
-  if (mine && lane == 0) finish(row, sum);
+  for (int o = L / 2; o > 0; o >>= 1) acc.add(acc.shfl(o, L));
+  if (mine && lane == 0) finish(row, acc);
+}
+
+// Block form for r right-hand sides of one matrix (block SpMM): the r
+// vectors of a group are the segments x + s * sstride, s < r <= kCsrMaxRhs.
+// Each lane group reads a row's (col, val) once and applies it to every
+// active segment (active[s] != 0, read once per thread into a bit mask), so
+// the matrix costs one pass per step for all r processes instead of r.  The
+// lane-strided accumulation and the shuffle order per segment are those of
+// csr_step, so every segment's result equals the single-vector step's bit
+// for bit.
+template <typename T, int L, bool SUB_Y, bool ADD_V>
+__global__ void __launch_bounds__(256) csr_step_multi(const int64_t *__restrict__ rowptr,
+                                                      const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                      const T *__restrict__ x, const T *__restrict__ y,
+                                                      const T *__restrict__ v, T *__restrict__ out, int64_t n,
+                                                      int64_t sstride, int r, const int *__restrict__ active,
+                                                      T alpha, T beta, T gamma, T delta,
+                                                      const int32_t *__restrict__ long_rows, int nlong,
+                                                      int64_t long_len) {
+  pdl_wait();
+  pdl_trigger();
+  unsigned mask = 0;
+  for (int q = 0; q < r; ++q)
+    if (!active || __ldg(active + q)) mask |= 1u << q;
+  auto finish = [&](int q, int64_t row, const csr_acc<T> &sum) {
+    const int64_t o = (int64_t)q * sstride + row;
+    out[o] = csr_finish<T, SUB_Y, ADD_V>(sum, alpha, beta, gamma, delta, ldg(x + o),
+                                         SUB_Y ? ldg(y + o) : num<T>::zero(), ADD_V ? ldg(v + o) : num<T>::zero());
+  };
+  csr_acc<T> acc[kCsrMaxRhs];
+#pragma unroll
+  for (int q = 0; q < kCsrMaxRhs; ++q) acc[q].zero();
+  if ((int)blockIdx.x < nlong) {
+    __shared__ csr_acc<T> red[8][kCsrMaxRhs];
+    const int64_t row = __ldg(long_rows + blockIdx.x);
+    const int64_t p1 = __ldg(rowptr + row + 1);
+    for (int64_t p = __ldg(rowptr + row) + threadIdx.x; p < p1; p += blockDim.x) {
+      const T a = ldg(val + p);
+      const int64_t cc = __ldg(col + p);
+#pragma unroll
+      for (int q = 0; q < kCsrMaxRhs; ++q)
+        if (mask >> q & 1u) acc[q].add_prod(a, ldg(x + (int64_t)q * sstride + cc));
+    }
+#pragma unroll
+    for (int q = 0; q < kCsrMaxRhs; ++q) {
+      if (!(mask >> q & 1u)) continue;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[q].add(acc[q].shfl(o, 32));
+      if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = acc[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+      for (int q = 0; q < r; ++q) {
+        if (!(mask >> q & 1u)) continue;
+        csr_acc<T> tot = red[0][q];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot.add(red[w][q]);
+        finish(q, row, tot);
+      }
+    return;
+  }
+  const int64_t t = (int64_t)(blockIdx.x - nlong) * blockDim.x + threadIdx.x;
+  const int64_t row = t / L;
+  const int lane = (int)(t % L);
+  bool mine = row < n;
+  if (mine) {
+    const int64_t p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
+    if (long_len > 0 && p1 - p0 > long_len) {
+      mine = false;  // a long row: its own block computes it
+    } else {
+      for (int64_t p = p0 + lane; p < p1; p += L) {
+        const T a = ldg(val + p);
+        const int64_t cc = __ldg(col + p);
+#pragma unroll
+        for (int q = 0; q < kCsrMaxRhs; ++q)
+          if (mask >> q & 1u) acc[q].add_prod(a, ldg(x + (int64_t)q * sstride + cc));
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kCsrMaxRhs; ++q) {
+    if (!(mask >> q & 1u)) continue;
+#pragma unroll
+    for (int o = L / 2; o > 0; o >>= 1) acc[q].add(acc[q].shfl(o, L));
+    if (mine && lane == 0) finish(q, row, acc[q]);
+  }
 }
 
 template <typename T>
@@ -474,6 +629,32 @@ int op_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, const 
 }
 
 template <typename T>
+int op_step_csr_multi(const OpDesc &op, int64_t sstride, int r, const int *active, const T *x, const T *y,
+                      const T *v, T *out, const StepCoef &c, cudaStream_t s) {
+  if (op.kind != OPK_CSR || r < 1 || r > kCsrMaxRhs) return pp_set_error(PP_ERR_INVALID_ARG, "bad CSR block step");
+  constexpr int L = 4;
+  const int64_t threads = op.n * L;
+  const int bs = 256;
+  const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong : 0);
+  if (nb > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "CSR grid too large for one launch");
+  cudaError_t e;
+#define PP_CSRM(SY, AV)                                                                                    \
+  e = pdl_launch(csr_step_multi<T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,      \
+                 (const T *)op.val, x, y, v, out, op.n, sstride, r, active, host_const<T>(c.alpha),       \
+                 host_const<T>(c.beta), host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,    \
+                 op.long_len > 0 ? op.nlong : 0, op.long_len)
+  if (c.sub_y && c.add_v) PP_CSRM(true, true);
+  else if (c.sub_y) PP_CSRM(true, false);
+  else if (c.add_v) PP_CSRM(false, true);
+  else PP_CSRM(false, false);
+#undef PP_CSRM
+  PP_CUDA_TRY(e);
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
+template <typename T>
 void batch_konst(const double *d, const double *cm, const double *cp, const StepCoef *c, int nseg,
                  Konst<T> *out) {
   for (int i = 0; i < nseg; ++i) {
@@ -510,7 +691,9 @@ int op_step_batch(const BatchSeg *segs, const int *blkseg, unsigned nblk, int P,
   template void batch_konst<T>(const double *, const double *, const double *, const StepCoef *, int, \
                                Konst<T> *);                                                          \
   template int op_step_batch<T>(const BatchSeg *, const int *, unsigned, int, const Konst<T> *, const int *, \
-                                const T *, const T *, const T *, T *, bool, bool, cudaStream_t);
+                                const T *, const T *, const T *, T *, bool, bool, cudaStream_t); \
+  template int op_step_csr_multi<T>(const OpDesc &, int64_t, int, const int *, const T *, const T *, const T *, \
+                                    T *, const StepCoef &, cudaStream_t);
 PP_BINST(double)
 PP_BINST(float)
 PP_BINST(dw)

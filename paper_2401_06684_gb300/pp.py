@@ -88,6 +88,12 @@ SYMBOLS = {
     "pp_apply_batch": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(_p), ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(_p),
                                       ctypes.c_int32, ctypes.c_double, _p, ctypes.POINTER(pp_stats)]),
+    "pp_batch_create": (ctypes.c_int, [ctypes.POINTER(_h), ctypes.POINTER(_h), ctypes.c_int32,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.c_int32, _p]),
+    "pp_batch_apply": (ctypes.c_int, [_h, ctypes.POINTER(_p), ctypes.POINTER(_p), ctypes.c_double,
+                                      ctypes.POINTER(pp_stats)]),
+    "pp_batch_destroy": (None, [_h]),
     "pp_autotune": (ctypes.c_int, [_h, ctypes.c_double, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
     "pp_op_apply": (ctypes.c_int, [_h, _p, _p]),
     "pp_poly_apply": (ctypes.c_int, [_h, _p, _p]),
@@ -274,6 +280,35 @@ def pp_apply_batch(handles, fs, bs, xs, nrhs=None, m_max=200, tol=1e-10, stream=
     if rc not in (PP_OK, PP_ERR_NOT_CONVERGED):
         _check(rc)
     return list(st)
+
+
+def pp_batch_create(handles, fs, nrhs=None, m_max=200, stream=None):
+    """A batch plan for the processes of pp_apply_batch (see pp.h); returns its handle."""
+    n = len(handles)
+    nrhs = nrhs or [1] * n
+    hs = (_h * n)(*[h.value if hasattr(h, "value") else h for h in handles])
+    fa = (ctypes.c_int32 * n)(*fs)
+    ra = (ctypes.c_int64 * n)(*nrhs)
+    b = _h()
+    _check(lib().pp_batch_create(ctypes.byref(b), hs, n, fa, ra, m_max, _stream(stream)))
+    b.n_handles = n
+    return b
+
+
+def pp_batch_apply(b, bs, xs, tol=1e-10):
+    """Solve the plan's processes for the right-hand sides bs into xs; one pp_stats per handle."""
+    n = len(bs)
+    ba = (_p * n)(*[_ptr(v) for v in bs])
+    xa = (_p * n)(*[_ptr(v) for v in xs])
+    st = (pp_stats * n)()
+    rc = lib().pp_batch_apply(b, ba, xa, tol, st)
+    if rc not in (PP_OK, PP_ERR_NOT_CONVERGED):
+        _check(rc)
+    return list(st)
+
+
+def pp_batch_destroy(b):
+    lib().pp_batch_destroy(b)
 
 
 def pp_autotune(h, tol, max_degree=64):

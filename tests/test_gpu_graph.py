@@ -3,16 +3,16 @@ the in-degree Laplacian L of a directed graph (non-Hermitian CSR, singular
 with a semi-simple zero eigenvalue), computed as L^{-1/2}(L b) (Sec. 4) with
 Arnoldi + CGS2 and q interpolating at Ritz or harmonic Ritz values
 (Sec. 5.2).  The reference is the oracle's plain Arnoldi at tolerance 1e-13
-(the paper's reference for this example); the library's solves run at
-1e-11 and must land within 1e-7 of it in FP64 (Example 3's target) and
-within 2e-7 in double-word and mixed precision (z^{1/2} is ill-conditioned
-next to the zero eigenvalue: two dense roots of such a matrix already differ
-by a few 1e-9, and double-word rounding, 2^-48 against FP64's 2^-53, lands
-the result at 0.5-1.3e-7 depending on the summation order of the
-Gram-Schmidt inner products).  Ritz interpolants need not be positive on
-the whole spectrum (Sec. 5.2 argues it at the Ritz values only): the tests
-check positivity against the dense eigenvalues and, where it fails, that the
-library returns the root the method then defines."""
+(the paper's reference for this example; it agrees with the dense Schur
+root to 2e-14 on this graph); the library's solves run at 1e-11 and must
+land within 1e-7 of it, Example 3's target, in FP64, double-word and mixed
+precision.  (The degree-15 Ritz interpolant is large between its nodes and
+amplifies the rounding of the operator chain: FP64 lands at 2e-9, and the
+double-word path meets the target because its CSR step computes in FP64.)
+Ritz interpolants need not be positive on the whole spectrum (Sec. 5.2
+argues it at the Ritz values only): the tests check positivity against the
+dense eigenvalues and, where it fails, that the library returns the root
+the method then defines."""
 import functools
 
 import numpy as np
@@ -28,8 +28,7 @@ pytestmark = pytest.mark.gpu
 
 PREC = {"f64": 0, "dw": 1, "mixed": 2}
 N, M = 1500, 12000
-TOL = 1e-7  # Example 3's target
-TOL_PREC = {"f64": TOL, "dw": 2e-7, "mixed": 2e-7}
+TOL = 1e-7  # Example 3's target, for every precision
 # (degree, kind) whose q is positive on the whole spectrum of this graph
 # (checked against the dense eigenvalues in the test), and ones where it is
 # not: Sec. 5.2 can only argue positivity at the Ritz values
@@ -102,18 +101,26 @@ def q_on_spectrum(pp, h):
 
 
 def solve_and_compare(pp, h, b, xref, degree, prec):
+    # stopping checks every 32/d iterations, Example 3's cadence
+    o = pp.pp_default_opts()
+    o.precision = PREC[prec]
+    o.check_every = max(1, 32 // (degree + 1))
+    pp.pp_set_opts(h, o)
     xd = torch.empty(N, dtype=torch.float64, device="cuda")
     st = pp.pp_apply(h, pp.PP_SQRT, dev(b), xd, m_max=800, tol=1e-11)
     assert st.status == pp.PP_OK
-    assert rel(host(xd), xref) < TOL_PREC[prec]
-    # the stopping checks every 32/d iterations of Example 3 give the same answer
-    if degree > 0 and prec == "dw":
-        o = pp.pp_default_opts()
-        o.precision = PREC[prec]
-        o.check_every = max(1, 32 // (degree + 1))
+    assert rel(host(xd), xref) < TOL
+    # with a preconditioner, the 64/d cadence of Example 1 gives the same answer.
+    # (Not for plain Arnoldi, degree 0: on this singular L its iterates reach
+    # 1e-13 and then drift away, rounding feeding the null space of L into the
+    # basis -- after about 200 steps in FP64, 170 in double-word -- and checks
+    # 64 steps apart let the double-word run pass that point before its
+    # estimate falls below 1e-11.)
+    if degree > 0:
+        o.check_every = 0
         pp.pp_set_opts(h, o)
         st = pp.pp_apply(h, pp.PP_SQRT, dev(b), xd, m_max=800, tol=1e-11)
-        assert st.status == pp.PP_OK and rel(host(xd), xref) < TOL_PREC[prec]
+        assert st.status == pp.PP_OK and rel(host(xd), xref) < TOL
 
 
 @pytest.mark.parametrize("prec", ["f64", "dw", "mixed"])
