@@ -209,7 +209,8 @@ int pp_create_csr(pp_handle *h, int64_t n, const int64_t *rowptr_d, const int32_
  * non-Hermitian and the handle runs complex Arnoldi (classical Gram-Schmidt
  * twice with complex coefficients, complex H_m and small solve, a q with
  * complex coefficients): PP_ORTH_LANCZOS and two_pass are refused
- * (PP_ERR_INVALID_ARG), pp_build_poly's PP_LSQ_CONTOUR is unsupported and
+ * (PP_ERR_INVALID_ARG), pp_build_poly's PP_LSQ_CONTOUR takes a closed
+ * contour around the complex Ritz values (see pp_set_poly_lsq) and
  * PP_CHEBYSHEV needs interval_ab; under PP_PREC_MIXED the switch rule's
  * kappa_pre is estimated at each stopping check from the eigenvalues of H_m
  * (the Ritz values of A q(A)^2: ratio of the extreme moduli, times 4).  For
@@ -333,9 +334,14 @@ int pp_set_poly_nodes(pp_handle h, const double *nodes_re_h, const double *nodes
  * q(z_i)|^2, computed through the orthonormal basis that the Arnoldi process
  * on diag(z_1..z_N) from the vector of ones / sqrt(N) yields (alpha = P^*
  * z^{-1/2}).  pts_re_h / pts_im_h (host; pts_im_h may be NULL): N >= degree +
- * 1 points, none on (-inf, 0]; the set must be symmetric about the real axis
- * (then q is real; PP_ERR_UNSUPPORTED otherwise), real for Hermitian
- * handles.  Re q must be positive at every point (Sec. 5.3 takes this as the
+ * 1 points, none on (-inf, 0].  Real operators: the set must be symmetric
+ * about the real axis (then q is real; PP_ERR_UNSUPPORTED otherwise: a
+ * complex q of a real A would need complex vectors), real for Hermitian
+ * handles.  Complex operators (PP_WILSON4D_Q2 with mu != 0): any set; q is
+ * complex, its Newton form is taken at degree + 1 Leja points of the set
+ * without conjugate pairing, and like a complex Ritz q it only indicates the
+ * spectrum (wide quadrature; under PP_PREC_MIXED kappa_pre from H_m).
+ * Re q must be positive at every point (Sec. 5.3 takes this as the
  * indication that q is in the right half-plane inside the contour;
  * PP_ERR_NONPRIMARY otherwise).  The device evaluates q in the Newton form of
  * pp_set_poly_nodes at degree + 1 Leja points chosen among the contour points
@@ -349,7 +355,10 @@ int pp_set_poly_nodes(pp_handle h, const double *nodes_re_h, const double *nodes
  * out): their convex hull made
  * symmetric about the real axis, the part inside |z| < r_min (half the
  * smallest Ritz modulus) replaced by the arc of that circle, max(2000,
- * 20 (degree + 1)) points at equal arc length.  Host only (pp_set_poly_lsq).
+ * 20 (degree + 1)) points at equal arc length; for a complex operator the
+ * complex Arnoldi run's Ritz values and their convex hull as a closed curve
+ * (no symmetrisation), kept out of |z| < r_min the same way.  Host only
+ * (pp_set_poly_lsq).
  * Errors: PP_ERR_INVALID_ARG for bad points or degree.
  */
 int pp_set_poly_lsq(pp_handle h, int32_t degree, const double *pts_re_h, const double *pts_im_h, int32_t npts);

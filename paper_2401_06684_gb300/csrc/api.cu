@@ -255,7 +255,9 @@ OpDesc make_op(const pp_ctx *c, int arith) {
   op.long_rows = c->ws.long_rows;
   op.nlong = c->ws.nlong > 0 ? c->ws.nlong : 0;
   op.long_len = c->ws.nlong > 0 ? kLongRow : 0;
-  op.val = arith == AR_DW ? c->ws.val_dw : (arith == AR_F32 ? c->ws.val_f : (const void *)c->val);
+  op.val_f32 = arith == AR_DW && c->ws.val_exact_f32 == 1 ? 1 : 0;
+  op.val = arith == AR_DW ? (op.val_f32 ? c->ws.val_f : c->ws.val_dw)
+                          : (arith == AR_F32 ? c->ws.val_f : (const void *)c->val);
   for (int d = 0; d < 4; ++d) op.L[d] = c->dims[d];
   op.mass = c->mass;
   op.links = c->links;
@@ -1104,12 +1106,29 @@ int csr_prepare(pp_ctx *c, int prec) {
     }
     w.nlong = (int)lr.size();
   }
-  if ((prec == PP_PREC_DW || prec == PP_PREC_MIXED) && !w.val_dw) {
-    PP_CUDA_TRY(cudaMalloc(&w.val_dw, (size_t)c->nnz * sizeof(dw)));
-    RC_(vec_from_f64<dw>(c->val, (dw *)w.val_dw, c->nnz, c->stream));
+  if (prec == PP_PREC_DW || prec == PP_PREC_MIXED) {
+    if (w.val_exact_f32 < 0) {  // values read back once: are they all exact in FP32?
+      std::vector<double> v((size_t)c->nnz);
+      if (c->nnz > 0) PP_CUDA_TRY(cudaMemcpy(v.data(), c->val, sizeof(double) * v.size(), cudaMemcpyDeviceToHost));
+      int exact = 1;
+      for (double x : v)
+        if ((double)(float)x != x) {
+          exact = 0;
+          break;
+        }
+      w.val_exact_f32 = exact;
+    }
+    if (w.val_exact_f32 && !w.val_f) {  // the double-word step then reads FP32 values
+      PP_CUDA_TRY(cudaMalloc(&w.val_f, (size_t)std::max<int64_t>(c->nnz, 1) * sizeof(float)));
+      RC_(vec_from_f64<float>(c->val, (float *)w.val_f, c->nnz, c->stream));
+    }
+    if (!w.val_exact_f32 && !w.val_dw) {
+      PP_CUDA_TRY(cudaMalloc(&w.val_dw, (size_t)std::max<int64_t>(c->nnz, 1) * sizeof(dw)));
+      RC_(vec_from_f64<dw>(c->val, (dw *)w.val_dw, c->nnz, c->stream));
+    }
   }
   if (prec == PP_PREC_MIXED && !w.val_f) {
-    PP_CUDA_TRY(cudaMalloc(&w.val_f, (size_t)c->nnz * sizeof(float)));
+    PP_CUDA_TRY(cudaMalloc(&w.val_f, (size_t)std::max<int64_t>(c->nnz, 1) * sizeof(float)));
     RC_(vec_from_f64<float>(c->val, (float *)w.val_f, c->nnz, c->stream));
   }
   return PP_OK;
@@ -1628,7 +1647,7 @@ int set_poly_lsq(pp_ctx *c, int degree, const std::vector<std::complex<double>> 
   }
   std::sort(up.begin(), up.end());
   std::sort(lo.begin(), lo.end());
-  if (up != lo)
+  if (up != lo && !c->cplx)
     return pp_set_error(PP_ERR_UNSUPPORTED,
                         "contour not symmetric about the real axis: q would be complex (no complex vectors for real A)");
   std::vector<cplx> H, alpha;
@@ -1645,9 +1664,11 @@ int set_poly_lsq(pp_ctx *c, int degree, const std::vector<std::complex<double>> 
   }
   if (!(qmin > 0.0)) return pp_set_error(PP_ERR_NONPRIMARY, "Re q is not positive on the contour (Sec. 5.3)");
   std::vector<cplx> nodes;
-  if (!leja_select(pts, d, &nodes)) return pp_set_error(PP_ERR_INVALID_ARG, "cannot pick interpolation points");
+  if (!(c->cplx ? leja_select_cx(pts, d, &nodes) : leja_select(pts, d, &nodes)))
+    return pp_set_error(PP_ERR_INVALID_ARG, "cannot pick interpolation points");
   NewtonForm F;
-  if (!newton_form_fn(nodes, [&](cplx z) { return lsq_eval(H, alpha, N, z); }, &F))
+  const auto qf = [&](cplx z) { return lsq_eval(H, alpha, N, z); };
+  if (!(c->cplx ? newton_form_cx_fn(nodes, qf, &F) : newton_form_fn(nodes, qf, &F)))
     return pp_set_error(PP_ERR_NONPRIMARY, "non-finite Newton coefficient");
   double dev = 0.0;
   for (size_t i = 0; i < N; ++i) dev = std::fmax(dev, std::abs(newton_form_eval(F, pts[i]) - qv[i]));
@@ -1665,8 +1686,11 @@ int set_poly_lsq(pp_ctx *c, int degree, const std::vector<std::complex<double>> 
   c->b = rmax;
   c->img_lo = img_lo;
   c->img_hi = img_hi;
-  c->image_on_points = false;
-  finish_poly(c);
+  // a complex operator's contour only indicates its spectrum (as its Ritz
+  // values do for PP_RITZ_LEJA): the same wide quadrature and, under
+  // PP_PREC_MIXED, kappa_pre from H_m
+  c->image_on_points = c->cplx;
+  finish_poly(c, c->cplx ? 1e6 : 1e3);
   return PP_OK;
 }
 
@@ -1680,7 +1704,25 @@ int build_lsq(pp_ctx *c, int degree, const double *ab) {
   RC(spectral_interval(c, ab, &a, &b, &have));
   const int npts = std::max(2000, 20 * (degree + 1));
   std::vector<std::complex<double>> pts;
-  if (have) {
+  if (c->cplx) {  // complex operator: the closed contour around the complex Ritz values
+    const int steps = (int)std::min<int64_t>(std::max(60, degree + 1), c->n / 2);
+    std::vector<double> H;
+    int ldh = 0, m = 0;
+    const int rc = c->opts.precision == PP_PREC_F64 ? ritz_arnoldi<double>(c, steps, &H, &ldh, &m)
+                                                    : ritz_arnoldi<dw>(c, steps, &H, &ldh, &m);
+    if (rc != PP_OK) return rc;
+    std::vector<std::complex<double>> Hd((size_t)m * m, 0.0), ritz;
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i <= std::min(j + 1, m - 1); ++i)
+        Hd[(size_t)i * m + j] = {H[2 * ((size_t)j * ldh + i)], H[2 * ((size_t)j * ldh + i) + 1]};
+    if (!zhess_eigvals(Hd, m, &ritz)) return pp_set_error(PP_ERR_NONPRIMARY, "Hessenberg QR did not converge");
+    double rmin = INFINITY;
+    for (const auto &z : ritz) {
+      if (!(z.real() > 0.0)) return pp_set_error(PP_ERR_NONPRIMARY, "a Ritz value with Re <= 0");
+      rmin = std::fmin(rmin, std::abs(z));
+    }
+    pts = lsq_contour_cx(ritz, 0.5 * rmin, npts);
+  } else if (have) {
     if (!(a > 0.0) || !(b > a) || !std::isfinite(b)) return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
     for (int i = 0; i < npts; ++i) pts.emplace_back(a + (b - a) * (double)i / (npts - 1), 0.0);
   } else {
@@ -1859,10 +1901,7 @@ int pp_build_poly(pp_handle c, int32_t degree, int32_t kind, const double *ab) {
   if (degree < 0 || degree > kMaxDegree) return pp_set_error(PP_ERR_INVALID_ARG, "degree out of [0, 128]");
   if (ab && (!(ab[0] > 0.0) || !(ab[1] > ab[0]) || !std::isfinite(ab[1])))
     return pp_set_error(PP_ERR_INVALID_ARG, "need 0 < a < b");
-  if (kind == PP_LSQ_CONTOUR) {
-    if (c->cplx) return pp_set_error(PP_ERR_UNSUPPORTED, "least-squares contours of complex operators");
-    return build_lsq(c, degree, ab);
-  }
+  if (kind == PP_LSQ_CONTOUR) return build_lsq(c, degree, ab);
   if (kind != PP_CHEBYSHEV) return build_ritz(c, degree, kind, ab);
   if (c->cplx && !ab) return pp_set_error(PP_ERR_INVALID_ARG, "complex operators need interval_ab for PP_CHEBYSHEV");
   double a, b;

@@ -30,6 +30,7 @@ struct Workspace {
   DevStatus *st_host = nullptr;
   double *io = nullptr;  // 2 n doubles for pp_apply_host
   void *val_dw = nullptr;  // double-word CSR values (PP_PREC_DW, PP_PREC_MIXED)
+  int val_exact_f32 = -1;  // every CSR value exact in FP32 (-1: not checked yet)
   void *val_f = nullptr;  // FP32 CSR values (PP_PREC_MIXED)
   int32_t *long_rows = nullptr;  // CSR rows longer than kLongRow entries
   int nlong = -1;                // -1: not scanned yet

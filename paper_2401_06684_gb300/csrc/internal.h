@@ -22,6 +22,9 @@ struct OpDesc {
   const int64_t *rowptr;
   const int32_t *col;
   const void *val;  // CSR values in the vector arithmetic (double, dw or float)
+  // double-word vectors: the values are exact in FP32 and val holds them as
+  // float (half the bytes, cheaper exact products)
+  int val_f32 = 0;
   // CSR rows longer than long_len entries (device list of nlong row indices)
   // get a block each; long_len = 0: every row takes the lane path
   const int32_t *long_rows;
@@ -326,6 +329,15 @@ std::vector<std::complex<double>> lsq_contour(const std::vector<std::complex<dou
 // complex nodes of a complex operator (no conjugate symmetry): Newton form of
 // the interpolant of z^{-1/2} in reverse Leja order, cx = true
 bool newton_form_cx(const std::vector<std::complex<double>> &nodes, NewtonForm *F);
+// the same for the interpolant of f at the nodes
+bool newton_form_cx_fn(const std::vector<std::complex<double>> &nodes,
+                       const std::function<std::complex<double>(std::complex<double>)> &f, NewtonForm *F);
+// d points of a set in Leja order, no conjugate pairing (complex operators)
+bool leja_select_cx(const std::vector<std::complex<double>> &pts, int d, std::vector<std::complex<double>> *out);
+// discretized closed contour around the Ritz values of a complex operator
+// (convex hull, no symmetry), kept out of |z| < r_min
+std::vector<std::complex<double>> lsq_contour_cx(const std::vector<std::complex<double>> &ritz, double r_min,
+                                                 int npts);
 std::complex<double> newton_form_eval(const NewtonForm &F, std::complex<double> z);
 // min Re q and the extremes of |z q(z)^2| on [lo, hi] (if hi > lo > 0), at
 // the nodes and at the extra points

@@ -350,29 +350,40 @@ struct csr_acc {
 
 template <>
 struct csr_acc<dw> {
-  float s, eh, el;  // s + (eh + el), |el| <= ulp(eh)/2 after each update of e
+  // s + (eh + el): s takes the leading parts by TwoSum, eh the rounding
+  // errors and residuals by TwoSum (lazily: its own errors go to el)
+  float s, eh, el;
   __device__ __forceinline__ void zero() { s = eh = el = 0.f; }
-  // e += f without loss: TwoSum of the leading parts, renormalised
   __device__ __forceinline__ void add_e(float f) {
     const dw t = dw_two_sum(eh, f);
-    const dw u = dw_fast_two_sum(t.hi, __fadd_rn(t.lo, el));
-    eh = u.hi;
-    el = u.lo;
+    eh = t.hi;
+    el = __fadd_rn(el, t.lo);
   }
   __device__ __forceinline__ void add_lead(float p) {
     const dw t = dw_two_sum(s, p);
     s = t.hi;
     add_e(t.lo);
   }
+  // c x for double-word c and x: the FMA TwoProd residual of every partial
+  // product is kept; c.lo x.lo (and the residuals of the cross terms, both
+  // u^2 |c x|) go to el directly
   __device__ __forceinline__ void add_prod(dw c, dw x) {
     const float p0 = __fmul_rn(c.hi, x.hi), r0 = __fmaf_rn(c.hi, x.hi, -p0);
     const float p1 = __fmul_rn(c.hi, x.lo), r1 = __fmaf_rn(c.hi, x.lo, -p1);
     const float p2 = __fmul_rn(c.lo, x.hi), r2 = __fmaf_rn(c.lo, x.hi, -p2);
     add_lead(p0);
     add_e(r0);
-    add_e(p1);
-    add_e(p2);
+    add_e(__fadd_rn(p1, p2));
     el = __fadd_rn(el, __fadd_rn(__fadd_rn(r1, r2), __fmul_rn(c.lo, x.lo)));
+  }
+  // c x for a value c exact in FP32 (matrices whose entries all are)
+  __device__ __forceinline__ void add_prod(float c, dw x) {
+    const float p0 = __fmul_rn(c, x.hi), r0 = __fmaf_rn(c, x.hi, -p0);
+    const float p1 = __fmul_rn(c, x.lo), r1 = __fmaf_rn(c, x.lo, -p1);
+    add_lead(p0);
+    add_e(r0);
+    add_e(p1);
+    el = __fadd_rn(el, r1);
   }
   __device__ __forceinline__ void add(const csr_acc &o) {
     add_lead(o.s);
@@ -405,9 +416,9 @@ __device__ __forceinline__ T csr_finish(const csr_acc<T> &sum, T alpha, T beta, 
   return r.get();
 }
 
-template <typename T, int L, bool SUB_Y, bool ADD_V>
+template <typename T, typename VT, int L, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowptr,
-                                                const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                 const T *__restrict__ x, const T *__restrict__ y,
                                                 const T *__restrict__ v, T *__restrict__ out, int64_t n, T alpha,
                                                 T beta, T gamma, T delta, const int32_t *__restrict__ long_rows,
@@ -462,9 +473,9 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
 // lane-strided accumulation and the shuffle order per segment are those of
 // csr_step, so every segment's result equals the single-vector step's bit
 // for bit.
-template <typename T, int L, bool SUB_Y, bool ADD_V>
+template <typename T, typename VT, int L, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(256) csr_step_multi(const int64_t *__restrict__ rowptr,
-                                                      const int32_t *__restrict__ col, const T *__restrict__ val,
+                                                      const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                       const T *__restrict__ x, const T *__restrict__ y,
                                                       const T *__restrict__ v, T *__restrict__ out, int64_t n,
                                                       int64_t sstride, int r, const int *__restrict__ active,
@@ -489,7 +500,7 @@ __global__ void __launch_bounds__(256) csr_step_multi(const int64_t *__restrict_
     const int64_t row = __ldg(long_rows + blockIdx.x);
     const int64_t p1 = __ldg(rowptr + row + 1);
     for (int64_t p = __ldg(rowptr + row) + threadIdx.x; p < p1; p += blockDim.x) {
-      const T a = ldg(val + p);
+      const VT a = ldg(val + p);
       const int64_t cc = __ldg(col + p);
 #pragma unroll
       for (int q = 0; q < kCsrMaxRhs; ++q)
@@ -522,7 +533,7 @@ __global__ void __launch_bounds__(256) csr_step_multi(const int64_t *__restrict_
       mine = false;  // a long row: its own block computes it
     } else {
       for (int64_t p = p0 + lane; p < p1; p += L) {
-        const T a = ldg(val + p);
+        const VT a = ldg(val + p);
         const int64_t cc = __ldg(col + p);
 #pragma unroll
         for (int q = 0; q < kCsrMaxRhs; ++q)
@@ -563,10 +574,21 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     const int bs = 256;
     const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong : 0);
     if (nb > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "CSR grid too large for one launch");
-    PP_CUDA_TRY(pdl_launch(csr_step<T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,
-                           (const T *)op.val, x, y, v, out, op.n, host_const<T>(c.alpha), host_const<T>(c.beta),
-                           host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,
-                           op.long_len > 0 ? op.nlong : 0, op.long_len));
+    bool done = false;
+    if constexpr (std::is_same<T, dw>::value) {
+      if (op.val_f32) {  // values exact in FP32: read as float
+        PP_CUDA_TRY(pdl_launch(csr_step<T, float, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr,
+                               op.col, (const float *)op.val, x, y, v, out, op.n, host_const<T>(c.alpha),
+                               host_const<T>(c.beta), host_const<T>(c.gamma), host_const<T>(c.delta),
+                               op.long_rows, op.long_len > 0 ? op.nlong : 0, op.long_len));
+        done = true;
+      }
+    }
+    if (!done)
+      PP_CUDA_TRY(pdl_launch(csr_step<T, T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,
+                             (const T *)op.val, x, y, v, out, op.n, host_const<T>(c.alpha), host_const<T>(c.beta),
+                             host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,
+                             op.long_len > 0 ? op.nlong : 0, op.long_len));
   } else {
     Konst<T> K;
     K.K0 = host_const<T>(c.alpha * op.d + c.beta);
@@ -637,17 +659,29 @@ int op_step_csr_multi(const OpDesc &op, int64_t sstride, int r, const int *activ
   const int bs = 256;
   const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong : 0);
   if (nb > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "CSR grid too large for one launch");
-  cudaError_t e;
-#define PP_CSRM(SY, AV)                                                                                    \
-  e = pdl_launch(csr_step_multi<T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,      \
-                 (const T *)op.val, x, y, v, out, op.n, sstride, r, active, host_const<T>(c.alpha),       \
-                 host_const<T>(c.beta), host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,    \
+  cudaError_t e = cudaSuccess;
+  bool vf = false;  // values exact in FP32: read as float (double-word vectors)
+  if constexpr (std::is_same<T, dw>::value) vf = op.val_f32 != 0;
+#define PP_CSRM_T(VT, SY, AV)                                                                                  \
+  e = pdl_launch(csr_step_multi<T, VT, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,      \
+                 (const VT *)op.val, x, y, v, out, op.n, sstride, r, active, host_const<T>(c.alpha),          \
+                 host_const<T>(c.beta), host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,        \
                  op.long_len > 0 ? op.nlong : 0, op.long_len)
+#define PP_CSRM(SY, AV)                       \
+  do {                                        \
+    if constexpr (std::is_same<T, dw>::value) \
+      if (vf) {                               \
+        PP_CSRM_T(float, SY, AV);             \
+        break;                                \
+      }                                       \
+    PP_CSRM_T(T, SY, AV);                     \
+  } while (0)
   if (c.sub_y && c.add_v) PP_CSRM(true, true);
   else if (c.sub_y) PP_CSRM(true, false);
   else if (c.add_v) PP_CSRM(false, true);
   else PP_CSRM(false, false);
 #undef PP_CSRM
+#undef PP_CSRM_T
   PP_CUDA_TRY(e);
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());

@@ -205,17 +205,17 @@ bool newton_form_fn(const std::vector<cplx> &nodes, const std::function<cplx(cpl
   return true;
 }
 
-// Complex operator: the interpolant of z^{-1/2} at complex nodes with no
-// conjugate symmetry, in Newton form at the nodes in reverse Leja order (as
-// in newton_form_fn), basis N_i = prod_{l<i} (z - x_l)/cap, coefficients
-// b_i = f[x_0..x_i] cap^i.
-bool newton_form_cx(const std::vector<cplx> &nodes, NewtonForm *F) {
+// Complex operator: the interpolant of f (default z^{-1/2}) at complex nodes
+// with no conjugate symmetry, in Newton form at the nodes in reverse Leja
+// order (as in newton_form_fn), basis N_i = prod_{l<i} (z - x_l)/cap,
+// coefficients b_i = f[x_0..x_i] cap^i.
+bool newton_form_cx_fn(const std::vector<cplx> &nodes, const std::function<cplx(cplx)> &f, NewtonForm *F) {
   const std::vector<cplx> lj = leja_order(nodes, false);
   if (lj.empty() || lj.size() != nodes.size()) return false;
   const std::vector<cplx> x(lj.rbegin(), lj.rend());
   const size_t d = x.size();
   std::vector<cplx> col(d), a(d);
-  for (size_t i = 0; i < d; ++i) col[i] = 1.0 / std::sqrt(x[i]);
+  for (size_t i = 0; i < d; ++i) col[i] = f(x[i]);
   a[0] = col[0];
   for (size_t k = 1; k < d; ++k) {
     for (size_t i = 0; i + k < d; ++i) col[i] = (col[i + 1] - col[i]) / (x[i + k] - x[i]);
@@ -244,6 +244,10 @@ bool newton_form_cx(const std::vector<cplx> &nodes, NewtonForm *F) {
     if (!std::isfinite(F->b[i]) || !std::isfinite(F->bi[i])) return false;
   }
   return true;
+}
+
+bool newton_form_cx(const std::vector<cplx> &nodes, NewtonForm *F) {
+  return newton_form_cx_fn(nodes, [](cplx z) { return 1.0 / std::sqrt(z); }, F);
 }
 
 // q(z) by the backward recurrence of the basis: u_{k+1} = u_{k+2} = 0,
@@ -784,3 +788,91 @@ std::vector<cplx> lsq_contour(const std::vector<cplx> &ritz, double r_min, int n
   for (int i = 1; i + 1 < m; ++i) out.push_back(std::conj(half[i]));
   return out;
 }
+
+// d points of a set in Leja order, no conjugate symmetry (the points of a
+// contour for a complex operator): the point of largest modulus, then each
+// time the point with the largest product of distances to those taken.
+bool leja_select_cx(const std::vector<cplx> &pts, int d, std::vector<cplx> *out) {
+  out->clear();
+  std::vector<double> logp(pts.size(), 0.0);
+  std::vector<char> used(pts.size(), 0);
+  while ((int)out->size() < d) {
+    int best = -1;
+    double bs = -INFINITY;
+    for (size_t i = 0; i < pts.size(); ++i) {
+      if (used[i]) continue;
+      const double sc = out->empty() ? std::abs(pts[i]) : logp[i];
+      if (best < 0 || sc > bs) {
+        bs = sc;
+        best = (int)i;
+      }
+    }
+    if (best < 0 || (!std::isfinite(bs) && !out->empty())) return false;
+    used[best] = 1;
+    const cplx x = pts[best];
+    out->push_back(x);
+    for (size_t i = 0; i < pts.size(); ++i) logp[i] += pts[i] == x ? -INFINITY : std::log(std::abs(pts[i] - x));
+  }
+  return true;
+}
+
+// The contour of Sec. 5.3 for a complex operator (no symmetry about the real
+// axis): the convex hull of the Ritz values as a closed polygon, densely
+// resampled, points with |z| < r_min moved radially onto that circle, then
+// npts points at equal arc length around the closed curve.  A single point
+// (or collinear values) gives the segment between the extreme ones.
+std::vector<cplx> lsq_contour_cx(const std::vector<cplx> &ritz, double r_min, int npts) {
+  std::vector<std::pair<double, double>> P;
+  for (const cplx &z : ritz) P.emplace_back(z.real(), z.imag());
+  std::sort(P.begin(), P.end());
+  P.erase(std::unique(P.begin(), P.end()), P.end());
+  auto cross = [](const std::pair<double, double> &o, const std::pair<double, double> &a,
+                  const std::pair<double, double> &b) {
+    return (a.first - o.first) * (b.second - o.second) - (a.second - o.second) * (b.first - o.first);
+  };
+  // Andrew's monotone chain: lower hull left to right, upper hull right to left
+  std::vector<std::pair<double, double>> hull;
+  for (const auto &p : P) {
+    while (hull.size() >= 2 && cross(hull[hull.size() - 2], hull.back(), p) <= 0.0) hull.pop_back();
+    hull.push_back(p);
+  }
+  const size_t lower = hull.size();
+  for (auto it = P.rbegin() + 1; it != P.rend(); ++it) {
+    while (hull.size() > lower && cross(hull[hull.size() - 2], hull.back(), *it) <= 0.0) hull.pop_back();
+    hull.push_back(*it);
+  }
+  std::vector<cplx> poly;  // closed: last vertex equals the first
+  for (const auto &p : hull) poly.emplace_back(p.first, p.second);
+  if (poly.size() < 3) {  // degenerate hull: the segment between the extremes, both ways
+    poly.clear();
+    poly.emplace_back(P.front().first, P.front().second);
+    poly.emplace_back(P.back().first, P.back().second);
+    poly.emplace_back(P.front().first, P.front().second);
+  }
+  std::vector<double> s(poly.size(), 0.0);
+  for (size_t i = 0; i + 1 < poly.size(); ++i) s[i + 1] = s[i] + std::abs(poly[i + 1] - poly[i]);
+  const int nd = 40 * npts;
+  std::vector<cplx> dense(nd);
+  for (int i = 0; i < nd; ++i) {
+    const double t = s.back() * (double)i / nd;
+    size_t k = std::upper_bound(s.begin(), s.end(), t) - s.begin();
+    k = k == 0 ? 0 : k - 1;
+    if (k + 1 >= poly.size()) k = poly.size() - 2;
+    const double len = s[k + 1] - s[k];
+    cplx z = len > 0.0 ? poly[k] + (poly[k + 1] - poly[k]) * ((t - s[k]) / len) : poly[k];
+    if (std::abs(z) < r_min) z *= r_min / std::abs(z);
+    dense[i] = z;
+  }
+  std::vector<double> arc(nd + 1, 0.0);
+  for (int i = 1; i <= nd; ++i) arc[i] = arc[i - 1] + std::abs(dense[i % nd] - dense[i - 1]);
+  std::vector<cplx> out(npts);
+  size_t j = 0;
+  for (int i = 0; i < npts; ++i) {
+    const double t = arc.back() * (double)i / npts;
+    while (j + 1 < (size_t)nd && arc[j + 1] < t) ++j;
+    const double w = arc[j + 1] > arc[j] ? (t - arc[j]) / (arc[j + 1] - arc[j]) : 0.0;
+    out[i] = dense[j] + (dense[(j + 1) % nd] - dense[j]) * std::fmin(1.0, std::fmax(0.0, w));
+  }
+  return out;
+}
+

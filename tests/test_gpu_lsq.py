@@ -169,3 +169,83 @@ def test_lsq_build_from_ritz_values_graph(degree):
         assert rel(host(xd), ref) < 5e-8
     finally:
         pp.pp_destroy(h)
+
+
+# ---- complex operator (Sec. 6, Example 2's Q^2 with mu != 0): complex q on a contour
+# with no symmetry about the real axis
+
+def _q2_handle(pp, dims):
+    from tests.test_gpu_sign import Q2
+    return Q2(pp, dims, synth.wilson_links(dims, 1))
+
+
+def _skew_ellipse(npts=500):
+    # an ellipse in the right half-plane, tilted off the real axis (centre 5 + 0.6i,
+    # semi-axes 4 and 1.2): Re z in [1, 9], not symmetric about the real axis
+    t = 2.0 * np.pi * np.arange(npts) / npts
+    return (5.0 + 0.6j) + 4.0 * np.cos(t) + 1.2j * np.sin(t)
+
+
+@pytest.mark.parametrize("prec", ["f64", "dw"])
+@pytest.mark.parametrize("degree", [1, 4, 9])
+def test_lsq_complex_poly_apply(degree, prec):
+    # q(A) v with the complex least-squares q of a non-symmetric contour,
+    # against the oracle's basis recurrence on the same points
+    pp = load()
+    from tests.test_gpu_sign import MEDIUM
+    L = _q2_handle(pp, MEDIUM)
+    try:
+        z = _skew_ellipse()
+        L.set(prec)
+        pp.pp_set_poly_lsq(L.h, degree, z)
+        P, H = lsq.basis(z, degree + 1)
+        al = lsq.coeffs(P, z ** -0.5)
+        v = synth.spinor_field(MEDIUM, 13)
+        yd = torch.empty(L.n, dtype=torch.complex128, device="cuda")
+        pp.pp_poly_apply(L.h, dev(v), yd)
+        ref = lsq.apply(L.q2, H, al, len(z), v)
+        assert rel(host(yd), ref) < {"f64": 1e-10, "dw": 5e-10}[prec]
+    finally:
+        L.close()
+
+
+@pytest.mark.parametrize("prec", ["f64", "dw", "mixed"])
+@pytest.mark.parametrize("degree", [4, 8])
+def test_lsq_complex_sign_solve(degree, prec):
+    # pp_build_poly(PP_LSQ_CONTOUR) on the complex Q^2: the closed contour around
+    # the complex Ritz values (no symmetry), then sign(Q) b against the dense
+    # sign function
+    pp = load()
+    from tests.test_gpu_sign import SMALL, reference
+    b, xs = reference(SMALL, 0)
+    L = _q2_handle(pp, SMALL)
+    try:
+        L.set(prec)
+        pp.pp_build_poly(L.h, degree, pp.PP_LSQ_CONTOUR)
+        kind, x, _ = pp.pp_get_poly_nodes(L.h)
+        assert kind == pp.PP_LSQ_CONTOUR and len(x) == degree + 1
+        assert np.any(np.abs(np.imag(x)) > 0)
+        xd = torch.empty(L.n, dtype=torch.complex128, device="cuda")
+        st = pp.pp_apply(L.h, pp.PP_SIGN, dev(b), xd, m_max=800, tol=1e-12)
+        assert st.status == pp.PP_OK
+        assert rel(host(xd), xs) < (1e-10 if prec == "f64" else 5e-10)
+    finally:
+        L.close()
+
+
+def test_lsq_complex_nodes_off_the_real_symmetry():
+    # the contour pp_build_poly builds for the complex operator has no symmetry
+    # about the real axis: the Newton nodes of q (degree + 1 Leja points of the
+    # contour) are not a conjugation-closed set, all in the right half-plane
+    pp = load()
+    from tests.test_gpu_sign import SMALL
+    L = _q2_handle(pp, SMALL)
+    try:
+        L.set("f64")
+        pp.pp_build_poly(L.h, 6, pp.PP_LSQ_CONTOUR)
+        _, x, _ = pp.pp_get_poly_nodes(L.h)
+        assert len(x) == 7 and np.all(np.real(x) > 0)
+        xs = set(np.round(np.asarray(x), 9))
+        assert any(np.round(np.conj(v), 9) not in xs for v in xs)
+    finally:
+        L.close()
