@@ -339,6 +339,18 @@ def oracle_reference(args, seed=0, run=None):
                     f"{r['history'][-1][1]:.1e} < {tight:g} ({r['iters']} iterations)")
 
 
+def accuracy_target(args):
+    """The relative error the workload's result must meet: Example 3's 1e-7 for
+    the graph Laplacian, the metric's 1e-8 for mixed precision and for the
+    workloads quoted at 1e-8, 1e-10 for the FP64-grade runs of the others."""
+    if args.kind == "graphcsr":
+        return 1e-7
+    if args.prec == "mixed" or args.workload in ("laplace2048", "laplace8192", "wilson16x32", "sign16x32",
+                                                  "sign32x64"):
+        return 1e-8
+    return 1e-10
+
+
 def rel_err(x, ref):
     return float(np.linalg.norm(x - ref) / np.linalg.norm(ref))
 
@@ -801,7 +813,7 @@ def run_ours(args):
                           else {"dw": "double-word FP32 pairs (FP64-grade)", "f64": "IEEE FP64"}[args.prec]),
             "data": "synthetic (b ~ N(0,1), seed = rank)", "config": config(args, ws),
             "accuracy": {"rel_err_vs_oracle": err_or_none(x_timed), "oracle": ref_how,
-                         "target": 1e-8 if args.prec == "mixed" else 1e-10,
+                         "target": accuracy_target(args),
                          id_name: ident, "est_err_last": stats[-1]["est_err"]},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
