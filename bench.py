@@ -710,6 +710,13 @@ def run_ours(args):
     pst = solve().as_dict()
     pp.pp_set_opts(h, o)
     chain_ms, chain_bytes, chain_launches = pst["chain_ms"], pst["chain_bytes"], pst["chain_launches"]
+    # where the profiled solve's time goes (direct launches with events: slower than the timed,
+    # graph-replayed solves; "other" = start vector, reconstruction, launch gaps and the host
+    # round trip of every stopping check)
+    breakdown = {"profiled_solve_ms": pst["ms_total"], "chain_ms": chain_ms, "orth_ms": pst["orth_ms"],
+                 "small_solve_ms": pst["small_ms"],
+                 "other_ms": pst["ms_total"] - chain_ms - pst["orth_ms"] - pst["small_ms"],
+                 "checks": pst["checks"]}
     achieved = chain_bytes / (chain_ms / 1e3) / 1e9 if chain_ms > 0 else None
     peak, peak_src = load_peak()
     traffic = (traffic_from_profile(os.path.join(ROOT, "paper_2401_06684_gb300", "csrc", "ops.cu"))
@@ -843,6 +850,7 @@ def run_ours(args):
             "clocks": clocks,
             "switch_iter": stats[-1]["switch_iter"],
             "iters": m_full, "mvms": stats[-1]["mvms"], "wall_s": wall,
+            "breakdown": breakdown,
             "companions": comp or None,
             "plain_gpu": plain or None,
         }

@@ -156,7 +156,11 @@ typedef struct pp_stats {
   int32_t switch_iter;    /* PP_PREC_MIXED: Krylov dimension at which the loop
                              moved to FP32 (-1: never); 0 for the other settings */
   int32_t reserved_i;
-  double reserved[2];
+  double orth_ms;         /* opts.profile = 1: device time of the orthogonalization
+                             (inner products, updates, norms) of every Krylov step,
+                             CUDA events around each step's                       */
+  double small_ms;        /* opts.profile = 1: device time of the stopping checks'
+                             small projected solves, CUDA events around each     */
 } pp_stats;
 
 /* Defaults for pp_opts (all fields). */

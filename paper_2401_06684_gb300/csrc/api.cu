@@ -73,10 +73,11 @@ void ws_free(Workspace &w) {
 }
 
 // Profiling brackets a run of consecutive operator launches (one q(A)
-// application or one product with A) with a pair of events on the handle's
-// stream; the per-launch average then includes the short gaps between the
-// launches of a run.
-int prof_begin(pp_ctx *c) {
+// application or one product with A; category 0), the orthogonalization of
+// a Krylov step (1) or a stopping check's small solve (2) with a pair of
+// events on the handle's stream; the per-launch average of the operator runs
+// then includes the short gaps between the launches of a run.
+int prof_begin(pp_ctx *c, int cat = 0) {
   if (!c->opts.profile) return PP_OK;
   if (c->prof_used + 2 > c->prof_ev.size()) {
     for (int i = 0; i < 64; ++i) {
@@ -85,6 +86,8 @@ int prof_begin(pp_ctx *c) {
       c->prof_ev.push_back(e);
     }
   }
+  if (c->prof_cat.size() < c->prof_ev.size() / 2) c->prof_cat.resize(c->prof_ev.size() / 2);
+  c->prof_cat[c->prof_used / 2] = cat;
   PP_CUDA_TRY(cudaEventRecord(c->prof_ev[c->prof_used], c->stream));
   return PP_OK;
 }
@@ -129,9 +132,10 @@ int run_op_timed(pp_ctx *c, const OpDesc &op, const T *x, const T *y, const T *v
   return prof_end(c);
 }
 
-double prof_ms(pp_ctx *c) {
+double prof_ms(pp_ctx *c, int cat = 0) {
   double t = 0.0;
   for (size_t i = 0; i + 1 < c->prof_used; i += 2) {
+    if (c->prof_cat[i / 2] != cat) continue;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, c->prof_ev[i], c->prof_ev[i + 1]) == cudaSuccess) t += ms;
   }
@@ -332,33 +336,14 @@ struct Solve {
   int64_t mvms, ip;
 };
 
-// Krylov step j in arithmetic T (Algorithm 1 or 2, one pass of the loop):
-// w = A q(A)^2 v_j applied in three stages, orthogonalization against the
-// stored basis (columns of V in arithmetic T), h_{j+1,j} = ||w|| and
-// v_{j+1} = w / h_{j+1,j} in column j+1 of V.
+// The orthogonalization of Krylov step j: w (column j + 1 of V) against the
+// basis by Lanczos or CGS2 (complex CGS2 for complex operators), h_{j+1,j} =
+// ||w|| and v_{j+1} = w / h_{j+1,j}.
 template <typename T>
-int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double bd_rel) {
+int orth_step(Solve &S, T *V, T *vj, T *wv, int j, double bd_rel) {
   pp_ctx *c = S.c;
   cudaStream_t s = S.s;
   const int64_t n = S.n, ldv = S.ldv;
-  T *pb[3] = {t[2], t[3], t[4]};
-  T *vj = V + (size_t)j * ldv;
-  T *wv = V + (size_t)(j + 1) * ldv;
-  if (S.plain) {          // Arnoldi on A itself
-    RC(run_op<T>(c, op, vj, nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
-    S.mvms += 1;
-  } else if (!S.right) {  // Algorithm 1: u = A v_j, y = q(A) u, w = q(A) y
-    RC(run_op_timed<T>(c, op, vj, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
-    RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
-    RC(poly_apply_t<T>(c, op, t[1], wv, pb));
-    S.mvms += 2 * S.deg + 1;
-  } else {                // Algorithm 2: y_j = q(A) v_j, u = q(A) y_j, w = A u
-    T *yj = Y + (size_t)j * ldv;
-    RC(poly_apply_t<T>(c, op, vj, yj, pb));
-    RC(poly_apply_t<T>(c, op, yj, t[0], pb));
-    RC(run_op_timed<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
-    S.mvms += 2 * S.deg + 1;
-  }
   const int nb = S.nb;
   if (S.cx) {  // complex CGS2: h = V^* w (conjugated), w -= V h, twice
     double *hc = S.H + (size_t)2 * j * S.ldh;
@@ -400,6 +385,38 @@ int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double b
     S.ip += 2 * J + 1;
   }
   return vec_scale<T>(wv, wv, n, 1.0, S.scal, s);
+}
+
+// Krylov step j in arithmetic T (Algorithm 1 or 2, one pass of the loop):
+// w = A q(A)^2 v_j applied in three stages, orthogonalization against the
+// stored basis (columns of V in arithmetic T), h_{j+1,j} = ||w|| and
+// v_{j+1} = w / h_{j+1,j} in column j+1 of V.
+template <typename T>
+int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double bd_rel) {
+  pp_ctx *c = S.c;
+  cudaStream_t s = S.s;
+  const int64_t n = S.n, ldv = S.ldv;
+  T *pb[3] = {t[2], t[3], t[4]};
+  T *vj = V + (size_t)j * ldv;
+  T *wv = V + (size_t)(j + 1) * ldv;
+  if (S.plain) {          // Arnoldi on A itself
+    RC(run_op<T>(c, op, vj, nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
+    S.mvms += 1;
+  } else if (!S.right) {  // Algorithm 1: u = A v_j, y = q(A) u, w = q(A) y
+    RC(run_op_timed<T>(c, op, vj, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
+    RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
+    RC(poly_apply_t<T>(c, op, t[1], wv, pb));
+    S.mvms += 2 * S.deg + 1;
+  } else {                // Algorithm 2: y_j = q(A) v_j, u = q(A) y_j, w = A u
+    T *yj = Y + (size_t)j * ldv;
+    RC(poly_apply_t<T>(c, op, vj, yj, pb));
+    RC(poly_apply_t<T>(c, op, yj, t[0], pb));
+    RC(run_op_timed<T>(c, op, t[0], nullptr, nullptr, wv, {1.0, 0.0, 0.0, false, false}));
+    S.mvms += 2 * S.deg + 1;
+  }
+  RC_(prof_begin(c, 1));
+  RC_(orth_step<T>(S, V, vj, wv, j, bd_rel));
+  return prof_end(c);
 }
 
 // Extra factor on a kappa_pre estimated from H_m rather than bounded by an
@@ -727,6 +744,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
           RC(krylov_step<T2>(S, op2, V2, Y2, t2, j,
                              std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
       }
+      RC(prof_begin(c, 2));
       if (S.cx)  // S.s: the capture stream while a segment records
         RC(small_hess_quad_c(S.H, ldh, j1, S.sig, S.wt, K, S.X, w.hess, S.s));
       else if (S.lanczos)
@@ -737,7 +755,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
         RC(small_combine_c(S.X, K, j1, mp, S.z, S.zprev, tol, w.st, S.s));
       else
         RC(small_combine(S.X, K, j1, mp, S.z, S.zprev, tol, w.st, S.s));
-      return PP_OK;
+      return prof_end(c);
     };
     RC(run_segment(c, S, ((uint64_t)j0 << 34) | ((uint64_t)j1 << 2) | (uint64_t)ph, body));
     m = j1;
@@ -810,6 +828,8 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
     out->chain_launches = c->chain_launches;
     out->chain_bytes = c->chain_bytes;
     out->chain_ms = c->opts.profile ? prof_ms(c) : 0.0;
+    out->orth_ms = c->opts.profile ? prof_ms(c, 1) : 0.0;
+    out->small_ms = c->opts.profile ? prof_ms(c, 2) : 0.0;
     out->switch_iter = switched_at;
   }
   if (status != PP_OK) pp_set_error(status, "m_max reached before the stopping estimate fell below tol");

@@ -87,6 +87,7 @@ struct pp_ctx {
   double chain_bytes = 0.0;
   std::vector<cudaEvent_t> prof_ev;  // start/stop pairs, grown on demand
   size_t prof_used = 0;
+  std::vector<int> prof_cat;  // category of each pair: 0 operator chain, 1 orthogonalization, 2 small solve
   // segment graphs of pp_apply, keyed by (first step, end step, phase); valid
   // while seg_sig (workspace pointers, q, options, tol) is unchanged
   std::map<uint64_t, SegGraph> segs;

@@ -47,7 +47,7 @@ class pp_stats(ctypes.Structure):
                 ("launches", ctypes.c_int64), ("chain_launches", ctypes.c_int64),
                 ("chain_bytes", ctypes.c_double), ("chain_ms", ctypes.c_double),
                 ("switch_iter", ctypes.c_int32), ("reserved_i", ctypes.c_int32),
-                ("reserved", ctypes.c_double * 2)]
+                ("orth_ms", ctypes.c_double), ("small_ms", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}

@@ -126,9 +126,13 @@ def test_argument_validation():
     assert e.value.status == pp.PP_ERR_INVALID_ARG
     hq = pp.pp_create_stencil(pp.PP_WILSON4D_Q2, (4, 4, 4, 4), [-1.4, 0.3], links=64, dtype=pp.PP_C128)
     try:
-        with pytest.raises(pp.PPError) as e:  # no contours for complex operators
-            pp.pp_build_poly(hq, 4, pp.PP_LSQ_CONTOUR)
-        assert e.value.status == pp.PP_ERR_UNSUPPORTED
+        # least squares on a contour of a complex operator: any point set (host work only)
+        t = 2.0 * np.pi * np.arange(200) / 200
+        z = (5.0 + 0.6j) + 4.0 * np.cos(t) + 1.2j * np.sin(t)
+        pp.pp_set_poly_lsq(hq, 4, z)
+        kind, x, _ = pp.pp_get_poly_nodes(hq)
+        assert kind == pp.PP_LSQ_CONTOUR and len(x) == 5 and np.any(np.abs(np.imag(x)) > 0)
+        assert all(np.min(np.abs(z - v)) < 1e-12 for v in x)  # Leja points of the contour
         with pytest.raises(pp.PPError) as e:  # Chebyshev needs the interval
             pp.pp_build_poly(hq, 4)
         assert e.value.status == pp.PP_ERR_INVALID_ARG
