@@ -49,6 +49,8 @@ namespace {
 constexpr int kMaxDegree = 128;
 // CSR rows with more entries than this get a block of their own
 constexpr int64_t kLongRow = 64;
+// ... and rows with more than this get a whole block (the others a warp)
+constexpr int64_t kBlockRow = 1024;
 constexpr int kMaxM = 4096;
 constexpr double kBreakdownRel = 1e-12;
 constexpr int kIntervalSteps = 200;
@@ -257,8 +259,10 @@ OpDesc make_op(const pp_ctx *c, int arith) {
   op.rowptr = c->rowptr;
   op.col = c->col;
   op.long_rows = c->ws.long_rows;
-  op.nlong = c->ws.nlong > 0 ? c->ws.nlong : 0;
-  op.long_len = c->ws.nlong > 0 ? kLongRow : 0;
+  const bool scanned = c->ws.nlong > 0 || c->ws.nwarp > 0;
+  op.nlong = scanned ? c->ws.nlong : 0;
+  op.nwarp = scanned ? c->ws.nwarp : 0;
+  op.long_len = scanned ? kLongRow : 0;
   op.val_f32 = arith == AR_DW && c->ws.val_exact_f32 == 1 ? 1 : 0;
   op.val = arith == AR_DW ? (op.val_f32 ? c->ws.val_f : c->ws.val_dw)
                           : (arith == AR_F32 ? c->ws.val_f : (const void *)c->val);
@@ -1114,17 +1118,27 @@ int csr_prepare(pp_ctx *c, int prec) {
     c->nnz = nnz;
   }
   if (w.nlong < 0) {
-    // rows longer than kLongRow entries, listed once per handle (rowptr read back)
+    // rows longer than kLongRow entries, listed once per handle (rowptr read
+    // back): those above kBlockRow first (a block each), then the others (a
+    // warp each)
     std::vector<int64_t> rp((size_t)c->n + 1);
     PP_CUDA_TRY(cudaMemcpy(rp.data(), c->rowptr, sizeof(int64_t) * rp.size(), cudaMemcpyDeviceToHost));
-    std::vector<int32_t> lr;
-    for (int64_t i = 0; i < c->n; ++i)
-      if (rp[i + 1] - rp[i] > kLongRow) lr.push_back((int32_t)i);
+    std::vector<int32_t> lr, wr;
+    for (int64_t i = 0; i < c->n; ++i) {
+      const int64_t len = rp[i + 1] - rp[i];
+      if (len > kBlockRow)
+        lr.push_back((int32_t)i);
+      else if (len > kLongRow)
+        wr.push_back((int32_t)i);
+    }
+    const size_t nl = lr.size();
+    lr.insert(lr.end(), wr.begin(), wr.end());
     if (!lr.empty()) {
       PP_CUDA_TRY(cudaMalloc(&w.long_rows, sizeof(int32_t) * lr.size()));
       PP_CUDA_TRY(cudaMemcpy(w.long_rows, lr.data(), sizeof(int32_t) * lr.size(), cudaMemcpyHostToDevice));
     }
-    w.nlong = (int)lr.size();
+    w.nlong = (int)nl;
+    w.nwarp = (int)wr.size();
   }
   if (prec == PP_PREC_DW || prec == PP_PREC_MIXED) {
     if (w.val_exact_f32 < 0) {  // values read back once: are they all exact in FP32?

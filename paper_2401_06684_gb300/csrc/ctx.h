@@ -32,8 +32,9 @@ struct Workspace {
   void *val_dw = nullptr;  // double-word CSR values (PP_PREC_DW, PP_PREC_MIXED)
   int val_exact_f32 = -1;  // every CSR value exact in FP32 (-1: not checked yet)
   void *val_f = nullptr;  // FP32 CSR values (PP_PREC_MIXED)
-  int32_t *long_rows = nullptr;  // CSR rows longer than kLongRow entries
-  int nlong = -1;                // -1: not scanned yet
+  int32_t *long_rows = nullptr;  // CSR rows longer than kLongRow entries: block rows, then warp rows
+  int nlong = -1;                // rows with a block each (-1: not scanned yet)
+  int nwarp = 0;                 // rows with a warp each
   void *Vf = nullptr;     // FP32 basis of the second phase (PP_PREC_MIXED)
   void *Yf = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

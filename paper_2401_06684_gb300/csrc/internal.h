@@ -25,11 +25,13 @@ struct OpDesc {
   // double-word vectors: the values are exact in FP32 and val holds them as
   // float (half the bytes, cheaper exact products)
   int val_f32 = 0;
-  // CSR rows longer than long_len entries (device list of nlong row indices)
-  // get a block each; long_len = 0: every row takes the lane path
+  // CSR rows longer than long_len entries: long_rows lists first the nlong
+  // rows that get a block each, then the nwarp rows that get a warp each;
+  // long_len = 0: every row takes the lane path
   const int32_t *long_rows;
   int nlong;
   int64_t long_len;
+  int nwarp = 0;
   // Wilson D^H D: lattice extents, mass shift, complex64 links and one
   // scratch vector (in the vector arithmetic) for the intermediate D x
   int64_t L[4];

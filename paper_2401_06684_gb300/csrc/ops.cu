@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
                                                 const T *__restrict__ x, const T *__restrict__ y,
                                                 const T *__restrict__ v, T *__restrict__ out, int64_t n, T alpha,
                                                 T beta, T gamma, T delta, const int32_t *__restrict__ long_rows,
-                                                int nlong, int64_t long_len) {
+                                                int nlong, int nwarp, int64_t long_len) {
   pdl_wait();
   pdl_trigger();
   auto finish = [&](int64_t row, const csr_acc<T> &sum) {
@@ -449,14 +449,26 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
     }
     return;
   }
-  const int64_t t = (int64_t)(blockIdx.x - nlong) * blockDim.x + threadIdx.x;
+  const int nwb = (nwarp + 7) / 8;  // blocks of 8 warps, a warp per medium row
+  if ((int)blockIdx.x < nlong + nwb) {
+    const int wi = ((int)blockIdx.x - nlong) * 8 + (int)(threadIdx.x >> 5), ln = threadIdx.x & 31;
+    if (wi >= nwarp) return;
+    const int64_t row = __ldg(long_rows + nlong + wi);
+    const int64_t p1 = __ldg(rowptr + row + 1);
+    for (int64_t p = __ldg(rowptr + row) + ln; p < p1; p += 32) acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl(o, 32));
+    if (ln == 0) finish(row, acc);
+    return;
+  }
+  const int64_t t = (int64_t)(blockIdx.x - nlong - nwb) * blockDim.x + threadIdx.x;
   const int64_t row = t / L;
   const int lane = (int)(t % L);
   bool mine = row < n;
   if (mine) {
     const int64_t p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
     if (long_len > 0 && p1 - p0 > long_len)
-      mine = false;  // a long row: its own block computes it
+      mine = false;  // a long row: its own block or warp computes it
     else
       for (int64_t p = p0 + lane; p < p1; p += L) acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
   }
@@ -481,7 +493,7 @@ __global__ void __launch_bounds__(256) csr_step_multi(const int64_t *__restrict_
                                                       int64_t sstride, int r, const int *__restrict__ active,
                                                       T alpha, T beta, T gamma, T delta,
                                                       const int32_t *__restrict__ long_rows, int nlong,
-                                                      int64_t long_len) {
+                                                      int nwarp, int64_t long_len) {
   pdl_wait();
   pdl_trigger();
   unsigned mask = 0;
@@ -523,14 +535,36 @@ __global__ void __launch_bounds__(256) csr_step_multi(const int64_t *__restrict_
       }
     return;
   }
-  const int64_t t = (int64_t)(blockIdx.x - nlong) * blockDim.x + threadIdx.x;
+  const int nwb = (nwarp + 7) / 8;  // blocks of 8 warps, a warp per medium row
+  if ((int)blockIdx.x < nlong + nwb) {
+    const int wi = ((int)blockIdx.x - nlong) * 8 + (int)(threadIdx.x >> 5), ln = threadIdx.x & 31;
+    if (wi >= nwarp) return;
+    const int64_t row = __ldg(long_rows + nlong + wi);
+    const int64_t p1 = __ldg(rowptr + row + 1);
+    for (int64_t p = __ldg(rowptr + row) + ln; p < p1; p += 32) {
+      const VT a = ldg(val + p);
+      const int64_t cc = __ldg(col + p);
+#pragma unroll
+      for (int q = 0; q < kCsrMaxRhs; ++q)
+        if (mask >> q & 1u) acc[q].add_prod(a, ldg(x + (int64_t)q * sstride + cc));
+    }
+#pragma unroll
+    for (int q = 0; q < kCsrMaxRhs; ++q) {
+      if (!(mask >> q & 1u)) continue;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[q].add(acc[q].shfl(o, 32));
+      if (ln == 0) finish(q, row, acc[q]);
+    }
+    return;
+  }
+  const int64_t t = (int64_t)(blockIdx.x - nlong - nwb) * blockDim.x + threadIdx.x;
   const int64_t row = t / L;
   const int lane = (int)(t % L);
   bool mine = row < n;
   if (mine) {
     const int64_t p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
     if (long_len > 0 && p1 - p0 > long_len) {
-      mine = false;  // a long row: its own block computes it
+      mine = false;  // a long row: its own block or warp computes it
     } else {
       for (int64_t p = p0 + lane; p < p1; p += L) {
         const VT a = ldg(val + p);
@@ -572,7 +606,7 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
     const int L = 4;
     const int64_t threads = op.n * L;
     const int bs = 256;
-    const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong : 0);
+    const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong + (op.nwarp + 7) / 8 : 0);
     if (nb > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "CSR grid too large for one launch");
     bool done = false;
     if constexpr (std::is_same<T, dw>::value) {
@@ -580,7 +614,8 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
         PP_CUDA_TRY(pdl_launch(csr_step<T, float, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr,
                                op.col, (const float *)op.val, x, y, v, out, op.n, host_const<T>(c.alpha),
                                host_const<T>(c.beta), host_const<T>(c.gamma), host_const<T>(c.delta),
-                               op.long_rows, op.long_len > 0 ? op.nlong : 0, op.long_len));
+                               op.long_rows, op.long_len > 0 ? op.nlong : 0, op.long_len > 0 ? op.nwarp : 0,
+                               op.long_len));
         done = true;
       }
     }
@@ -588,7 +623,7 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
       PP_CUDA_TRY(pdl_launch(csr_step<T, T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,
                              (const T *)op.val, x, y, v, out, op.n, host_const<T>(c.alpha), host_const<T>(c.beta),
                              host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,
-                             op.long_len > 0 ? op.nlong : 0, op.long_len));
+                             op.long_len > 0 ? op.nlong : 0, op.long_len > 0 ? op.nwarp : 0, op.long_len));
   } else {
     Konst<T> K;
     K.K0 = host_const<T>(c.alpha * op.d + c.beta);
@@ -657,7 +692,7 @@ int op_step_csr_multi(const OpDesc &op, int64_t sstride, int r, const int *activ
   constexpr int L = 4;
   const int64_t threads = op.n * L;
   const int bs = 256;
-  const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong : 0);
+  const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong + (op.nwarp + 7) / 8 : 0);
   if (nb > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "CSR grid too large for one launch");
   cudaError_t e = cudaSuccess;
   bool vf = false;  // values exact in FP32: read as float (double-word vectors)
@@ -666,7 +701,7 @@ int op_step_csr_multi(const OpDesc &op, int64_t sstride, int r, const int *activ
   e = pdl_launch(csr_step_multi<T, VT, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,      \
                  (const VT *)op.val, x, y, v, out, op.n, sstride, r, active, host_const<T>(c.alpha),          \
                  host_const<T>(c.beta), host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,        \
-                 op.long_len > 0 ? op.nlong : 0, op.long_len)
+                 op.long_len > 0 ? op.nlong : 0, op.long_len > 0 ? op.nwarp : 0, op.long_len)
 #define PP_CSRM(SY, AV)                       \
   do {                                        \
     if constexpr (std::is_same<T, dw>::value) \
