@@ -42,7 +42,8 @@ METRIC = "f(A)b solves/sec and SpMV-chain HBM GB/s (% roofline) at 1e-8 rel err 
 # name -> (description, operator, grid, func (+1 sqrt / -1 invsqrt), degree, tol, orth)
 WORKLOADS = {
     "convdiff128": ("3D convection-diffusion 128^3 upwind 7-point (n=2097152, c*h=0.5), f=A^(1/2), "
-                    "Arnoldi CGS2", "convdiff3d7", (128, 128, 128), 1, 16, 1e-10, "cgs2"),
+                    "Arnoldi with classical Gram-Schmidt twice, second pass delayed one step (DCGS2)",
+                    "convdiff3d7", (128, 128, 128), 1, 16, 1e-10, "dcgs2"),
     "laplace2048": ("2D Laplacian 2048^2 5-point matrix-free (n=4194304), f=A^(-1/2), Lanczos; "
                     "1e-8 target, estimate tolerance 1e-9", "laplace2d5", (2048, 2048), -1, 16, 1e-9,
                     "lanczos"),
@@ -105,6 +106,8 @@ def parse():
     p.add_argument("--two-pass", action="store_true",
                    help="two-pass Lanczos (O(n) basis memory, twice the operator passes)")
     p.add_argument("--autotune", action="store_true", help="degree and tile from pp_autotune")
+    p.add_argument("--orth", default=None, choices=["cgs2", "dcgs2"],
+                   help="Gram-Schmidt of the Arnoldi workloads (default: the workload's)")
     a = p.parse_args()
     w = WORKLOADS[a.workload]
     a.desc, a.kind, a.dims, a.func = w[0], w[1], w[2], w[3]
@@ -112,7 +115,9 @@ def parse():
     a.tol = w[5] if a.tol is None else a.tol
     if a.m_max is None:
         a.m_max = 200 if a.workload == "sign32x64" else 1000
-    a.orth = w[6]
+    if a.orth is not None and w[6] not in ("cgs2", "dcgs2"):
+        p.error("--orth applies to the Arnoldi workloads only")
+    a.orth = w[6] if a.orth is None else a.orth
     a.n = 1
     for d in a.dims:
         a.n *= d
@@ -224,6 +229,8 @@ def oracle_timed(args, m_max, tol, seed=0, budget_s=None, P=None, max_iters=None
     if P is None:
         P = oracle_problem(args, seed)
     mv, rhs = P["mv"], P["rhs"]
+    # delayed reorthogonalization builds the CGS2 basis in exact arithmetic: the oracle runs CGS2
+    orth = "cgs2" if args.orth == "dcgs2" else args.orth
     stamps = []
     t0 = time.perf_counter()
 
@@ -252,20 +259,20 @@ def oracle_timed(args, m_max, tol, seed=0, budget_s=None, P=None, max_iters=None
                 x, an = ritz.ritz_poly(mv, n, args.degree, harmonic=args.poly == "harmonic", hermitian=False)
                 qf = (args.degree, lambda v: ritz.newton_apply(mv, an, x, v))
             r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, q=qf, side="left", m_max=m_max, tol=tol,
-                                  k_chk=max(1, 32 // (args.degree + 1)), orth=args.orth, on_iter=hook)
+                                  k_chk=max(1, 32 // (args.degree + 1)), orth=orth, on_iter=hook)
         elif args.kind == "wilsonq2":  # Example 2: complex Ritz q (set-up), (Q^2)^{-1/2} b, then Q
             from oracle import ritz, sign
             x, an = ritz.ritz_poly(mv, rhs.shape[0], args.degree, complex_=True, hermitian=False)
             qf = (args.degree, lambda v: ritz.newton_apply(mv, an, x, v))
             xs, r = sign.sign_krylov(P["Q"], rhs, q=qf, side="left", m_max=m_max, tol=tol,
-                                     k_chk=max(1, 64 // (args.degree + 1)), orth=args.orth, on_iter=hook)
+                                     k_chk=max(1, 64 // (args.degree + 1)), orth=orth, on_iter=hook)
             r = dict(r, x=xs)
         else:
             a, b = P["ab"]
             c = cheb.interp_coeffs(a, b, args.degree + 1)
             r = krylov.pp_arnoldi(mv, rhs, 0.5 * args.func, c, (a, b), side="left", m_max=m_max, tol=tol,
-                                  k_chk=max(1, 64 // (args.degree + 1)), hermitian=args.orth == "lanczos",
-                                  orth=args.orth, on_iter=hook)
+                                  k_chk=max(1, 64 // (args.degree + 1)), hermitian=orth == "lanczos",
+                                  orth=orth, on_iter=hook)
     except _OutOfBudget:
         r = None
     t_end = time.perf_counter()
@@ -335,7 +342,7 @@ def oracle_reference(args, seed=0, run=None):
     else:
         r, _, _ = oracle_timed(args, 1000, tight, seed)
     return r["x"], (f"oracle Algorithm 1 (FP64, {'Ritz' if args.kind == 'graphcsr' else 'Chebyshev'} q of "
-                    f"degree {args.degree}, {args.orth}) to a stopping estimate of "
+                    f"degree {args.degree}, {'cgs2' if args.orth == 'dcgs2' else args.orth}) to a stopping estimate of "
                     f"{r['history'][-1][1]:.1e} < {tight:g} ({r['iters']} iterations)")
 
 
@@ -649,6 +656,7 @@ def run_ours(args):
         if args.two_pass or args.workload == "laplace8192":  # O(n) basis memory: two-pass Lanczos
             o.two_pass = 1
         o.clenshaw = 1 if args.clenshaw else 0
+        o.orth = {"cgs2": pp.PP_ORTH_CGS2, "dcgs2": pp.PP_ORTH_DCGS2}.get(args.orth, pp.PP_ORTH_AUTO)
         if args.kind == "graphcsr":  # Example 3 checks every 32/d iterations
             o.check_every = max(1, 32 // (args.degree + 1))
         if args.kind == "wilsonq2":  # Example 2 checks every 64/d iterations

@@ -110,7 +110,30 @@ typedef enum {
 typedef enum {
   PP_ORTH_AUTO = 0,     /* Lanczos for Hermitian A, CGS2 Arnoldi otherwise        */
   PP_ORTH_LANCZOS = 1,  /* three-term recurrence, no reorthogonalization          */
-  PP_ORTH_CGS2 = 2      /* classical Gram-Schmidt twice against the whole basis   */
+  PP_ORTH_CGS2 = 2,     /* classical Gram-Schmidt twice against the whole basis   */
+  PP_ORTH_DCGS2 = 3     /* classical Gram-Schmidt twice with the second pass
+                           delayed by one step: the operator is applied to the
+                           candidate after its first pass, whose second pass,
+                           normalization (beta^2 = ||u||^2 - ||V^T u||^2) and the
+                           first pass of the next candidate are formed from one
+                           sweep of inner products (V^T u, V^T y, u.u, u.y) and
+                           applied in one update sweep, the new column's
+                           coefficients following from linearity and the
+                           Arnoldi relation of the earlier columns; two sweeps
+                           over the basis per step instead of three plus a
+                           normalization (a stopping check adds one inner-
+                           product sweep).  Same H_m and basis as CGS2 up to
+                           rounding.  Where the q(A) chain amplifies rounding
+                           strongly its results level off above CGS2's (a
+                           degree-15 Ritz q on a 281,903-node graph
+                           Laplacian: 1.3e-8 against 2e-10 in FP64, 2.3e-7
+                           against 7e-9 in double-word); with Chebyshev q on
+                           convection-diffusion the two agree.  Left
+                           preconditioning of real operators
+                           (PP_ERR_UNSUPPORTED otherwise); batched solves use
+                           CGS2.  No counterpart in the paper, which
+                           reorthogonalizes without saying how (Sec. 6,
+                           Example 3).                                          */
 } pp_orth;
 
 typedef struct pp_opts {

@@ -146,7 +146,7 @@ double prof_ms(pp_ctx *c, int cat = 0) {
 
 // Layout of the FP64 scratch (offsets in doubles).
 struct DLayout {
-  size_t H, h1, part, X, tri, z, zprev, sig, wt, scal, total;
+  size_t H, h1, part, X, tri, z, zprev, sig, wt, scal, dd, total;
   int ldh, nb, K;
 };
 
@@ -164,7 +164,7 @@ DLayout dlayout(const pp_ctx *c, int m_cap) {
   L.h1 = o;
   o += cw * (m_cap + 1);
   L.part = o;
-  o += cw * L.nb * (m_cap + 1);
+  o += 2 * L.nb * (m_cap + 1);  // complex: (re, im) per column; delayed reorthogonalization: 2J + 2 columns
   L.X = o;
   o += cw * L.K * m_cap;
   L.tri = o;
@@ -179,6 +179,8 @@ DLayout dlayout(const pp_ctx *c, int m_cap) {
   o += (size_t)L.K;
   L.scal = o;
   o += 8;
+  L.dd = o;  // delayed reorthogonalization: the reduced inner products (2 m + 2) and s, d (2 m)
+  o += 4 * ((size_t)m_cap + 2);
   L.total = o;
   return L;
 }
@@ -331,9 +333,10 @@ struct Solve {
   pp_ctx *c;
   cudaStream_t s;
   int64_t n, ldv;
-  double *H, *h1, *part, *X, *tri, *z, *zprev, *sig, *wt, *scal;
+  double *H, *h1, *part, *X, *tri, *z, *zprev, *sig, *wt, *scal, *dd;
   int ldh, nb, K;
   bool right, lanczos;
+  bool dcgs = false;  // Arnoldi with delayed reorthogonalization (left, real)
   bool plain = false;  // w = A v_j alone (the node run of Sec. 5.2)
   bool cx = false;     // complex Gram-Schmidt, H complex (column j at H + 2 j ldh)
   int deg;
@@ -420,6 +423,47 @@ int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double b
   }
   RC_(prof_begin(c, 1));
   RC_(orth_step<T>(S, V, vj, wv, j, bd_rel));
+  return prof_end(c);
+}
+
+// Step j of Arnoldi with delayed reorthogonalization (opts.orth =
+// PP_ORTH_DCGS2; left preconditioning, real arithmetic): column j holds the
+// candidate u_j (one Gram-Schmidt pass, unnormalized), y = A q(A)^2 u_j goes
+// to column j + 1; one sweep forms the inner products, one block the
+// coefficients, and one more sweep leaves v_j in column j and the candidate
+// u_{j+1} in column j + 1 (vec.cu, k_dot2 / k_dcgs_coef / k_update2).
+// Afterwards columns 0..j of V and columns 0..j-1 of H are final.
+template <typename T>
+int krylov_step_d(Solve &S, const OpDesc &op, T *V, T *t[6], int j, double bd_rel) {
+  pp_ctx *c = S.c;
+  cudaStream_t s = S.s;
+  const int64_t n = S.n, ldv = S.ldv;
+  T *pb[3] = {t[2], t[3], t[4]};
+  T *u = V + (size_t)j * ldv;
+  T *y = V + (size_t)(j + 1) * ldv;
+  RC(run_op_timed<T>(c, op, u, nullptr, nullptr, t[0], {1.0, 0.0, 0.0, false, false}));
+  RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
+  RC(poly_apply_t<T>(c, op, t[1], y, pb));
+  S.mvms += 2 * S.deg + 1;
+  RC_(prof_begin(c, 1));
+  double *R = S.dd, *co = S.dd + 2 * (size_t)(j + 1);
+  RC(vec_dot2<T>(V, ldv, j, u, y, n, S.part, s));
+  RC(reduce_cols(S.part, S.nb, 2 * j + 2, 0, R, nullptr, s));
+  RC(dcgs_coef(R, j, S.H, S.ldh, S.h1, co, S.scal, bd_rel, c->ws.st, s));
+  RC(vec_update2<T>(V, ldv, j, co, S.scal, u, y, n, s));
+  S.ip += 2 * (int64_t)j + 2;
+  return prof_end(c);
+}
+
+// Before the stopping check at Krylov dimension m of the delayed scheme: the
+// second pass of column m - 1 (H[0:m, m-1] += V_{0:m}^T u_m, u_m in column m).
+template <typename T>
+int dcgs_finalize(Solve &S, T *V, int m) {
+  pp_ctx *c = S.c;
+  RC_(prof_begin(c, 1));
+  RC(vec_multi_dot<T>(V, S.ldv, m, V + (size_t)m * S.ldv, S.n, S.part, S.nb, S.s));
+  RC(reduce_cols(S.part, S.nb, m, 2, S.dd, S.H + (size_t)(m - 1) * S.ldh, S.s));
+  S.ip += m;
   return prof_end(c);
 }
 
@@ -633,12 +677,14 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   S.sig = D + L.sig;
   S.wt = D + L.wt;
   S.scal = D + L.scal;
+  S.dd = D + L.dd;
   S.ldh = L.ldh;
   S.nb = L.nb;
   S.K = L.K;
   S.right = right;
   S.lanczos = c->opts.orth == PP_ORTH_LANCZOS || (c->opts.orth == PP_ORTH_AUTO && c->hermitian);
   S.cx = c->cplx;
+  S.dcgs = c->opts.orth == PP_ORTH_DCGS2;
   S.deg = c->degree;
   S.mvms = 0;
   S.ip = 0;
@@ -722,7 +768,10 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
       if (right)
         for (int col = 0; col < m_now; ++col)
           RC((vec_convert<T1, T2>(Y1 + (size_t)col * ldv, Y2 + (size_t)col * ldv, n, s)));
-      nv1 = m_now + 1;
+      // the leading columns the result takes from the phase-1 basis: 0..m_now,
+      // or 0..m_now-1 with delayed reorthogonalization, whose column m_now
+      // still holds the candidate (its final form is written in phase 2)
+      nv1 = S.dcgs && m_now > 0 ? m_now : m_now + 1;
       ny1 = m_now;
       phase = 2;
     }
@@ -742,11 +791,21 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
     const int mp = mprev, ph = phase;
     auto body = [&]() -> int {
       for (int j = j0; j < j1; ++j) {
-        if (ph == 1)
+        if (S.dcgs && ph == 1)
+          RC(krylov_step_d<T1>(S, op1, V1, t1, j, kBreakdownRel));
+        else if (S.dcgs)
+          RC(krylov_step_d<T2>(S, op2, V2, t2, j, std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
+        else if (ph == 1)
           RC(krylov_step<T1>(S, op1, V1, Y1, t1, j, kBreakdownRel));
         else
           RC(krylov_step<T2>(S, op2, V2, Y2, t2, j,
                              std::is_same<T2, float>::value ? kBreakdownRelF32 : kBreakdownRel));
+      }
+      if (S.dcgs) {  // the check's Hessenberg matrix needs column j1 - 1 final
+        if (ph == 1)
+          RC(dcgs_finalize<T1>(S, V1, j1));
+        else
+          RC(dcgs_finalize<T2>(S, V2, j1));
       }
       RC(prof_begin(c, 2));
       if (S.cx)  // S.s: the capture stream while a segment records
@@ -1917,7 +1976,7 @@ int pp_set_opts(pp_handle c, const pp_opts *o) {
   if (o->side != PP_LEFT && o->side != PP_RIGHT) return pp_set_error(PP_ERR_INVALID_ARG, "bad side");
   if (o->precision != PP_PREC_F64 && o->precision != PP_PREC_DW && o->precision != PP_PREC_MIXED)
     return pp_set_error(PP_ERR_INVALID_ARG, "bad precision");
-  if (o->orth < PP_ORTH_AUTO || o->orth > PP_ORTH_CGS2) return pp_set_error(PP_ERR_INVALID_ARG, "bad orth");
+  if (o->orth < PP_ORTH_AUTO || o->orth > PP_ORTH_DCGS2) return pp_set_error(PP_ERR_INVALID_ARG, "bad orth");
   if (o->check_every < 0) return pp_set_error(PP_ERR_INVALID_ARG, "check_every < 0");
   if (o->profile != 0 && o->profile != 1) return pp_set_error(PP_ERR_INVALID_ARG, "profile must be 0 or 1");
   if (o->two_pass != 0 && o->two_pass != 1) return pp_set_error(PP_ERR_INVALID_ARG, "two_pass must be 0 or 1");
@@ -2045,6 +2104,9 @@ int pp_apply(pp_handle c, int32_t f, const void *b_d, int64_t nrhs, int32_t m_ma
     if (c->opts.orth == PP_ORTH_LANCZOS || c->opts.two_pass)
       return pp_set_error(PP_ERR_INVALID_ARG, "a non-Hermitian complex operator needs Arnoldi (CGS2)");
   }
+  if (c->opts.orth == PP_ORTH_DCGS2 && (c->cplx || c->opts.side == PP_RIGHT))
+    return pp_set_error(PP_ERR_UNSUPPORTED,
+                        "delayed reorthogonalization is implemented for left preconditioning of real operators");
   if (nrhs > 1 && c->op_kind == OPK_WILSON) {
     // Wilson handles: the columns one after another on the handle
     // (the later ones replay the captured segment graphs)

@@ -779,6 +779,261 @@ __global__ void __launch_bounds__(TPB) k_scale_c(const T *__restrict__ in, T *__
   }
 }
 
+
+// ---- Arnoldi with delayed reorthogonalization (opts.orth = PP_ORTH_DCGS2) ----
+//
+// Step j holds the final basis columns V_0..V_{j-1} and, in column j, the
+// candidate u_j = w_{j-1} - V h1 left by the previous step's single
+// Gram-Schmidt pass (unnormalized); y = A q(A)^2 u_j is applied to it before
+// it is reorthogonalized.  One sweep forms s = V^T u, t = V^T y, a = u.u,
+// g = u.y; a one-block kernel turns them into v_j = (u - V s)/beta, beta^2 =
+// a - s.s (the second CGS pass of column j-1, whose h is h1 + s), and the
+// first-pass coefficients of A q(A)^2 v_j = (y - V H s)/beta (linearity and
+// the Arnoldi relation of the earlier columns); a second sweep writes v_j
+// and the next candidate u_{j+1} = y/beta - V d - e u.  Two sweeps over V
+// per step instead of the three of CGS2 plus the normalization pass.
+
+// partials[chunk*(2J+2) + c]: c < J: V_c.u, J + c: V_c.y, 2J: u.u, 2J+1: u.y
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_dot2(const T *__restrict__ V, int64_t ldv, int J, const T *__restrict__ u,
+                                              const T *__restrict__ y, int64_t n, double *__restrict__ partials) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename acc_of<T>::type;
+  __shared__ double red[2 * CG + 2][TPB / 32];
+  const int c0 = blockIdx.y * CG;
+  const int ncol = max(0, min(CG, J - c0));
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  const int64_t stride = 2 * (int64_t)J + 2;
+  T uv[U], yv[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int64_t r = base + (int64_t)k * TPB;
+    uv[k] = (r < n) ? ldg(u + r) : num<T>::zero();
+    yv[k] = (r < n) ? ldg(y + r) : num<T>::zero();
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (blockIdx.y == 0) {  // u.u and u.y
+    A aa, ag;
+    acc_set(aa, num<T>::zero());
+    acc_set(ag, num<T>::zero());
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      acc_add_prod(aa, uv[k], uv[k]);
+      acc_add_prod(ag, uv[k], yv[k]);
+    }
+    const T sa = warp_reduce_d(acc_get(aa)), sg = warp_reduce_d(acc_get(ag));
+    if (lane == 0) {
+      red[2 * CG][wid] = num<T>::to_d(sa);
+      red[2 * CG + 1][wid] = num<T>::to_d(sg);
+    }
+  }
+  constexpr int CU = sizeof(T) == 4 ? 4 : 2;
+  for (int g0 = 0; g0 < ncol; g0 += CU) {
+    T vals[CU][U];
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      const T *col = V + (int64_t)(c0 + min(g0 + q, ncol - 1)) * ldv;
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int64_t r = base + (int64_t)k * TPB;
+        vals[q][k] = (r < n && g0 + q < ncol) ? ldg(col + r) : num<T>::zero();
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      if (g0 + q >= ncol) break;
+      A as, at;
+      acc_set(as, num<T>::zero());
+      acc_set(at, num<T>::zero());
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (base + (int64_t)k * TPB < n) {
+          acc_add_prod(as, vals[q][k], uv[k]);
+          acc_add_prod(at, vals[q][k], yv[k]);
+        }
+      const T ss = warp_reduce_d(acc_get(as)), st = warp_reduce_d(acc_get(at));
+      if (lane == 0) {
+        red[g0 + q][wid] = num<T>::to_d(ss);
+        red[CG + g0 + q][wid] = num<T>::to_d(st);
+      }
+    }
+  }
+  __syncthreads();
+  const int tix = threadIdx.x;
+  double sum = 0.0;
+  int slot = -1;
+  int64_t out = 0;
+  if (tix < ncol) {
+    slot = tix;
+    out = c0 + tix;
+  } else if (tix >= CG && tix < CG + ncol) {
+    slot = tix;
+    out = J + c0 + (tix - CG);
+  } else if (blockIdx.y == 0 && (tix == 2 * CG || tix == 2 * CG + 1)) {
+    slot = tix;
+    out = 2 * J + (tix - 2 * CG);
+  }
+  if (slot >= 0) {
+    for (int q = 0; q < TPB / 32; ++q) sum += red[slot][q];
+    partials[(int64_t)blockIdx.x * stride + out] = sum;
+  }
+}
+
+// u <- (u - V s) / beta (= v_j) and y <- y / beta - V d - e u (= u_{j+1}), in place;
+// co = [s_0..s_{J-1}, d_0..d_{J-1}], sc = [1/beta, e]
+template <typename T>
+__global__ void __launch_bounds__(TPB) k_update2(const T *__restrict__ V, int64_t ldv, int J,
+                                                 const double *__restrict__ co, const double *__restrict__ sc,
+                                                 T *__restrict__ u, T *__restrict__ y, int64_t n) {
+  pdl_wait();
+  pdl_trigger();
+  using A = typename acc_of<T>::type;
+  extern __shared__ unsigned char smem_raw[];
+  T *ns = reinterpret_cast<T *>(smem_raw);  // -s
+  T *nd = ns + J;                            // -d
+  for (int c = threadIdx.x; c < J; c += TPB) {
+    ns[c] = num<T>::from_d(-co[c]);
+    nd[c] = num<T>::from_d(-co[J + c]);
+  }
+  const T ib = num<T>::from_d(sc[0]), ne = num<T>::from_d(-sc[1]);
+  __syncthreads();
+  const int64_t base = (int64_t)blockIdx.x * CHUNK + threadIdx.x;
+  A a1[U], a2[U];
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int64_t r = base + (int64_t)k * TPB;
+    const T ur = (r < n) ? u[r] : num<T>::zero();
+    const T yr = (r < n) ? y[r] : num<T>::zero();
+    acc_set(a1[k], ur);
+    acc_set_prod(a2[k], ib, yr);
+    acc_add_prod(a2[k], ne, ur);
+  }
+  constexpr int CU = sizeof(T) == 4 ? 4 : 2;
+  int c = 0;
+  for (; c + CU <= J; c += CU) {
+    T vals[CU][U];
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      const T *col = V + (int64_t)(c + q) * ldv;
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        const int64_t r = base + (int64_t)k * TPB;
+        vals[q][k] = (r < n) ? ldg(col + r) : num<T>::zero();
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < CU; ++q) {
+      const T sq = ns[c + q], dq = nd[c + q];
+#pragma unroll
+      for (int k = 0; k < U; ++k)
+        if (base + (int64_t)k * TPB < n) {
+          acc_add_prod(a1[k], sq, vals[q][k]);
+          acc_add_prod(a2[k], dq, vals[q][k]);
+        }
+    }
+  }
+  for (; c < J; ++c) {
+    const T *col = V + (int64_t)c * ldv;
+    const T sq = ns[c], dq = nd[c];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int64_t r = base + (int64_t)k * TPB;
+      if (r < n) {
+        const T vv = ldg(col + r);
+        acc_add_prod(a1[k], sq, vv);
+        acc_add_prod(a2[k], dq, vv);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < U; ++k) {
+    const int64_t r = base + (int64_t)k * TPB;
+    if (r < n) {
+      A v;
+      acc_set_prod(v, ib, acc_get(a1[k]));
+      u[r] = acc_get(v);
+      y[r] = acc_get(a2[k]);
+    }
+  }
+}
+
+// The step's coefficients (one block, FP64).  R = [s (J), t (J), a, g];
+// h1s = the first-pass coefficients of column J-1 (J values), kept from the
+// previous step.  Writes H[0:J, J-1] = h1s + s, H[J, J-1] = beta, the new
+// first-pass coefficients h1_new (J + 1 values) into h1s and into H[0:J+1, J],
+// co = [s, d], sc = [1/beta, e]; a vanishing or non-finite beta sets the
+// status (breakdown at Krylov dimension J, or bad) and zeroes 1/beta, d, e.
+__global__ void __launch_bounds__(256) k_dcgs_coef(const double *__restrict__ R, int J, double *__restrict__ H, int ldh,
+                                                   double *__restrict__ h1s, double *__restrict__ co,
+                                                   double *__restrict__ sc, double rel, DevStatus *st) {
+  pdl_wait();
+  pdl_trigger();
+  __shared__ double red[32];
+  __shared__ double p[kDcgsMaxJ + 1];
+  __shared__ double sh_beta, sh_ok;
+  const double *s = R, *t = R + J;
+  const double a = R[2 * J], g = R[2 * J + 1];
+  double ss = 0.0, st_ = 0.0, rr = 0.0;
+  for (int i = threadIdx.x; i < J; i += blockDim.x) {
+    ss += s[i] * s[i];
+    st_ += s[i] * t[i];
+    const double hf = h1s[i] + s[i];
+    rr += hf * hf;
+  }
+  ss = block_sum(ss, red);
+  st_ = block_sum(st_, red);
+  rr = block_sum(rr, red);
+  if (threadIdx.x == 0) {
+    const double b2 = a - ss;
+    const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
+    const bool finite = isfinite(a) && isfinite(ss) && isfinite(g);
+    bool bd = !(beta > 0.0) || (J > 0 && beta <= rel * sqrt(rr + beta * beta));
+    if (!finite) {
+      st->bad = 1;
+      bd = true;
+    }
+    if (bd && !st->breakdown) {
+      st->breakdown = 1;
+      st->m_bd = J;
+    }
+    sh_beta = beta;
+    sh_ok = bd ? 0.0 : 1.0;
+  }
+  __syncthreads();
+  const double beta = sh_beta;
+  const bool ok = sh_ok != 0.0;
+  if (J > 0) {  // column J-1: the second pass added
+    for (int i = threadIdx.x; i < J; i += blockDim.x) H[(size_t)(J - 1) * ldh + i] = h1s[i] + s[i];
+    if (threadIdx.x == 0) H[(size_t)(J - 1) * ldh + J] = ok ? beta : 0.0;
+  }
+  __syncthreads();
+  // p = H[0:J+1, 0:J] s (upper Hessenberg: row i from column i-1 on)
+  for (int i = threadIdx.x; i <= J; i += blockDim.x) {
+    double v = 0.0;
+    for (int k = i > 0 ? i - 1 : 0; k < J; ++k) v += H[(size_t)k * ldh + i] * s[k];
+    p[i] = v;
+  }
+  __syncthreads();
+  const double ib = ok ? 1.0 / beta : 0.0;
+  const double vy = (g - st_) * ib;  // v_j . y
+  const double hJ = (vy - p[J]) * ib;
+  const double cJ = p[J] * ib + hJ;
+  for (int i = threadIdx.x; i <= J; i += blockDim.x) {
+    const double hn = i < J ? (t[i] - p[i]) * ib : hJ;
+    h1s[i] = ok ? hn : 0.0;
+    H[(size_t)J * ldh + i] = ok ? hn : 0.0;
+    if (i < J) {
+      const double ci = p[i] * ib + hn;
+      co[i] = s[i];
+      co[J + i] = ok ? ci - cJ * s[i] * ib : 0.0;
+    }
+  }
+  if (threadIdx.x == 0) {
+    sc[0] = ib;
+    sc[1] = ok ? cJ * ib : 0.0;
+  }
+}
 }  // namespace
 
 int vec_nchunks(int64_t n) { return (int)nchunks(n); }
@@ -957,6 +1212,33 @@ int vec_scale_c(const T *in, T *out, int64_t n, double cr, double ci, cudaStream
   return PP_OK;
 }
 
+template <typename T>
+int vec_dot2(const T *V, int64_t ldv, int J, const T *u, const T *y, int64_t n, double *partials, cudaStream_t s) {
+  dim3 grd(nchunks(n), (unsigned)std::max(1, (J + CG - 1) / CG));
+  PP_CUDA_TRY(pdl_launch(k_dot2<T>, grd, dim3(TPB), 0, s, V, ldv, J, u, y, n, partials));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+template <typename T>
+int vec_update2(const T *V, int64_t ldv, int J, const double *co, const double *sc, T *u, T *y, int64_t n,
+                cudaStream_t s) {
+  const size_t sm = (size_t)2 * std::max(J, 1) * sizeof(T);
+  if (sm > 48 * 1024) PP_CUDA_TRY(cudaFuncSetAttribute(k_update2<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  PP_CUDA_TRY(pdl_launch(k_update2<T>, dim3(nchunks(n)), dim3(TPB), sm, s, V, ldv, J, co, sc, u, y, n));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+int dcgs_coef(const double *R, int J, double *H, int ldh, double *h1s, double *co, double *sc, double rel,
+              DevStatus *st, cudaStream_t s) {
+  if (J > kDcgsMaxJ) return pp_set_error(PP_ERR_INVALID_ARG, "delayed reorthogonalization: basis too wide");
+  PP_CUDA_TRY(pdl_launch(k_dcgs_coef, dim3(1), dim3(256), 0, s, R, J, H, ldh, h1s, co, sc, rel, st));
+  ++pp_launch_count();
+  PP_CUDA_TRY(cudaGetLastError());
+  return PP_OK;
+}
+
 #define PP_INST(T)                                                                                  \
   template int vec_from_f64<T>(const double *, T *, int64_t, cudaStream_t);                       \
   template int vec_to_f64<T>(const T *, double *, int64_t, cudaStream_t);                         \
@@ -975,6 +1257,9 @@ int vec_scale_c(const T *in, T *out, int64_t n, double cr, double ci, cudaStream
                                   cudaStream_t, const Seg &, const int *);                        \
   template int vec_update_dot<T>(const T *, int64_t, int, const double *, T *, int64_t, double *,  \
                                  cudaStream_t, const Seg &);                                      \
+  template int vec_dot2<T>(const T *, int64_t, int, const T *, const T *, int64_t, double *, cudaStream_t); \
+  template int vec_update2<T>(const T *, int64_t, int, const double *, const double *, T *, T *, int64_t,  \
+                              cudaStream_t);                                                       \
   template int vec_multi_dot_c<T>(const T *, int64_t, int, const T *, int64_t, double *, cudaStream_t); \
   template int vec_multi_update_c<T>(const T *, int64_t, int, const double *, T *, int64_t, double *, \
                                      cudaStream_t);                                               \

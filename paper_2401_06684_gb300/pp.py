@@ -28,7 +28,7 @@ PP_CHEBYSHEV, PP_RITZ_LEJA, PP_HARMONIC_RITZ, PP_LSQ_CONTOUR, PP_NODES = 0, 1, 2
 PP_LAPLACE2D5, PP_LAPLACE3D7, PP_CONVDIFF3D7_UPWIND, PP_WILSON4D_DHD, PP_WILSON4D_Q2 = 0, 1, 2, 3, 4
 PP_LEFT, PP_RIGHT = 0, 1
 PP_PREC_F64, PP_PREC_DW, PP_PREC_MIXED = 0, 1, 2
-PP_ORTH_AUTO, PP_ORTH_LANCZOS, PP_ORTH_CGS2 = 0, 1, 2
+PP_ORTH_AUTO, PP_ORTH_LANCZOS, PP_ORTH_CGS2, PP_ORTH_DCGS2 = 0, 1, 2, 3
 
 LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "libppsqrt.so")
 

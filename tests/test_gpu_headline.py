@@ -3,7 +3,8 @@
 3D upwind convection-diffusion on the 128^3 grid (n = 2,097,152, c*h = 0.5),
 x = A^{1/2} b = A^{-1/2}(A b) (Sec. 4), Chebyshev q of degree 16 on the exact
 spectral interval, left preconditioning (Algorithm 1), CGS2 Arnoldi, stopping
-estimate 1e-10 (Sec. 6, Example 1's rule, a check every 64/d iterations).
+estimate 1e-10 (Sec. 6, Example 1's rule, a check every 64/d iterations);
+classical Gram-Schmidt twice (CGS2) and its delayed form (PP_ORTH_DCGS2).
 
 The reference is the oracle's own Algorithm 1 in FP64 (numpy/scipy, the CSR
 products of the sparse operator on the host cores) run to a stopping
@@ -53,12 +54,14 @@ def handle():
     pp.pp_destroy(h)
 
 
+@pytest.mark.parametrize("orth", ["cgs2", "dcgs2"])
 @pytest.mark.parametrize("prec", ["mixed", "dw", "f64"])
-def test_convdiff128_sqrt_vs_oracle(oracle_run, handle, prec):
+def test_convdiff128_sqrt_vs_oracle(oracle_run, handle, prec, orth):
     A, rhs, xs = oracle_run
     pp, h = handle
     o = pp.pp_default_opts()
     o.precision = PREC[prec]
+    o.orth = {"cgs2": pp.PP_ORTH_CGS2, "dcgs2": pp.PP_ORTH_DCGS2}[orth]
     pp.pp_set_opts(h, o)
     b = torch.from_numpy(rhs).cuda()
     x = torch.empty_like(b)
