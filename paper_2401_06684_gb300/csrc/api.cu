@@ -431,7 +431,8 @@ int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double b
 // candidate u_j (one Gram-Schmidt pass, unnormalized), y = A q(A)^2 u_j goes
 // to column j + 1; one sweep forms the inner products, one block the
 // coefficients, and one more sweep leaves v_j in column j and the candidate
-// u_{j+1} in column j + 1 (vec.cu, k_dot2 / k_dcgs_coef / k_update2).
+// u_{j+1} in column j + 1 (vec.cu, k_dot2 / k_dcgs_coef / k_update2; k_dcgs_coef also
+// sums the sweep's per-chunk partials, a block per column).
 // Afterwards columns 0..j of V and columns 0..j-1 of H are final.
 template <typename T>
 int krylov_step_d(Solve &S, const OpDesc &op, T *V, T *t[6], int j, double bd_rel) {
@@ -448,8 +449,7 @@ int krylov_step_d(Solve &S, const OpDesc &op, T *V, T *t[6], int j, double bd_re
   RC_(prof_begin(c, 1));
   double *R = S.dd, *co = S.dd + 2 * (size_t)(j + 1);
   RC(vec_dot2<T>(V, ldv, j, u, y, n, S.part, s));
-  RC(reduce_cols(S.part, S.nb, 2 * j + 2, 0, R, nullptr, s));
-  RC(dcgs_coef(R, j, S.H, S.ldh, S.h1, co, S.scal, bd_rel, c->ws.st, s));
+  RC(dcgs_coef(S.part, S.nb, j, R, S.H, S.ldh, S.h1, co, S.scal, bd_rel, c->ws.st, s));
   RC(vec_update2<T>(V, ldv, j, co, S.scal, u, y, n, s));
   S.ip += 2 * (int64_t)j + 2;
   return prof_end(c);

@@ -265,21 +265,22 @@ struct DevStatus {
   double est;
   double beta0;
   double znorm;
-  double pad;
+  unsigned int ticket;  // finished reduction blocks of k_dcgs_coef (its last block resets it)
+  int pad;
 };
 // Arnoldi with delayed reorthogonalization (vec.cu): the inner products of
 // the candidate u and y = A q(A)^2 u with the basis (partials of 2J + 2
-// columns: V^T u, V^T y, u.u, u.y), the step's coefficients (one block,
-// FP64; J <= kDcgsMaxJ) and the update sweep that writes v_j into u's column
-// and the next candidate into y's.
+// columns: V^T u, V^T y, u.u, u.y), their sums and the step's coefficients
+// (FP64; J <= kDcgsMaxJ; R receives the 2J + 2 sums) and the update sweep
+// that writes v_j into u's column and the next candidate into y's.
 constexpr int kDcgsMaxJ = 4096;
 template <typename T>
 int vec_dot2(const T *V, int64_t ldv, int J, const T *u, const T *y, int64_t n, double *partials, cudaStream_t s);
 template <typename T>
 int vec_update2(const T *V, int64_t ldv, int J, const double *co, const double *sc, T *u, T *y, int64_t n,
                 cudaStream_t s);
-int dcgs_coef(const double *R, int J, double *H, int ldh, double *h1s, double *co, double *sc, double rel,
-              DevStatus *st, cudaStream_t s);
+int dcgs_coef(const double *partials, int nb, int J, double *R, double *H, int ldh, double *h1s, double *co,
+              double *sc, double rel, DevStatus *st, cudaStream_t s);
 int norm_finalize(const double *partials, int nb, double *beta_out, double *inv_out,
                   const double *ref, int nref, double rel, int m_here, DevStatus *st,
                   cudaStream_t s, const Seg &S = Seg());

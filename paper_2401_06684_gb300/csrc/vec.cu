@@ -794,12 +794,44 @@ __global__ void __launch_bounds__(TPB) k_scale_c(const T *__restrict__ in, T *__
 // per step instead of the three of CGS2 plus the normalization pass.
 
 // partials[chunk*(2J+2) + c]: c < J: V_c.u, J + c: V_c.y, 2J: u.u, 2J+1: u.y
+
+__device__ __forceinline__ float bfly_shfl(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double bfly_shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ dw bfly_shfl(dw v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// Warp reduce-scatter of 16 values per lane (recursive halving): at each of
+// the offsets 16, 8, 4, 2 a lane keeps one half of its values, sends the
+// other half to its partner and adds what it receives; the offset-1 step
+// completes the sum.  15 + 1 additions instead of 16 x 5 for 16 separate
+// reductions.  Afterwards lane l holds the warp total of value bfly_index(l)
+// (lanes l and l ^ 1 hold the same one).
+__device__ __forceinline__ int bfly_index(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_dot2(const T *__restrict__ V, int64_t ldv, int J, const T *__restrict__ u,
+__device__ __forceinline__ T warp_reduce_scatter16(T (&v)[16], int lane) {
+#pragma unroll
+  for (int h = 8; h >= 1; h >>= 1) {
+    const bool up = (lane & (2 * h)) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + bfly_shfl(send, 2 * h);
+    }
+  }
+  return v[0] + bfly_shfl(v[0], 1);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 : 2) k_dot2(const T *__restrict__ V, int64_t ldv, int J, const T *__restrict__ u,
                                               const T *__restrict__ y, int64_t n, double *__restrict__ partials) {
   pdl_wait();
   pdl_trigger();
   using A = typename acc_of<T>::type;
+  static_assert(CG == 8, "the reduce-scatter takes 2 x 8 column sums");
   __shared__ double red[2 * CG + 2][TPB / 32];
   const int c0 = blockIdx.y * CG;
   const int ncol = max(0, min(CG, J - c0));
@@ -828,36 +860,48 @@ __global__ void __launch_bounds__(TPB) k_dot2(const T *__restrict__ V, int64_t l
       red[2 * CG + 1][wid] = num<T>::to_d(sg);
     }
   }
-  constexpr int CU = sizeof(T) == 4 ? 4 : 2;
-  for (int g0 = 0; g0 < ncol; g0 += CU) {
-    T vals[CU][U];
+  if (ncol > 0) {
+    // the group's column sums stay in registers until one reduce-scatter
+    A as[CG], at[CG];
 #pragma unroll
-    for (int q = 0; q < CU; ++q) {
-      const T *col = V + (int64_t)(c0 + min(g0 + q, ncol - 1)) * ldv;
-#pragma unroll
-      for (int k = 0; k < U; ++k) {
-        const int64_t r = base + (int64_t)k * TPB;
-        vals[q][k] = (r < n && g0 + q < ncol) ? ldg(col + r) : num<T>::zero();
-      }
+    for (int q = 0; q < CG; ++q) {
+      acc_set(as[q], num<T>::zero());
+      acc_set(at[q], num<T>::zero());
     }
+    constexpr int CU = sizeof(T) == 4 ? 4 : 2;
 #pragma unroll
-    for (int q = 0; q < CU; ++q) {
-      if (g0 + q >= ncol) break;
-      A as, at;
-      acc_set(as, num<T>::zero());
-      acc_set(at, num<T>::zero());
+    for (int g0 = 0; g0 < CG; g0 += CU) {
+      if (g0 < ncol) {  // uniform over the block
+        T vals[CU][U];
 #pragma unroll
-      for (int k = 0; k < U; ++k)
-        if (base + (int64_t)k * TPB < n) {
-          acc_add_prod(as, vals[q][k], uv[k]);
-          acc_add_prod(at, vals[q][k], yv[k]);
+        for (int q = 0; q < CU; ++q) {
+          const T *col = V + (int64_t)(c0 + min(g0 + q, ncol - 1)) * ldv;
+#pragma unroll
+          for (int k = 0; k < U; ++k) {
+            const int64_t r = base + (int64_t)k * TPB;
+            vals[q][k] = (r < n && g0 + q < ncol) ? ldg(col + r) : num<T>::zero();
+          }
         }
-      const T ss = warp_reduce_d(acc_get(as)), st = warp_reduce_d(acc_get(at));
-      if (lane == 0) {
-        red[g0 + q][wid] = num<T>::to_d(ss);
-        red[CG + g0 + q][wid] = num<T>::to_d(st);
+#pragma unroll
+        for (int q = 0; q < CU; ++q)
+          if (g0 + q < ncol) {
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+              acc_add_prod(as[g0 + q], vals[q][k], uv[k]);
+              acc_add_prod(at[g0 + q], vals[q][k], yv[k]);
+            }
+          }
       }
     }
+    T v[16];
+#pragma unroll
+    for (int q = 0; q < CG; ++q) {
+      v[q] = acc_get(as[q]);
+      v[CG + q] = acc_get(at[q]);
+    }
+    const T tot = warp_reduce_scatter16(v, lane);
+    const int idx = bfly_index(lane);  // idx < CG: V_{c0+idx}.u, else V_{c0+idx-CG}.y
+    if ((lane & 1) == 0 && (idx & (CG - 1)) < ncol) red[idx][wid] = num<T>::to_d(tot);
   }
   __syncthreads();
   const int tix = threadIdx.x;
@@ -883,7 +927,7 @@ __global__ void __launch_bounds__(TPB) k_dot2(const T *__restrict__ V, int64_t l
 // u <- (u - V s) / beta (= v_j) and y <- y / beta - V d - e u (= u_{j+1}), in place;
 // co = [s_0..s_{J-1}, d_0..d_{J-1}], sc = [1/beta, e]
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_update2(const T *__restrict__ V, int64_t ldv, int J,
+__global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 : 2) k_update2(const T *__restrict__ V, int64_t ldv, int J,
                                                  const double *__restrict__ co, const double *__restrict__ sc,
                                                  T *__restrict__ u, T *__restrict__ y, int64_t n) {
   pdl_wait();
@@ -958,69 +1002,106 @@ __global__ void __launch_bounds__(TPB) k_update2(const T *__restrict__ V, int64_
   }
 }
 
-// The step's coefficients (one block, FP64).  R = [s (J), t (J), a, g];
+// The step's coefficients, FP64.  Block c of the 2J + 2 blocks sums column c
+// of the inner-product sweep's partials (nb chunks x (2J + 2), row-major) in
+// a fixed order into R[c]; the last block to finish (a ticket in the status)
+// reads R = [s (J), t (J), a, g] and does the algebra with few FP64
+// operations (one SM retires only about two FP64 additions per clock).
 // h1s = the first-pass coefficients of column J-1 (J values), kept from the
 // previous step.  Writes H[0:J, J-1] = h1s + s, H[J, J-1] = beta, the new
-// first-pass coefficients h1_new (J + 1 values) into h1s and into H[0:J+1, J],
-// co = [s, d], sc = [1/beta, e]; a vanishing or non-finite beta sets the
-// status (breakdown at Krylov dimension J, or bad) and zeroes 1/beta, d, e.
-__global__ void __launch_bounds__(256) k_dcgs_coef(const double *__restrict__ R, int J, double *__restrict__ H, int ldh,
-                                                   double *__restrict__ h1s, double *__restrict__ co,
-                                                   double *__restrict__ sc, double rel, DevStatus *st) {
+// first-pass coefficients h1_new (J + 1 values) into h1s and into
+// H[0:J+1, J], co = [s, d], sc = [1/beta, e]; a vanishing or non-finite beta
+// sets the status (breakdown at Krylov dimension J, or bad) and zeroes
+// 1/beta, d, e.  Dynamic shared memory: 2J + 1 doubles (s and p = H s).
+__global__ void __launch_bounds__(256) k_dcgs_coef(const double *__restrict__ part, int nb, int J, double *R,
+                                                   double *__restrict__ H, int ldh, double *__restrict__ h1s,
+                                                   double *__restrict__ co, double *__restrict__ sc, double rel,
+                                                   DevStatus *st) {
   pdl_wait();
   pdl_trigger();
+  extern __shared__ double shm[];
   __shared__ double red[32];
-  __shared__ double p[kDcgsMaxJ + 1];
-  __shared__ double sh_beta, sh_ok;
-  const double *s = R, *t = R + J;
-  const double a = R[2 * J], g = R[2 * J + 1];
-  double ss = 0.0, st_ = 0.0, rr = 0.0;
-  for (int i = threadIdx.x; i < J; i += blockDim.x) {
-    ss += s[i] * s[i];
-    st_ += s[i] * t[i];
-    const double hf = h1s[i] + s[i];
-    rr += hf * hf;
+  __shared__ int last;
+  __shared__ double sh_beta, sh_ok, sh_st;
+  const int S = 2 * J + 2, c = blockIdx.x, tid = threadIdx.x, lane = tid & 31;
+  {
+    double v = 0.0;
+    for (int b = tid; b < nb; b += blockDim.x) v += part[(int64_t)b * S + c];
+    v = block_sum(v, red);
+    if (tid == 0) {
+      R[c] = v;
+      __threadfence();
+      last = atomicAdd(&st->ticket, 1u) == (unsigned)S - 1;
+    }
+    __syncthreads();
+    if (!last) return;
   }
-  ss = block_sum(ss, red);
-  st_ = block_sum(st_, red);
-  rr = block_sum(rr, red);
-  if (threadIdx.x == 0) {
-    const double b2 = a - ss;
-    const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
-    const bool finite = isfinite(a) && isfinite(ss) && isfinite(g);
-    bool bd = !(beta > 0.0) || (J > 0 && beta <= rel * sqrt(rr + beta * beta));
-    if (!finite) {
-      st->bad = 1;
-      bd = true;
+  __threadfence();
+  double *s = shm;      // J
+  double *p = shm + J;  // J + 1
+  for (int i = tid; i < J; i += blockDim.x) s[i] = __ldcg(R + i);
+  const double a = __ldcg(R + 2 * J), g = __ldcg(R + 2 * J + 1);
+  if (tid < 32) {  // s.s, s.t, |h1s + s|^2 in one warp
+    double ss = 0.0, st_ = 0.0, rr = 0.0;
+    for (int i = lane; i < J; i += 32) {
+      const double si = __ldcg(R + i), ti = __ldcg(R + J + i), hf = h1s[i] + si;
+      ss += si * si;
+      st_ += si * ti;
+      rr += hf * hf;
     }
-    if (bd && !st->breakdown) {
-      st->breakdown = 1;
-      st->m_bd = J;
+    ss = warp_sum(ss);
+    st_ = warp_sum(st_);
+    rr = warp_sum(rr);
+    if (lane == 0) {
+      st->ticket = 0;
+      const double b2 = a - ss;
+      const double beta = b2 > 0.0 ? sqrt(b2) : 0.0;
+      const bool finite = isfinite(a) && isfinite(ss) && isfinite(g);
+      bool bd = !(beta > 0.0) || (J > 0 && beta <= rel * sqrt(rr + beta * beta));
+      if (!finite) {
+        st->bad = 1;
+        bd = true;
+      }
+      if (bd && !st->breakdown) {
+        st->breakdown = 1;
+        st->m_bd = J;
+      }
+      sh_beta = beta;
+      sh_ok = bd ? 0.0 : 1.0;
+      sh_st = st_;
     }
-    sh_beta = beta;
-    sh_ok = bd ? 0.0 : 1.0;
   }
   __syncthreads();
   const double beta = sh_beta;
   const bool ok = sh_ok != 0.0;
-  if (J > 0) {  // column J-1: the second pass added
-    for (int i = threadIdx.x; i < J; i += blockDim.x) H[(size_t)(J - 1) * ldh + i] = h1s[i] + s[i];
-    if (threadIdx.x == 0) H[(size_t)(J - 1) * ldh + J] = ok ? beta : 0.0;
-  }
-  __syncthreads();
-  // p = H[0:J+1, 0:J] s (upper Hessenberg: row i from column i-1 on)
-  for (int i = threadIdx.x; i <= J; i += blockDim.x) {
+  const double hlast = ok ? beta : 0.0;  // H[J, J-1]
+  // row i of p = H[0:J+1, 0:J] s (upper Hessenberg: from column i-1 on); column J-1
+  // is h1s + s (rows < J) and beta (row J), the rest is final from earlier steps
+  for (int i = tid; i <= J; i += blockDim.x) {
     double v = 0.0;
-    for (int k = i > 0 ? i - 1 : 0; k < J; ++k) v += H[(size_t)k * ldh + i] * s[k];
+    int k = i > 0 ? i - 1 : 0;
+    for (; k + 8 <= J - 1; k += 8) {
+      double hv[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) hv[q] = H[(size_t)(k + q) * ldh + i];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v += hv[q] * s[k + q];
+    }
+    for (; k < J - 1; ++k) v += H[(size_t)k * ldh + i] * s[k];
+    if (J > 0) {
+      const double hc = i < J ? h1s[i] + s[i] : hlast;
+      v += hc * s[J - 1];
+      H[(size_t)(J - 1) * ldh + i] = hc;
+    }
     p[i] = v;
   }
   __syncthreads();
   const double ib = ok ? 1.0 / beta : 0.0;
-  const double vy = (g - st_) * ib;  // v_j . y
+  const double vy = (g - sh_st) * ib;  // v_j . y
   const double hJ = (vy - p[J]) * ib;
   const double cJ = p[J] * ib + hJ;
-  for (int i = threadIdx.x; i <= J; i += blockDim.x) {
-    const double hn = i < J ? (t[i] - p[i]) * ib : hJ;
+  for (int i = tid; i <= J; i += blockDim.x) {
+    const double hn = i < J ? (__ldcg(R + J + i) - p[i]) * ib : hJ;
     h1s[i] = ok ? hn : 0.0;
     H[(size_t)J * ldh + i] = ok ? hn : 0.0;
     if (i < J) {
@@ -1029,7 +1110,7 @@ __global__ void __launch_bounds__(256) k_dcgs_coef(const double *__restrict__ R,
       co[J + i] = ok ? ci - cJ * s[i] * ib : 0.0;
     }
   }
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     sc[0] = ib;
     sc[1] = ok ? cJ * ib : 0.0;
   }
@@ -1230,10 +1311,13 @@ int vec_update2(const T *V, int64_t ldv, int J, const double *co, const double *
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
 }
-int dcgs_coef(const double *R, int J, double *H, int ldh, double *h1s, double *co, double *sc, double rel,
-              DevStatus *st, cudaStream_t s) {
+int dcgs_coef(const double *partials, int nb, int J, double *R, double *H, int ldh, double *h1s, double *co,
+              double *sc, double rel, DevStatus *st, cudaStream_t s) {
   if (J > kDcgsMaxJ) return pp_set_error(PP_ERR_INVALID_ARG, "delayed reorthogonalization: basis too wide");
-  PP_CUDA_TRY(pdl_launch(k_dcgs_coef, dim3(1), dim3(256), 0, s, R, J, H, ldh, h1s, co, sc, rel, st));
+  const size_t sm = sizeof(double) * ((size_t)2 * J + 1);
+  if (sm > 48 * 1024) PP_CUDA_TRY(cudaFuncSetAttribute(k_dcgs_coef, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  PP_CUDA_TRY(pdl_launch(k_dcgs_coef, dim3(2 * J + 2), dim3(256), sm, s, partials, nb, J, R, H, ldh, h1s, co, sc, rel,
+                         st));
   ++pp_launch_count();
   PP_CUDA_TRY(cudaGetLastError());
   return PP_OK;
