@@ -199,10 +199,52 @@ __global__ void __launch_bounds__(TPB) k_lanczos_update(T *__restrict__ w, const
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+__device__ __forceinline__ float bfly_shfl(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double bfly_shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ dw bfly_shfl(dw v, int o) {
+  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
+
+// Warp reduce-scatter of K (8 or 16) values per lane by recursive halving:
+// at the offsets 16, 8, ... (log2 K of them) a lane keeps one half of its
+// values, sends the other half to its partner and adds what it receives;
+// the remaining offsets complete the sum.  K - 1 + 5 - log2 K additions
+// instead of 5 K for K separate reductions, with the same pairing of lanes
+// as warp_reduce_d (offset 16 first), so each total is bit for bit the
+// separate reduction's.  Afterwards lane l holds the warp total of value
+// rs_index<K>(l); rs_writer<K>(l) picks one lane per value.
+template <int K>
+__device__ __forceinline__ int rs_index(int lane) {
+  static_assert(K == 8 || K == 16, "reduce-scatter of 8 or 16 values");
+  return K == 16 ? (lane >> 1) & 15 : (lane >> 2) & 7;
+}
+template <int K>
+__device__ __forceinline__ bool rs_writer(int lane) {
+  return (lane & (32 / K - 1)) == 0;
+}
+template <int K, typename T>
+__device__ __forceinline__ T warp_reduce_scatter(T (&v)[K], int lane) {
+  static_assert(K == 8 || K == 16, "reduce-scatter of 8 or 16 values");
+#pragma unroll
+  for (int h = K / 2, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + bfly_shfl(send, o);
+    }
+  }
+  T r = v[0];
+#pragma unroll
+  for (int o = K == 16 ? 1 : 2; o >= 1; o >>= 1) r = r + bfly_shfl(r, o);
+  return r;
+}
+
 // partials[chunk*J + c] = sum over the chunk of V_c . w, for the CG columns
 // c = blockIdx.y*CG + g of this block.
 template <typename T>
-__global__ void __launch_bounds__(TPB) k_multi_dot(const T *__restrict__ V, int64_t ldv, int J,
+__global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 4 : 3) k_multi_dot(const T *__restrict__ V, int64_t ldv, int J,
                                                    const T *__restrict__ w, int64_t n,
                                                    double *__restrict__ partials, Seg S) {
   pdl_wait();
@@ -223,31 +265,40 @@ __global__ void __launch_bounds__(TPB) k_multi_dot(const T *__restrict__ V, int6
     wv[u] = (r < n) ? ldg(w + r) : num<T>::zero();
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // CU columns per pass, their loads issued together (same per-column order)
+  // CU columns per pass, their loads issued together; the block's CG column
+  // sums stay in registers until one reduce-scatter
   constexpr int CU = sizeof(T) == 4 ? 4 : 2;
-  for (int g0 = 0; g0 < ncol; g0 += CU) {
-    T vals[CU][U];
+  A acc[CG];
 #pragma unroll
-    for (int q = 0; q < CU; ++q) {
-      const T *col = V + (int64_t)(c0 + min(g0 + q, ncol - 1)) * ldv;
+  for (int q = 0; q < CG; ++q) acc_set(acc[q], num<T>::zero());
 #pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int64_t r = base + (int64_t)u * TPB;
-        vals[q][u] = (r < n && g0 + q < ncol) ? ldg(col + r) : num<T>::zero();
+  for (int g0 = 0; g0 < CG; g0 += CU) {
+    if (g0 < ncol) {  // uniform over the block
+      T vals[CU][U];
+#pragma unroll
+      for (int q = 0; q < CU; ++q) {
+        const T *col = V + (int64_t)(c0 + min(g0 + q, ncol - 1)) * ldv;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int64_t r = base + (int64_t)u * TPB;
+          vals[q][u] = (r < n && g0 + q < ncol) ? ldg(col + r) : num<T>::zero();
+        }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < CU; ++q) {
-      if (g0 + q >= ncol) break;
-      A acc;
-      acc_set(acc, num<T>::zero());
+      for (int q = 0; q < CU; ++q)
+        if (g0 + q < ncol) {
 #pragma unroll
-      for (int u = 0; u < U; ++u)
-        if (base + (int64_t)u * TPB < n) acc_add_prod(acc, vals[q][u], wv[u]);
-      const T s = warp_reduce_d(acc_get(acc));
-      if (lane == 0) red[g0 + q][wid] = num<T>::to_d(s);
+          for (int u = 0; u < U; ++u)
+            if (base + (int64_t)u * TPB < n) acc_add_prod(acc[g0 + q], vals[q][u], wv[u]);
+        }
     }
   }
+  T v[CG];
+#pragma unroll
+  for (int q = 0; q < CG; ++q) v[q] = acc_get(acc[q]);
+  const T tot = warp_reduce_scatter<CG>(v, lane);
+  const int idx = rs_index<CG>(lane);
+  if (rs_writer<CG>(lane) && idx < ncol) red[idx][wid] = num<T>::to_d(tot);
   __syncthreads();
   if (threadIdx.x < ncol) {
     double s = 0.0;
@@ -376,13 +427,12 @@ __global__ void __launch_bounds__(TPB) k_update_dot(const T *__restrict__ V, int
       if (c < J) acc_add_prod(dacc[c], vv[c], wr);
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T dv[JMAX];
 #pragma unroll
-  for (int c = 0; c < JMAX; ++c) {
-    if (c < J) {
-      const T sc = warp_reduce_d(acc_get(dacc[c]));
-      if (lane == 0) red[c][wid] = num<T>::to_d(sc);
-    }
-  }
+  for (int c = 0; c < JMAX; ++c) dv[c] = acc_get(dacc[c]);
+  const T tot = warp_reduce_scatter<JMAX>(dv, lane);
+  const int idx = rs_index<JMAX>(lane);
+  if (rs_writer<JMAX>(lane) && idx < J) red[idx][wid] = num<T>::to_d(tot);
   __syncthreads();
   if (threadIdx.x < J) {
     double sum = 0.0;
@@ -795,36 +845,6 @@ __global__ void __launch_bounds__(TPB) k_scale_c(const T *__restrict__ in, T *__
 
 // partials[chunk*(2J+2) + c]: c < J: V_c.u, J + c: V_c.y, 2J: u.u, 2J+1: u.y
 
-__device__ __forceinline__ float bfly_shfl(float v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-__device__ __forceinline__ double bfly_shfl(double v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-__device__ __forceinline__ dw bfly_shfl(dw v, int o) {
-  return {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
-}
-
-// Warp reduce-scatter of 16 values per lane (recursive halving): at each of
-// the offsets 16, 8, 4, 2 a lane keeps one half of its values, sends the
-// other half to its partner and adds what it receives; the offset-1 step
-// completes the sum.  15 + 1 additions instead of 16 x 5 for 16 separate
-// reductions.  Afterwards lane l holds the warp total of value bfly_index(l)
-// (lanes l and l ^ 1 hold the same one).
-__device__ __forceinline__ int bfly_index(int lane) {
-  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
-}
-template <typename T>
-__device__ __forceinline__ T warp_reduce_scatter16(T (&v)[16], int lane) {
-#pragma unroll
-  for (int h = 8; h >= 1; h >>= 1) {
-    const bool up = (lane & (2 * h)) != 0;
-#pragma unroll
-    for (int i = 0; i < h; ++i) {
-      const T send = up ? v[i] : v[i + h];
-      const T keep = up ? v[i + h] : v[i];
-      v[i] = keep + bfly_shfl(send, 2 * h);
-    }
-  }
-  return v[0] + bfly_shfl(v[0], 1);
-}
-
 template <typename T>
 __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 : 2) k_dot2(const T *__restrict__ V, int64_t ldv, int J, const T *__restrict__ u,
                                               const T *__restrict__ y, int64_t n, double *__restrict__ partials) {
@@ -899,9 +919,9 @@ __global__ void __launch_bounds__(TPB, sizeof(T) == 4 ? 3 : 2) k_dot2(const T *_
       v[q] = acc_get(as[q]);
       v[CG + q] = acc_get(at[q]);
     }
-    const T tot = warp_reduce_scatter16(v, lane);
-    const int idx = bfly_index(lane);  // idx < CG: V_{c0+idx}.u, else V_{c0+idx-CG}.y
-    if ((lane & 1) == 0 && (idx & (CG - 1)) < ncol) red[idx][wid] = num<T>::to_d(tot);
+    const T tot = warp_reduce_scatter<16>(v, lane);
+    const int idx = rs_index<16>(lane);  // idx < CG: V_{c0+idx}.u, else V_{c0+idx-CG}.y
+    if (rs_writer<16>(lane) && (idx & (CG - 1)) < ncol) red[idx][wid] = num<T>::to_d(tot);
   }
   __syncthreads();
   const int tix = threadIdx.x;
