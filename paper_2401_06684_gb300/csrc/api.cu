@@ -763,11 +763,9 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   int phase = 1, nv1 = 0, ny1 = 0;
   auto switch_phase = [&](int m_now) -> int {
     if constexpr (!std::is_same<T1, T2>::value) {
-      for (int col = 0; col <= m_now; ++col)
-        RC((vec_convert<T1, T2>(V1 + (size_t)col * ldv, V2 + (size_t)col * ldv, n, s)));
-      if (right)
-        for (int col = 0; col < m_now; ++col)
-          RC((vec_convert<T1, T2>(Y1 + (size_t)col * ldv, Y2 + (size_t)col * ldv, n, s)));
+      // columns 0..m_now are contiguous at stride ldv in both bases: one launch
+      RC((vec_convert<T1, T2>(V1, V2, (int64_t)(m_now + 1) * ldv, s)));
+      if (right && m_now > 0) RC((vec_convert<T1, T2>(Y1, Y2, (int64_t)m_now * ldv, s)));
       // the leading columns the result takes from the phase-1 basis: 0..m_now,
       // or 0..m_now-1 with delayed reorthogonalization, whose column m_now
       // still holds the candidate (its final form is written in phase 2)

@@ -771,11 +771,9 @@ struct GroupPlan : GroupBase {
         if (right && !Y2g.p) BRC(Y2g.init(N, std::max(kFirstCols, 2 * (m_now + 1)), m_max, s));
         BRC(V2g.ensure(m_now + 1, s));
         if (right) BRC(Y2g.ensure(std::max(m_now, 1), s));
-        for (int col = 0; col <= m_now; ++col)
-          BRC((vec_convert<T1, T2>(V1g.p + (size_t)col * N, (T2 *)V2g.p + (size_t)col * N, N, s)));
-        if (right)
-          for (int col = 0; col < m_now; ++col)
-            BRC((vec_convert<T1, T2>(Y1g.p + (size_t)col * N, (T2 *)Y2g.p + (size_t)col * N, N, s)));
+        // columns 0..m_now are contiguous at stride N in both bases: one launch
+        BRC((vec_convert<T1, T2>(V1g.p, (T2 *)V2g.p, (int64_t)(m_now + 1) * N, s)));
+        if (right && m_now > 0) BRC((vec_convert<T1, T2>(Y1g.p, (T2 *)Y2g.p, (int64_t)m_now * N, s)));
         nv1 = m_now + 1;
         ny1 = m_now;
         phase = 2;

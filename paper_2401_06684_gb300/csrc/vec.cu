@@ -18,6 +18,8 @@
 // A block finds its segment from the chunk table, skips inactive segments,
 // and reads its per-segment FP64 scalars at base + segment * dstride.  A
 // single vector is the case nseg = 1.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -100,8 +102,15 @@ template <typename TI, typename TO>
 __global__ void k_convert(const TI *__restrict__ in, TO *__restrict__ out, int64_t n) {
   pdl_wait();
   pdl_trigger();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = num<TO>::from_d(num<TI>::to_d(in[i]));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<TI, dw>::value && std::is_same<TO, float>::value) {
+      // one FP32 addition rounds hi + lo correctly (no FP64 pipe, no double rounding)
+      const dw v = in[i];
+      out[i] = __fadd_rn(v.hi, v.lo);
+    } else {
+      out[i] = num<TO>::from_d(num<TI>::to_d(in[i]));
+    }
+  }
 }
 
 // out = in * (c * c_dev[segment]) (c_dev may be NULL); inactive segments untouched
