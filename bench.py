@@ -44,6 +44,9 @@ WORKLOADS = {
     "convdiff128": ("3D convection-diffusion 128^3 upwind 7-point (n=2097152, c*h=0.5), f=A^(1/2), "
                     "Arnoldi with classical Gram-Schmidt twice, second pass delayed one step (DCGS2)",
                     "convdiff3d7", (128, 128, 128), 1, 16, 1e-10, "dcgs2"),
+    "convdiff256": ("3D convection-diffusion 256^3 upwind 7-point (n=16777216, c*h=0.5; vectors of 67 MB in FP32: "
+                    "the chain out of L2), f=A^(1/2), Arnoldi DCGS2, the default workload at 8x the size",
+                    "convdiff3d7", (256, 256, 256), 1, 16, 1e-10, "dcgs2"),
     "laplace2048": ("2D Laplacian 2048^2 5-point matrix-free (n=4194304), f=A^(-1/2), Lanczos; "
                     "1e-8 target, estimate tolerance 1e-9", "laplace2d5", (2048, 2048), -1, 16, 1e-9,
                     "lanczos"),
@@ -106,6 +109,8 @@ def parse():
     p.add_argument("--two-pass", action="store_true",
                    help="two-pass Lanczos (O(n) basis memory, twice the operator passes)")
     p.add_argument("--autotune", action="store_true", help="degree and tile from pp_autotune")
+    p.add_argument("--halo", action="store_true",
+                   help="FP32 stencil Horner steps two per launch through TMA-staged halo tiles (opts.halo)")
     p.add_argument("--orth", default=None, choices=["cgs2", "dcgs2"],
                    help="Gram-Schmidt of the Arnoldi workloads (default: the workload's)")
     a = p.parse_args()
@@ -176,6 +181,7 @@ def config(args, ws):
                      if args.kind in ("graphcsr", "wilsonq2") else "chebyshev"), "degree": args.degree,
             "q_eval": "clenshaw" if args.clenshaw else "newton-horner at Leja-ordered nodes",
             "side": "left", "orth": args.orth, "tol": args.tol, "rhs_per_rank": 1,
+            "fp32_stencil_steps": "two per launch, TMA-staged halo tiles" if args.halo else "one per launch",
             "parallelism": f"replicas{ws}", "l2": "flushed between timed steps (256 MB write)"}
 
 
@@ -657,6 +663,7 @@ def run_ours(args):
             o.two_pass = 1
         o.clenshaw = 1 if args.clenshaw else 0
         o.orth = {"cgs2": pp.PP_ORTH_CGS2, "dcgs2": pp.PP_ORTH_DCGS2}.get(args.orth, pp.PP_ORTH_AUTO)
+        o.halo = 1 if args.halo else 0
         if args.kind == "graphcsr":  # Example 3 checks every 32/d iterations
             o.check_every = max(1, 32 // (args.degree + 1))
         if args.kind == "wilsonq2":  # Example 2 checks every 64/d iterations

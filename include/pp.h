@@ -158,7 +158,23 @@ typedef struct pp_opts {
                            streams per step.  1: for PP_CHEBYSHEV the matrix
                            Clenshaw recurrence of the Chebyshev series (Sec. 5.1),
                            four streams per step (ignored for the Ritz kinds).   */
-  int32_t reserved[5];
+  int32_t halo;         /* 1: in the FP32 arithmetic of a solve (PP_PREC_MIXED after
+                           the switch) on a 2D/3D stencil grid with nx % 4 == 0,
+                           the Horner steps of q(A) after the first run two at a
+                           time in one kernel: the tile of w with a two-point halo
+                           and the tile of v with a one-point halo are loaded into
+                           shared memory by the tensor memory accelerator, the
+                           first step is evaluated on the tile plus a one-point
+                           halo there and the second on the tile (three vector
+                           streams per pair instead of six; the same values bit
+                           for bit).  Real-node q only (Chebyshev, real Ritz
+                           values); other cases run single steps.  Measured
+                           slower than single steps on every workload here (the
+                           pair kernel is bound by its shared-memory reads: 128^3
+                           convection-diffusion 142.5 -> 129.9 solves/s, 256^3
+                           11.70 -> 10.83, 2048^2 Laplacian equal).  No
+                           counterpart in the paper.  0 (default): single steps.  */
+  int32_t reserved[4];
 } pp_opts;
 
 typedef struct pp_stats {

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libppsqrt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "batch.cu", "ops.cu", "vec.cu", "small.cu", "wilson.cu", "poly.cpp"]
+SOURCES = ["api.cu", "batch.cu", "ops.cu", "halo.cu", "vec.cu", "small.cu", "wilson.cu", "poly.cpp"]
 
 
 def nvcc():

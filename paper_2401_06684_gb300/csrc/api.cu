@@ -290,10 +290,54 @@ OpDesc make_op(const pp_ctx *c, int arith) {
 // Clenshaw recurrence with the first two steps folded (b_{k+1} = 0, b_k =
 // c_k x).  Horner steps read no second previous iterate; the same buffer
 // rotation serves both.
+// Two Horner steps in one launch (halo.cu), counted as one launch moving
+// three vectors (w and v read, the result written).
+int run_pair(pp_ctx *c, const OpDesc &op, const float *w, const float *v, float *out, const StepCoef &a,
+             const StepCoef &b) {
+  RC_(op_pair_step(op, w, v, out, a, b, c->pair_err, c->stream));
+  c->chain_launches += 1;
+  c->chain_bytes += 3.0 * sizeof(float) * (double)c->n;
+  return PP_OK;
+}
+
+// q(A) v with the real-node Horner steps after the first taken two at a time
+// (opts.halo, FP32, inside a solve).  Only for a q without conjugate-pair
+// steps: those read the vector two steps back, which a pair keeps in shared
+// memory only.
+bool pair_path(const pp_ctx *c, const OpDesc &op, const float *in, const float *out, float *const bufs[3], int k) {
+  if (c->opts.halo != 1 || c->pair_err == nullptr || k < 3 || !poly_horner(c) || c->nf.cx || in == out) return false;
+  for (int t = 1; t < k; ++t) {
+    const StepCoef sc = poly_step_coef(c, t);
+    if (sc.sub_y || !sc.add_v) return false;
+  }
+  return op_pair_ok(op, in, bufs[0], out) && op_pair_ok(op, bufs[1], in, bufs[0]);
+}
+
+int poly_apply_pairs(pp_ctx *c, const OpDesc &op, const float *in, float *out, float *bufs[3], int k) {
+  float *B[2] = {bufs[0], bufs[1]};
+  RC(run_op<float>(c, op, in, nullptr, nullptr, B[0], poly_step_coef(c, 0)));
+  const float *cur = B[0];
+  int nxt = 1;
+  for (int t = 1; t <= k - 1;) {
+    const bool two = t + 1 <= k - 1;
+    float *dst = (two ? t + 1 : t) == k - 1 ? out : B[nxt];
+    if (two)
+      RC(run_pair(c, op, cur, in, dst, poly_step_coef(c, t), poly_step_coef(c, t + 1)));
+    else
+      RC(run_op<float>(c, op, cur, nullptr, in, dst, poly_step_coef(c, t)));
+    cur = dst;
+    nxt ^= 1;
+    t += two ? 2 : 1;
+  }
+  return PP_OK;
+}
+
 template <typename T>
 int poly_apply_raw(pp_ctx *c, const OpDesc &op, const T *in, T *out, T *bufs[3]) {
   const int k = (int)c->coef.size() - 1;
   cudaStream_t s = c->stream;
+  if constexpr (std::is_same<T, float>::value)
+    if (pair_path(c, op, in, out, bufs, k)) return poly_apply_pairs(c, op, in, out, bufs, k);
   if (k == 0) {
     if (c->nf.cx) return vec_scale_c<T>(in, out, c->n, c->nf.b[0], c->nf.bi[0], s);
     return vec_scale<T>(in, out, c->n, poly_const(c), nullptr, s);
@@ -547,7 +591,7 @@ void segs_validate(pp_ctx *c, double tol) {
                                c->poly_gen, (uint64_t)c->degree, (uint64_t)c->opts.side,
                                (uint64_t)c->opts.precision, (uint64_t)c->opts.orth,
                                (uint64_t)c->opts.check_every, (uint64_t)c->opts.clenshaw,
-                               (uint64_t)c->tile_bdx, tb};
+                               (uint64_t)c->opts.halo, (uint64_t)c->tile_bdx, tb};
   if (sig != c->seg_sig) {
     segs_clear(c);
     c->seg_sig = sig;
@@ -662,6 +706,13 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   const int64_t n = c->n, ldv = w.ldv;
   const DLayout L = dlayout(c, w.m_cap);
   double *D = w.dmem;
+  // paired stencil launches (opts.halo) report a failed TMA wait to the status
+  // record, which this solve reads at every stopping check
+  struct PairErrScope {
+    pp_ctx *c;
+    ~PairErrScope() { c->pair_err = nullptr; }
+  } pair_scope{c};
+  c->pair_err = &w.st->tma_err;
   Solve S;
   S.c = c;
   S.s = s;
@@ -735,6 +786,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
   PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
   PP_CUDA_TRY(cudaStreamSynchronize(s));
   DevStatus hs = *w.st_host;
+  if (hs.tma_err) return pp_set_error(PP_ERR_TIMEOUT, "a paired stencil launch gave up waiting for its TMA loads");
   if (hs.bad) return pp_set_error(PP_ERR_INVALID_ARG, "non-finite norm of the start vector");
   if (hs.breakdown) {  // zero start vector: f(A) 0 = 0
     PP_CUDA_TRY(cudaMemsetAsync(x_dev, 0, sizeof(double) * n, s));
@@ -827,6 +879,7 @@ int solve(pp_ctx *c, int f, const double *b_dev, int m_max, double tol, double *
       PP_CUDA_TRY(cudaMemcpyAsync(w.st_host, w.st, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
       PP_CUDA_TRY(cudaStreamSynchronize(s));
       hs = *w.st_host;
+      if (hs.tma_err) return pp_set_error(PP_ERR_TIMEOUT, "a paired stencil launch gave up waiting for its TMA loads");
       if (hs.bad) return pp_set_error(PP_ERR_CUDA, "non-finite values in the Krylov process");
       if (hs.breakdown) {
         bd = true;
@@ -1979,6 +2032,7 @@ int pp_set_opts(pp_handle c, const pp_opts *o) {
   if (o->profile != 0 && o->profile != 1) return pp_set_error(PP_ERR_INVALID_ARG, "profile must be 0 or 1");
   if (o->two_pass != 0 && o->two_pass != 1) return pp_set_error(PP_ERR_INVALID_ARG, "two_pass must be 0 or 1");
   if (o->clenshaw != 0 && o->clenshaw != 1) return pp_set_error(PP_ERR_INVALID_ARG, "clenshaw must be 0 or 1");
+  if (o->halo != 0 && o->halo != 1) return pp_set_error(PP_ERR_INVALID_ARG, "halo must be 0 or 1");
   c->opts = *o;
   return PP_OK;
 }

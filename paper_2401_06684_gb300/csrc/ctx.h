@@ -86,6 +86,9 @@ struct pp_ctx {
   // operator-launch accounting of the current call (pp_stats.chain_*)
   int64_t chain_launches = 0;
   double chain_bytes = 0.0;
+  // set by a solve while it runs: the status word that paired stencil launches
+  // (opts.halo) report a failed TMA wait to, read at every stopping check
+  int *pair_err = nullptr;
   std::vector<cudaEvent_t> prof_ev;  // start/stop pairs, grown on demand
   size_t prof_used = 0;
   std::vector<int> prof_cat;  // category of each pair: 0 operator chain, 1 orthogonalization, 2 small solve

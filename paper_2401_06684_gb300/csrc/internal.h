@@ -266,7 +266,7 @@ struct DevStatus {
   double beta0;
   double znorm;
   unsigned int ticket;  // finished reduction blocks of k_dcgs_coef (its last block resets it)
-  int pad;
+  int tma_err;          // a paired stencil launch gave up waiting for its TMA loads
 };
 // Arnoldi with delayed reorthogonalization (vec.cu): the inner products of
 // the candidate u and y = A q(A)^2 u with the basis (partials of 2J + 2
@@ -274,6 +274,15 @@ struct DevStatus {
 // (FP64; J <= kDcgsMaxJ; R receives the 2J + 2 sums) and the update sweep
 // that writes v_j into u's column and the next candidate into y's.
 constexpr int kDcgsMaxJ = 4096;
+
+// Two consecutive real-node Horner steps of q(A) v on a stencil grid in one
+// launch (halo.cu): w'' = step_b(step_a(w)), both adding delta v; FP32.
+// op_pair_ok: the grid and pointers qualify (stencil, nx % 4 == 0, 16-byte
+// aligned vectors, the tensor-map encoder available).  *err is set if a
+// block's bounded wait on its TMA loads runs out.
+bool op_pair_ok(const OpDesc &op, const void *w, const void *v, const void *out);
+int op_pair_step(const OpDesc &op, const float *w, const float *v, float *out, const StepCoef &a,
+                 const StepCoef &b, int *err, cudaStream_t s);
 template <typename T>
 int vec_dot2(const T *V, int64_t ldv, int J, const T *u, const T *y, int64_t n, double *partials, cudaStream_t s);
 template <typename T>

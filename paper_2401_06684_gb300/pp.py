@@ -36,7 +36,8 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "l
 class pp_opts(ctypes.Structure):
     _fields_ = [("side", ctypes.c_int32), ("precision", ctypes.c_int32), ("orth", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("two_pass", ctypes.c_int32), ("clenshaw", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("two_pass", ctypes.c_int32), ("clenshaw", ctypes.c_int32), ("halo", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class pp_stats(ctypes.Structure):
