@@ -391,8 +391,11 @@ int small_hess_quad(const double *H, int ldh, int m, const double *sig, const do
                     double *X, double *scratch, cudaStream_t s, const Seg &S) {
   if (m <= 64) {
     const size_t per_warp = ((size_t)(m + 1) * m + 2 * (size_t)m) * sizeof(double);
+    // at most 2 nodes per block: the rotations are chains of dependent FP64
+    // operations, and GB300's FP64 pipe is narrow, so spreading the nodes over
+    // more SMs shortens the launch (8 per block left most SMs idle)
     int wpb = (int)((48 * 1024) / per_warp);
-    if (wpb > 8) wpb = 8;
+    if (wpb > 2) wpb = 2;
     if (wpb < 1) wpb = 1;
     const unsigned grid = (unsigned)((K + wpb - 1) / wpb);
     PP_CUDA_TRY(pdl_launch(k_hess_quad_warp, dim3(grid, S.nseg), dim3(32 * wpb), per_warp * wpb, s, H, ldh, m, sig, wt, K, X, S));
