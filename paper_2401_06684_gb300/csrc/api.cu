@@ -51,6 +51,10 @@ constexpr int kMaxDegree = 128;
 constexpr int64_t kLongRow = 64;
 // ... and rows with more than this get a whole block (the others a warp)
 constexpr int64_t kBlockRow = 1024;
+// CSR rows of the lane path are sorted by length within windows of this many
+// rows when the variance of their lengths exceeds kPermMinVar
+constexpr size_t kPermWindow = 4096;
+constexpr double kPermMinVar = 1.0;
 constexpr int kMaxM = 4096;
 constexpr double kBreakdownRel = 1e-12;
 constexpr int kIntervalSteps = 200;
@@ -67,6 +71,7 @@ void ws_free(Workspace &w) {
   if (w.val_dw) cudaFree(w.val_dw);
   if (w.val_f) cudaFree(w.val_f);
   if (w.long_rows) cudaFree(w.long_rows);
+  if (w.csr_perm) cudaFree(w.csr_perm);
   if (w.Vf) cudaFree(w.Vf);
   if (w.Yf) cudaFree(w.Yf);
   if (w.ev0) cudaEventDestroy(w.ev0);
@@ -265,6 +270,8 @@ OpDesc make_op(const pp_ctx *c, int arith) {
   op.nlong = scanned ? c->ws.nlong : 0;
   op.nwarp = scanned ? c->ws.nwarp : 0;
   op.long_len = scanned ? kLongRow : 0;
+  op.perm = c->ws.csr_perm;
+  op.nshort = c->ws.nshort;
   op.val_f32 = arith == AR_DW && c->ws.val_exact_f32 == 1 ? 1 : 0;
   op.val = arith == AR_DW ? (op.val_f32 ? c->ws.val_f : c->ws.val_dw)
                           : (arith == AR_F32 ? c->ws.val_f : (const void *)c->val);
@@ -587,7 +594,8 @@ void segs_validate(pp_ctx *c, double tol) {
                                (uint64_t)(uintptr_t)w.Vf,  (uint64_t)(uintptr_t)w.Yf,
                                (uint64_t)(uintptr_t)w.hess, (uint64_t)(uintptr_t)w.st,
                                (uint64_t)(uintptr_t)w.val_dw, (uint64_t)(uintptr_t)w.val_f,
-                               (uint64_t)(uintptr_t)w.long_rows, (uint64_t)w.ldv,
+                               (uint64_t)(uintptr_t)w.long_rows, (uint64_t)(uintptr_t)w.csr_perm,
+                               (uint64_t)w.ldv,
                                c->poly_gen, (uint64_t)c->degree, (uint64_t)c->opts.side,
                                (uint64_t)c->opts.precision, (uint64_t)c->opts.orth,
                                (uint64_t)c->opts.check_every, (uint64_t)c->opts.clenshaw,
@@ -1249,6 +1257,33 @@ int csr_prepare(pp_ctx *c, int prec) {
     }
     w.nlong = (int)nl;
     w.nwarp = (int)wr.size();
+    // the lane path's rows sorted by length within windows of kPermWindow
+    // rows, where the lengths vary: a warp serves 32 / L rows, and with rows
+    // of mixed lengths (a power-law graph) each warp ran as many rounds as
+    // its longest row.  The windows keep the rows' accesses local.  The sum
+    // of each row is computed exactly as before.
+    std::vector<int32_t> sr;
+    sr.reserve((size_t)c->n);
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = 0; i < c->n; ++i) {
+      const int64_t len = rp[i + 1] - rp[i];
+      if (len > kLongRow) continue;
+      sr.push_back((int32_t)i);
+      s1 += (double)len;
+      s2 += (double)len * (double)len;
+    }
+    const double ns = (double)sr.size();
+    if (!sr.empty() && s2 / ns - (s1 / ns) * (s1 / ns) > kPermMinVar) {
+      auto len_of = [&](int32_t r) { return rp[(size_t)r + 1] - rp[(size_t)r]; };
+      for (size_t w0 = 0; w0 < sr.size(); w0 += kPermWindow) {
+        const size_t w1 = std::min(sr.size(), w0 + (size_t)kPermWindow);
+        std::stable_sort(sr.begin() + w0, sr.begin() + w1,
+                         [&](int32_t a, int32_t b) { return len_of(a) < len_of(b); });
+      }
+      PP_CUDA_TRY(cudaMalloc(&w.csr_perm, sizeof(int32_t) * sr.size()));
+      PP_CUDA_TRY(cudaMemcpy(w.csr_perm, sr.data(), sizeof(int32_t) * sr.size(), cudaMemcpyHostToDevice));
+      w.nshort = (int64_t)sr.size();
+    }
   }
   if (prec == PP_PREC_DW || prec == PP_PREC_MIXED) {
     if (w.val_exact_f32 < 0) {  // values read back once: are they all exact in FP32?

@@ -35,6 +35,10 @@ struct Workspace {
   int32_t *long_rows = nullptr;  // CSR rows longer than kLongRow entries: block rows, then warp rows
   int nlong = -1;                // rows with a block each (-1: not scanned yet)
   int nwarp = 0;                 // rows with a warp each
+  // CSR rows of the lane path sorted by length within windows of rows, where
+  // the lengths vary (NULL: rows in their own order)
+  int32_t *csr_perm = nullptr;
+  int64_t nshort = 0;
   void *Vf = nullptr;     // FP32 basis of the second phase (PP_PREC_MIXED)
   void *Yf = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -32,6 +32,11 @@ struct OpDesc {
   int nlong;
   int64_t long_len;
   int nwarp = 0;
+  // the rows of the lane path in the order the lane groups take them (sorted
+  // by length within windows, so that the rows of a warp take about as many
+  // rounds); NULL: row t for lane group t
+  const int32_t *perm = nullptr;
+  int64_t nshort = 0;
   // Wilson D^H D: lattice extents, mass shift, complex64 links and one
   // scratch vector (in the vector arithmetic) for the intermediate D x
   int64_t L[4];

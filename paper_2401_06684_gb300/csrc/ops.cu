@@ -416,13 +416,40 @@ __device__ __forceinline__ T csr_finish(const csr_acc<T> &sum, T alpha, T beta, 
   return r.get();
 }
 
+// acc += sum over p = p0, p0 + stride, ... < p1 of val[p] x[col[p]], U entries
+// per round with all their loads issued before the first product (the
+// dependent col -> x gathers of a round overlap); the products are added in
+// the order of the plain loop, so the sum is bit for bit the same.
+template <typename T, typename VT, int U>
+__device__ __forceinline__ void csr_row_sum(csr_acc<T> &acc, const int32_t *__restrict__ col,
+                                            const VT *__restrict__ val, const T *__restrict__ x, int64_t p0,
+                                            int64_t p1, int64_t stride) {
+  int64_t p = p0;
+  for (; p + (U - 1) * stride < p1; p += U * stride) {
+    int32_t c[U];
+    VT a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      c[u] = __ldg(col + p + u * stride);
+      a[u] = ldg(val + p + u * stride);
+    }
+    T xv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) xv[u] = ldg(x + c[u]);
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc.add_prod(a[u], xv[u]);
+  }
+  for (; p < p1; p += stride) acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
+}
+
 template <typename T, typename VT, int L, bool SUB_Y, bool ADD_V>
 __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowptr,
                                                 const int32_t *__restrict__ col, const VT *__restrict__ val,
                                                 const T *__restrict__ x, const T *__restrict__ y,
                                                 const T *__restrict__ v, T *__restrict__ out, int64_t n, T alpha,
                                                 T beta, T gamma, T delta, const int32_t *__restrict__ long_rows,
-                                                int nlong, int nwarp, int64_t long_len) {
+                                                int nlong, int nwarp, int64_t long_len,
+                                                const int32_t *__restrict__ perm, int64_t nshort) {
   pdl_wait();
   pdl_trigger();
   auto finish = [&](int64_t row, const csr_acc<T> &sum) {
@@ -436,8 +463,7 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
     __shared__ csr_acc<T> red[8];
     const int64_t row = __ldg(long_rows + blockIdx.x);
     const int64_t p1 = __ldg(rowptr + row + 1);
-    for (int64_t p = __ldg(rowptr + row) + threadIdx.x; p < p1; p += blockDim.x)
-      acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
+    csr_row_sum<T, VT, 4>(acc, col, val, x, __ldg(rowptr + row) + threadIdx.x, p1, blockDim.x);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl(o, 32));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
@@ -455,22 +481,24 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
     if (wi >= nwarp) return;
     const int64_t row = __ldg(long_rows + nlong + wi);
     const int64_t p1 = __ldg(rowptr + row + 1);
-    for (int64_t p = __ldg(rowptr + row) + ln; p < p1; p += 32) acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
+    csr_row_sum<T, VT, 4>(acc, col, val, x, __ldg(rowptr + row) + ln, p1, 32);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc.add(acc.shfl(o, 32));
     if (ln == 0) finish(row, acc);
     return;
   }
   const int64_t t = (int64_t)(blockIdx.x - nlong - nwb) * blockDim.x + threadIdx.x;
-  const int64_t row = t / L;
+  const int64_t slot = t / L;
   const int lane = (int)(t % L);
-  bool mine = row < n;
+  bool mine = slot < (perm ? nshort : n);
+  int64_t row = slot;
   if (mine) {
+    if (perm) row = __ldg(perm + slot);
     const int64_t p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
     if (long_len > 0 && p1 - p0 > long_len)
       mine = false;  // a long row: its own block or warp computes it
     else
-      for (int64_t p = p0 + lane; p < p1; p += L) acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
+      csr_row_sum<T, VT, 2>(acc, col, val, x, p0 + lane, p1, L);
   }
 #pragma unroll
   for (int o = L / 2; o > 0; o >>= 1) acc.add(acc.shfl(o, L));
@@ -493,7 +521,8 @@ __global__ void __launch_bounds__(256) csr_step_multi(const int64_t *__restrict_
                                                       int64_t sstride, int r, const int *__restrict__ active,
                                                       T alpha, T beta, T gamma, T delta,
                                                       const int32_t *__restrict__ long_rows, int nlong,
-                                                      int nwarp, int64_t long_len) {
+                                                      int nwarp, int64_t long_len,
+                                                      const int32_t *__restrict__ perm, int64_t nshort) {
   pdl_wait();
   pdl_trigger();
   unsigned mask = 0;
@@ -558,10 +587,12 @@ __global__ void __launch_bounds__(256) csr_step_multi(const int64_t *__restrict_
     return;
   }
   const int64_t t = (int64_t)(blockIdx.x - nlong - nwb) * blockDim.x + threadIdx.x;
-  const int64_t row = t / L;
+  const int64_t slot = t / L;
   const int lane = (int)(t % L);
-  bool mine = row < n;
+  bool mine = slot < (perm ? nshort : n);
+  int64_t row = slot;
   if (mine) {
+    if (perm) row = __ldg(perm + slot);
     const int64_t p0 = __ldg(rowptr + row), p1 = __ldg(rowptr + row + 1);
     if (long_len > 0 && p1 - p0 > long_len) {
       mine = false;  // a long row: its own block or warp computes it
@@ -604,7 +635,7 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
                 cudaStream_t s) {
   if (op.kind == OPK_CSR) {
     const int L = 4;
-    const int64_t threads = op.n * L;
+    const int64_t threads = (op.perm ? op.nshort : op.n) * L;
     const int bs = 256;
     const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong + (op.nwarp + 7) / 8 : 0);
     if (nb > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "CSR grid too large for one launch");
@@ -615,7 +646,7 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
                                op.col, (const float *)op.val, x, y, v, out, op.n, host_const<T>(c.alpha),
                                host_const<T>(c.beta), host_const<T>(c.gamma), host_const<T>(c.delta),
                                op.long_rows, op.long_len > 0 ? op.nlong : 0, op.long_len > 0 ? op.nwarp : 0,
-                               op.long_len));
+                               op.long_len, op.perm, op.nshort));
         done = true;
       }
     }
@@ -623,7 +654,8 @@ int launch_step(const OpDesc &op, const T *x, const T *y, const T *v, T *out, co
       PP_CUDA_TRY(pdl_launch(csr_step<T, T, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,
                              (const T *)op.val, x, y, v, out, op.n, host_const<T>(c.alpha), host_const<T>(c.beta),
                              host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,
-                             op.long_len > 0 ? op.nlong : 0, op.long_len > 0 ? op.nwarp : 0, op.long_len));
+                             op.long_len > 0 ? op.nlong : 0, op.long_len > 0 ? op.nwarp : 0, op.long_len, op.perm,
+                             op.nshort));
   } else {
     Konst<T> K;
     K.K0 = host_const<T>(c.alpha * op.d + c.beta);
@@ -690,7 +722,7 @@ int op_step_csr_multi(const OpDesc &op, int64_t sstride, int r, const int *activ
                       const T *v, T *out, const StepCoef &c, cudaStream_t s) {
   if (op.kind != OPK_CSR || r < 1 || r > kCsrMaxRhs) return pp_set_error(PP_ERR_INVALID_ARG, "bad CSR block step");
   constexpr int L = 4;
-  const int64_t threads = op.n * L;
+  const int64_t threads = (op.perm ? op.nshort : op.n) * L;
   const int bs = 256;
   const int64_t nb = (threads + bs - 1) / bs + (op.long_len > 0 ? op.nlong + (op.nwarp + 7) / 8 : 0);
   if (nb > 0x7fffffffll) return pp_set_error(PP_ERR_INVALID_ARG, "CSR grid too large for one launch");
@@ -701,7 +733,7 @@ int op_step_csr_multi(const OpDesc &op, int64_t sstride, int r, const int *activ
   e = pdl_launch(csr_step_multi<T, VT, L, SY, AV>, dim3((unsigned)nb), dim3(bs), 0, s, op.rowptr, op.col,      \
                  (const VT *)op.val, x, y, v, out, op.n, sstride, r, active, host_const<T>(c.alpha),          \
                  host_const<T>(c.beta), host_const<T>(c.gamma), host_const<T>(c.delta), op.long_rows,        \
-                 op.long_len > 0 ? op.nlong : 0, op.long_len > 0 ? op.nwarp : 0, op.long_len)
+                 op.long_len > 0 ? op.nlong : 0, op.long_len > 0 ? op.nwarp : 0, op.long_len, op.perm, op.nshort)
 #define PP_CSRM(SY, AV)                       \
   do {                                        \
     if constexpr (std::is_same<T, dw>::value) \
