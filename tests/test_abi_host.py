@@ -97,6 +97,31 @@ def test_quadrature_rule_accuracy(kind, herm):
         pp.pp_destroy(h)
 
 
+@pytest.mark.parametrize("nodes", [
+    [0.8, 1.5 + 0.7j, 1.5 - 0.7j, 3.0 + 1.2j, 3.0 - 1.2j, 5.0, 2.2],
+    [0.8, 2.0 + 2.5j, 2.0 - 2.5j, 5.0, 2.2],
+], ids=["pairs7", "wide_pair"])
+def test_quadrature_rule_on_wide_sectors(nodes):
+    # complex q nodes widen the sector the small solve's rule must cover
+    # (1.5 |arg| of the widest node, at most 0.45 pi): the rule still gives
+    # z^{-1/2} to 1e-13 over the widened image interval and that sector
+    pp = load()
+    z = np.array(nodes)
+    h = pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (5, 4, 3), [0.5])
+    try:
+        pp.pp_set_poly_nodes(h, z, interval_ab=(0.2, 7.0))
+        _, _, img = pp.pp_get_poly(h)
+        s, w = pp.pp_get_quadrature(h)
+        theta = max(np.pi / 3, min(0.45 * np.pi, 1.5 * np.max(np.abs(np.angle(z)))))
+        assert np.all(s > 0) and np.all(w > 0) and len(s) < 600
+        r = np.geomspace(img[0] * 1e-3, img[1] * 1e3, 2001)
+        zz = (r[:, None] * np.exp(1j * np.linspace(-theta, theta, 9))[None, :]).ravel()
+        approx = (w[None, :] / (s[None, :] + zz[:, None])).sum(1)
+        assert np.max(np.abs(approx * np.sqrt(zz) - 1)) < 1e-13
+    finally:
+        pp.pp_destroy(h)
+
+
 def test_argument_validation():
     pp = load()
     with pytest.raises(pp.PPError) as e:
