@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(256) csr_step(const int64_t *__restrict__ rowp
     if (long_len > 0 && p1 - p0 > long_len)
       mine = false;  // a long row: its own block or warp computes it
     else
-      csr_row_sum<T, VT, 2>(acc, col, val, x, p0 + lane, p1, L);
+      for (int64_t p = p0 + lane; p < p1; p += L) acc.add_prod(ldg(val + p), ldg(x + __ldg(col + p)));
   }
 #pragma unroll
   for (int o = L / 2; o > 0; o >>= 1) acc.add(acc.shfl(o, L));
