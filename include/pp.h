@@ -560,10 +560,16 @@ int pp_poly_apply_static(pp_handle h, const void *x_d, void *y_d);
 
 /*
  * Read back the quadrature rule of the small projected solve: H^{-1/2} e_1 =
- * sum_k wt_h[k] (H + sig_h[k] I)^{-1} e_1, the trapezoid rule in u = log t for
+ * sum_k wt_h[k] (H + sig_h[k] I)^{-1} e_1, a trapezoid rule for
  * z^{-1/2} = (2/pi) int_0^inf (t^2 + z)^{-1} dt (an integral representation
  * of the inverse square root; the paper uses a Schur square root instead,
- * Sec. 3.1).  *K = number of nodes; up to cap entries are written.
+ * Sec. 3.1), in u = log t after the substitution u = u_c + a sinh(w) whose
+ * tails decay double-exponentially (the plain rule in u where that needs
+ * fewer nodes).  It is built with q and checked there to a few 1e-15
+ * relative on the image interval widened by 10^3 (10^6 for Ritz q without an
+ * interval) and, for non-Hermitian A, on the sector |arg z| <= theta that
+ * the nodes of q ask for.  *K = number of nodes; up to cap entries are
+ * written.
  */
 int pp_get_quadrature(pp_handle h, double *sig_h, double *wt_h, int32_t cap, int32_t *K);
 
