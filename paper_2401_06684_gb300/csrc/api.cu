@@ -452,8 +452,7 @@ int orth_step(Solve &S, T *V, T *vj, T *wv, int j, double bd_rel) {
 template <typename T>
 int krylov_step(Solve &S, const OpDesc &op, T *V, T *Y, T *t[6], int j, double bd_rel) {
   pp_ctx *c = S.c;
-  cudaStream_t s = S.s;
-  const int64_t n = S.n, ldv = S.ldv;
+  const int64_t ldv = S.ldv;
   T *pb[3] = {t[2], t[3], t[4]};
   T *vj = V + (size_t)j * ldv;
   T *wv = V + (size_t)(j + 1) * ldv;
@@ -1196,11 +1195,15 @@ int op_apply_t(pp_ctx *c, const double *x, double *y) {
   RC(ensure_ws(c, c->opts.precision, c->ws.m_cap > 0 ? c->ws.m_cap : 1, false));
   const OpDesc op = make_op(c, arith_of<T>());
   T *t0 = (T *)c->ws.tmp, *t1 = t0 + c->ws.ldv;
-  if (std::is_same<T, double>::value)
+  if constexpr (std::is_same<T, double>::value) {
+    (void)t0;
+    (void)t1;
     return op_step<T>(op, (const T *)x, nullptr, nullptr, (T *)y, {1.0, 0.0, 0.0, false, false}, c->stream);
-  RC(vec_from_f64<T>(x, t0, c->n, c->stream));
-  RC(op_step<T>(op, t0, nullptr, nullptr, t1, {1.0, 0.0, 0.0, false, false}, c->stream));
-  return vec_to_f64<T>(t1, y, c->n, c->stream);
+  } else {
+    RC(vec_from_f64<T>(x, t0, c->n, c->stream));
+    RC(op_step<T>(op, t0, nullptr, nullptr, t1, {1.0, 0.0, 0.0, false, false}, c->stream));
+    return vec_to_f64<T>(t1, y, c->n, c->stream);
+  }
 }
 
 template <typename T>
@@ -1210,10 +1213,13 @@ int poly_apply_api_t(pp_ctx *c, const double *x, double *y) {
   T *t[6];
   for (int i = 0; i < 6; ++i) t[i] = (T *)c->ws.tmp + (size_t)i * c->ws.ldv;
   T *pb[3] = {t[2], t[3], t[4]};
-  if (std::is_same<T, double>::value) return poly_apply_t<T>(c, op, (const T *)x, (T *)y, pb);
-  RC(vec_from_f64<T>(x, t[0], c->n, c->stream));
-  RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
-  return vec_to_f64<T>(t[1], y, c->n, c->stream);
+  if constexpr (std::is_same<T, double>::value) {
+    return poly_apply_t<T>(c, op, (const T *)x, (T *)y, pb);
+  } else {
+    RC(vec_from_f64<T>(x, t[0], c->n, c->stream));
+    RC(poly_apply_t<T>(c, op, t[0], t[1], pb));
+    return vec_to_f64<T>(t[1], y, c->n, c->stream);
+  }
 }
 
 // ---- q(A) x without device allocation (pp_poly_apply_static) ----
