@@ -122,6 +122,40 @@ def test_quadrature_rule_on_wide_sectors(nodes):
         pp.pp_destroy(h)
 
 
+def test_quadrature_rule_is_compact():
+    # the sinh-substituted rule needs far fewer nodes than the plain trapezoid
+    # rule in log t at the same accuracy: on the 128^3 convection-diffusion
+    # image (widened by 10^3) the plain rule takes about 450 nodes
+    pp = load()
+    h = pp.pp_create_stencil(pp.PP_CONVDIFF3D7_UPWIND, (128, 128, 128), [0.5])
+    try:
+        pp.pp_build_poly(h, 16)
+        s, w = pp.pp_get_quadrature(h)
+        assert len(s) < 250
+    finally:
+        pp.pp_destroy(h)
+
+
+def test_option_ranges():
+    pp = load()
+    h = pp.pp_create_stencil(pp.PP_LAPLACE2D5, (8, 8))
+    try:
+        for field, good, bad in (("orth", (0, 1, 2, 3), (-1, 4)), ("halo", (0, 1), (2, -1)),
+                                 ("clenshaw", (0, 1), (2,)), ("two_pass", (0, 1), (2,))):
+            for v in good:
+                o = pp.pp_default_opts()
+                setattr(o, field, v)
+                pp.pp_set_opts(h, o)
+            for v in bad:
+                o = pp.pp_default_opts()
+                setattr(o, field, v)
+                with pytest.raises(pp.PPError) as e:
+                    pp.pp_set_opts(h, o)
+                assert e.value.status == pp.PP_ERR_INVALID_ARG, (field, v)
+    finally:
+        pp.pp_destroy(h)
+
+
 def test_argument_validation():
     pp = load()
     with pytest.raises(pp.PPError) as e:
