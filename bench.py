@@ -45,7 +45,8 @@ WORKLOADS = {
                     "Arnoldi with classical Gram-Schmidt twice, second pass delayed one step (DCGS2)",
                     "convdiff3d7", (128, 128, 128), 1, 16, 1e-10, "dcgs2"),
     "convdiff256": ("3D convection-diffusion 256^3 upwind 7-point (n=16777216, c*h=0.5; vectors of 67 MB in FP32: "
-                    "the chain out of L2), f=A^(1/2), Arnoldi DCGS2, the default workload at 8x the size",
+                    "the chain out of L2), f=A^(1/2), Arnoldi DCGS2, the default workload at 8x the size; basis capped at "
+                    "100 columns (42 iterations)",
                     "convdiff3d7", (256, 256, 256), 1, 16, 1e-10, "dcgs2"),
     "laplace2048": ("2D Laplacian 2048^2 5-point matrix-free (n=4194304), f=A^(-1/2), Lanczos; "
                     "1e-8 target, estimate tolerance 1e-9", "laplace2d5", (2048, 2048), -1, 16, 1e-9,
@@ -118,8 +119,8 @@ def parse():
     a.desc, a.kind, a.dims, a.func = w[0], w[1], w[2], w[3]
     a.degree = w[4] if a.degree is None else a.degree
     a.tol = w[5] if a.tol is None else a.tol
-    if a.m_max is None:
-        a.m_max = 200 if a.workload == "sign32x64" else 1000
+    if a.m_max is None:  # the 256^3 and 32^3 x 64 bases would not need 1000 columns (tens of GB each)
+        a.m_max = {"sign32x64": 200, "convdiff256": 100}.get(a.workload, 1000)
     if a.orth is not None and w[6] not in ("cgs2", "dcgs2"):
         p.error("--orth applies to the Arnoldi workloads only")
     a.orth = w[6] if a.orth is None else a.orth
