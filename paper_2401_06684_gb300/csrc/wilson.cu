@@ -58,10 +58,6 @@ template <>
 __device__ __forceinline__ float from_f<float>(float f) {
   return f;
 }
-template <>
-__device__ __forceinline__ dw from_f<dw>(float f) {
-  return {f, 0.f};
-}
 
 // a + S b and a + S i b for S = +1 / -1
 template <int S, typename T>
