@@ -93,7 +93,7 @@ def parse():
     p.add_argument("--prec", default="mixed", choices=["dw", "f64", "mixed"])
     p.add_argument("--tol", type=float, default=None, help="default: the workload's")
     p.add_argument("--m-max", type=int, default=None,
-                   help="basis size cap (default 1000; 200 for sign32x64, whose vectors are 403 MB)")
+                   help="basis size cap (default 1000; 200 for sign32x64, whose vectors are 403 MB; 100 for convdiff256)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true", help="skip the degree-0 in-GPU baselines")
     p.add_argument("--no-companions", action="store_true",
